@@ -1,0 +1,291 @@
+"""FP64 CPU oracle for the Language Embedded 3D Gaussians hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by `tests/`, `__graft_entry__.smoke()` and
+the CPU-baseline leg of `bench.py`, never by the product package.  It shares
+no code with the CUDA library.  The C sources in this directory state what
+each step computes and which passage of the paper it follows; this module
+only compiles them (gcc, -ffp-contract=off) and marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sysconfig
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCES = ["keypath.c", "sh.c", "project.c", "binning.c", "composite.c", "decoder.c", "query.c", "train.c"]
+LIB = os.path.join(HERE, "liboracle.so")
+TILE = 16
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so in place (plain C11, FP64, OpenMP over pixels)."""
+    srcs = [os.path.join(HERE, s) for s in SOURCES]
+    if not force and os.path.exists(LIB):
+        newest = max(os.path.getmtime(p) for p in srcs + [os.path.join(HERE, "oracle.h")])
+        if os.path.getmtime(LIB) >= newest:
+            return LIB
+    cmd = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-Wall", "-Wno-unused-function", "-o", LIB + ".tmp"] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(LIB)
+        _lib.orc_exp_f32.restype = C.c_float
+        _lib.orc_exp_f32.argtypes = [C.c_float]
+        _lib.orc_bin.restype = C.c_int64
+        _lib.orc_tile_list.restype = C.c_int
+        _lib.orc_l1.restype = C.c_double
+        _lib.orc_sh_count.restype = C.c_int
+    return _lib
+
+
+class OrcCam(C.Structure):
+    _fields_ = [("view", C.c_float * 12), ("campos", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("W", C.c_int32), ("H", C.c_int32),
+                ("near_z", C.c_float), ("bg", C.c_float * 3)]
+
+
+def cam_struct(cam) -> OrcCam:
+    c = OrcCam()
+    c.view[:] = [float(v) for v in np.asarray(cam.view, np.float32)]
+    c.campos[:] = [float(v) for v in np.asarray(cam.campos, np.float32)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.W, c.H = cam.W, cam.H
+    c.near_z = cam.near
+    c.bg[:] = [float(v) for v in np.asarray(cam.bg, np.float32)]
+    return c
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, np.float64)
+
+
+def exp_f32(x: float) -> float:
+    return lib().orc_exp_f32(float(x))
+
+
+def sh_basis(deg: int, d):
+    n = (deg + 1) ** 2
+    d = _f64(d)
+    Y = np.zeros(n)
+    dY = np.zeros((n, 3))
+    lib().orc_sh_basis(C.c_int(deg), _p(d), _p(Y), _p(dY))
+    return Y, dY
+
+
+def keypath(scene, cam) -> dict:
+    N = scene.N
+    out = dict(depth=np.zeros(N, np.float32), mean2d=np.zeros((N, 2), np.float32),
+               cov2d=np.zeros((N, 3), np.float32), radius=np.zeros(N, np.int32),
+               rect=np.zeros((N, 4), np.int32), tiles=np.zeros(N, np.int32))
+    cs = cam_struct(cam)
+    m, ls, q = _f32(scene.means), _f32(scene.log_scales), _f32(scene.quats)
+    lib().orc_keypath(C.c_int(N), _p(m), _p(ls), _p(q), C.byref(cs), _p(out["depth"]), _p(out["mean2d"]),
+                      _p(out["cov2d"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]))
+    return out
+
+
+def project(scene, cam, tiles) -> dict:
+    N = scene.N
+    out = dict(mean2d=np.zeros((N, 2)), depth=np.zeros(N), cov2d=np.zeros((N, 3)), conic=np.zeros((N, 3)),
+               opacity=np.zeros(N), rgb=np.zeros((N, 3)), clamp=np.zeros(N, np.uint8))
+    cs = cam_struct(cam)
+    args = [_f64(scene.means), _f64(scene.log_scales), _f64(scene.quats), _f64(scene.opacity_raw), _f64(scene.sh)]
+    tiles = np.ascontiguousarray(tiles, np.int32)
+    lib().orc_project(C.c_int(N), C.c_int(scene.sh_degree), *[_p(a) for a in args], C.byref(cs), _p(tiles),
+                      _p(out["mean2d"]), _p(out["depth"]), _p(out["cov2d"]), _p(out["conic"]),
+                      _p(out["opacity"]), _p(out["rgb"]), _p(out["clamp"]))
+    return out
+
+
+def project_bwd(scene, cam, tiles, d_mean2d, d_conic, d_opacity, d_rgb) -> dict:
+    N = scene.N
+    nc = (scene.sh_degree + 1) ** 2
+    out = dict(means=np.zeros((N, 3)), log_scales=np.zeros((N, 3)), quats=np.zeros((N, 4)),
+               opacity_raw=np.zeros(N), sh=np.zeros((N, nc, 3)))
+    cs = cam_struct(cam)
+    args = [_f64(scene.means), _f64(scene.log_scales), _f64(scene.quats), _f64(scene.opacity_raw), _f64(scene.sh)]
+    tiles = np.ascontiguousarray(tiles, np.int32)
+    g = [_f64(d_mean2d), _f64(d_conic), _f64(d_opacity), _f64(d_rgb)]
+    lib().orc_project_bwd(C.c_int(N), C.c_int(scene.sh_degree), *[_p(a) for a in args], C.byref(cs), _p(tiles),
+                          *[_p(a) for a in g], _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]),
+                          _p(out["opacity_raw"]), _p(out["sh"]))
+    return out
+
+
+def bin(cam, kp):
+    """Keys, sorted Gaussian ids and per-tile ranges (stable sort of 64-bit keys)."""
+    N = kp["tiles"].shape[0]
+    K = int(kp["tiles"].astype(np.int64).sum())
+    keys = np.zeros(max(K, 1), np.uint64)
+    vals = np.zeros(max(K, 1), np.uint32)
+    ntiles = cam.tiles_x * cam.tiles_y
+    ranges = np.zeros((ntiles, 2), np.uint32)
+    cs = cam_struct(cam)
+    K2 = lib().orc_bin(C.c_int(N), C.byref(cs), _p(kp["depth"]), _p(kp["rect"]), _p(kp["tiles"]),
+                       _p(keys), _p(vals), _p(ranges))
+    assert K2 == K
+    return keys[:K], vals[:K], ranges
+
+
+def tile_list(kp, tx: int, ty: int) -> np.ndarray:
+    N = kp["tiles"].shape[0]
+    out = np.zeros(max(N, 1), np.uint32)
+    n = lib().orc_tile_list(C.c_int(N), _p(kp["depth"]), _p(kp["rect"]), _p(kp["tiles"]), C.c_int(tx),
+                            C.c_int(ty), _p(out))
+    return out[:n].copy()
+
+
+def lists_for_tiles(cam, kp, tiles_xy):
+    """Brute-force per-tile lists packed as (vals, ranges) for the given tiles only
+    (all other tiles empty).  Used for crops of scenes too large to bin fully."""
+    ntiles = cam.tiles_x * cam.tiles_y
+    ranges = np.zeros((ntiles, 2), np.uint32)
+    chunks = []
+    pos = 0
+    for tx, ty in tiles_xy:
+        ids = tile_list(kp, tx, ty)
+        t = ty * cam.tiles_x + tx
+        ranges[t] = (pos, pos + len(ids))
+        pos += len(ids)
+        chunks.append(ids)
+    vals = np.concatenate(chunks) if chunks else np.zeros(0, np.uint32)
+    return vals.astype(np.uint32), ranges
+
+
+def render(cam, scene, proj, vals, ranges, window=None) -> dict:
+    x0, y0, x1, y1 = window if window is not None else (0, 0, cam.W, cam.H)
+    ww, wh = x1 - x0, y1 - y0
+    out = dict(rgb=np.zeros((3, wh, ww)), feat=np.zeros((8, wh, ww)), unc=np.zeros((wh, ww)),
+               T=np.zeros((wh, ww)), n_contrib=np.zeros((wh, ww), np.int32), flip=np.zeros((wh, ww), np.uint8))
+    cs = cam_struct(cam)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.uint32)
+    feat, unc = _f32(scene.feat), _f32(scene.unc)
+    lib().orc_render(C.byref(cs), C.c_int(scene.N), _p(vals), _p(ranges), _p(proj["mean2d"]), _p(proj["conic"]),
+                     _p(proj["opacity"]), _p(proj["rgb"]), _p(feat), _p(unc), C.c_int(x0), C.c_int(y0),
+                     C.c_int(x1), C.c_int(y1), _p(out["rgb"]), _p(out["feat"]), _p(out["unc"]), _p(out["T"]),
+                     _p(out["n_contrib"]), _p(out["flip"]))
+    return out
+
+
+def render_bwd(cam, scene, proj, vals, ranges, dL_drgb, dL_dfeat, dL_dunc, window=None) -> dict:
+    x0, y0, x1, y1 = window if window is not None else (0, 0, cam.W, cam.H)
+    N = scene.N
+    out = dict(mean2d=np.zeros((N, 2)), conic=np.zeros((N, 3)), opacity=np.zeros(N), rgb=np.zeros((N, 3)),
+               feat=np.zeros((N, 8)), unc=np.zeros(N))
+    cs = cam_struct(cam)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.uint32)
+    feat, unc = _f32(scene.feat), _f32(scene.unc)
+    g = [_f64(dL_drgb), _f64(dL_dfeat), _f64(dL_dunc)]
+    lib().orc_render_bwd(C.byref(cs), C.c_int(N), _p(vals), _p(ranges), _p(proj["mean2d"]), _p(proj["conic"]),
+                         _p(proj["opacity"]), _p(proj["rgb"]), _p(feat), _p(unc), C.c_int(x0), C.c_int(y0),
+                         C.c_int(x1), C.c_int(y1), *[_p(a) for a in g], _p(out["mean2d"]), _p(out["conic"]),
+                         _p(out["opacity"]), _p(out["rgb"]), _p(out["feat"]), _p(out["unc"]))
+    return out
+
+
+def decoder_fwd(feat, dec):
+    """feat: [d_in, P] (any float); returns logits [N, P] in FP64."""
+    feat = _f64(feat)
+    d_in, P = feat.shape
+    _, h1, h2, ncb = dec.dims
+    logits = np.zeros((ncb, P))
+    w = [_f64(a) for a in (dec.W1, dec.b1, dec.W2, dec.b2, dec.W3, dec.b3)]
+    lib().orc_decoder_fwd(C.c_int(P), C.c_int(d_in), C.c_int(h1), C.c_int(h2), C.c_int(ncb), _p(feat),
+                          *[_p(a) for a in w], _p(logits))
+    return logits
+
+
+def softmax_argmax(logits):
+    logits = _f64(logits)
+    ncb, P = logits.shape
+    prob = np.zeros_like(logits)
+    am = np.zeros(P, np.int32)
+    lib().orc_softmax_argmax(C.c_int(P), C.c_int(ncb), _p(logits), _p(prob), _p(am))
+    return prob, am
+
+
+def decoder_loss(feat, unc, target, dec, lambda_ce=1.0, lambda_u=1.0) -> dict:
+    feat = _f64(feat)
+    d_in, P = feat.shape
+    unc = _f64(unc).reshape(P)
+    target = np.ascontiguousarray(target, np.int32).reshape(P)
+    _, h1, h2, ncb = dec.dims
+    out = dict(loss=np.zeros(2), d_feat=np.zeros((d_in, P)), d_unc=np.zeros(P), dW1=np.zeros((h1, d_in)),
+               db1=np.zeros(h1), dW2=np.zeros((h2, h1)), db2=np.zeros(h2), dW3=np.zeros((ncb, h2)),
+               db3=np.zeros(ncb))
+    w = [_f64(a) for a in (dec.W1, dec.b1, dec.W2, dec.b2, dec.W3, dec.b3)]
+    lib().orc_decoder_loss(C.c_int(P), C.c_int(d_in), C.c_int(h1), C.c_int(h2), C.c_int(ncb), _p(feat), _p(unc),
+                           _p(target), *[_p(a) for a in w], C.c_double(lambda_ce), C.c_double(lambda_u),
+                           _p(out["loss"]), _p(out["d_feat"]), _p(out["d_unc"]), _p(out["dW1"]), _p(out["db1"]),
+                           _p(out["dW2"]), _p(out["db2"]), _p(out["dW3"]), _p(out["db3"]))
+    return out
+
+
+def query(prob, qin):
+    prob = _f64(prob)
+    ncb, P = prob.shape
+    cb, text, negs = _f32(qin.codebook), _f32(qin.text), _f32(qin.negs)
+    Q = text.shape[0]
+    rel = np.zeros((Q, P))
+    lib().orc_query(C.c_int(P), C.c_int(ncb), _p(prob), _p(cb), C.c_int(cb.shape[1]), C.c_int(qin.d_clip),
+                    _p(text), C.c_int(Q), _p(negs), C.c_int(negs.shape[0]), _p(rel))
+    return rel
+
+
+def l1(img, target):
+    img = _f64(img)
+    target = _f32(target)
+    grad = np.zeros_like(img)
+    loss = lib().orc_l1(C.c_int64(img.size), _p(img), _p(target), _p(grad))
+    return loss, grad
+
+
+def adam(param, grad, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place FP64 Adam step on contiguous float64 arrays."""
+    for a in (param, grad, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    lib().orc_adam(C.c_int64(param.size), _p(param), _p(grad), _p(m), _p(v), C.c_int(step), C.c_double(lr),
+                   C.c_double(b1), C.c_double(b2), C.c_double(eps))
+
+
+# ---------------------------------------------------------------------------
+def forward(scene, cam, window=None, binned=True):
+    """Whole forward pass: key path, FP64 projection, binning, compositing.
+    binned=False builds the per-tile lists by brute force (only the tiles the
+    window touches), for scenes too large to bin in full."""
+    kp = keypath(scene, cam)
+    proj = project(scene, cam, kp["tiles"])
+    if binned:
+        keys, vals, ranges = bin(cam, kp)
+    else:
+        x0, y0, x1, y1 = window
+        tl = [(tx, ty) for ty in range(y0 // TILE, (y1 - 1) // TILE + 1)
+              for tx in range(x0 // TILE, (x1 - 1) // TILE + 1)]
+        keys = None
+        vals, ranges = lists_for_tiles(cam, kp, tl)
+    img = render(cam, scene, proj, vals, ranges, window)
+    return dict(kp=kp, proj=proj, keys=keys, vals=vals, ranges=ranges, img=img)

@@ -1,0 +1,509 @@
+"""Pins for the FP64 oracle: closed forms, invariants, library special cases,
+brute force and finite differences.  CPU only (no GPU, no CUDA library).
+
+Each test pins one oracle function to something other than itself, so that a
+dropped term, a wrong sign or index or a transposed operand fails here.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2311_18482_gb300 import synth
+
+Y00 = 0.5 / math.sqrt(math.pi)         # textbook l=0 real spherical harmonic
+
+
+def ident_camera(W=32, H=32, f=100.0, bg=(0.0, 0.0, 0.0)):
+    view = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32)
+    return synth.Camera(view=view, campos=np.zeros(3, np.float32), fx=f, fy=f, cx=(W - 1) / 2, cy=(H - 1) / 2,
+                        W=W, H=H, bg=np.asarray(bg, np.float32))
+
+
+def tiny_scene(means, log_scales, quats=None, opacity=None, rgb=None, feat=None, unc=None):
+    n = len(means)
+    means = np.asarray(means, np.float32).reshape(n, 3)
+    log_scales = np.asarray(log_scales, np.float32).reshape(n, 3)
+    quats = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)) if quats is None else np.asarray(quats, np.float32)
+    o = np.full(n, 0.5) if opacity is None else np.asarray(opacity, np.float64)
+    opacity_raw = np.log(o / (1 - o)).astype(np.float32)
+    rgb = np.full((n, 3), 0.5) if rgb is None else np.asarray(rgb, np.float64)
+    sh = ((rgb - 0.5) / Y00).astype(np.float32).reshape(n, 1, 3)
+    feat = np.zeros((n, 8), np.float32) if feat is None else np.asarray(feat, np.float32)
+    unc = np.zeros(n, np.float32) if unc is None else np.asarray(unc, np.float32)
+    return synth.Scene(means, log_scales, quats, opacity_raw, sh, feat, unc, 0)
+
+
+# --------------------------------------------------------------------------- exp
+def test_exp_f32_accuracy(orc):
+    xs = np.concatenate([np.linspace(-20, 20, 20001), np.random.default_rng(0).normal(-3, 0.5, 5000)])
+    xs = xs.astype(np.float32)
+    got = np.array([orc.exp_f32(float(x)) for x in xs], np.float64)
+    ref = np.exp(xs.astype(np.float64))
+    assert np.max(np.abs(got / ref - 1)) < 2.5e-7
+
+
+# --------------------------------------------------------------------------- SH
+def _real_sh_scipy(l, m, d):
+    from scipy import special
+    theta = math.acos(max(-1.0, min(1.0, d[2])))
+    phi = math.atan2(d[1], d[0])
+    am = abs(m)
+    if hasattr(special, "sph_harm_y"):
+        Ylm = complex(special.sph_harm_y(l, am, theta, phi))
+    else:
+        Ylm = complex(special.sph_harm(am, l, phi, theta))
+    if m == 0:
+        return Ylm.real
+    return math.sqrt(2) * (Ylm.real if m > 0 else Ylm.imag)
+
+
+def test_sh_matches_scipy(orc):
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        Y, _ = orc.sh_basis(3, d)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                assert abs(Y[l * l + l + m] - _real_sh_scipy(l, m, d)) < 1e-12, (l, m)
+
+
+def test_sh_orthonormal(orc):
+    x, w = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    G = np.zeros((16, 16))
+    for ct, wt in zip(x, w):
+        st = math.sqrt(1 - ct * ct)
+        for k in range(nphi):
+            ph = 2 * math.pi * k / nphi
+            d = np.array([st * math.cos(ph), st * math.sin(ph), ct])
+            Y, _ = orc.sh_basis(3, d)
+            G += np.outer(Y, Y) * wt * (2 * math.pi / nphi)
+    assert np.max(np.abs(G - np.eye(16))) < 1e-12
+
+
+def test_sh_tangent_gradient(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        t = rng.standard_normal(3)
+        t -= d * (d @ t)
+        t /= np.linalg.norm(t)
+        _, dY = orc.sh_basis(3, d)
+        h = 1e-6
+        yp, _ = orc.sh_basis(3, (d + h * t) / np.linalg.norm(d + h * t))
+        ym, _ = orc.sh_basis(3, (d - h * t) / np.linalg.norm(d - h * t))
+        assert np.max(np.abs((yp - ym) / (2 * h) - dY @ t)) < 1e-7
+
+
+# --------------------------------------------------------------------------- projection
+def test_single_isotropic_gaussian_conic(orc):
+    f, z, s = 100.0, 4.0, 0.05
+    cam = ident_camera(f=f)
+    sc = tiny_scene([[0, 0, z]], [[math.log(s)] * 3])
+    s = math.exp(float(sc.log_scales[0, 0]))          # the FP32-stored scale
+    kp = orc.keypath(sc, cam)
+    pr = orc.project(sc, cam, kp["tiles"])
+    a = (f * s / z) ** 2 + 0.3
+    np.testing.assert_allclose(pr["cov2d"][0], [a, 0, a], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(pr["conic"][0], [1 / a, 0, 1 / a], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(pr["mean2d"][0], [cam.cx, cam.cy], atol=1e-12)
+    assert pr["depth"][0] == z
+    r = math.ceil(3 * math.sqrt(a))
+    assert kp["radius"][0] == r
+    # screen mean 15.5 +- r: tiles [floor((15.5-r)/16), floor((15.5+r+15)/16)) clamped to [0,2)
+    lo = max(0, math.floor((15.5 - r) / 16))
+    hi = min(2, math.floor((15.5 + r + 15) / 16))
+    assert list(kp["rect"][0]) == [lo, lo, hi, hi]
+    np.testing.assert_allclose(kp["cov2d"][0], [a, 0, a], rtol=1e-6)
+
+
+def test_anisotropic_axis_aligned_and_rotated(orc):
+    f, z = 100.0, 5.0
+    s = (0.08, 0.02, 0.05)
+    cam = ident_camera(f=f)
+    q90 = [math.cos(math.pi / 4), 0, 0, math.sin(math.pi / 4)]
+    sc = tiny_scene([[0, 0, z], [0, 0, z]], [[math.log(v) for v in s]] * 2, quats=[[1, 0, 0, 0], q90])
+    s = np.exp(sc.log_scales[0].astype(np.float64))
+    kp = orc.keypath(sc, cam)
+    pr = orc.project(sc, cam, kp["tiles"])
+    a = (f * s[0] / z) ** 2 + 0.3
+    c = (f * s[1] / z) ** 2 + 0.3
+    np.testing.assert_allclose(pr["cov2d"][0], [a, 0, c], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(pr["cov2d"][1], [c, 0, a], rtol=1e-12, atol=1e-12)
+
+
+def _quat_matrix_scipy(q):
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = q
+    return Rotation.from_quat([x, y, z, w]).as_matrix()
+
+
+def test_projection_vs_numerical_jacobian(orc):
+    """Sigma2 = J Sigma J^T + 0.3 I with J the numerical Jacobian of the pinhole
+    map and Sigma from a library rotation; mean2d / depth from the pinhole map."""
+    c = synth.config("c2", n=300, W=320, H=240)
+    sc, cam = c["scene"], c["camera"]
+    kp = orc.keypath(sc, cam)
+    pr = orc.project(sc, cam, kp["tiles"])
+    V = cam.view.astype(np.float64).reshape(3, 4)
+
+    def pin(p):
+        t = V[:, :3] @ p + V[:, 3]
+        return np.array([cam.fx * t[0] / t[2] + cam.cx, cam.fy * t[1] / t[2] + cam.cy])
+
+    lim = 1.3 * 0.5 * cam.W / cam.fx
+    checked = 0
+    for i in np.nonzero(kp["tiles"] > 0)[0][:100]:
+        p = sc.means[i].astype(np.float64)
+        t = V[:, :3] @ p + V[:, 3]
+        if abs(t[0] / t[2]) > lim * 0.99 or abs(t[1] / t[2]) > 1.3 * 0.5 * cam.H / cam.fy * 0.99:
+            continue
+        J = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = 1e-6
+            J[:, k] = (pin(p + e) - pin(p - e)) / 2e-6
+        R = _quat_matrix_scipy(sc.quats[i].astype(np.float64) / np.linalg.norm(sc.quats[i]))
+        S = np.diag(np.exp(2 * sc.log_scales[i].astype(np.float64)))
+        Sig2 = J @ R @ S @ R.T @ J.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(pr["cov2d"][i], [Sig2[0, 0], Sig2[0, 1], Sig2[1, 1]], rtol=1e-6,
+                                   atol=1e-6 * Sig2[0, 0])
+        np.testing.assert_allclose(pr["mean2d"][i], pin(p), rtol=1e-12)
+        assert abs(pr["depth"][i] - t[2]) < 1e-12
+        checked += 1
+    assert checked > 50
+
+
+def test_keypath_fp32_agrees_with_fp64(orc):
+    c = synth.config("c2", n=2000, W=320, H=240)
+    sc, cam = c["scene"], c["camera"]
+    kp = orc.keypath(sc, cam)
+    pr = orc.project(sc, cam, kp["tiles"])
+    v = kp["tiles"] > 0
+    assert v.sum() > 500
+    np.testing.assert_allclose(kp["mean2d"][v], pr["mean2d"][v], rtol=1e-5, atol=1e-3)
+    np.testing.assert_allclose(kp["depth"][v], pr["depth"][v], rtol=1e-6)
+    np.testing.assert_allclose(kp["cov2d"][v], pr["cov2d"][v], rtol=1e-4, atol=1e-4 * np.abs(pr["cov2d"][v]).max())
+
+
+# --------------------------------------------------------------------------- compositing closed forms
+def _pixel_center_mean(cam, px, py, z):
+    return [(px - cam.cx) * z / cam.fx, (py - cam.cy) * z / cam.fy, z]
+
+
+def test_two_gaussian_compositing(orc):
+    cam = ident_camera(bg=(0.2, 0.3, 0.4))
+    o1, o2 = 0.6, 0.7
+    c1, c2 = np.array([0.9, 0.1, 0.2]), np.array([0.1, 0.8, 0.3])
+    ls = [[math.log(0.02)] * 3] * 2
+    for swap in (False, True):
+        z1, z2 = (3.0, 4.0) if not swap else (4.0, 3.0)
+        sc = tiny_scene([_pixel_center_mean(cam, 16, 16, z1), _pixel_center_mean(cam, 16, 16, z2)], ls,
+                        opacity=[o1, o2], rgb=[c1, c2], feat=[[1] * 8, [3] * 8], unc=[0.25, 0.75])
+        out = orc.forward(sc, cam)
+        img = out["img"]
+        if not swap:
+            (fa, oa), (fb, ob) = (c1, o1), (c2, o2)
+            ua, ub, va, vb = 1.0, 3.0, 0.25, 0.75
+        else:
+            (fa, oa), (fb, ob) = (c2, o2), (c1, o1)
+            ua, ub, va, vb = 3.0, 1.0, 0.75, 0.25
+        expect = fa * oa + fb * ob * (1 - oa) + cam.bg * (1 - oa) * (1 - ob)
+        np.testing.assert_allclose(img["rgb"][:, 16, 16], expect, rtol=1e-6)
+        np.testing.assert_allclose(img["feat"][:, 16, 16], ua * oa + ub * ob * (1 - oa), rtol=1e-6)
+        np.testing.assert_allclose(img["unc"][16, 16], va * oa + vb * ob * (1 - oa), rtol=1e-6)
+        np.testing.assert_allclose(img["T"][16, 16], (1 - oa) * (1 - ob), rtol=1e-6)
+        assert img["n_contrib"][16, 16] == 2
+        keys = out["keys"]
+        # the nearer Gaussian comes first in its tile
+        t = (16 // 16) * cam.tiles_x + 16 // 16
+        s, e = out["ranges"][t]
+        first = out["vals"][s]
+        assert first == (0 if not swap else 1)
+
+
+def test_partition_of_unity(orc):
+    """Sum_i alpha_i T_i + T_final = 1: equal colours and bg = that colour render it exactly;
+    equal features v render v (1 - T_final)."""
+    c = synth.config("c1", n=500, W=64, H=64)
+    sc = c["scene"]
+    cam = c["camera"]
+    col = np.array([0.3, 0.6, 0.9], np.float32)
+    cam.bg = col.copy()
+    sc.sh[:] = 0
+    sc.sh[:, 0, :] = (col - 0.5) / Y00
+    sc.feat[:] = 2.5
+    sc.unc[:] = 0.4
+    out = orc.forward(sc, cam)
+    img = out["img"]
+    for ch in range(3):
+        np.testing.assert_allclose(img["rgb"][ch], col[ch], rtol=1e-6)
+    np.testing.assert_allclose(img["feat"], np.broadcast_to(2.5 * (1 - img["T"]), img["feat"].shape),
+                               rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(img["unc"], float(np.float32(0.4)) * (1 - img["T"]), rtol=1e-9, atol=1e-12)
+    assert img["T"].min() >= 1e-4 and img["T"].max() <= 1.0
+
+
+def test_termination_alpha_08(orc):
+    """Identical alpha = 0.8 Gaussians on one pixel: T = 0.2^k; the sixth would
+    give 6.4e-5 < 1e-4, so five are blended and T_final = 3.2e-4."""
+    cam = ident_camera()
+    n = 8
+    sc = tiny_scene([_pixel_center_mean(cam, 16, 16, 2.0 + 0.1 * k) for k in range(n)],
+                    [[math.log(0.02)] * 3] * n, opacity=[0.8] * n)
+    img = orc.forward(sc, cam)["img"]
+    assert img["n_contrib"][16, 16] == 5
+    np.testing.assert_allclose(img["T"][16, 16], 0.2 ** 5, rtol=1e-6)  # FP32-stored opacity
+
+
+# --------------------------------------------------------------------------- binning
+def test_tiled_render_equals_brute_force(orc):
+    c = synth.config("c1")
+    sc, cam = c["scene"], c["camera"]
+    out = orc.forward(sc, cam)
+    tl = [(tx, ty) for ty in range(cam.tiles_y) for tx in range(cam.tiles_x)]
+    vals_b, ranges_b = orc.lists_for_tiles(cam, out["kp"], tl)
+    img_b = orc.render(cam, sc, out["proj"], vals_b, ranges_b)
+    for k in ("rgb", "feat", "unc", "T", "n_contrib"):
+        assert np.array_equal(out["img"][k], img_b[k]), k
+
+
+def test_binning_invariants(orc):
+    c = synth.config("c2", n=3000, W=160, H=120)
+    sc, cam = c["scene"], c["camera"]
+    kp = orc.keypath(sc, cam)
+    keys, vals, ranges = orc.bin(cam, kp)
+    assert len(keys) == kp["tiles"].sum()
+    assert np.all(keys[1:] >= keys[:-1])
+    # multiset of (tile, id) equals the rectangle enumeration
+    want = []
+    for i in np.nonzero(kp["tiles"] > 0)[0]:
+        x0, y0, x1, y1 = kp["rect"][i]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                want.append((ty * cam.tiles_x + tx, i))
+    got = sorted(zip((keys >> np.uint64(32)).astype(np.int64).tolist(), vals.tolist()))
+    assert got == sorted(want)
+    # low word is the depth's float bits
+    assert np.array_equal((keys & np.uint64(0xFFFFFFFF)).astype(np.uint32), kp["depth"].view(np.uint32)[vals])
+    # ranges partition the sorted list by tile id
+    tid = (keys >> np.uint64(32)).astype(np.int64)
+    for t in range(cam.tiles_x * cam.tiles_y):
+        s, e = ranges[t]
+        if s == e:
+            assert not np.any(tid == t)
+        else:
+            assert np.all(tid[s:e] == t) and (s == 0 or tid[s - 1] != t) and (e == len(tid) or tid[e] != t)
+    # ties (equal depth) keep the lower index first
+    for t in range(cam.tiles_x * cam.tiles_y):
+        s, e = ranges[t]
+        k = keys[s:e]
+        v = vals[s:e]
+        same = k[1:] == k[:-1]
+        assert np.all(v[1:][same] > v[:-1][same])
+
+
+# --------------------------------------------------------------------------- backward: finite differences
+def test_render_bwd_matches_fd(orc):
+    c = synth.config("c1", n=300, W=64, H=64)
+    sc, cam = c["scene"], c["camera"]
+    cam.bg = np.array([0.1, 0.2, 0.3], np.float32)
+    out = orc.forward(sc, cam)
+    proj, vals, ranges = out["proj"], out["vals"], out["ranges"]
+    rng = np.random.default_rng(5)
+    dr, df, du = rng.standard_normal((3, 64, 64)), rng.standard_normal((8, 64, 64)), rng.standard_normal((64, 64))
+
+    def loss(pr, scn):
+        im = orc.render(cam, scn, pr, vals, ranges)
+        return (im["rgb"] * dr).sum() + (im["feat"] * df).sum() + (im["unc"] * du).sum()
+
+    g = orc.render_bwd(cam, sc, proj, vals, ranges, dr, df, du)
+    vis = np.nonzero(out["kp"]["tiles"] > 0)[0]
+    pick = rng.choice(vis, 12, replace=False)
+    for i in pick:
+        for key, n in (("mean2d", 2), ("conic", 3), ("opacity", 1), ("rgb", 3)):
+            for k in range(n):
+                h = 1e-6 * max(1.0, abs(proj[key].reshape(len(proj[key]), -1)[i, k]))
+                pp = {kk: vv.copy() for kk, vv in proj.items()}
+                pm = {kk: vv.copy() for kk, vv in proj.items()}
+                pp[key].reshape(len(pp[key]), -1)[i, k] += h
+                pm[key].reshape(len(pm[key]), -1)[i, k] -= h
+                fd = (loss(pp, sc) - loss(pm, sc)) / (2 * h)
+                an = g[key].reshape(len(g[key]), -1)[i, k]
+                assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (key, i, k, fd, an)
+        # features and uncertainty enter linearly: the derivative is exact blending weight
+        for k in range(8):
+            sp = synth.Scene(**{**sc.__dict__, "feat": sc.feat.copy()})
+            sp.feat[i, k] += 1.0
+            fd = loss(proj, sp) - loss(proj, sc)
+            assert abs(fd - g["feat"][i, k]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_project_bwd_matches_fd(orc):
+    c = synth.config("c2", n=400, W=320, H=240)
+    sc, cam = c["scene"], c["camera"]
+    kp = orc.keypath(sc, cam)
+    tiles = kp["tiles"]
+    rng = np.random.default_rng(6)
+    N = sc.N
+    w = dict(mean2d=rng.standard_normal((N, 2)), conic=rng.standard_normal((N, 3)) * 100,
+             opacity=rng.standard_normal(N), rgb=rng.standard_normal((N, 3)))
+
+    def L(s):
+        p = orc.project(s, cam, tiles)
+        return sum((p[k] * w[k]).sum() for k in w), p
+
+    base, pr = L(sc)
+    g = orc.project_bwd(sc, cam, tiles, w["mean2d"], w["conic"], w["opacity"], w["rgb"])
+    vis = np.nonzero(tiles > 0)[0]
+    pick = rng.choice(vis, 10, replace=False)
+    for i in pick:
+        for key in ("means", "log_scales", "quats", "opacity_raw", "sh"):
+            arr = getattr(sc, key).astype(np.float64)
+            flat_n = arr.reshape(N, -1).shape[1]
+            for k in range(flat_n):
+                h = 1e-6
+                sp = synth.Scene(**{**sc.__dict__, key: arr.copy()})
+                sm = synth.Scene(**{**sc.__dict__, key: arr.copy()})
+                getattr(sp, key).reshape(N, -1)[i, k] += h
+                getattr(sm, key).reshape(N, -1)[i, k] -= h
+                fd = (L(sp)[0] - L(sm)[0]) / (2 * h)
+                an = g[key].reshape(N, -1)[i, k]
+                assert abs(fd - an) <= 2e-6 * max(1.0, abs(fd)), (key, i, k, fd, an)
+
+
+# --------------------------------------------------------------------------- decoder
+def test_decoder_matches_library(orc):
+    from scipy.special import logsumexp, softmax
+    dec = synth.decoder_init(7, 32)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((8, 200))
+    z = orc.decoder_fwd(f, dec)
+    W1, b1, W2, b2, W3, b3 = [a.astype(np.float64) for a in (dec.W1, dec.b1, dec.W2, dec.b2, dec.W3, dec.b3)]
+    h1 = np.maximum(W1 @ f + b1[:, None], 0)
+    h2 = np.maximum(W2 @ h1 + b2[:, None], 0)
+    np.testing.assert_allclose(z, W3 @ h2 + b3[:, None], rtol=1e-12, atol=1e-12)
+    prob, am = orc.softmax_argmax(z)
+    np.testing.assert_allclose(prob, softmax(z, axis=0), rtol=1e-12)
+    assert np.array_equal(am, np.argmax(z, axis=0))
+    tgt = rng.integers(0, 32, 200)
+    u = rng.uniform(0, 1, 200)
+    out = orc.decoder_loss(f, u, tgt, dec, 1.0, 1.0)
+    ce = logsumexp(z, axis=0) - z[tgt, np.arange(200)]
+    np.testing.assert_allclose(out["loss"], [(ce * (1 - u)).mean(), u.mean()], rtol=1e-12)
+
+
+def test_decoder_argmax_ties_lowest():
+    # ties -> lowest index (closed form on a hand-made logit column)
+    import oracle
+    z = np.array([[1.0], [3.0], [3.0], [2.0]])
+    _, am = oracle.softmax_argmax(z)
+    assert am[0] == 1
+
+
+def test_decoder_loss_fd(orc):
+    dec = synth.decoder_init(8, 16)
+    rng = np.random.default_rng(8)
+    P = 50
+    f = rng.standard_normal((8, P))
+    u = rng.uniform(0, 1, P)
+    tgt = rng.integers(0, 16, P)
+    lce, lu = 1.0, 0.7
+
+    def Ls(ff, uu, d):
+        o = orc.decoder_loss(ff, uu, tgt, d, lce, lu)
+        return lce * o["loss"][0] + lu * o["loss"][1]
+
+    g = orc.decoder_loss(f, u, tgt, dec, lce, lu)
+    h = 1e-6
+    for p in range(0, P, 7):
+        for k in range(8):
+            fp, fm = f.copy(), f.copy()
+            fp[k, p] += h
+            fm[k, p] -= h
+            fd = (Ls(fp, u, dec) - Ls(fm, u, dec)) / (2 * h)
+            assert abs(fd - g["d_feat"][k, p]) < 1e-7 * max(1, abs(fd))
+        up, um = u.copy(), u.copy()
+        up[p] += h
+        um[p] -= h
+        fd = (Ls(f, up, dec) - Ls(f, um, dec)) / (2 * h)
+        assert abs(fd - g["d_unc"][p]) < 1e-7 * max(1, abs(fd))
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        arr = getattr(dec, name)
+        flat = arr.reshape(-1)
+        for idx in rng.choice(flat.size, 5, replace=False):
+            d64 = synth.Decoder(**{k: v.astype(np.float64) for k, v in dec.__dict__.items()})
+            dp = synth.Decoder(**{k: v.copy() for k, v in d64.__dict__.items()})
+            dm = synth.Decoder(**{k: v.copy() for k, v in d64.__dict__.items()})
+            getattr(dp, name).reshape(-1)[idx] += h
+            getattr(dm, name).reshape(-1)[idx] -= h
+            fd = (Ls(f, u, dp) - Ls(f, u, dm)) / (2 * h)
+            an = g["d" + name].reshape(-1)[idx]
+            assert abs(fd - an) < 1e-7 * max(1, abs(fd)), (name, idx, fd, an)
+
+
+# --------------------------------------------------------------------------- query
+def test_relevancy_closed_form(orc):
+    rng = np.random.default_rng(9)
+    d_clip, d = 16, 24
+    q = synth.unit_rows(rng, 2, d_clip)
+    negs = synth.unit_rows(rng, 3, d_clip)
+    cb = synth.unit_rows(rng, 5, d)
+    # entry 2's CLIP part is parallel to text 0
+    cb[2, :d_clip] = 0.7 * q[0]
+    qin = synth.QueryInputs(cb, q, negs, d_clip)
+    prob = np.zeros((5, 3))
+    prob[2, 0] = 1.0                           # one-hot: F = S_2, phi = q_0
+    prob[:, 1] = 0.2                           # uniform: F = mean of rows
+    prob[0, 2] = 1.0
+    rel = orc.query(prob, qin)
+    q0 = q[0].astype(np.float64)
+    s2 = cb[2, :d_clip].astype(np.float64)       # one-hot: F = S_2, parallel to q_0 up to FP32 rounding
+    phi0 = s2 / np.linalg.norm(s2)
+    sq = float(phi0 @ q0)
+    want = min(math.exp(sq) / (math.exp(sq) + math.exp(float(phi0 @ n))) for n in negs.astype(np.float64))
+    assert abs(rel[0, 0] - want) < 1e-12
+    assert abs(want - min(math.e / (math.e + math.exp(float(q0 @ n))) for n in negs)) < 1e-6
+    F = cb.astype(np.float64).mean(0)[:d_clip]
+    phi = F / np.linalg.norm(F)
+    for j in range(2):
+        w = min(1 / (1 + math.exp(float(phi @ n) - float(phi @ q[j]))) for n in negs)
+        assert abs(rel[j, 1] - w) < 1e-12
+    # a text equal to a negative has relevancy <= 1/2
+    qin2 = synth.QueryInputs(cb, negs[:1].copy(), negs, d_clip)
+    rel2 = orc.query(prob, qin2)
+    assert np.all(rel2 <= 0.5 + 1e-15)
+
+
+# --------------------------------------------------------------------------- training
+def test_adam_first_step_and_torch(orc):
+    import torch
+    rng = np.random.default_rng(10)
+    g = rng.standard_normal(100)
+    p = rng.standard_normal(100)
+    m = np.zeros(100)
+    v = np.zeros(100)
+    p1 = p.copy()
+    orc.adam(p1, g, m, v, 1)
+    np.testing.assert_allclose(p1, p - 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+    # five steps against torch.optim.Adam (CPU, float64)
+    tp = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    p2, m2, v2 = p.copy(), np.zeros(100), np.zeros(100)
+    for step in range(1, 6):
+        gs = rng.standard_normal(100)
+        tp.grad = torch.tensor(gs)
+        opt.step()
+        orc.adam(p2, gs, m2, v2, step)
+    np.testing.assert_allclose(p2, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_l1(orc):
+    img = np.array([0.5, 0.25, 0.875, 0.375])
+    tgt = np.array([0.25, 0.25, 1.0, 0.0], np.float32)
+    loss, g = orc.l1(img, tgt)
+    assert loss == (0.25 + 0 + 0.125 + 0.375) / 4
+    np.testing.assert_array_equal(g, [0.25, 0, -0.25, 0.25])
