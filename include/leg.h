@@ -1,0 +1,245 @@
+/*
+ * leg.h -- C ABI of the GB300 (sm_103a) hot path of Language Embedded 3D
+ * Gaussians (arXiv 2311.18482): the tile-based differentiable Gaussian
+ * rasterizer carrying RGB, the compact semantic feature s_G and the
+ * uncertainty u, its backward pass, the semantic decoder D_MLP with its
+ * cross-entropy training step, open-vocabulary relevancy queries and Adam.
+ *
+ * Conventions for every entry point
+ *   - Pointers are DEVICE pointers owned by the caller unless a comment says
+ *     "host".  The library never allocates device memory; scratch comes from a
+ *     caller workspace whose size a *_workspace call reports.
+ *   - `stream` is a cudaStream_t passed as void*; all work is enqueued on it
+ *     asynchronously.  Only le_bin_sort synchronizes (once, to read the
+ *     instance count K back to the host).
+ *   - Every call returns an le_status.  On error nothing is launched (argument
+ *     errors) or the CUDA error is reported (LE_ERR_CUDA); le_last_error()
+ *     returns a message for the calling thread.  The library never aborts and
+ *     never traps on the device.
+ *   - Arrays are row-major, FP32 unless stated.  Per-Gaussian data is
+ *     structure-of-arrays indexed by Gaussian id; images are planar
+ *     [channel][H][W]; pixel (i, j) is sampled at integer coordinates.
+ *   - 16-byte alignment is required for `splat`, `grad2d`, `sh` and the
+ *     decoder weights (torch allocations satisfy it).
+ */
+#ifndef LEG_H
+#define LEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LE_OK = 0,
+    LE_ERR_INVALID_ARG = 1,   /* null/misaligned pointer, bad size */
+    LE_ERR_CAPACITY = 2,      /* instance count K exceeds the caller's capacity */
+    LE_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+    LE_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    LE_ERR_UNSUPPORTED = 5    /* shape not supported by the requested path */
+} le_status;
+
+#define LE_TILE 16            /* screen tiles are 16 x 16 pixels */
+#define LE_DFEAT 8            /* compact semantic feature width d_s (Sec. 4) */
+#define LE_SPLAT_STRIDE 20    /* floats per splat / grad2d record */
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  Host struct.
+ * p_cam of Eq. 1 (eq:render): view = world->camera [R | t] (3x4, row-major),
+ * campos = camera centre (for the SH view direction). */
+typedef struct le_camera {
+    float view[12];
+    float campos[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_z;             /* Gaussians with view z <= near_z are culled (3DGS: 0.2) */
+    float bg[3];              /* background colour; feature / uncertainty backgrounds are 0 */
+} le_camera;
+
+/* The 3D Gaussians G (Sec. 3.1: position p, covariance Sigma via scale and
+ * rotation, colour c via SH, opacity alpha; Sec. 3.4: semantic feature s_G in
+ * R^8 and uncertainty u).  Host struct of device pointers. */
+typedef struct le_gaussians {
+    int32_t n;
+    int32_t sh_degree;        /* 0..3; sh has (sh_degree+1)^2 coefficients per channel */
+    const float* means;       /* [n,3] */
+    const float* log_scales;  /* [n,3]  scale = exp(log_scale) */
+    const float* quats;       /* [n,4]  (w,x,y,z), normalised inside */
+    const float* opacity_raw; /* [n]    opacity = sigmoid(opacity_raw) */
+    const float* sh;          /* [n,(deg+1)^2,3], coefficient k = l^2+l+m, m=-l..l */
+    const float* feat;        /* [n,8]  s_G */
+    const float* unc;         /* [n]    u */
+} le_gaussians;
+
+/* Gradients with the same shapes as le_gaussians.  Host struct of device pointers. */
+typedef struct le_gaussian_grads {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_raw;
+    float* sh;
+    float* feat;
+    float* unc;
+} le_gaussian_grads;
+
+/* Screen-space state produced by le_preprocess.  Host struct of device pointers.
+ * splat record, 20 floats per Gaussian (80 bytes, the unit the renderer reads):
+ *   [0,1] mean2d x,y  [2,3,4] conic A,B,C (inverse 2D covariance)  [5] opacity
+ *   [6,7,8] rgb  [9] u  [10..17] s_G  [18,19] unused
+ * grad2d records (le_render_bwd) use the same layout for dL/d of each field. */
+typedef struct le_projected {
+    float* splat;             /* [n,20] */
+    float* depth;             /* [n]  view-space z (sort key) */
+    int32_t* radius;          /* [n]  0 = culled */
+    uint16_t* rect;           /* [n,4] tile rectangle x0,y0,x1,y1 (half-open) */
+    int32_t* tiles_touched;   /* [n]  (x1-x0)(y1-y0), 0 = culled */
+    uint8_t* clamp_mask;      /* [n]  bit c set when colour channel c was clamped at 0 */
+} le_projected;
+
+/* ---------------------------------------------------------------------------
+ * le_preprocess -- project every Gaussian (Eq. 1 (eq:render); the 3DGS
+ * projection that Sec. 4 says the method reuses):
+ *   Sigma = R S S^T R^T, t = R_c p + t_c, J = d(pinhole)/dt with t_x/t_z,
+ *   t_y/t_z clamped to +-1.3 (W/2)/f inside J, Sigma2 = J R_c Sigma R_c^T J^T
+ *   + 0.3 I, conic = Sigma2^-1, radius = ceil(3 sqrt(lambda_max)), tile rect,
+ *   rgb = max(0, SH(dir) + 0.5).
+ * Depth, screen mean, Sigma2, radius and rect are computed by a fixed
+ * sequence of IEEE FP32 operations (explicit FMA chains, exp by Cody-Waite
+ * reduction + degree-7 Taylor) so that binning is reproducible bit for bit.
+ * Culled Gaussians get radius = tiles_touched = 0 and a zero splat record.
+ * Errors: LE_ERR_INVALID_ARG for n < 0, sh_degree outside 0..3, null or
+ * misaligned pointers. */
+le_status le_preprocess(const le_gaussians* g, const le_camera* cam, le_projected* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * le_bin_sort -- duplicate each visible Gaussian once per tile of its rect,
+ * key each copy (tile_id << 32) | float_bits(depth), tile_id = ty*TX + tx,
+ * order the copies by key with ties kept in emission order (Gaussian index),
+ * and cut the order into per-tile ranges (the 3DGS binning of Sec. 4; tie
+ * rule and empty range (0,0) are readings).  Implemented as an LSD radix sort
+ * of the 64-bit keys whose depth digits are sorted on the Gaussians before
+ * duplication (all copies of a Gaussian share them), then the tile digits on
+ * the copies -- the same order as a stable sort of the full keys.
+ *   depth, rect, tiles_touched: from le_preprocess (n entries)
+ *   workspace: le_bin_sort_workspace(n, k_cap) bytes, 256-byte aligned
+ *   sorted_ids:  [k_cap] out, Gaussian id of each copy in key order
+ *   sorted_keys: [k_cap] out, nullable; the 64-bit keys in order
+ *   tile_ranges: [TX*TY, 2] out, [start, end) into sorted_ids
+ *   k_out: HOST pointer, receives K (always, also on LE_ERR_CAPACITY)
+ * Synchronizes `stream` once to read K.  LE_ERR_CAPACITY when K > k_cap
+ * (nothing after the count is launched; retry with k_cap >= *k_out). */
+le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* bytes);
+le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
+                      const int32_t* tiles_touched, void* workspace, size_t workspace_bytes, int64_t k_cap,
+                      uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
+                      void* stream);
+
+/* ---------------------------------------------------------------------------
+ * le_render_fwd -- per pixel, front to back over its tile's range:
+ *   power = -(A dx^2 + C dy^2)/2 - B dx dy (d = mean2d - pixel), skip if > 0;
+ *   alpha = min(0.99, o e^power), skip if alpha < 1/255; stop before the
+ *   Gaussian that would make T (1 - alpha) < 1e-4;
+ *   C += f alpha T for rgb (Eq. 1), s_G (R_s, Sec. 3.4.1), u (R_u, Sec. 3.4.2);
+ *   T <- T (1 - alpha); finally rgb += T bg.
+ *   out_rgb [3,H,W], out_feat [8,H,W], out_unc [H,W], T_final [H,W],
+ *   n_contrib [H,W] = 1 + range position of the last blended Gaussian (0 if none).
+ * Errors: LE_ERR_INVALID_ARG for null pointers or bad camera size. */
+le_status le_render_fwd(const le_camera* cam, int32_t n, const float* splat, const uint32_t* sorted_ids,
+                        const uint32_t* tile_ranges, float* out_rgb, float* out_feat, float* out_unc,
+                        float* T_final, int32_t* n_contrib, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * le_render_bwd -- gradient of a loss L through le_render_fwd and
+ * le_preprocess ("differentiable rendering and gradient descent", Sec. 3.1).
+ * Each tile is walked back to front, recomputing the per-pixel transmittance
+ * from T_final by division (no per-Gaussian state is stored); per-Gaussian
+ * contributions are reduced across each warp before one atomic add per warp.
+ *   dL_drgb [3,H,W], dL_dfeat [8,H,W], dL_dunc [H,W]: upstream gradients
+ *   grad2d [n,20]: out (caller memory, zeroed by the call), dL/d of the splat
+ *                  record fields (screen-space gradients)
+ *   out: dL/d of every Gaussian parameter (overwritten, not accumulated).
+ * Derivatives of branches are those of the branch taken (alpha clamp at 0.99,
+ * guard-band clamp, colour clamp).  Errors: LE_ERR_INVALID_ARG. */
+le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                        const uint32_t* sorted_ids, const uint32_t* tile_ranges, const float* T_final,
+                        const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
+                        const float* dL_dunc, float* grad2d, const le_gaussian_grads* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Semantic decoder D_MLP (Eq. 8, eq:lem_dec; supp. Tab. dmlp): per-pixel MLP
+ * d_in(=8) -> h1 -> h2 -> n_cb, ReLU, ReLU, linear.  FP32 device weights
+ * [out][in] row-major (a 1x1 convolution's weight), 16-byte aligned. */
+typedef struct le_decoder {
+    int32_t d_in, h1, h2, n_cb;
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+} le_decoder;
+
+typedef struct le_decoder_grads {
+    float *W1, *b1, *W2, *b2, *W3, *b3;   /* overwritten */
+} le_decoder_grads;
+
+#define LE_DECODE_UNFUSED_FP32 0   /* FP32 CUDA cores, activations and logits through HBM */
+#define LE_DECODE_FUSED_BF16 1     /* tcgen05 BF16 tensor cores, FP32 accumulation in TMEM,
+                                      logits never leave the chip */
+
+/* le_decode -- inference (target == NULL) or training step (target != NULL).
+ *   feat [8,P] = R_s, unc [P] = R_u (training only)
+ *   inference outputs (each nullable): argmax [P] (ties -> lowest id),
+ *     prob [n_cb,P] = softmax (M_infer, supp. Sec. "Inference"),
+ *     logits [n_cb,P] (unfused path only)
+ *   training (Eqs. 9-12): loss [2] = (L_CE, L_u) with
+ *     L_CE = sum CE_px (1 - u_px)/P, L_u = sum u_px / P (overwritten);
+ *     d_feat [8,P], d_unc [P], dgrads = gradient of
+ *     L_s = lambda_ce L_CE + lambda_u L_u (u is differentiated too).
+ *   workspace: le_decode_workspace bytes.
+ * Fused path supports d_in = 8, h1 = 64, h2 = 128, n_cb in {16..256, multiple
+ * of 16} (training: n_cb <= 128); otherwise LE_ERR_UNSUPPORTED. */
+le_status le_decode_workspace(int32_t mode, int32_t P, const le_decoder* dec, size_t* bytes);
+le_status le_decode(int32_t mode, int32_t P, const float* feat, const float* unc, const le_decoder* dec,
+                    const int32_t* target, float lambda_ce, float lambda_u, float* loss, float* d_feat,
+                    float* d_unc, const le_decoder_grads* dgrads, int32_t* argmax, float* prob, float* logits,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * le_query -- relevancy of the language feature map F = M_infer S against
+ * text prompts (supp. Sec. "Inference"; relevancy "in accordance with LERF",
+ * reading: phi = F_clip/|F_clip|, rel_j = min_k e^{phi.q_j}/(e^{phi.q_j} +
+ * e^{phi.n_k}), temperature 1; F_clip = first d_clip dims of F).
+ *   codebook S [n_cb,d], text [Q,d_clip], negs [n_neg,d_clip], relevancy [Q,P].
+ *   mode LE_DECODE_UNFUSED_FP32: prob [n_cb,P] given (from le_decode);
+ *     F is materialised in FP32 chunks through the workspace.
+ *   mode LE_DECODE_FUSED_BF16: feat [8,P] + dec given; decode, softmax and
+ *     relevancy in one tcgen05 kernel using |F_clip|^2 = p^T (S_c S_c^T) p and
+ *     phi.q = p.(S_c q) / |F_clip| (never forms F).
+ * dec is required in both modes (its n_cb is the codebook size).  Q >= 1,
+ * n_neg >= 1, Q + n_neg <= 16. */
+le_status le_query_workspace(int32_t mode, int32_t P, int32_t n_cb, int32_t d_clip, size_t* bytes);
+le_status le_query(int32_t mode, int32_t P, const float* feat, const le_decoder* dec, const float* prob,
+                   const float* codebook, int32_t d, int32_t d_clip, const float* text, int32_t Q,
+                   const float* negs, int32_t n_neg, float* relevancy, void* workspace, size_t workspace_bytes,
+                   void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Training helpers (Sec. 4).
+ * le_rgb_l1: L = mean |img - target| over n values, loss[0] = L (device
+ *   scalar, overwritten), grad = sign(img - target)/n (the 3DGS RGB loss's
+ *   L1 term; reading).
+ * le_adam: in-place Adam over one flat buffer (lr 1e-3 and betas (0.9,
+ *   0.999) in the paper; eps is a reading), step >= 1, then clamp to
+ *   [clamp_lo, clamp_hi] (pass -inf/+inf for none; u uses [0,1], Sec. 3.4.2). */
+le_status le_rgb_l1(int64_t n, const float* img, const float* target, float* loss, float* grad, void* stream);
+le_status le_adam(int64_t n, float* param, const float* grad, float* m, float* v, int32_t step, float lr,
+                  float beta1, float beta2, float eps, float clamp_lo, float clamp_hi, void* stream);
+
+/* Message for the last error on the calling thread (static storage). */
+const char* le_last_error(void);
+/* Number of kernel launches this library issued on the calling thread since the
+ * last le_reset_launch_count(). */
+int64_t le_launch_count(void);
+void le_reset_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEG_H */

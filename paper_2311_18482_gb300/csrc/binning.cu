@@ -1,0 +1,439 @@
+// Tile binning: 64-bit (tile | depth) keys, their stable order and the per-tile
+// ranges of the 3DGS rasterizer the paper reuses (Sec. 4).
+//
+// The order is that of a stable sort of key = (tile_id << 32) | bits(depth)
+// over the copies emitted Gaussian by Gaussian.  It is computed as an LSD
+// radix sort of that key in which the four depth digits are sorted on the N
+// Gaussians *before* they are duplicated (every copy of a Gaussian carries the
+// same low word), and only the tile digits are sorted on the K copies:
+//   1. e[i] = bits(depth_i) << 32 | i          (culled: 0xFFFFFFFF, sorted last)
+//   2. LSD radix sort of e on bits 32..63       4 passes over N
+//   3. exclusive scan of tiles_touched in that order -> offsets, K
+//   4. emit copies (tile << 32 | id) in that order, rect row by row
+//   5. LSD radix sort of the copies on the tile bits   ceil(tile_bits/8) passes over K
+//   6. ids, optional full keys, ranges.
+// Each radix pass is reduce-then-scan: per-block digit histograms, one global
+// exclusive scan (digit-major), then a stable block-local scatter staged in
+// shared memory so the global writes come out in digit runs.  No kernel waits
+// on another block, so nothing can spin.
+#include "common.cuh"
+
+namespace leg {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;   // 4096 elements per block
+constexpr int kWarps = kThreads / 32;
+
+// ----------------------------------------------------------------------------
+// Exclusive scan of u32 (3 kernels).  `In` yields element i.
+
+struct DirectIn {
+    const uint32_t* p;
+    __device__ uint32_t operator()(int i) const { return p[i]; }
+};
+
+struct GatherTiles {          // tiles_touched of the Gaussian at depth-sorted position i
+    const uint64_t* e;
+    const int* tiles;
+    __device__ uint32_t operator()(int i) const { return (uint32_t)tiles[(uint32_t)e[i]]; }
+};
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < kWarps ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kWarps) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = (w > 0 ? warp_sums[w - 1] : 0u) + x - v;
+    if (total) *total = warp_sums[kWarps - 1];
+    return before;
+}
+
+template <class In>
+__global__ void __launch_bounds__(kThreads) scan_reduce_kernel(In in, int n, uint32_t* partials)
+{
+    __shared__ uint32_t ws[kWarps];
+    const int base = blockIdx.x * kTile;
+    uint32_t s = 0;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = base + k * kThreads + threadIdx.x;
+        if (i < n) s += in(i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kWarps; ++w) t += ws[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// Single block: exclusive scan of nb partials in place (nb <= 1024 * 16), total -> *total.
+__global__ void __launch_bounds__(1024) scan_partials_kernel(uint32_t* partials, int nb, uint32_t* total)
+{
+    __shared__ uint32_t ws[32];
+    const int per = (nb + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += partials[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    uint32_t run = (w > 0 ? ws[w - 1] : 0u) + x - s;
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t v = partials[i];
+        partials[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 1023) *total = ws[31];
+}
+
+// out[i] = partials[block] + exclusive prefix of in within the block.  out may alias in.
+template <class In>
+__global__ void __launch_bounds__(kThreads) scan_apply_kernel(In in, int n, uint32_t* out, const uint32_t* partials)
+{
+    __shared__ uint32_t sm[kTile + kTile / 32];
+    __shared__ uint32_t ws[kWarps];
+    const int base = blockIdx.x * kTile;
+    for (int k = 0; k < kItems; ++k) {
+        const int j = k * kThreads + threadIdx.x;
+        const int i = base + j;
+        sm[j + (j >> 5)] = i < n ? in(i) : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int j = threadIdx.x * kItems + k;
+        v[k] = sm[j + (j >> 5)];
+        s += v[k];
+    }
+    uint32_t run = block_exclusive_scan(s, ws, nullptr) + partials[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int j = threadIdx.x * kItems + k;
+        sm[j + (j >> 5)] = run;
+        run += v[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < kItems; ++k) {
+        const int j = k * kThreads + threadIdx.x;
+        const int i = base + j;
+        if (i < n) out[i] = sm[j + (j >> 5)];
+    }
+}
+
+template <class In>
+le_status exclusive_scan(In in, int n, uint32_t* out, uint32_t* partials, uint32_t* total, cudaStream_t s)
+{
+    const int nb = (n + kTile - 1) / kTile;
+    if (nb > 1024 * 16) {
+        set_error("scan of %d elements exceeds the supported size", n);
+        return LE_ERR_CAPACITY;
+    }
+    scan_reduce_kernel<In><<<nb, kThreads, 0, s>>>(in, n, partials);
+    LE_LAUNCHED();
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nb, total);
+    LE_LAUNCHED();
+    scan_apply_kernel<In><<<nb, kThreads, 0, s>>>(in, n, out, partials);
+    LE_LAUNCHED();
+    return LE_OK;
+}
+
+// ----------------------------------------------------------------------------
+// One stable LSD radix pass over u64 elements on digit (e >> shift) & (2^bits - 1).
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t e, int shift, uint32_t mask)
+{
+    return (uint32_t)(e >> shift) & mask;
+}
+
+__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t* __restrict__ in, int n, int shift,
+                                                              int bits, uint32_t* __restrict__ counts, int nb)
+{
+    __shared__ uint32_t hist[256];
+    const uint32_t radix = 1u << bits, mask = radix - 1;
+    for (uint32_t d = threadIdx.x; d < radix; d += kThreads) hist[d] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kTile;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = base + k * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&hist[digit_of(in[i], shift, mask)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < radix; d += kThreads) counts[(size_t)d * nb + blockIdx.x] = hist[d];
+}
+
+// offs = exclusive scan of the digit-major counts, with offs[radix*nb] = n.
+__global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t* __restrict__ in,
+                                                                 uint64_t* __restrict__ out, int n, int shift,
+                                                                 int bits, const uint32_t* __restrict__ offs, int nb)
+{
+    __shared__ uint64_t stage[kTile];
+    __shared__ uint32_t warp_cnt[kWarps][256];
+    __shared__ uint32_t gbase[256], lbase[256];
+    __shared__ uint32_t ws[kWarps];
+    const uint32_t radix = 1u << bits, mask = radix - 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = blockIdx.x * kTile;
+    const int cnt = min(kTile, n - base);
+
+    // block's digit counts from the scanned offsets, local exclusive prefix over digits
+    uint32_t c = 0;
+    if (threadIdx.x < (int)radix) {
+        const size_t k = (size_t)threadIdx.x * nb + blockIdx.x;
+        gbase[threadIdx.x] = offs[k];
+        c = offs[k + 1] - offs[k];
+    }
+    const uint32_t lb = block_exclusive_scan(c, ws, nullptr);
+    if (threadIdx.x < (int)radix) lbase[threadIdx.x] = lb;
+    for (int j = threadIdx.x; j < kWarps * 256; j += kThreads) (&warp_cnt[0][0])[j] = 0;
+    __syncthreads();
+
+    // each warp owns the contiguous sub-range [w*512, (w+1)*512) of the block
+    const uint32_t lt = (1u << lane) - 1u;
+    uint64_t e[kItems];
+    uint32_t dg[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int j = w * (kTile / kWarps) + k * 32 + lane;
+        const bool valid = j < cnt;
+        e[k] = valid ? in[base + j] : 0ull;
+        dg[k] = valid ? digit_of(e[k], shift, mask) : 0xFFFFFFFFu;
+        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const uint32_t peers = __match_any_sync(vm, dg[k]);
+            if (lane == __ffs(peers) - 1) warp_cnt[w][dg[k]] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps per digit
+    for (uint32_t d = threadIdx.x; d < radix; d += kThreads) {
+        uint32_t run = 0;
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const uint32_t v = warp_cnt[ww][d];
+            warp_cnt[ww][d] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int j = w * (kTile / kWarps) + k * 32 + lane;
+        const bool valid = j < cnt;
+        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+        uint32_t peers = 0, pos = 0;
+        if (valid) {
+            peers = __match_any_sync(vm, dg[k]);
+            pos = lbase[dg[k]] + warp_cnt[w][dg[k]] + __popc(peers & lt);
+        }
+        __syncwarp();
+        if (valid) {
+            if (lane == __ffs(peers) - 1) warp_cnt[w][dg[k]] += __popc(peers);
+            stage[pos] = e[k];
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += kThreads) {
+        const uint64_t v = stage[j];
+        const uint32_t d = digit_of(v, shift, mask);
+        out[gbase[d] + (j - lbase[d])] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------
+__global__ void depth_elems_kernel(int n, const float* __restrict__ depth, const int* __restrict__ tiles,
+                                   uint64_t* __restrict__ e)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t hi = tiles[i] > 0 ? __float_as_uint(depth[i]) : 0xFFFFFFFFu;
+    e[i] = ((uint64_t)hi << 32) | (uint32_t)i;
+}
+
+__global__ void emit_kernel(int n, const uint64_t* __restrict__ dsorted, const int* __restrict__ tiles,
+                            const ushort4* __restrict__ rect, const uint32_t* __restrict__ offsets, int TX,
+                            uint64_t* __restrict__ inst)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t gid = (uint32_t)dsorted[j];
+    if (tiles[gid] <= 0) return;
+    const ushort4 r = rect[gid];
+    uint32_t o = offsets[j];
+    for (int ty = r.y; ty < r.w; ++ty)
+        for (int tx = r.x; tx < r.z; ++tx) inst[o++] = ((uint64_t)(uint32_t)(ty * TX + tx) << 32) | gid;
+}
+
+__global__ void finalize_kernel(int K, const uint64_t* __restrict__ inst, const float* __restrict__ depth,
+                                uint32_t* __restrict__ ids, uint64_t* __restrict__ keys, uint32_t* __restrict__ ranges)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const uint64_t e = inst[k];
+    const uint32_t t = (uint32_t)(e >> 32), gid = (uint32_t)e;
+    ids[k] = gid;
+    if (keys) keys[k] = ((uint64_t)t << 32) | __float_as_uint(depth[gid]);
+    if (k == 0 || (uint32_t)(inst[k - 1] >> 32) != t) ranges[2 * t] = (uint32_t)k;
+    if (k == K - 1 || (uint32_t)(inst[k + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(k + 1);
+}
+
+// ----------------------------------------------------------------------------
+struct SortWs {
+    uint64_t *eA, *eB, *iA, *iB;
+    uint32_t *offsets, *counts, *partials, *misc;
+    size_t bytes;
+};
+
+inline int nblocks(int64_t n) { return (int)((n + kTile - 1) / kTile); }
+
+SortWs sort_ws_layout(char* base, int32_t n, int64_t k_cap)
+{
+    SortWs w;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base ? base + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    const int nb = nblocks(n > k_cap ? (int64_t)n : k_cap);
+    const size_t count_len = (size_t)256 * nb + 1;
+    const size_t scan_max = count_len > (size_t)n + 1 ? count_len : (size_t)n + 1;
+    w.eA = (uint64_t*)take(sizeof(uint64_t) * (size_t)n);
+    w.eB = (uint64_t*)take(sizeof(uint64_t) * (size_t)n);
+    w.iA = (uint64_t*)take(sizeof(uint64_t) * (size_t)k_cap);
+    w.iB = (uint64_t*)take(sizeof(uint64_t) * (size_t)k_cap);
+    w.offsets = (uint32_t*)take(sizeof(uint32_t) * ((size_t)n + 1));
+    w.counts = (uint32_t*)take(sizeof(uint32_t) * count_len);
+    w.partials = (uint32_t*)take(sizeof(uint32_t) * (scan_max / kTile + 2));
+    w.misc = (uint32_t*)take(sizeof(uint32_t) * 64);
+    w.bytes = off;
+    return w;
+}
+
+// Sort n u64 elements by bits [lo_bit, lo_bit + nbits) (stable, LSD).  Result in *cur.
+le_status radix_sort(uint64_t*& cur, uint64_t*& alt, int n, int lo_bit, int nbits, const SortWs& w, cudaStream_t s)
+{
+    if (n <= 0) return LE_OK;
+    const int nb = nblocks(n);
+    for (int b = 0; b < nbits; b += 8) {
+        const int bits = nbits - b < 8 ? nbits - b : 8;
+        const int shift = lo_bit + b;
+        const int len = (1 << bits) * nb;
+        radix_hist_kernel<<<nb, kThreads, 0, s>>>(cur, n, shift, bits, w.counts, nb);
+        LE_LAUNCHED();
+        le_status st = exclusive_scan(DirectIn{w.counts}, len, w.counts, w.partials, w.counts + len, s);
+        if (st != LE_OK) return st;
+        radix_scatter_kernel<<<nb, kThreads, 0, s>>>(cur, alt, n, shift, bits, w.counts, nb);
+        LE_LAUNCHED();
+        uint64_t* t = cur;
+        cur = alt;
+        alt = t;
+    }
+    return LE_OK;
+}
+
+}  // namespace
+}  // namespace leg
+
+using namespace leg;
+
+extern "C" le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* bytes)
+{
+    LE_CHECK_ARG(bytes != nullptr, "bytes is null");
+    LE_CHECK_ARG(n >= 0 && k_cap >= 0 && k_cap < (int64_t)1 << 31, "n or k_cap out of range");
+    *bytes = sort_ws_layout(nullptr, n, k_cap).bytes;
+    return LE_OK;
+}
+
+extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
+                                 const int32_t* tiles_touched, void* workspace, size_t workspace_bytes, int64_t k_cap,
+                                 uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
+                                 void* stream)
+{
+    le_status st = check_camera(cam);
+    if (st != LE_OK) return st;
+    LE_CHECK_ARG(n >= 0 && k_cap >= 0 && k_cap < (int64_t)1 << 31, "n or k_cap out of range");
+    LE_CHECK_ARG(k_out != nullptr && tile_ranges != nullptr, "k_out and tile_ranges are required");
+    LE_CHECK_ARG(n == 0 || (depth && rect && tiles_touched), "null input pointer");
+    LE_CHECK_ARG(k_cap == 0 || sorted_ids, "sorted_ids is null");
+    LE_CHECK_ARG(workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u) == 0,
+                 "workspace must be non-null and 256-byte aligned");
+    LE_CHECK_ARG((reinterpret_cast<uintptr_t>(rect) & 7u) == 0, "rect must be 8-byte aligned");
+    const SortWs w = sort_ws_layout(static_cast<char*>(workspace), n, k_cap);
+    LE_CHECK_ARG(workspace_bytes >= w.bytes, "workspace too small: %zu < %zu", workspace_bytes, w.bytes);
+    cudaStream_t s = as_stream(stream);
+    const int TX = tiles_x(cam), TY = tiles_y(cam);
+    const int ntiles = TX * TY;
+    LE_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ntiles, s));
+    *k_out = 0;
+    if (n == 0) return LE_OK;
+
+    // 1-2: sort Gaussians by depth (visible first)
+    depth_elems_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, depth, tiles_touched, w.eA);
+    LE_LAUNCHED();
+    uint64_t *cur = w.eA, *alt = w.eB;
+    if ((st = radix_sort(cur, alt, n, 32, 32, w, s)) != LE_OK) return st;
+    // 3: instance offsets in depth order, K
+    if ((st = exclusive_scan(GatherTiles{cur, tiles_touched}, n, w.offsets, w.partials, w.misc, s)) != LE_OK)
+        return st;
+    uint32_t K32 = 0;
+    LE_CUDA(cudaMemcpyAsync(&K32, w.misc, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LE_CUDA(cudaStreamSynchronize(s));
+    *k_out = K32;
+    if ((int64_t)K32 > k_cap) {
+        set_error("instance count K = %u exceeds k_cap = %lld", K32, (long long)k_cap);
+        return LE_ERR_CAPACITY;
+    }
+    const int K = (int)K32;
+    if (K == 0) return LE_OK;
+    // 4: emit copies in depth order
+    emit_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cur, tiles_touched, reinterpret_cast<const ushort4*>(rect),
+                                               w.offsets, TX, w.iA);
+    LE_LAUNCHED();
+    // 5: stable sort of the copies by tile id
+    int tile_bits = 1;
+    while ((1 << tile_bits) < ntiles) ++tile_bits;
+    uint64_t *icur = w.iA, *ialt = w.iB;
+    if ((st = radix_sort(icur, ialt, K, 32, tile_bits, w, s)) != LE_OK) return st;
+    // 6: ids, keys, ranges
+    finalize_kernel<<<(K + 255) / 256, 256, 0, s>>>(K, icur, depth, sorted_ids, sorted_keys, tile_ranges);
+    LE_LAUNCHED();
+    return LE_OK;
+}

@@ -1,0 +1,88 @@
+// Internal helpers shared by the CUDA translation units of libleg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/leg.h"
+
+namespace leg {
+
+// Per-thread error message and launch counter (host side).
+void set_error(const char* fmt, ...);
+void count_launch(int n = 1);
+
+#define LE_CHECK_ARG(cond, ...)                 \
+    do {                                        \
+        if (!(cond)) {                          \
+            ::leg::set_error(__VA_ARGS__);      \
+            return LE_ERR_INVALID_ARG;          \
+        }                                       \
+    } while (0)
+
+#define LE_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::leg::set_error("%s failed: %s", #call, cudaGetErrorString(e_));           \
+            return LE_ERR_CUDA;                                                         \
+        }                                                                               \
+    } while (0)
+
+// After a kernel launch: record it and check for launch errors.
+#define LE_LAUNCHED()                                                                   \
+    do {                                                                                \
+        ::leg::count_launch();                                                          \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess) {                                                        \
+            ::leg::set_error("kernel launch failed at %s:%d: %s", __FILE__, __LINE__,    \
+                             cudaGetErrorString(e_));                                   \
+            return LE_ERR_CUDA;                                                         \
+        }                                                                               \
+    } while (0)
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+inline int tiles_x(const le_camera* c) { return (c->width + LE_TILE - 1) / LE_TILE; }
+inline int tiles_y(const le_camera* c) { return (c->height + LE_TILE - 1) / LE_TILE; }
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Camera values the kernels need, passed by value.
+struct CamParams {
+    float view[12];
+    float campos[3];
+    float fx, fy, cx, cy;
+    int W, H, TX, TY;
+    float near_z;
+    float bg[3];
+};
+
+inline CamParams cam_params(const le_camera* c)
+{
+    CamParams p;
+    for (int i = 0; i < 12; ++i) p.view[i] = c->view[i];
+    for (int i = 0; i < 3; ++i) p.campos[i] = c->campos[i];
+    p.fx = c->fx;
+    p.fy = c->fy;
+    p.cx = c->cx;
+    p.cy = c->cy;
+    p.W = c->width;
+    p.H = c->height;
+    p.TX = tiles_x(c);
+    p.TY = tiles_y(c);
+    p.near_z = c->near_z;
+    for (int i = 0; i < 3; ++i) p.bg[i] = c->bg[i];
+    return p;
+}
+
+inline le_status check_camera(const le_camera* c)
+{
+    LE_CHECK_ARG(c != nullptr, "camera is null");
+    LE_CHECK_ARG(c->width > 0 && c->height > 0 && c->width <= 16384 && c->height <= 16384,
+                 "camera size %dx%d out of range", c->width, c->height);
+    LE_CHECK_ARG(c->fx > 0.f && c->fy > 0.f, "focal lengths must be positive");
+    return LE_OK;
+}
+
+}  // namespace leg

@@ -1,0 +1,277 @@
+// Tile-based front-to-back compositing of RGB (Eq. 1), the compact semantic
+// feature s_G (R_s, Sec. 3.4.1) and the uncertainty u (R_u, Sec. 3.4.2), and
+// its backward pass.
+//
+// One CTA per 16x16 tile, one thread per pixel.  The tile's depth-ordered
+// range is streamed through shared memory in batches of 256 splat records
+// (80 B each, one coalesced 16-byte load group per thread); every thread then
+// reads the batch by broadcast.  The CTA stops fetching once every pixel's
+// transmittance has dropped below 1e-4 (__syncthreads_count ballot).
+//
+// The backward walks the same range back to front from each pixel's last
+// contributor, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
+// transmittance, sums each Gaussian's 18 gradient terms over the warp with
+// shuffles and issues one vectorised atomic add per warp.
+#include "common.cuh"
+
+namespace leg {
+le_status preprocess_backward(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                              const float* grad2d, const le_gaussian_grads* out, cudaStream_t s);
+le_status check_gaussians(const le_gaussians* g);
+
+namespace {
+
+constexpr int kBlock = LE_TILE * LE_TILE;
+
+// power = -(A dx^2 + C dy^2)/2 - B dx dy with a fixed operation order, so the
+// forward and backward kernels take identical skip decisions.
+__device__ __forceinline__ float splat_power(float A, float B, float C, float dx, float dy)
+{
+    const float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+}
+
+__device__ __forceinline__ float splat_alpha0(float opacity, float power)
+{
+    return __fmul_rn(opacity, __expf(power));
+}
+
+__global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
+                                                            const uint32_t* __restrict__ ids,
+                                                            const uint2* __restrict__ ranges,
+                                                            float* __restrict__ out_rgb, float* __restrict__ out_feat,
+                                                            float* __restrict__ out_unc, float* __restrict__ T_final,
+                                                            int* __restrict__ n_contrib)
+{
+    __shared__ float4 rec[5][kBlock];
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.TX, ty = tile / cam.TX;
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
+    const bool inside = px < cam.W && py < cam.H;
+    const uint2 rg = ranges[tile];
+    const int n = (int)(rg.y - rg.x);
+    const float fpx = (float)px, fpy = (float)py;
+
+    bool done = !inside;
+    float T = 1.f;
+    float acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
+    int last = 0;
+
+    for (int b0 = 0; b0 < n; b0 += kBlock) {
+        if (__syncthreads_count(done) == kBlock) break;
+        const int k = b0 + threadIdx.x;
+        if (k < n) {
+            const float4* r = splat + (size_t)ids[rg.x + k] * 5;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
+        }
+        __syncthreads();
+        const int cnt = min(kBlock, n - b0);
+        for (int j = 0; !done && j < cnt; ++j) {
+            const float4 g0 = rec[0][j], g1 = rec[1][j];
+            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
+            const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
+            if (power > 0.f) continue;
+            const float alpha = fminf(0.99f, splat_alpha0(g1.y, power));
+            if (alpha < (1.f / 255.f)) continue;
+            const float test = T * (1.f - alpha);
+            if (test < 1e-4f) {
+                done = true;
+                break;
+            }
+            const float w = alpha * T;
+            const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
+            acc[0] = fmaf(g1.z, w, acc[0]);
+            acc[1] = fmaf(g1.w, w, acc[1]);
+            acc[2] = fmaf(g2.x, w, acc[2]);
+            acc[3] = fmaf(g2.y, w, acc[3]);     // uncertainty
+            acc[4] = fmaf(g2.z, w, acc[4]);     // feature 0..7
+            acc[5] = fmaf(g2.w, w, acc[5]);
+            acc[6] = fmaf(g3.x, w, acc[6]);
+            acc[7] = fmaf(g3.y, w, acc[7]);
+            acc[8] = fmaf(g3.z, w, acc[8]);
+            acc[9] = fmaf(g3.w, w, acc[9]);
+            acc[10] = fmaf(g4.x, w, acc[10]);
+            acc[11] = fmaf(g4.y, w, acc[11]);
+            T = test;
+            last = b0 + j + 1;
+        }
+    }
+    if (!inside) return;
+    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
+    out_rgb[o] = acc[0] + T * cam.bg[0];
+    out_rgb[P + o] = acc[1] + T * cam.bg[1];
+    out_rgb[2 * P + o] = acc[2] + T * cam.bg[2];
+    out_unc[o] = acc[3];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[4 + c];
+    T_final[o] = T;
+    n_contrib[o] = last;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kBlock) render_bwd_kernel(
+    CamParams cam, const float4* __restrict__ splat, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
+    const float* __restrict__ T_final, const int* __restrict__ n_contrib, const float* __restrict__ dL_drgb,
+    const float* __restrict__ dL_dfeat, const float* __restrict__ dL_dunc, float4* __restrict__ grad2d)
+{
+    __shared__ float4 rec[5][kBlock];
+    __shared__ uint32_t sid[kBlock];
+    __shared__ int s_max;
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.TX, ty = tile / cam.TX;
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
+    const bool inside = px < cam.W && py < cam.H;
+    const uint2 rg = ranges[tile];
+    const float fpx = (float)px, fpy = (float)py;
+    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
+
+    float dC[12];
+    float T = 0.f;
+    int last = 0;
+    if (inside) {
+        T = T_final[o];
+        last = n_contrib[o];
+        dC[0] = dL_drgb[o];
+        dC[1] = dL_drgb[P + o];
+        dC[2] = dL_drgb[2 * P + o];
+        dC[3] = dL_dunc[o];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dC[4 + c] = dL_dfeat[c * P + o];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) dC[c] = 0.f;
+    }
+    const float Tf = T;
+    const float bgdot = cam.bg[0] * dC[0] + cam.bg[1] * dC[1] + cam.bg[2] * dC[2];
+    float acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
+
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    const int wmax = __reduce_max_sync(0xffffffffu, last);
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_max, wmax);
+    __syncthreads();
+    const int nproc = s_max;
+    const int lane = threadIdx.x & 31;
+
+    for (int b_end = nproc; b_end > 0; b_end -= kBlock) {
+        const int b_start = max(0, b_end - kBlock);
+        __syncthreads();
+        const int k = b_start + threadIdx.x;
+        if (k < b_end) {
+            const uint32_t gid = ids[rg.x + k];
+            sid[threadIdx.x] = gid;
+            const float4* r = splat + (size_t)gid * 5;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
+        }
+        __syncthreads();
+        for (int j = b_end - b_start - 1; j >= 0; --j) {
+            const int pos = b_start + j;
+            const float4 g0 = rec[0][j], g1 = rec[1][j];
+            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
+            const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
+            const float G = __expf(power);
+            const float a0 = __fmul_rn(g1.y, G);
+            const float alpha = fminf(0.99f, a0);
+            const bool contrib = pos < last && power <= 0.f && alpha >= (1.f / 255.f);
+            if (!__any_sync(0xffffffffu, contrib)) continue;
+            float gr[18];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) gr[q] = 0.f;
+            if (contrib) {
+                T = T / (1.f - alpha);
+                const float w = alpha * T;
+                const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
+                const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
+                float dalpha = 0.f;
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    gr[6 + c] = w * dC[c];                  // rgb (6..8), unc (9), feat (10..17)
+                    dalpha = fmaf((f[c] - acc[c]) * T, dC[c], dalpha);
+                    acc[c] = fmaf(alpha, f[c] - acc[c], acc[c]);
+                }
+                dalpha -= Tf / (1.f - alpha) * bgdot;
+                if (a0 < 0.99f) {
+                    const float dpow = dalpha * alpha;
+                    gr[5] = dalpha * G;
+                    gr[2] = -0.5f * dpow * dx * dx;
+                    gr[3] = -dpow * dx * dy;
+                    gr[4] = -0.5f * dpow * dy * dy;
+                    gr[0] = dpow * (-g0.z * dx - g0.w * dy);
+                    gr[1] = dpow * (-g1.x * dy - g0.w * dx);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 18; ++q) gr[q] = warp_sum(gr[q]);
+            if (lane == 0) {
+                float4* dst = grad2d + (size_t)sid[j] * 5;
+                atomicAdd(dst, make_float4(gr[0], gr[1], gr[2], gr[3]));
+                atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
+                atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
+                atomicAdd(dst + 3, make_float4(gr[12], gr[13], gr[14], gr[15]));
+                atomicAdd(reinterpret_cast<float2*>(dst + 4), make_float2(gr[16], gr[17]));
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace leg
+
+using namespace leg;
+
+extern "C" le_status le_render_fwd(const le_camera* cam, int32_t n, const float* splat, const uint32_t* sorted_ids,
+                                   const uint32_t* tile_ranges, float* out_rgb, float* out_feat, float* out_unc,
+                                   float* T_final, int32_t* n_contrib, void* stream)
+{
+    le_status st = check_camera(cam);
+    if (st != LE_OK) return st;
+    LE_CHECK_ARG(n >= 0, "n < 0");
+    LE_CHECK_ARG(tile_ranges && out_rgb && out_feat && out_unc && T_final && n_contrib, "null output pointer");
+    LE_CHECK_ARG(n == 0 || (splat && aligned16(splat)), "splat must be non-null and 16-byte aligned");
+    LE_CHECK_ARG((reinterpret_cast<uintptr_t>(tile_ranges) & 7u) == 0, "tile_ranges must be 8-byte aligned");
+    const CamParams cp = cam_params(cam);
+    render_fwd_kernel<<<cp.TX * cp.TY, kBlock, 0, as_stream(stream)>>>(
+        cp, reinterpret_cast<const float4*>(splat), sorted_ids, reinterpret_cast<const uint2*>(tile_ranges), out_rgb,
+        out_feat, out_unc, T_final, n_contrib);
+    LE_LAUNCHED();
+    return LE_OK;
+}
+
+extern "C" le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                   const uint32_t* sorted_ids, const uint32_t* tile_ranges, const float* T_final,
+                                   const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
+                                   const float* dL_dunc, float* grad2d, const le_gaussian_grads* out, void* stream)
+{
+    le_status st = check_camera(cam);
+    if (st != LE_OK) return st;
+    if ((st = check_gaussians(g)) != LE_OK) return st;
+    LE_CHECK_ARG(pr && out, "null projected / grads struct");
+    LE_CHECK_ARG(tile_ranges && T_final && n_contrib && dL_drgb && dL_dfeat && dL_dunc, "null input pointer");
+    if (g->n == 0) return LE_OK;
+    LE_CHECK_ARG(pr->splat && pr->tiles_touched && pr->clamp_mask && aligned16(pr->splat), "bad projected pointers");
+    LE_CHECK_ARG(grad2d && aligned16(grad2d), "grad2d must be non-null and 16-byte aligned");
+    LE_CHECK_ARG(out->means && out->log_scales && out->quats && out->opacity_raw && out->sh && out->feat && out->unc,
+                 "null gradient pointer");
+    LE_CHECK_ARG(aligned16(out->quats) && aligned16(out->feat), "quats/feat gradients must be 16-byte aligned");
+    cudaStream_t s = as_stream(stream);
+    const CamParams cp = cam_params(cam);
+    LE_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * LE_SPLAT_STRIDE * (size_t)g->n, s));
+    render_bwd_kernel<<<cp.TX * cp.TY, kBlock, 0, s>>>(cp, reinterpret_cast<const float4*>(pr->splat), sorted_ids,
+                                                        reinterpret_cast<const uint2*>(tile_ranges), T_final,
+                                                        n_contrib, dL_drgb, dL_dfeat, dL_dunc,
+                                                        reinterpret_cast<float4*>(grad2d));
+    LE_LAUNCHED();
+    return preprocess_backward(cam, g, pr, grad2d, out, s);
+}

@@ -229,13 +229,13 @@ def config(name: str, n: int | None = None, W: int | None = None, H: int | None 
     if name == "c1":
         W = W or 128
         H = H or 128
-        scene = uniform_cube_scene(0, n or 2000)
+        scene = uniform_cube_scene(0, 2000 if n is None else n)
         cam = look_at_camera((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), W, H, 60.0)
         return dict(scene=scene, camera=cam)
     if name == "c2":
         W = W or 640
         H = H or 480
-        scene = cluster_scene(1, n or 100_000, 20)
+        scene = cluster_scene(1, 100_000 if n is None else n, 20)
         cam = circle_pose(pose, 16, W, H)
         dec = decoder_init(101, 128)
         return dict(scene=scene, camera=cam, decoder=dec, target_idx=voronoi_index_map(1001 + pose, W, H, 128),
@@ -243,20 +243,20 @@ def config(name: str, n: int | None = None, W: int | None = None, H: int | None 
     if name == "c3":
         W = W or 1296
         H = H or 840
-        scene = cluster_scene(2, n or 1_000_000, 50)
+        scene = cluster_scene(2, 1_000_000 if n is None else n, 50)
         cam = circle_pose(pose, 16, W, H)
         return dict(scene=scene, camera=cam)
     if name == "c4":
         W = W or 1920
         H = H or 1080
-        scene = cluster_scene(3, n or 3_000_000, 50)
+        scene = cluster_scene(3, 3_000_000 if n is None else n, 50)
         cam = circle_pose(pose, 16, W, H)
         dec = decoder_init(103, 256)
         return dict(scene=scene, camera=cam, decoder=dec, query=query_inputs(303, 256))
     if name == "c5":
         W = W or 1296
         H = H or 840
-        scene = cluster_scene(4, n or 1_000_000, 50, unc="zero")
+        scene = cluster_scene(4, 1_000_000 if n is None else n, 50, unc="zero")
         cam = circle_pose(pose, 16, W, H)
         dec = decoder_init(104, 128)
         return dict(scene=scene, camera=cam, decoder=dec,

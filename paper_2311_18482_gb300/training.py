@@ -1,0 +1,123 @@
+"""One training step of the Language Embedded 3D Gaussians hot path on one GPU,
+driven entirely through the C ABI with preallocated device buffers:
+
+  le_preprocess -> le_bin_sort -> le_render_fwd -> le_rgb_l1 (RGB loss, Sec. 4)
+  -> le_decode (D_MLP + uncertainty-weighted CE + L_u, Eqs. 8-12, training mode)
+  -> le_render_bwd (all Gaussian parameter gradients)
+  -> le_adam (Gaussians + decoder; u clamped to [0,1], Sec. 3.4.2)
+
+All parameters live in one flat FP32 buffer (each tensor a 16-byte aligned
+view), so Adam is two launches over contiguous memory.  The loss weights are
+the paper's (all lambda = 1, Sec. 4).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+_FIELDS = ("means", "log_scales", "quats", "opacity_raw", "sh", "feat")
+_DEC = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def _pad4(n):
+    return (n + 3) // 4 * 4
+
+
+class FlatParams:
+    """Views of the Gaussian and decoder parameters in one flat buffer; unc last."""
+
+    def __init__(self, scene, dec, device):
+        N = scene.N
+        shapes = {"means": (N, 3), "log_scales": (N, 3), "quats": (N, 4), "opacity_raw": (N,),
+                  "sh": (N, scene.sh.shape[1], 3), "feat": (N, 8)}
+        for k in _DEC:
+            shapes[k] = getattr(dec, k).shape
+        shapes["unc"] = (N,)
+        self.order = list(_FIELDS) + list(_DEC) + ["unc"]
+        self.offsets, off = {}, 0
+        for k in self.order:
+            n = 1
+            for d in shapes[k]:
+                n *= d
+            self.offsets[k] = (off, n, shapes[k])
+            off = _pad4(off + n)
+        self.total = off
+        self.unc_offset = self.offsets["unc"][0]
+        self.sh_degree = scene.sh_degree
+        self.device = device
+
+    def views(self, flat):
+        return {k: flat[o:o + n].view(*shp) for k, (o, n, shp) in self.offsets.items()}
+
+
+class TrainState:
+    def __init__(self, scene, dec, W, H, device="cuda", decoder_mode=B.FUSED_BF16, lr=1e-3):
+        self.layout = FlatParams(scene, dec, device)
+        L = self.layout
+        self.params = torch.zeros(L.total, dtype=torch.float32, device=device)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        pv = L.views(self.params)
+        src = {k: getattr(scene, k) for k in list(_FIELDS) + ["unc"]}
+        src.update({k: getattr(dec, k) for k in _DEC})
+        for k, t in pv.items():
+            t.copy_(torch.from_numpy(src[k]).reshape(t.shape))
+        self.pv, self.gv = pv, L.views(self.grads)
+        self.g = B.Gaussians(pv["means"], pv["log_scales"], pv["quats"], pv["opacity_raw"], pv["sh"], pv["feat"],
+                             pv["unc"], scene.sh_degree)
+        self.gg = B.grads_struct(B.Gaussians(*(self.gv[k] for k in list(_FIELDS) + ["unc"]), scene.sh_degree))
+        self.dec = B.decoder_struct(*(pv[k] for k in _DEC))
+        self.dgrad = B.decoder_grads_struct([self.gv[k] for k in _DEC])
+        N, P = scene.N, W * H
+        self.W, self.H, self.P = W, H, P
+        self.proj = B.Projected.empty(N, device)
+        self.bins = B.BinSortBuffers()
+        self.img = B.Image.empty(H, W, device)
+        self.loss = torch.zeros(3, dtype=torch.float32, device=device)     # L1, L_CE, L_u
+        self.d_rgb = torch.empty((3, H, W), dtype=torch.float32, device=device)
+        self.d_feat = torch.empty((8, H, W), dtype=torch.float32, device=device)
+        self.d_unc = torch.empty((H, W), dtype=torch.float32, device=device)
+        self.grad2d = torch.empty((N, B.SPLAT_STRIDE), dtype=torch.float32, device=device)
+        self.mode = decoder_mode
+        self.dec_ws = torch.empty(max(B.le_decode_workspace(decoder_mode, P, self.dec), 1), dtype=torch.uint8,
+                                  device=device)
+        self.step_count = 0
+        self.lr = lr
+        self.K = 0
+        self.events = None
+
+    def _mark(self, name):
+        if self.events is not None:
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            self.events.append((name, ev))
+
+    def step(self, cam, rgb_target, idx_target):
+        """One fwd+bwd+Adam step on view `cam`; returns the device loss vector (L1, L_CE, L_u)."""
+        self._mark("start")
+        B.le_preprocess(self.g, cam, self.proj)
+        self._mark("preprocess")
+        ids, ranges, self.K, _ = B.le_bin_sort(cam, self.proj, self.bins)
+        self._mark("bin_sort")
+        B.le_render_fwd(cam, self.proj, ids, ranges, self.img)
+        self._mark("render_fwd")
+        B.le_rgb_l1(self.img.rgb, rgb_target, self.loss[0:1], self.d_rgb)
+        B.le_decode_raw(self.mode, self.P, self.img.feat, self.img.unc, self.dec, idx_target, 1.0, 1.0,
+                        self.loss[1:3], self.d_feat, self.d_unc, self.dgrad, None, None, None, self.dec_ws)
+        self._mark("decoder")
+        cs, gs, ps = B.camera_struct(cam), self.g.struct(), self.proj.struct()
+        import ctypes as C
+        B._check(B.load().le_render_bwd(C.byref(cs), C.byref(gs), C.byref(ps), B._ptr(ids), B._ptr(ranges),
+                                        B._ptr(self.img.T), B._ptr(self.img.n_contrib), B._ptr(self.d_rgb),
+                                        B._ptr(self.d_feat), B._ptr(self.d_unc), B._ptr(self.grad2d),
+                                        C.byref(self.gg), B._stream()))
+        self._mark("render_bwd")
+        self.step_count += 1
+        u0 = self.layout.unc_offset
+        B.le_adam(self.params[:u0], self.grads[:u0], self.m[:u0], self.v[:u0], self.step_count, lr=self.lr)
+        B.le_adam(self.params[u0:], self.grads[u0:], self.m[u0:], self.v[u0:], self.step_count, lr=self.lr,
+                  clamp_lo=0.0, clamp_hi=1.0)
+        self._mark("adam")
+        return self.loss

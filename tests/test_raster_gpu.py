@@ -1,0 +1,222 @@
+"""GPU parity of the rasterizer (preprocess, binning, render forward and
+backward) against the FP64 oracle, through the C ABI.
+
+Bars: bit-exact for integers (tiles, keys, sorted order, ranges, n_contrib);
+1e-5 relative (per-tensor infinity norm) for per-Gaussian FP32 values; 1e-4
+for images, T_final and all gradients.  Pixels the oracle flags as sitting on
+a threshold (flip pixels) are excluded from image comparisons and get zero
+upstream gradient on both sides.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2311_18482_gb300 import synth
+from parity import rel_err, to_np, upstream
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _run(leg, sc, cam):
+    g = leg.Gaussians.from_scene(sc)
+    proj = leg.le_preprocess(g, cam)
+    ids, ranges, K, keys = leg.le_bin_sort(cam, proj, want_keys=True)
+    img = leg.le_render_fwd(cam, proj, ids, ranges)
+    torch.cuda.synchronize()
+    return g, proj, ids, ranges, K, keys, img
+
+
+def _check_preprocess(proj, sc, kp, pr):
+    vis = kp["tiles"] > 0
+    assert np.array_equal(to_np(proj.tiles_touched), kp["tiles"])
+    assert np.array_equal(to_np(proj.radius), kp["radius"])
+    assert np.array_equal(to_np(proj.rect).view(np.uint16).astype(np.int32), kp["rect"])
+    assert np.array_equal(to_np(proj.depth).view(np.uint32)[vis], kp["depth"].view(np.uint32)[vis])
+    sp = to_np(proj.splat)
+    assert np.array_equal(sp[vis, 0:2].view(np.uint32), kp["mean2d"][vis].view(np.uint32))
+    assert rel_err(sp[vis, 2:5], pr["conic"][vis]) < 1e-5
+    assert rel_err(sp[vis, 5], pr["opacity"][vis]) < 1e-5
+    assert rel_err(sp[vis, 6:9], pr["rgb"][vis]) < 1e-5
+    assert np.array_equal(sp[vis, 9], sc.unc[vis])
+    assert np.array_equal(sp[vis, 10:18], sc.feat[vis])
+    assert np.all(sp[~vis] == 0)
+
+
+def _check_image(img, ref, mask=None):
+    ok = ref["flip"] == 0
+    if mask is not None:
+        ok &= mask
+    assert ok.mean() > 0.99
+    for k, r in (("rgb", ref["rgb"]), ("feat", ref["feat"])):
+        assert rel_err(to_np(getattr(img, k))[:, ok], r[:, ok]) < 1e-4, k
+    assert rel_err(to_np(img.unc)[ok], ref["unc"][ok]) < 1e-4
+    assert rel_err(to_np(img.T)[ok], ref["T"][ok]) < 1e-4
+    assert np.array_equal(to_np(img.n_contrib)[ok], ref["n_contrib"][ok])
+
+
+@pytest.mark.parametrize("case", [("c1", {}), ("c1", dict(n=700, W=100, H=75)), ("c2", dict(n=20000, W=320, H=240))])
+def test_forward_parity(leg, orc, case):
+    name, kw = case
+    c = synth.config(name, **kw)
+    sc, cam = c["scene"], c["camera"]
+    cam.bg = np.array([0.1, 0.2, 0.3], np.float32)
+    g, proj, ids, ranges, K, keys, img = _run(leg, sc, cam)
+    ref = orc.forward(sc, cam)
+    _check_preprocess(proj, sc, ref["kp"], ref["proj"])
+    assert K == len(ref["vals"])
+    assert np.array_equal(to_np(keys).view(np.uint64), ref["keys"])
+    assert np.array_equal(to_np(ids).view(np.uint32), ref["vals"])
+    assert np.array_equal(to_np(ranges).view(np.uint32), ref["ranges"])
+    _check_image(img, ref["img"])
+
+
+@pytest.mark.parametrize("case", [("c1", {}), ("c1", dict(n=700, W=100, H=75)), ("c2", dict(n=20000, W=320, H=240))])
+def test_backward_parity(leg, orc, case):
+    name, kw = case
+    c = synth.config(name, **kw)
+    sc, cam = c["scene"], c["camera"]
+    cam.bg = np.array([0.1, 0.2, 0.3], np.float32)
+    g, proj, ids, ranges, K, keys, img = _run(leg, sc, cam)
+    ref = orc.forward(sc, cam)
+    ok = ref["img"]["flip"] == 0
+    dr, df, du = upstream(np.random.default_rng(11), cam.H, cam.W, ok)
+    grads, grad2d = leg.le_render_bwd(cam, g, proj, ids, ranges, img, _t(dr), _t(df), _t(du))
+    torch.cuda.synchronize()
+    g2 = orc.render_bwd(cam, sc, ref["proj"], ref["vals"], ref["ranges"], dr, df, du)
+    gp = orc.project_bwd(sc, cam, ref["kp"]["tiles"], g2["mean2d"], g2["conic"], g2["opacity"], g2["rgb"])
+    G = to_np(grad2d)
+    assert rel_err(G[:, 0:2], g2["mean2d"]) < 1e-4
+    assert rel_err(G[:, 2:5], g2["conic"]) < 1e-4
+    assert rel_err(G[:, 5], g2["opacity"]) < 1e-4
+    assert rel_err(G[:, 6:9], g2["rgb"]) < 1e-4
+    assert rel_err(G[:, 9], g2["unc"]) < 1e-4
+    assert rel_err(G[:, 10:18], g2["feat"]) < 1e-4
+    for k in ("means", "log_scales", "quats", "opacity_raw", "sh"):
+        assert rel_err(to_np(getattr(grads, k)), gp[k]) < 1e-4, k
+    assert rel_err(to_np(grads.feat), g2["feat"]) < 1e-4
+    assert rel_err(to_np(grads.unc), g2["unc"]) < 1e-4
+
+
+def test_autograd_function(leg, orc):
+    c = synth.config("c1", n=800, W=64, H=64)
+    sc, cam = c["scene"], c["camera"]
+    ref = orc.forward(sc, cam)
+    ok = ref["img"]["flip"] == 0
+    dr, df, du = upstream(np.random.default_rng(12), cam.H, cam.W, ok)
+    params = [torch.from_numpy(getattr(sc, k)).cuda().requires_grad_(True)
+              for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat", "unc")]
+    rgb, feat, unc, T = leg.rasterize(*params, cam, sc.sh_degree)
+    loss = (rgb * _t(dr)).sum() + (feat * _t(df)).sum() + (unc * _t(du)).sum()
+    loss.backward()
+    g2 = orc.render_bwd(cam, sc, ref["proj"], ref["vals"], ref["ranges"], dr, df, du)
+    gp = orc.project_bwd(sc, cam, ref["kp"]["tiles"], g2["mean2d"], g2["conic"], g2["opacity"], g2["rgb"])
+    for p, k in zip(params, ("means", "log_scales", "quats", "opacity_raw", "sh")):
+        assert rel_err(to_np(p.grad), gp[k]) < 1e-4, k
+    assert rel_err(to_np(params[5].grad), g2["feat"]) < 1e-4
+    assert rel_err(to_np(params[6].grad), g2["unc"]) < 1e-4
+
+
+def test_degenerate_scenes(leg, orc):
+    # all Gaussians behind the camera: K = 0, background everywhere, zero gradients
+    c = synth.config("c1", n=50, W=40, H=24)
+    sc, cam = c["scene"], c["camera"]
+    cam.bg = np.array([0.25, 0.5, 0.75], np.float32)
+    sc.means[:, 2] = -10.0
+    g, proj, ids, ranges, K, keys, img = _run(leg, sc, cam)
+    assert K == 0
+    assert np.all(to_np(ranges) == 0)
+    assert np.allclose(to_np(img.rgb), cam.bg[:, None, None])
+    assert np.all(to_np(img.T) == 1) and np.all(to_np(img.n_contrib) == 0)
+    dr, df, du = upstream(np.random.default_rng(0), cam.H, cam.W)
+    grads, _ = leg.le_render_bwd(cam, g, proj, ids, ranges, img, _t(dr), _t(df), _t(du))
+    assert torch.all(grads.means == 0) and torch.all(grads.sh == 0)
+    # single Gaussian, empty scene
+    c1 = synth.config("c1", n=1, W=16, H=16)
+    g, proj, ids, ranges, K, keys, img = _run(leg, c1["scene"], c1["camera"])
+    ref = orc.forward(c1["scene"], c1["camera"])
+    assert K == len(ref["vals"])
+    _check_image(img, ref["img"])
+    c0 = synth.config("c1", n=0, W=16, H=16)
+    g, proj, ids, ranges, K, keys, img = _run(leg, c0["scene"], c0["camera"])
+    assert K == 0 and np.all(to_np(img.T) == 1)
+
+
+def test_deterministic_binning(leg):
+    c = synth.config("c2", n=50000, W=320, H=240)
+    sc, cam = c["scene"], c["camera"]
+    a = _run(leg, sc, cam)
+    b = _run(leg, sc, cam)
+    assert torch.equal(a[2], b[2]) and torch.equal(a[3], b[3])
+    assert torch.equal(a[6].rgb, b[6].rgb)
+
+
+@pytest.mark.parametrize("name", ["c3"])
+def test_full_size_crop_parity(leg, orc, name):
+    """Full-size scene (1M Gaussians, 1296x840, the bench's launch configuration):
+    preprocess on every Gaussian, binning on sampled tiles, images and gradients
+    on the 64x64 centre crop (upstream gradient zero elsewhere)."""
+    c = synth.config(name)
+    sc, cam = c["scene"], c["camera"]
+    g, proj, ids, ranges, K, keys, img = _run(leg, sc, cam)
+    kp = orc.keypath(sc, cam)
+    pr = orc.project(sc, cam, kp["tiles"])
+    _check_preprocess(proj, sc, kp, pr)
+    assert K == int(kp["tiles"].astype(np.int64).sum())
+    ids_np = to_np(ids).view(np.uint32)
+    rg = to_np(ranges).view(np.uint32)
+    rng = np.random.default_rng(3)
+    for t in rng.choice(cam.tiles_x * cam.tiles_y, 12, replace=False):
+        tx, ty = t % cam.tiles_x, t // cam.tiles_x
+        want = orc.tile_list(kp, tx, ty)
+        assert np.array_equal(ids_np[rg[t, 0]:rg[t, 1]], want)
+    x0, y0 = (cam.W // 2 - 32) // 16 * 16, (cam.H // 2 - 32) // 16 * 16
+    win = (x0, y0, x0 + 64, y0 + 64)
+    tl = [(tx, ty) for ty in range(y0 // 16, y0 // 16 + 4) for tx in range(x0 // 16, x0 // 16 + 4)]
+    vals, rr = orc.lists_for_tiles(cam, kp, tl)
+    ref = orc.render(cam, sc, pr, vals, rr, win)
+    sub = lambda a: a[..., y0:y0 + 64, x0:x0 + 64]
+    ok = ref["flip"] == 0
+    for k in ("rgb", "feat"):
+        assert rel_err(sub(to_np(getattr(img, k)))[:, ok], ref[k][:, ok]) < 1e-4, k
+    assert rel_err(sub(to_np(img.T))[ok], ref["T"][ok]) < 1e-4
+    assert np.array_equal(sub(to_np(img.n_contrib))[ok], ref["n_contrib"][ok])
+    dr, df, du = upstream(np.random.default_rng(4), 64, 64, ok)
+    DR, DF, DU = np.zeros((3, cam.H, cam.W)), np.zeros((8, cam.H, cam.W)), np.zeros((cam.H, cam.W))
+    DR[:, y0:y0 + 64, x0:x0 + 64], DF[:, y0:y0 + 64, x0:x0 + 64], DU[y0:y0 + 64, x0:x0 + 64] = dr, df, du
+    grads, grad2d = leg.le_render_bwd(cam, g, proj, ids, ranges, img, _t(DR), _t(DF), _t(DU))
+    torch.cuda.synchronize()
+    g2 = orc.render_bwd(cam, sc, pr, vals, rr, dr, df, du, window=win)
+    gp = orc.project_bwd(sc, cam, kp["tiles"], g2["mean2d"], g2["conic"], g2["opacity"], g2["rgb"])
+    for k in ("means", "log_scales", "quats", "opacity_raw", "sh"):
+        assert rel_err(to_np(getattr(grads, k)), gp[k]) < 1e-4, k
+    assert rel_err(to_np(grads.feat), g2["feat"]) < 1e-4
+    assert rel_err(to_np(grads.unc), g2["unc"]) < 1e-4
+
+
+def test_l1_and_adam(leg, orc):
+    rng = np.random.default_rng(13)
+    n = 1003
+    img, tgt = rng.uniform(0, 1, n), rng.uniform(0, 1, n).astype(np.float32)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty(n, device="cuda")
+    leg.le_rgb_l1(_t(img), _t(tgt), loss, grad)
+    l_ref, g_ref = orc.l1(img.astype(np.float32).astype(np.float64), tgt)
+    assert abs(loss.item() - l_ref) < 1e-5 * l_ref
+    assert rel_err(to_np(grad), g_ref) < 1e-6
+    p = rng.standard_normal(n)
+    p_t, m_t, v_t = _t(p), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    p_o, m_o, v_o = p.astype(np.float32).astype(np.float64), np.zeros(n), np.zeros(n)
+    for step in range(1, 4):
+        gg = rng.standard_normal(n)
+        leg.le_adam(p_t, _t(gg), m_t, v_t, step)
+        orc.adam(p_o, gg.astype(np.float32).astype(np.float64), m_o, v_o, step)
+    assert rel_err(to_np(p_t), p_o) < 1e-5
+    # clamp to [0, 1] (the uncertainty's range)
+    u = _t(rng.uniform(-0.5, 1.5, 64))
+    leg.le_adam(u, torch.zeros(64, device="cuda"), torch.zeros(64, device="cuda"), torch.zeros(64, device="cuda"),
+                1, clamp_lo=0.0, clamp_hi=1.0)
+    assert float(u.min()) >= 0 and float(u.max()) <= 1
