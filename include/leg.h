@@ -136,6 +136,32 @@ le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const
                       void* stream);
 
 /* ---------------------------------------------------------------------------
+ * le_bin_sort_static -- le_bin_sort without a caller workspace.  (No
+ * counterpart in the paper: it is a deployment convenience of this library.)
+ * For callers that must not allocate device memory -- for example code that
+ * runs inside a host application or plugin whose device memory is owned and
+ * budgeted by someone else, or a per-frame path where the implicit
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine; its scratch is a
+ * statically sized device array inside this library (about 9.4 MB), which
+ * every GPU that loads the library holds until the process exits.
+ *   Limits: n <= LE_STATIC_MAX_GAUSSIANS, and at most LE_STATIC_MAX_INSTANCES
+ *   tile copies (k_cap is clamped to it).  Larger n -> LE_ERR_INVALID_ARG;
+ *   more copies -> LE_ERR_CAPACITY with *k_out = K and a message naming the
+ *   limit.  Inputs and outputs are those of le_bin_sort.
+ *   The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ *   All calls share the one array, which keeps the last call's contents (every
+ *   scratch word is rewritten before it is read, so nothing needs clearing):
+ *   calls whose GPU work overlaps -- on different streams or host threads --
+ *   race on it and must be serialised by the caller. */
+#define LE_STATIC_MAX_GAUSSIANS 65536
+#define LE_STATIC_MAX_INSTANCES 524288
+le_status le_bin_sort_static(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
+                             const int32_t* tiles_touched, int64_t k_cap, uint32_t* sorted_ids,
+                             uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * le_render_fwd -- per pixel, front to back over its tile's range:
  *   power = -(A dx^2 + C dy^2)/2 - B dx dy (d = mean2d - pixel), skip if > 0;
  *   alpha = min(0.99, o e^power), skip if alpha < 1/255; stop before the

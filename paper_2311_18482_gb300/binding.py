@@ -63,6 +63,8 @@ _SIG = {
     "le_bin_sort_workspace": [C.c_int32, C.c_int64, C.POINTER(C.c_size_t)],
     "le_bin_sort": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, C.c_size_t, C.c_int64, _P, _P, _P,
                     C.POINTER(C.c_int64), _P],
+    "le_bin_sort_static": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P,
+                           C.POINTER(C.c_int64), _P],
     "le_render_fwd": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "le_render_bwd": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P, _P, _P,
                       _P, _P, C.POINTER(LeGaussianGrads), _P],
@@ -265,6 +267,16 @@ def le_bin_sort(cam, proj: Projected, buffers: BinSortBuffers | None = None, k_c
         return (buffers.ids[:k], buffers.ranges[:ntiles], k,
                 buffers.keys[:k] if want_keys else None)
     raise LegError(LE_ERR_CAPACITY, "capacity retry failed")
+
+
+def le_bin_sort_static(cam, proj: Projected, sorted_ids, tile_ranges, sorted_keys=None):
+    """le_bin_sort with the library's static scratch (no workspace; see leg.h).
+    The caller provides the outputs; returns K."""
+    K = C.c_int64()
+    _check(load().le_bin_sort_static(C.byref(camera_struct(cam)), proj.depth.shape[0], _ptr(proj.depth),
+                                     _ptr(proj.rect), _ptr(proj.tiles_touched), sorted_ids.numel(),
+                                     _ptr(sorted_ids), _ptr(sorted_keys), _ptr(tile_ranges), C.byref(K), _stream()))
+    return K.value
 
 
 @dataclass

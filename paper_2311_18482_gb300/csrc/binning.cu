@@ -16,6 +16,8 @@
 // exclusive scan (digit-major), then a stable block-local scatter staged in
 // shared memory so the global writes come out in digit runs.  No kernel waits
 // on another block, so nothing can spin.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace leg {
@@ -436,4 +438,82 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     finalize_kernel<<<(K + 255) / 256, 256, 0, s>>>(K, icur, depth, sorted_ids, sorted_keys, tile_ranges);
     LE_LAUNCHED();
     return LE_OK;
+}
+
+// ----------------------------------------------------------------------------
+// le_bin_sort_static: le_bin_sort for callers that cannot allocate device
+// memory.  Its scratch is the file-scope array below, sized for at most
+// LE_STATIC_MAX_GAUSSIANS Gaussians and LE_STATIC_MAX_INSTANCES tile copies;
+// every GPU that loads this library holds it until the process exits.
+namespace leg {
+namespace {
+
+constexpr int32_t kStaticMaxN = LE_STATIC_MAX_GAUSSIANS;
+constexpr int64_t kStaticMaxK = LE_STATIC_MAX_INSTANCES;
+
+// Scratch bytes le_bin_sort needs at the limits (the same layout it uses for a
+// caller workspace), rounded up to 256 bytes.
+constexpr size_t static_bytes()
+{
+    // eA, eB: 8 B per Gaussian each; iA, iB: 8 B per copy each; offsets: 4 B per
+    // Gaussian + 1; digit counts: 256 per 4096-element block + 1; scan partials;
+    // 64 words of counters.  Each segment is rounded up to 256 bytes.
+    return (8 * (size_t)kStaticMaxN + 255) / 256 * 256 * 2 + (8 * (size_t)kStaticMaxK + 255) / 256 * 256 * 2 +
+           (4 * ((size_t)kStaticMaxN + 1) + 255) / 256 * 256 +
+           (4 * (256 * (size_t)(kStaticMaxK / 4096) + 1) + 255) / 256 * 256 +
+           (4 * ((256 * (size_t)(kStaticMaxK / 4096) + 1) / 4096 + 2) + 255) / 256 * 256 + 256;
+}
+
+__device__ __align__(256) unsigned char g_static_scratch[static_bytes()];
+
+// Device address of g_static_scratch per device, looked up on the first call
+// made with that device current.
+std::mutex g_static_mu;
+void* g_static_ptr[256] = {};
+
+le_status static_scratch(void** out)
+{
+    int dev = 0;
+    LE_CUDA(cudaGetDevice(&dev));
+    LE_CHECK_ARG(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (g_static_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("cudaGetSymbolAddress(static scratch) failed: %s", cudaGetErrorString(e));
+            return LE_ERR_CUDA;
+        }
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return LE_OK;
+}
+
+}  // namespace
+}  // namespace leg
+
+extern "C" le_status le_bin_sort_static(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
+                                        const int32_t* tiles_touched, int64_t k_cap, uint32_t* sorted_ids,
+                                        uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out, void* stream)
+{
+    LE_CHECK_ARG(n >= 0 && n <= kStaticMaxN, "n = %d exceeds the static-scratch limit of %d Gaussians", n,
+                 kStaticMaxN);
+    LE_CHECK_ARG(k_cap >= 0, "k_cap < 0");
+    if (k_cap > kStaticMaxK) k_cap = kStaticMaxK;
+    size_t need = 0;
+    le_status st = le_bin_sort_workspace(n, k_cap, &need);
+    if (st != LE_OK) return st;
+    if (need > sizeof(g_static_scratch)) {
+        set_error("static scratch too small for n = %d, k_cap = %lld", n, (long long)k_cap);
+        return LE_ERR_INVALID_ARG;
+    }
+    void* ws = nullptr;
+    if ((st = static_scratch(&ws)) != LE_OK) return st;
+    st = le_bin_sort(cam, n, depth, rect, tiles_touched, ws, sizeof(g_static_scratch), k_cap, sorted_ids, sorted_keys,
+                     tile_ranges, k_out, stream);
+    if (st == LE_ERR_CAPACITY && k_out && *k_out > kStaticMaxK)
+        set_error("instance count K = %lld exceeds the static-scratch limit of %lld tile copies",
+                  (long long)*k_out, (long long)kStaticMaxK);
+    return st;
 }
