@@ -258,6 +258,13 @@ le_status le_rgb_l1(int64_t n, const float* img, const float* target, float* los
 le_status le_adam(int64_t n, float* param, const float* grad, float* m, float* v, int32_t step, float lr,
                   float beta1, float beta2, float eps, float clamp_lo, float clamp_hi, void* stream);
 
+/* le_device_status -- synchronizes `stream`, then reports whether any
+ * tensor-core kernel (fused decode / query) gave up on a bounded wait since the
+ * last call: LE_ERR_TIMEOUT (and clears the record) or LE_OK.  Such a kernel
+ * stops issuing work, frees its tensor memory and returns; its outputs are
+ * then incomplete. */
+le_status le_device_status(void* stream);
+
 /* Message for the last error on the calling thread (static storage). */
 const char* le_last_error(void);
 /* Number of kernel launches this library issued on the calling thread since the

@@ -75,6 +75,7 @@ _SIG = {
     "le_query": [C.c_int32, C.c_int32, _P, C.POINTER(LeDecoder), _P, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P,
                  C.c_int32, _P, _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
+    "le_device_status": [_P],
     "le_adam": [C.c_int64, _P, _P, _P, _P, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
                 C.c_float, _P],
 }
@@ -116,6 +117,12 @@ def _ptr(t):
 
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def le_device_status():
+    """Synchronizes the current stream; raises LegError(LE_ERR_TIMEOUT) if a
+    tensor-core kernel gave up on a bounded wait."""
+    _check(load().le_device_status(_stream()))
 
 
 def launch_count() -> int:
