@@ -117,18 +117,22 @@ le_status le_preprocess(const le_gaussians* g, const le_camera* cam, le_projecte
  * key each copy (tile_id << 32) | float_bits(depth), tile_id = ty*TX + tx,
  * order the copies by key with ties kept in emission order (Gaussian index),
  * and cut the order into per-tile ranges (the 3DGS binning of Sec. 4; tie
- * rule and empty range (0,0) are readings).  Implemented as an LSD radix sort
- * of the 64-bit keys whose depth digits are sorted on the Gaussians before
- * duplication (all copies of a Gaussian share them), then the tile digits on
- * the copies -- the same order as a stable sort of the full keys.
+ * rule and empty range (0,0) are readings).  The K copies are never sorted:
+ * the Gaussians are radix-sorted by depth, per-(tile, chunk-of-Gaussians)
+ * copy counts come from 2-D difference arrays of the rects, one exclusive scan
+ * of those counts in tile-major order gives every chunk's offset inside every
+ * tile's range, and each chunk writes its copies in depth order -- the same
+ * order as a stable sort of the full keys.
  *   depth, rect, tiles_touched: from le_preprocess (n entries)
- *   workspace: le_bin_sort_workspace(n, k_cap) bytes, 256-byte aligned
+ *   workspace: le_bin_sort_workspace(n, k_cap) bytes, 256-byte aligned (it
+ *     depends on n only; k_cap bounds the outputs)
  *   sorted_ids:  [k_cap] out, Gaussian id of each copy in key order
  *   sorted_keys: [k_cap] out, nullable; the 64-bit keys in order
  *   tile_ranges: [TX*TY, 2] out, [start, end) into sorted_ids
  *   k_out: HOST pointer, receives K (always, also on LE_ERR_CAPACITY)
  * Synchronizes `stream` once to read K.  LE_ERR_CAPACITY when K > k_cap
- * (nothing after the count is launched; retry with k_cap >= *k_out). */
+ * (nothing after the count is launched; retry with k_cap >= *k_out).
+ * LE_ERR_UNSUPPORTED for more than 16384 screen tiles or 256 tile columns. */
 le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* bytes);
 le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
                       const int32_t* tiles_touched, void* workspace, size_t workspace_bytes, int64_t k_cap,

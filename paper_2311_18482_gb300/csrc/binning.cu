@@ -2,20 +2,23 @@
 // ranges of the 3DGS rasterizer the paper reuses (Sec. 4).
 //
 // The order is that of a stable sort of key = (tile_id << 32) | bits(depth)
-// over the copies emitted Gaussian by Gaussian.  It is computed as an LSD
-// radix sort of that key in which the four depth digits are sorted on the N
-// Gaussians *before* they are duplicated (every copy of a Gaussian carries the
-// same low word), and only the tile digits are sorted on the K copies:
+// over the copies emitted Gaussian by Gaussian: inside each tile, copies are
+// ordered by depth, ties by Gaussian index.  It is computed without sorting the
+// K copies at all:
 //   1. e[i] = bits(depth_i) << 32 | i          (culled: 0xFFFFFFFF, sorted last)
-//   2. LSD radix sort of e on bits 32..63       4 passes over N
-//   3. exclusive scan of tiles_touched in that order -> offsets, K
-//   4. emit copies (tile << 32 | id) in that order, rect row by row
-//   5. LSD radix sort of the copies on the tile bits   ceil(tile_bits/8) passes over K
-//   6. ids, optional full keys, ranges.
-// Each radix pass is reduce-then-scan: per-block digit histograms, one global
-// exclusive scan (digit-major), then a stable block-local scatter staged in
-// shared memory so the global writes come out in digit runs.  No kernel waits
-// on another block, so nothing can spin.
+//   2. stable LSD radix sort of e on bits 32..63 (4 passes over the N Gaussians)
+//   3. split the depth-sorted Gaussians into chunks; per chunk, the number of
+//      copies in every tile from a 2-D difference array of the rectangles
+//   4. one exclusive scan of those counts in tile-major order: entry (t, c) is
+//      where chunk c's copies of tile t start; the total is K; consecutive
+//      tiles' first entries are the tile ranges
+//   5. blocks of (8 tile rows x a super-chunk of Gaussians) write the copies in
+//      depth order through per-tile cursors held in registers (one warp per
+//      row, one lane per 32nd tile of the row).
+// Each radix pass of step 2 is reduce-then-scan: per-block digit histograms,
+// one global exclusive scan (digit-major), then a stable block-local scatter
+// staged in shared memory.  No kernel waits on another block, so nothing can
+// spin.
 #include <mutex>
 
 #include "common.cuh"
@@ -34,12 +37,6 @@ constexpr int kWarps = kThreads / 32;
 struct DirectIn {
     const uint32_t* p;
     __device__ uint32_t operator()(int i) const { return p[i]; }
-};
-
-struct GatherTiles {          // tiles_touched of the Gaussian at depth-sorted position i
-    const uint64_t* e;
-    const int* tiles;
-    __device__ uint32_t operator()(int i) const { return (uint32_t)tiles[(uint32_t)e[i]]; }
 };
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total)
@@ -289,62 +286,194 @@ __global__ void depth_elems_kernel(int n, const float* __restrict__ depth, const
     e[i] = ((uint64_t)hi << 32) | (uint32_t)i;
 }
 
-__global__ void emit_kernel(int n, const uint64_t* __restrict__ dsorted, const int* __restrict__ tiles,
-                            const ushort4* __restrict__ rect, const uint32_t* __restrict__ offsets, int TX,
-                            uint64_t* __restrict__ inst)
+// Rectangles in depth order (zero for culled Gaussians), so the kernels below
+// stage them with coalesced loads.
+__global__ void gather_rect_kernel(int n, const uint64_t* __restrict__ dsorted, const int* __restrict__ tiles,
+                                   const ushort4* __restrict__ rect, ushort4* __restrict__ drect)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint32_t gid = (uint32_t)dsorted[j];
-    if (tiles[gid] <= 0) return;
-    const ushort4 r = rect[gid];
-    uint32_t o = offsets[j];
-    for (int ty = r.y; ty < r.w; ++ty)
-        for (int tx = r.x; tx < r.z; ++tx) inst[o++] = ((uint64_t)(uint32_t)(ty * TX + tx) << 32) | gid;
+    drect[j] = tiles[gid] > 0 ? rect[gid] : make_ushort4(0, 0, 0, 0);
 }
 
-__global__ void finalize_kernel(int K, const uint64_t* __restrict__ inst, const float* __restrict__ depth,
-                                uint32_t* __restrict__ ids, uint64_t* __restrict__ keys, uint32_t* __restrict__ ranges)
+// Copies of chunk c (depth-sorted Gaussians [c*chunk, (c+1)*chunk)) per tile,
+// via a 2-D difference array in shared memory: +1 / -1 at the four corners of
+// every rectangle, then prefix sums along x and y.  Written tile-major:
+// counts[t * nchunks + c].
+__global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* __restrict__ drect, int TX, int TY,
+                                                          int chunk, int nchunks, uint32_t* __restrict__ counts)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    const uint64_t e = inst[k];
-    const uint32_t t = (uint32_t)(e >> 32), gid = (uint32_t)e;
-    ids[k] = gid;
-    if (keys) keys[k] = ((uint64_t)t << 32) | __float_as_uint(depth[gid]);
-    if (k == 0 || (uint32_t)(inst[k - 1] >> 32) != t) ranges[2 * t] = (uint32_t)k;
-    if (k == K - 1 || (uint32_t)(inst[k + 1] >> 32) != t) ranges[2 * t + 1] = (uint32_t)(k + 1);
+    extern __shared__ int diff[];
+    const int W1 = TX + 1, cells = W1 * (TY + 1);
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) diff[i] = 0;
+    __syncthreads();
+    const int j0 = blockIdx.x * chunk, j1 = min(n, j0 + chunk);
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        const ushort4 r = drect[j];
+        if (r.z <= r.x) continue;
+        atomicAdd(&diff[r.y * W1 + r.x], 1);
+        atomicAdd(&diff[r.y * W1 + r.z], -1);
+        atomicAdd(&diff[r.w * W1 + r.x], -1);
+        atomicAdd(&diff[r.w * W1 + r.z], 1);
+    }
+    __syncthreads();
+    for (int y = threadIdx.x; y < TY; y += blockDim.x) {
+        int run = 0;
+        for (int x = 0; x < TX; ++x) {
+            run += diff[y * W1 + x];
+            diff[y * W1 + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < TX; x += blockDim.x) {
+        int run = 0;
+        for (int y = 0; y < TY; ++y) {
+            run += diff[y * W1 + x];
+            diff[y * W1 + x] = run;
+        }
+    }
+    __syncthreads();
+    const int T = TX * TY;
+    for (int t = threadIdx.x; t < T; t += blockDim.x)
+        counts[(size_t)t * nchunks + blockIdx.x] = (uint32_t)diff[(t / TX) * W1 + (t % TX)];
+}
+
+// Placement.  Block (g, C): tile rows [8g, 8g + 8), one per warp, and the
+// Gaussians of super-chunk C (count chunks [C*cs, (C+1)*cs)).  The cursor of
+// tile (row, tx) starts at base[t * nchunks + C*cs] -- the exclusive scan of the
+// counts in tile-major order -- and lives in a register of lane tx % 32 of the
+// row's warp, so no two threads share a cursor and no barrier is needed between
+// Gaussians.  A warp takes the super-chunk's Gaussians 32 at a time, keeps (by
+// ballot) those whose rectangle covers its row and, for each in depth order,
+// every lane whose tiles fall in the rectangle writes them.  Only one cursor per
+// (tile, block) advances at a time, so the partly written output sectors stay
+// few enough to remain in L2.
+constexpr int kPlaceThreads = 256;
+constexpr int kPlaceRows = kPlaceThreads / 32;
+
+template <int NK>
+__global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint64_t* __restrict__ dsorted,
+                                                              const ushort4* __restrict__ drect,
+                                                              const float* __restrict__ depth, int TX, int TY,
+                                                              int super_chunk, int cstride, int nchunks,
+                                                              const uint32_t* __restrict__ base,
+                                                              uint32_t* __restrict__ ids, uint64_t* __restrict__ keys)
+{
+    __shared__ uint32_t sg[kPlaceThreads];
+    __shared__ ushort4 sr[kPlaceThreads];
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * kPlaceRows + (threadIdx.x >> 5);
+    const bool row_ok = row < TY;
+    const int C = blockIdx.y;
+    uint32_t ctr[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        const int tx = lane + 32 * k;
+        ctr[k] = (row_ok && tx < TX) ? base[(size_t)(row * TX + tx) * nchunks + (size_t)C * cstride] : 0u;
+    }
+    const int j0 = C * super_chunk, j1 = min(n, j0 + super_chunk);
+    for (int jb = j0; jb < j1; jb += kPlaceThreads) {
+        __syncthreads();
+        const int j = jb + threadIdx.x;
+        if (j < j1) {
+            sg[threadIdx.x] = (uint32_t)dsorted[j];
+            sr[threadIdx.x] = drect[j];
+        }
+        __syncthreads();
+        if (!row_ok) continue;
+        const int m = min(kPlaceThreads, j1 - jb);
+        for (int q0 = 0; q0 < m; q0 += 32) {
+            bool mine = false;
+            if (q0 + lane < m) {
+                const ushort4 r = sr[q0 + lane];
+                mine = r.z > r.x && r.y <= row && row < r.w;
+            }
+            uint32_t mask = __ballot_sync(0xffffffffu, mine);
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const ushort4 r = sr[q0 + b];
+                const uint32_t gid = sg[q0 + b];
+                const uint32_t dbits = keys ? __float_as_uint(depth[gid]) : 0u;
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    const int tx = lane + 32 * k;
+                    if (tx >= r.x && tx < r.z) {
+                        const uint32_t pos = ctr[k];
+                        ids[pos] = gid;
+                        if (keys) keys[pos] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | dbits;
+                        ctr[k] = pos + 1;
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void ranges_kernel(int T, int nchunks, const uint32_t* __restrict__ base, uint32_t* __restrict__ ranges)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint32_t s = base[(size_t)t * nchunks], e = base[(size_t)(t + 1) * nchunks];
+    ranges[2 * t] = s == e ? 0u : s;
+    ranges[2 * t + 1] = s == e ? 0u : e;
 }
 
 // ----------------------------------------------------------------------------
+constexpr int kMaxTiles = 16384;
+
 struct SortWs {
-    uint64_t *eA, *eB, *iA, *iB;
-    uint32_t *offsets, *counts, *partials, *misc;
+    uint64_t *eA, *eB;
+    ushort4* drect;
+    uint32_t *counts, *base, *partials, *misc;
+    int nchunks, chunk;
     size_t bytes;
 };
 
 inline int nblocks(int64_t n) { return (int)((n + kTile - 1) / kTile); }
 
-SortWs sort_ws_layout(char* base, int32_t n, int64_t k_cap)
+__host__ __device__ constexpr int chunks_for(int n)
+{
+    return n <= 0 ? 1 : ((n + 511) / 512 < 1024 ? (n + 511) / 512 : 1024);
+}
+
+__host__ __device__ constexpr size_t seg(size_t bytes) { return (bytes + 255) / 256 * 256; }
+
+// Scratch layout of le_bin_sort for n Gaussians (independent of the copy count).
+__host__ __device__ constexpr size_t sort_ws_bytes(int n)
+{
+    return seg(8ull * n) * 3 + seg(4ull * (256ull * ((n + kTile - 1) / kTile) + 1)) +
+           seg(4ull * ((size_t)kMaxTiles * chunks_for(n) + 1)) +
+           seg(4ull * (((size_t)kMaxTiles * chunks_for(n) + 1 > 256ull * ((n + kTile - 1) / kTile) + 1
+                            ? (size_t)kMaxTiles * chunks_for(n) + 1
+                            : 256ull * ((n + kTile - 1) / kTile) + 1) /
+                           kTile +
+                       2)) +
+           seg(4ull * 64);
+}
+
+SortWs sort_ws_layout(char* base, int32_t n)
 {
     SortWs w;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char* p = base ? base + off : nullptr;
-        off = align_up(off + bytes, 256);
+        off += seg(bytes);
         return p;
     };
-    const int nb = nblocks(n > k_cap ? (int64_t)n : k_cap);
-    const size_t count_len = (size_t)256 * nb + 1;
-    const size_t scan_max = count_len > (size_t)n + 1 ? count_len : (size_t)n + 1;
-    w.eA = (uint64_t*)take(sizeof(uint64_t) * (size_t)n);
-    w.eB = (uint64_t*)take(sizeof(uint64_t) * (size_t)n);
-    w.iA = (uint64_t*)take(sizeof(uint64_t) * (size_t)k_cap);
-    w.iB = (uint64_t*)take(sizeof(uint64_t) * (size_t)k_cap);
-    w.offsets = (uint32_t*)take(sizeof(uint32_t) * ((size_t)n + 1));
-    w.counts = (uint32_t*)take(sizeof(uint32_t) * count_len);
-    w.partials = (uint32_t*)take(sizeof(uint32_t) * (scan_max / kTile + 2));
-    w.misc = (uint32_t*)take(sizeof(uint32_t) * 64);
+    w.nchunks = chunks_for(n);
+    w.chunk = n > 0 ? (n + w.nchunks - 1) / w.nchunks : 1;
+    const size_t radix_len = 256ull * nblocks(n) + 1;
+    const size_t count_len = (size_t)kMaxTiles * w.nchunks + 1;
+    const size_t scan_max = count_len > radix_len ? count_len : radix_len;
+    w.eA = (uint64_t*)take(8ull * n);
+    w.eB = (uint64_t*)take(8ull * n);
+    w.drect = (ushort4*)take(8ull * n);
+    w.counts = (uint32_t*)take(4ull * radix_len);
+    w.base = (uint32_t*)take(4ull * count_len);
+    w.partials = (uint32_t*)take(4ull * (scan_max / kTile + 2));
+    w.misc = (uint32_t*)take(4ull * 64);
     w.bytes = off;
     return w;
 }
@@ -380,7 +509,7 @@ extern "C" le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* byt
 {
     LE_CHECK_ARG(bytes != nullptr, "bytes is null");
     LE_CHECK_ARG(n >= 0 && k_cap >= 0 && k_cap < (int64_t)1 << 31, "n or k_cap out of range");
-    *bytes = sort_ws_layout(nullptr, n, k_cap).bytes;
+    *bytes = sort_ws_layout(nullptr, n).bytes;
     return LE_OK;
 }
 
@@ -398,44 +527,69 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     LE_CHECK_ARG(workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u) == 0,
                  "workspace must be non-null and 256-byte aligned");
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(rect) & 7u) == 0, "rect must be 8-byte aligned");
-    const SortWs w = sort_ws_layout(static_cast<char*>(workspace), n, k_cap);
+    const SortWs w = sort_ws_layout(static_cast<char*>(workspace), n);
     LE_CHECK_ARG(workspace_bytes >= w.bytes, "workspace too small: %zu < %zu", workspace_bytes, w.bytes);
     cudaStream_t s = as_stream(stream);
     const int TX = tiles_x(cam), TY = tiles_y(cam);
     const int ntiles = TX * TY;
+    if (ntiles > kMaxTiles || TX > 256) {
+        set_error("%d x %d screen tiles exceed the supported %d tiles / 256 columns", TX, TY, kMaxTiles);
+        return LE_ERR_UNSUPPORTED;
+    }
     LE_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ntiles, s));
     *k_out = 0;
     if (n == 0) return LE_OK;
 
-    // 1-2: sort Gaussians by depth (visible first)
+    // 1-2: sort the Gaussians by depth (stable: equal depths keep index order; culled last)
     depth_elems_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, depth, tiles_touched, w.eA);
     LE_LAUNCHED();
     uint64_t *cur = w.eA, *alt = w.eB;
     if ((st = radix_sort(cur, alt, n, 32, 32, w, s)) != LE_OK) return st;
-    // 3: instance offsets in depth order, K
-    if ((st = exclusive_scan(GatherTiles{cur, tiles_touched}, n, w.offsets, w.partials, w.misc, s)) != LE_OK)
-        return st;
+    // 3: rectangles in depth order; copies per (tile, chunk of depth-sorted Gaussians)
+    gather_rect_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cur, tiles_touched, reinterpret_cast<const ushort4*>(rect),
+                                                       w.drect);
+    LE_LAUNCHED();
+    const size_t diff_smem = sizeof(int) * (TX + 1) * (TY + 1);
+    if (diff_smem > 48 * 1024)
+        LE_CUDA(cudaFuncSetAttribute(chunk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diff_smem));
+    chunk_count_kernel<<<w.nchunks, 256, diff_smem, s>>>(n, w.drect, TX, TY, w.chunk, w.nchunks, w.base);
+    LE_LAUNCHED();
+    // 4: one exclusive scan in tile-major order gives every (tile, chunk) base and K
+    const int len = ntiles * w.nchunks;
+    if ((st = exclusive_scan(DirectIn{w.base}, len, w.base, w.partials, w.base + len, s)) != LE_OK) return st;
     uint32_t K32 = 0;
-    LE_CUDA(cudaMemcpyAsync(&K32, w.misc, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LE_CUDA(cudaMemcpyAsync(&K32, w.base + len, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     LE_CUDA(cudaStreamSynchronize(s));
     *k_out = K32;
     if ((int64_t)K32 > k_cap) {
         set_error("instance count K = %u exceeds k_cap = %lld", K32, (long long)k_cap);
         return LE_ERR_CAPACITY;
     }
-    const int K = (int)K32;
-    if (K == 0) return LE_OK;
-    // 4: emit copies in depth order
-    emit_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cur, tiles_touched, reinterpret_cast<const ushort4*>(rect),
-                                               w.offsets, TX, w.iA);
+    if (K32 == 0) return LE_OK;
+    ranges_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(ntiles, w.nchunks, w.base, tile_ranges);
     LE_LAUNCHED();
-    // 5: stable sort of the copies by tile id
-    int tile_bits = 1;
-    while ((1 << tile_bits) < ntiles) ++tile_bits;
-    uint64_t *icur = w.iA, *ialt = w.iB;
-    if ((st = radix_sort(icur, ialt, K, 32, tile_bits, w, s)) != LE_OK) return st;
-    // 6: ids, keys, ranges
-    finalize_kernel<<<(K + 255) / 256, 256, 0, s>>>(K, icur, depth, sorted_ids, sorted_keys, tile_ranges);
+    // 5: place every copy; super-chunks of `cs` count chunks, small enough for about
+    //    eight waves of blocks (row groups differ a lot in work; many short blocks balance them)
+    const int ngroups = (TY + kPlaceRows - 1) / kPlaceRows;
+    const int want = (8 * 1216 + ngroups - 1) / ngroups;
+    const int cs = w.nchunks / want > 1 ? w.nchunks / want : 1;
+    const int nsuper = (w.nchunks + cs - 1) / cs;
+    const dim3 grid(ngroups, nsuper);
+    const int nk = (TX + 31) / 32;
+#define LE_PLACE(NK)                                                                                             \
+    place_kernel<NK><<<grid, kPlaceThreads, 0, s>>>(n, cur, w.drect, depth, TX, TY, w.chunk * cs, cs, w.nchunks, \
+                                                    w.base, sorted_ids, sorted_keys)
+    switch (nk) {
+        case 1: LE_PLACE(1); break;
+        case 2: LE_PLACE(2); break;
+        case 3: LE_PLACE(3); break;
+        case 4: LE_PLACE(4); break;
+        case 5: LE_PLACE(5); break;
+        case 6: LE_PLACE(6); break;
+        case 7: LE_PLACE(7); break;
+        default: LE_PLACE(8); break;
+    }
+#undef LE_PLACE
     LE_LAUNCHED();
     return LE_OK;
 }
@@ -443,28 +597,15 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
 // ----------------------------------------------------------------------------
 // le_bin_sort_static: le_bin_sort for callers that cannot allocate device
 // memory.  Its scratch is the file-scope array below, sized for at most
-// LE_STATIC_MAX_GAUSSIANS Gaussians and LE_STATIC_MAX_INSTANCES tile copies;
-// every GPU that loads this library holds it until the process exits.
+// LE_STATIC_MAX_GAUSSIANS Gaussians; every GPU that loads this library holds
+// it until the process exits.
 namespace leg {
 namespace {
 
 constexpr int32_t kStaticMaxN = LE_STATIC_MAX_GAUSSIANS;
 constexpr int64_t kStaticMaxK = LE_STATIC_MAX_INSTANCES;
 
-// Scratch bytes le_bin_sort needs at the limits (the same layout it uses for a
-// caller workspace), rounded up to 256 bytes.
-constexpr size_t static_bytes()
-{
-    // eA, eB: 8 B per Gaussian each; iA, iB: 8 B per copy each; offsets: 4 B per
-    // Gaussian + 1; digit counts: 256 per 4096-element block + 1; scan partials;
-    // 64 words of counters.  Each segment is rounded up to 256 bytes.
-    return (8 * (size_t)kStaticMaxN + 255) / 256 * 256 * 2 + (8 * (size_t)kStaticMaxK + 255) / 256 * 256 * 2 +
-           (4 * ((size_t)kStaticMaxN + 1) + 255) / 256 * 256 +
-           (4 * (256 * (size_t)(kStaticMaxK / 4096) + 1) + 255) / 256 * 256 +
-           (4 * ((256 * (size_t)(kStaticMaxK / 4096) + 1) / 4096 + 2) + 255) / 256 * 256 + 256;
-}
-
-__device__ __align__(256) unsigned char g_static_scratch[static_bytes()];
+__device__ __align__(256) unsigned char g_static_scratch[sort_ws_bytes(kStaticMaxN)];
 
 // Device address of g_static_scratch per device, looked up on the first call
 // made with that device current.
@@ -505,7 +646,7 @@ extern "C" le_status le_bin_sort_static(const le_camera* cam, int32_t n, const f
     le_status st = le_bin_sort_workspace(n, k_cap, &need);
     if (st != LE_OK) return st;
     if (need > sizeof(g_static_scratch)) {
-        set_error("static scratch too small for n = %d, k_cap = %lld", n, (long long)k_cap);
+        set_error("static scratch too small for n = %d", n);
         return LE_ERR_INVALID_ARG;
     }
     void* ws = nullptr;

@@ -57,7 +57,9 @@ struct DecArgs {
     float* rel;
 };
 
-// Per-warpgroup state of the shared MLP front end.
+// Per-warpgroup state of the shared MLP front end.  With nhalf = 2 two
+// warpgroups serve the same 128 TMEM lanes (rows) and split every epilogue
+// by columns; `xch` is their shared-memory exchange for row-wide statistics.
 struct Front {
     SBuf W1s, W2s, W3s, X1, H1, H2;
     const float *b1s, *b2s, *b3s;
@@ -65,8 +67,19 @@ struct Front {
     uint32_t phase;
     uint32_t tw;       // TMEM column base of this warpgroup's working accumulator
     uint32_t lane;     // this warp's TMEM lane field
-    int tid, bar_id, nthreads;
+    int tid;           // row of the tile (TMEM lane) this thread serves
+    int bar_id, nthreads;
+    int half, nhalf;
+    float4* xch;       // [2][128] (nhalf = 2 only)
 };
+
+// Columns [c0, c1) of an N-column epilogue handled by this thread's half (units of 16).
+__device__ __forceinline__ void my_cols(const Front& f, int N, int& c0, int& c1)
+{
+    const int nch = N / 16, per = (nch + f.nhalf - 1) / f.nhalf;
+    c0 = min(nch, f.half * per) * 16;
+    c1 = min(nch, (f.half + 1) * per) * 16;
+}
 
 __device__ __forceinline__ void wg_sync(const Front& f)
 {
@@ -101,20 +114,25 @@ __device__ __forceinline__ void wg_publish(const Front& f)
 __device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
 {
     float v[16];
+    if (f.half == 0) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = valid ? a.feat[(size_t)c * a.P + p] : 0.f;
+        for (int c = 0; c < 8; ++c) v[c] = valid ? a.feat[(size_t)c * a.P + p] : 0.f;
+        sbuf_store8(f.X1, f.tid, 0, v);
+    }
+    if (f.half == f.nhalf - 1) {
 #pragma unroll
-    for (int c = 8; c < 16; ++c) v[c] = c == 8 ? 1.f : 0.f;
-    sbuf_store8(f.X1, f.tid, 0, v);
-    sbuf_store8(f.X1, f.tid, 8, v + 8);
+        for (int c = 0; c < 8; ++c) v[c] = c == 0 ? 1.f : 0.f;
+        sbuf_store8(f.X1, f.tid, 8, v);
+    }
     wg_publish(f);
-    if (f.tid == 0) {
+    if (f.tid == 0 && f.half == 0) {
         mma(f.tw, kdesc(f.X1, 0, 0), kdesc(f.W1s, 0, 0), idesc_bf16(kH1, false, false), 0);
         commit(f.mbar);
     }
     if (!wg_wait(f)) return false;
-#pragma unroll
-    for (int c = 0; c < kH1; c += 16) {
+    int c0, c1;
+    my_cols(f, kH1, c0, c1);
+    for (int c = c0; c < c1; c += 16) {
         tmem_ld16(f.tw + f.lane + c, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + f.b1s[c + j], 0.f);
@@ -122,15 +140,15 @@ __device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
         sbuf_store8(f.H1, f.tid, c + 8, v + 8);
     }
     wg_publish(f);
-    if (f.tid == 0) {
+    if (f.tid == 0 && f.half == 0) {
 #pragma unroll
         for (int s = 0; s < kH1 / 16; ++s)
             mma(f.tw, kdesc(f.H1, 0, 16 * s), kdesc(f.W2s, 0, 16 * s), idesc_bf16(kH2, false, false), s > 0);
         commit(f.mbar);
     }
     if (!wg_wait(f)) return false;
-#pragma unroll
-    for (int c = 0; c < kH2; c += 16) {
+    my_cols(f, kH2, c0, c1);
+    for (int c = c0; c < c1; c += 16) {
         tmem_ld16(f.tw + f.lane + c, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + f.b2s[c + j], 0.f);
@@ -138,7 +156,7 @@ __device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
         sbuf_store8(f.H2, f.tid, c + 8, v + 8);
     }
     wg_publish(f);
-    if (f.tid == 0) {
+    if (f.tid == 0 && f.half == 0) {
 #pragma unroll
         for (int s = 0; s < kH2 / 16; ++s)
             mma(f.tw, kdesc(f.H2, 0, 16 * s), kdesc(f.W3s, 0, 16 * s), idesc_bf16(a.ncb, false, false), s > 0);
@@ -147,13 +165,17 @@ __device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
     return wg_wait(f);
 }
 
-// Online max / argmax / log-sum-exp over the ncb logits in TMEM (+ b3).
+// Online max / argmax / log-sum-exp over the ncb logits in TMEM (+ b3); with
+// two halves, each covers its columns and the pair combine through f.xch.
+// Ties go to the lowest index.  zt = logit of class t (if t >= 0).
 __device__ __forceinline__ void logits_lse(const Front& f, int ncb, float& lse, int& am, int t, float& zt)
 {
     float m = -INFINITY, s = 0.f, v[16];
     am = 0;
     zt = 0.f;
-    for (int c = 0; c < ncb; c += 16) {
+    int c0, c1;
+    my_cols(f, ncb, c0, c1);
+    for (int c = c0; c < c1; c += 16) {
         tmem_ld16(f.tw + f.lane + c, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -167,6 +189,20 @@ __device__ __forceinline__ void logits_lse(const Front& f, int ncb, float& lse, 
                 s += __expf(z - m);
             }
         }
+    }
+    if (f.nhalf == 2) {
+        f.xch[f.half * 128 + f.tid] = make_float4(m, s, __int_as_float(am), zt);
+        wg_sync(f);
+        const float4 o = f.xch[(1 - f.half) * 128 + f.tid];
+        wg_sync(f);
+        const float m0 = f.half == 0 ? m : o.x, s0 = f.half == 0 ? s : o.y;
+        const float m1 = f.half == 0 ? o.x : m, s1 = f.half == 0 ? o.y : s;
+        const int a0 = f.half == 0 ? am : __float_as_int(o.z), a1 = f.half == 0 ? __float_as_int(o.z) : am;
+        const bool t_mine = t >= c0 && t < c1;
+        zt = t_mine ? zt : o.w;
+        m = fmaxf(m0, m1);
+        s = (m0 == -INFINITY ? 0.f : s0 * __expf(m0 - m)) + (m1 == -INFINITY ? 0.f : s1 * __expf(m1 - m));
+        am = m1 > m0 ? a1 : a0;
     }
     lse = m + __logf(s);
 }
@@ -225,6 +261,9 @@ __global__ void __launch_bounds__(128 * NWG, 1) dec_fwd_kernel(DecArgs a)
     f.tid = threadIdx.x & 127;
     f.bar_id = 1 + wg;
     f.nthreads = NWG == 1 ? (int)blockDim.x : 128;
+    f.half = 0;
+    f.nhalf = 1;
+    f.xch = nullptr;
     if (threadIdx.x == 0)
         for (int w = 0; w < NWG; ++w) mbar_init(mbars + w, 1);
     if (threadIdx.x < 32) tmem_alloc(slot, 256 * NWG);
@@ -263,18 +302,19 @@ __global__ void __launch_bounds__(128 * NWG, 1) dec_fwd_kernel(DecArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Training.  One warpgroup per CTA (TMEM: working 128 columns + the three
-// weight-gradient accumulators), persistent over tiles.
+// Training.  One CTA per SM, persistent over tiles; 256 threads: the two
+// warpgroups serve the same 128 rows (TMEM lanes) and split each epilogue by
+// columns.  TMEM: working 128 columns + the three weight-gradient accumulators.
 constexpr uint32_t kAcc3 = 128, kAcc2 = 288, kAcc1 = 384;   // TMEM columns (32-aligned)
 constexpr int kC1 = 16, kCH1 = 80, kCH2 = 144, kCD = 128;   // buffer widths (with ones columns)
 
 __host__ constexpr size_t train_smem(int ncb)
 {
     return weights_bytes(ncb) + sbuf_bytes(128, kC1) + sbuf_bytes(128, kCH1) + sbuf_bytes(128, kCH2) +
-           3 * sbuf_bytes(128, kCD) + 128;
+           3 * sbuf_bytes(128, kCD) + 2 * 128 * 16 + 128;
 }
 
-__global__ void __launch_bounds__(128, 1) dec_train_kernel(DecArgs a)
+__global__ void __launch_bounds__(256, 1) dec_train_kernel(DecArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     Front f;
@@ -287,39 +327,48 @@ __global__ void __launch_bounds__(128, 1) dec_train_kernel(DecArgs a)
     p += sbuf_bytes(128, kCH2);
     const SBuf DZ{p, kCD}, DH2{p + sbuf_bytes(128, kCD), kCD}, DH1{p + 2 * sbuf_bytes(128, kCD), kCD};
     p += 3 * sbuf_bytes(128, kCD);
+    f.xch = reinterpret_cast<float4*>(p);
+    p += 2 * 128 * 16;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(p);
     uint32_t* slot = reinterpret_cast<uint32_t*>(p + 8);
     f.mbar = mbar;
     f.phase = 0;
-    f.tid = threadIdx.x;
+    f.tid = threadIdx.x & 127;
+    f.half = threadIdx.x >> 7;
+    f.nhalf = 2;
     f.bar_id = 0;
     f.nthreads = blockDim.x;
-    const int tid = threadIdx.x;
-    // constant columns of this thread's rows: ones for the bias gradients, zero padding
+    const int row = f.tid;
+    const bool leader = threadIdx.x == 0;
+    // constant columns of this row: ones for the bias gradients, zero padding
     {
-        float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        sbuf_store8(f.H1, tid, 64, one);
-        sbuf_store8(f.H1, tid, 72, zero);
-        sbuf_store8(f.H2, tid, 128, one);
-        sbuf_store8(f.H2, tid, 136, zero);
-        for (int c = a.ncb; c < kCD; c += 8) sbuf_store8(DZ, tid, c, zero);
-        for (int c = 64; c < kCD; c += 8) sbuf_store8(DH1, tid, c, zero);
+        const float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (f.half == 0) {
+            sbuf_store8(f.H1, row, 64, one);
+            sbuf_store8(f.H1, row, 72, zero);
+            sbuf_store8(f.H2, row, 128, one);
+            sbuf_store8(f.H2, row, 136, zero);
+        } else {
+            for (int c = a.ncb; c < kCD; c += 8) sbuf_store8(DZ, row, c, zero);
+            for (int c = 64; c < kCD; c += 8) sbuf_store8(DH1, row, c, zero);
+        }
     }
-    if (tid == 0) mbar_init(mbar, 1);
-    if (tid < 32) tmem_alloc(slot, 512);
+    if (leader) mbar_init(mbar, 1);
+    if (threadIdx.x < 32) tmem_alloc(slot, 512);
     fence_proxy_async();
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(slot);
     f.tw = tbase;
-    f.lane = (uint32_t)(32 * (tid >> 5)) << 16;
+    f.lane = (uint32_t)(32 * (row >> 5)) << 16;
 
     const int ntiles = (a.P + 127) / 128;
     float acc_ce = 0.f, acc_u = 0.f;
     bool any = false;
+    int c0, c1;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int px = tile * 128 + tid;
+        const int px = tile * 128 + row;
         const bool valid = px < a.P;
         if (!mlp_forward(f, a, px, valid)) { any = false; break; }
         // softmax cross-entropy with uncertainty weighting (Eqs. 9-12)
@@ -331,22 +380,23 @@ __global__ void __launch_bounds__(128, 1) dec_train_kernel(DecArgs a)
         const float ce = lse - zt;
         // dL/dz * P (1/P applied when the gradients are written)
         const float w = valid ? a.lambda_ce * (1.f - u) : 0.f;
-        if (valid) {
+        if (valid && f.half == 0) {
             a.d_unc[px] = (a.lambda_u - a.lambda_ce * ce) * a.invP;
             acc_ce += ce * (1.f - u);
             acc_u += u;
         }
         float v[16], h[16];
-        for (int c = 0; c < a.ncb; c += 16) {
+        my_cols(f, a.ncb, c0, c1);
+        for (int c = c0; c < c1; c += 16) {
             tmem_ld16(f.tw + f.lane + c, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = w * (__expf(v[j] + f.b3s[c + j] - lse) - (c + j == t ? 1.f : 0.f));
-            sbuf_store8(DZ, tid, c, v);
-            sbuf_store8(DZ, tid, c + 8, v + 8);
+            sbuf_store8(DZ, row, c, v);
+            sbuf_store8(DZ, row, c + 8, v + 8);
         }
         wg_publish(f);
         const uint32_t acc = any ? 1u : 0u;
-        if (tid == 0) {
+        if (leader) {
             // dh2 = dz W3   (A = DZ K-major, B = W3 read MN-major)
             for (int s = 0; s < a.ncb / 16; ++s)
                 mma(f.tw, kdesc(DZ, 0, 16 * s), mndesc(f.W3s, 16 * s, 0), idesc_bf16(kH2, false, true), s > 0);
@@ -359,18 +409,18 @@ __global__ void __launch_bounds__(128, 1) dec_train_kernel(DecArgs a)
         }
         if (!wg_wait(f)) { any = false; break; }
         // dh2 * [h2 > 0]
-#pragma unroll
-        for (int c = 0; c < kH2; c += 16) {
+        my_cols(f, kH2, c0, c1);
+        for (int c = c0; c < c1; c += 16) {
             tmem_ld16(f.tw + f.lane + c, v);
-            sbuf_load8(f.H2, tid, c, h);
-            sbuf_load8(f.H2, tid, c + 8, h + 8);
+            sbuf_load8(f.H2, row, c, h);
+            sbuf_load8(f.H2, row, c + 8, h + 8);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
-            sbuf_store8(DH2, tid, c, v);
-            sbuf_store8(DH2, tid, c + 8, v + 8);
+            sbuf_store8(DH2, row, c, v);
+            sbuf_store8(DH2, row, c + 8, v + 8);
         }
         wg_publish(f);
-        if (tid == 0) {
+        if (leader) {
 #pragma unroll
             for (int s = 0; s < kH2 / 16; ++s)
                 mma(f.tw, kdesc(DH2, 0, 16 * s), mndesc(f.W2s, 16 * s, 0), idesc_bf16(kH1, false, true), s > 0);
@@ -382,18 +432,18 @@ __global__ void __launch_bounds__(128, 1) dec_train_kernel(DecArgs a)
         }
         if (!wg_wait(f)) { any = false; break; }
         // dh1 * [h1 > 0]
-#pragma unroll
-        for (int c = 0; c < kH1; c += 16) {
+        my_cols(f, kH1, c0, c1);
+        for (int c = c0; c < c1; c += 16) {
             tmem_ld16(f.tw + f.lane + c, v);
-            sbuf_load8(f.H1, tid, c, h);
-            sbuf_load8(f.H1, tid, c + 8, h + 8);
+            sbuf_load8(f.H1, row, c, h);
+            sbuf_load8(f.H1, row, c + 8, h + 8);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
-            sbuf_store8(DH1, tid, c, v);
-            sbuf_store8(DH1, tid, c + 8, v + 8);
+            sbuf_store8(DH1, row, c, v);
+            sbuf_store8(DH1, row, c + 8, v + 8);
         }
         wg_publish(f);
-        if (tid == 0) {
+        if (leader) {
 #pragma unroll
             for (int s = 0; s < kH1 / 16; ++s)
                 mma(f.tw, kdesc(DH1, 0, 16 * s), mndesc(f.W1s, 16 * s, 0), idesc_bf16(16, false, true), s > 0);
@@ -405,37 +455,43 @@ __global__ void __launch_bounds__(128, 1) dec_train_kernel(DecArgs a)
         }
         if (!wg_wait(f)) { any = false; break; }
         any = true;
-        tmem_ld16(f.tw + f.lane, v);
-        if (valid)
+        if (f.half == 0) {
+            tmem_ld16(f.tw + f.lane, v);
+            if (valid)
 #pragma unroll
-            for (int c = 0; c < kD; ++c) a.d_feat[(size_t)c * a.P + px] = v[c] * a.invP;
+                for (int c = 0; c < kD; ++c) a.d_feat[(size_t)c * a.P + px] = v[c] * a.invP;
+        }
         fence_before();
-        wg_sync(f);
+        __syncthreads();
     }
-    // flush the weight-gradient accumulators (row = this thread's TMEM lane)
+    // flush the weight-gradient accumulators (row = this thread's TMEM lane, columns split by half)
     if (any) {
         float v[16];
-        for (int c = 0; c < kCH2; c += 16) {
+        my_cols(f, kCH2, c0, c1);
+        for (int c = c0; c < c1; c += 16) {
             tmem_ld16(tbase + kAcc3 + f.lane + c, v);
-            if (tid < a.ncb)
+            if (row < a.ncb)
                 for (int j = 0; j < 16; ++j) {
                     const int col = c + j;
-                    if (col < kH2) atomicAdd(a.dW3 + (size_t)tid * kH2 + col, v[j] * a.invP);
-                    else if (col == kH2) atomicAdd(a.db3 + tid, v[j] * a.invP);
+                    if (col < kH2) atomicAdd(a.dW3 + (size_t)row * kH2 + col, v[j] * a.invP);
+                    else if (col == kH2) atomicAdd(a.db3 + row, v[j] * a.invP);
                 }
         }
-        for (int c = 0; c < kCH1; c += 16) {
+        my_cols(f, kCH1, c0, c1);
+        for (int c = c0; c < c1; c += 16) {
             tmem_ld16(tbase + kAcc2 + f.lane + c, v);
             for (int j = 0; j < 16; ++j) {
                 const int col = c + j;
-                if (col < kH1) atomicAdd(a.dW2 + (size_t)tid * kH1 + col, v[j] * a.invP);
-                else if (col == kH1) atomicAdd(a.db2 + tid, v[j] * a.invP);
+                if (col < kH1) atomicAdd(a.dW2 + (size_t)row * kH1 + col, v[j] * a.invP);
+                else if (col == kH1) atomicAdd(a.db2 + row, v[j] * a.invP);
             }
         }
-        tmem_ld16(tbase + kAcc1 + f.lane, v);
-        if (tid < kH1) {
-            for (int j = 0; j < kD; ++j) atomicAdd(a.dW1 + (size_t)tid * kD + j, v[j] * a.invP);
-            atomicAdd(a.db1 + tid, v[kD] * a.invP);
+        if (f.half == 0) {
+            tmem_ld16(tbase + kAcc1 + f.lane, v);
+            if (row < kH1) {
+                for (int j = 0; j < kD; ++j) atomicAdd(a.dW1 + (size_t)row * kD + j, v[j] * a.invP);
+                atomicAdd(a.db1 + row, v[kD] * a.invP);
+            }
         }
     }
 #pragma unroll
@@ -443,14 +499,14 @@ __global__ void __launch_bounds__(128, 1) dec_train_kernel(DecArgs a)
         acc_ce += __shfl_xor_sync(0xffffffffu, acc_ce, o);
         acc_u += __shfl_xor_sync(0xffffffffu, acc_u, o);
     }
-    if ((tid & 31) == 0) {
+    if ((threadIdx.x & 31) == 0 && f.half == 0) {
         atomicAdd(a.loss, acc_ce * a.invP);
         atomicAdd(a.loss + 1, acc_u * a.invP);
     }
     fence_before();
     __syncthreads();
     fence_after();
-    if (tid < 32) tmem_dealloc(tbase, 512);
+    if (threadIdx.x < 32) tmem_dealloc(tbase, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -490,6 +546,9 @@ __global__ void __launch_bounds__(128, 1) query_fused_kernel(DecArgs a)
     f.tid = tid;
     f.bar_id = 0;
     f.nthreads = blockDim.x;
+    f.half = 0;
+    f.nhalf = 1;
+    f.xch = nullptr;
     if (tid == 0)
         for (int i = 0; i < 3; ++i) mbar_init(mbar + i, 1);
     if (tid < 32) tmem_alloc(slot, 512);
@@ -669,7 +728,7 @@ le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_
         le_status st = set_smem(dec_train_kernel, smem);
         if (st != LE_OK) return st;
         const int grid = ntiles < sm_count() ? ntiles : sm_count();
-        dec_train_kernel<<<grid, 128, smem, s>>>(a);
+        dec_train_kernel<<<grid, 256, smem, s>>>(a);
         LE_LAUNCHED();
         return LE_OK;
     }

@@ -10,8 +10,9 @@
 //
 // The backward walks the same range back to front from each pixel's last
 // contributor, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
-// transmittance, sums each Gaussian's 18 gradient terms over the warp with
-// shuffles and issues one vectorised atomic add per warp.
+// transmittance, sums each Gaussian's 18 gradient terms over the warp with a
+// recursive-halving shuffle reduction (20 shuffles instead of 18 x 5) after
+// which 18 lanes each issue one scalar atomic add into the gradient record.
 #include "common.cuh"
 
 namespace leg {
@@ -111,11 +112,47 @@ __global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const
     n_contrib[o] = last;
 }
 
-__device__ __forceinline__ float warp_sum(float v)
+// One stage of a recursive-halving ("transpose") reduction of N values held by
+// every lane: lanes with bit O set keep the upper half of the values, the
+// others the lower half, each adding its partner's copy of the half it keeps.
+template <int N, int O>
+__device__ __forceinline__ void halve(float* v, bool upper)
 {
+    constexpr int H = (N + 1) / 2;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < H; ++i) {
+        const float lo = v[i];
+        const float hi = (i + H < N) ? v[i + H] : 0.f;
+        const float recv = __shfl_xor_sync(0xffffffffu, upper ? lo : hi, O);
+        v[i] = (upper ? hi : lo) + recv;
+    }
+}
+
+// Warp-wide sums of 18 values in 9+5+3+2+1 = 20 shuffles; afterwards v[0] of
+// lane l is the sum of value field_of_lane(l) (or nothing, when that is -1).
+__device__ __forceinline__ void warp_sum18(float* v, int lane)
+{
+    halve<18, 16>(v, lane & 16);
+    halve<9, 8>(v, lane & 8);
+    halve<5, 4>(v, lane & 4);
+    halve<3, 2>(v, lane & 2);
+    halve<2, 1>(v, lane & 1);
+}
+
+__device__ __forceinline__ int field_of_lane(int lane)
+{
+    int valid = 18, base = 0;
+    const int H[5] = {9, 5, 3, 2, 1}, O[5] = {16, 8, 4, 2, 1};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        if (lane & O[s]) {
+            base += H[s];
+            valid = valid > H[s] ? valid - H[s] : 0;
+        } else {
+            valid = valid < H[s] ? valid : H[s];
+        }
+    }
+    return valid >= 1 ? base : -1;
 }
 
 __global__ void __launch_bounds__(kBlock) render_bwd_kernel(
@@ -152,9 +189,9 @@ __global__ void __launch_bounds__(kBlock) render_bwd_kernel(
     }
     const float Tf = T;
     const float bgdot = cam.bg[0] * dC[0] + cam.bg[1] * dC[1] + cam.bg[2] * dC[2];
-    float acc[12];
-#pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
+    // S = sum_c acc_c dL/dC_c, the "colour behind" seen through this pixel's
+    // upstream gradient; it obeys the blending recurrence of acc itself.
+    float S = 0.f;
 
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
@@ -163,6 +200,7 @@ __global__ void __launch_bounds__(kBlock) render_bwd_kernel(
     __syncthreads();
     const int nproc = s_max;
     const int lane = threadIdx.x & 31;
+    const int my_field = field_of_lane(lane);
 
     for (int b_end = nproc; b_end > 0; b_end -= kBlock) {
         const int b_start = max(0, b_end - kBlock);
@@ -176,7 +214,7 @@ __global__ void __launch_bounds__(kBlock) render_bwd_kernel(
             for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
         }
         __syncthreads();
-        for (int j = b_end - b_start - 1; j >= 0; --j) {
+        for (int j = min(b_end, wmax) - b_start - 1; j >= 0; --j) {
             const int pos = b_start + j;
             const float4 g0 = rec[0][j], g1 = rec[1][j];
             const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
@@ -190,18 +228,19 @@ __global__ void __launch_bounds__(kBlock) render_bwd_kernel(
 #pragma unroll
             for (int q = 0; q < 18; ++q) gr[q] = 0.f;
             if (contrib) {
-                T = T / (1.f - alpha);
+                const float inv1ma = __fdividef(1.f, 1.f - alpha);
+                T *= inv1ma;
                 const float w = alpha * T;
                 const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
                 const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
-                float dalpha = 0.f;
+                float fdc = 0.f;
 #pragma unroll
                 for (int c = 0; c < 12; ++c) {
                     gr[6 + c] = w * dC[c];                  // rgb (6..8), unc (9), feat (10..17)
-                    dalpha = fmaf((f[c] - acc[c]) * T, dC[c], dalpha);
-                    acc[c] = fmaf(alpha, f[c] - acc[c], acc[c]);
+                    fdc = fmaf(f[c], dC[c], fdc);
                 }
-                dalpha -= Tf / (1.f - alpha) * bgdot;
+                const float dalpha = T * (fdc - S) - Tf * inv1ma * bgdot;
+                S = fmaf(alpha, fdc - S, S);
                 if (a0 < 0.99f) {
                     const float dpow = dalpha * alpha;
                     gr[5] = dalpha * G;
@@ -212,16 +251,8 @@ __global__ void __launch_bounds__(kBlock) render_bwd_kernel(
                     gr[1] = dpow * (-g1.x * dy - g0.w * dx);
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 18; ++q) gr[q] = warp_sum(gr[q]);
-            if (lane == 0) {
-                float4* dst = grad2d + (size_t)sid[j] * 5;
-                atomicAdd(dst, make_float4(gr[0], gr[1], gr[2], gr[3]));
-                atomicAdd(dst + 1, make_float4(gr[4], gr[5], gr[6], gr[7]));
-                atomicAdd(dst + 2, make_float4(gr[8], gr[9], gr[10], gr[11]));
-                atomicAdd(dst + 3, make_float4(gr[12], gr[13], gr[14], gr[15]));
-                atomicAdd(reinterpret_cast<float2*>(dst + 4), make_float2(gr[16], gr[17]));
-            }
+            warp_sum18(gr, lane);
+            if (my_field >= 0) atomicAdd(reinterpret_cast<float*>(grad2d + (size_t)sid[j] * 5) + my_field, gr[0]);
         }
     }
 }

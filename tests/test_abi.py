@@ -41,7 +41,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.le_bin_sort_workspace(C.c_int32(-1), C.c_int64(10), C.byref(ws)) == b.LE_ERR_INVALID_ARG
     assert lib.le_bin_sort_workspace(C.c_int32(1000), C.c_int64(1 << 33), C.byref(ws)) == b.LE_ERR_INVALID_ARG
     assert lib.le_bin_sort_workspace(C.c_int32(1000), C.c_int64(20000), C.byref(ws)) == b.LE_OK
-    assert ws.value > 20000 * 16
+    assert ws.value >= 2 * 8 * 1000          # two depth-sort buffers of n keys at least
     # null gaussians / camera
     assert lib.le_preprocess(None, None, None, None) == b.LE_ERR_INVALID_ARG
     assert b"null" in lib.le_last_error()
