@@ -269,6 +269,12 @@ le_status le_adam(int64_t n, float* param, const float* grad, float* m, float* v
  * then incomplete. */
 le_status le_device_status(void* stream);
 
+/* le_selftest_bounded_wait -- exercises that failure path on purpose: one
+ * kernel waits on a barrier that nothing ever completes, gives up after the
+ * bounded wait (about a second) and records it, so the next le_device_status
+ * returns LE_ERR_TIMEOUT.  The GPU context stays usable. */
+le_status le_selftest_bounded_wait(void* stream);
+
 /* Message for the last error on the calling thread (static storage). */
 const char* le_last_error(void);
 /* Number of kernel launches this library issued on the calling thread since the

@@ -76,6 +76,7 @@ _SIG = {
                  C.c_int32, _P, _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
+    "le_selftest_bounded_wait": [_P],
     "le_adam": [C.c_int64, _P, _P, _P, _P, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
                 C.c_float, _P],
 }
@@ -123,6 +124,10 @@ def le_device_status():
     """Synchronizes the current stream; raises LegError(LE_ERR_TIMEOUT) if a
     tensor-core kernel gave up on a bounded wait."""
     _check(load().le_device_status(_stream()))
+
+
+def le_selftest_bounded_wait():
+    _check(load().le_selftest_bounded_wait(_stream()))
 
 
 def launch_count() -> int:

@@ -663,6 +663,16 @@ __global__ void gram_layout_kernel(const float* __restrict__ G, int ncb, unsigne
     }
 }
 
+// Self-test of the bounded-wait path: waits on an mbarrier that nothing ever
+// arrives at, gives up after the usual limit and records the timeout.
+__global__ void selftest_wait_kernel()
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0u)) atomicExch(&g_tc_error, 1);
+}
+
 int sm_count()
 {
     static int n = 0;
@@ -798,6 +808,13 @@ le_status query_fused(int32_t P, const float* feat, const le_decoder* d, const f
 }
 
 }  // namespace leg
+
+extern "C" le_status le_selftest_bounded_wait(void* stream)
+{
+    leg::selftest_wait_kernel<<<1, 32, 0, leg::as_stream(stream)>>>();
+    LE_LAUNCHED();
+    return LE_OK;
+}
 
 extern "C" le_status le_device_status(void* stream)
 {

@@ -350,18 +350,30 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
     float coef[NC * 3];
     load_sh(sh, i, NC, coef);
     float gdir[3] = {0.f, 0.f, 0.f};
-    float* dsh = d_sh + (size_t)i * NC * 3;
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
         float w = 0.f;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            dsh[3 * k + ch] = Y[k] * gcol[ch];
-            w = fmaf(gcol[ch], coef[3 * k + ch], w);
-        }
+        for (int ch = 0; ch < 3; ++ch) w = fmaf(gcol[ch], coef[3 * k + ch], w);
         gdir[0] = fmaf(w, dY[k][0], gdir[0]);
         gdir[1] = fmaf(w, dY[k][1], gdir[1]);
         gdir[2] = fmaf(w, dY[k][2], gdir[2]);
+    }
+    // dL/dsh_kc = Y_k dL/drgb_c, written with 16-byte stores where the stride allows
+    {
+        float* dsh = d_sh + (size_t)i * NC * 3;
+        if ((NC * 3) % 4 == 0) {
+#pragma unroll
+            for (int v = 0; v < NC * 3 / 4; ++v) {
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) o[e] = Y[(4 * v + e) / 3] * gcol[(4 * v + e) % 3];
+                reinterpret_cast<float4*>(dsh)[v] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < NC * 3; ++e) dsh[e] = Y[e / 3] * gcol[e % 3];
+        }
     }
     const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
     float Gp[3] = {(gdir[0] - dx * dd) * il, (gdir[1] - dy * dd) * il, (gdir[2] - dz * dd) * il};

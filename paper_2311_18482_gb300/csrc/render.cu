@@ -2,10 +2,12 @@
 // feature s_G (R_s, Sec. 3.4.1) and the uncertainty u (R_u, Sec. 3.4.2), and
 // its backward pass.
 //
-// One CTA per 16x16 tile, one thread per pixel.  The tile's depth-ordered
-// range is streamed through shared memory in batches of 256 splat records
-// (80 B each, one coalesced 16-byte load group per thread); every thread then
-// reads the batch by broadcast.  The CTA stops fetching once every pixel's
+// One CTA per 16x16 tile.  The tile's depth-ordered range is streamed through
+// shared memory in batches of 256 splat records (80 B each, 16-byte loads);
+// every thread then reads the batch by broadcast.  The forward runs one pixel
+// per thread (pixels stop at different depths; pairing them costs more than it
+// saves), the backward two (rows y and y + 8), so each staged record read, each
+// loop step and each warp reduction serves two pixels.  The CTA stops fetching once every pixel's
 // transmittance has dropped below 1e-4 (__syncthreads_count ballot).
 //
 // The backward walks the same range back to front from each pixel's last
@@ -37,79 +39,109 @@ __device__ __forceinline__ float splat_alpha0(float opacity, float power)
     return __fmul_rn(opacity, __expf(power));
 }
 
-__global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
-                                                            const uint32_t* __restrict__ ids,
-                                                            const uint2* __restrict__ ranges,
-                                                            float* __restrict__ out_rgb, float* __restrict__ out_feat,
-                                                            float* __restrict__ out_unc, float* __restrict__ T_final,
-                                                            int* __restrict__ n_contrib)
+// PPT pixels per thread: thread t serves column t % 16 of rows t / 16 + q * (16 / PPT),
+// so every staged record read and loop step is shared by PPT pixels.
+template <int PPT>
+__global__ void __launch_bounds__(kBlock / PPT) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
+                                                                  const uint32_t* __restrict__ ids,
+                                                                  const uint2* __restrict__ ranges,
+                                                                  float* __restrict__ out_rgb,
+                                                                  float* __restrict__ out_feat,
+                                                                  float* __restrict__ out_unc,
+                                                                  float* __restrict__ T_final,
+                                                                  int* __restrict__ n_contrib)
 {
+    constexpr int NT = kBlock / PPT;
     __shared__ float4 rec[5][kBlock];
     const int tile = blockIdx.x;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
-    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
-    const bool inside = px < cam.W && py < cam.H;
+    const int px = tx * LE_TILE + (threadIdx.x & 15);
     const uint2 rg = ranges[tile];
     const int n = (int)(rg.y - rg.x);
-    const float fpx = (float)px, fpy = (float)py;
+    const float fpx = (float)px;
 
-    bool done = !inside;
-    float T = 1.f;
-    float acc[12];
+    int py[PPT];
+    bool done[PPT];
+    float T[PPT], acc[PPT][12];
+    int last[PPT];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
-    int last = 0;
+    for (int q = 0; q < PPT; ++q) {
+        py[q] = ty * LE_TILE + (threadIdx.x >> 4) + q * (LE_TILE / PPT);
+        done[q] = !(px < cam.W && py[q] < cam.H);
+        T[q] = 1.f;
+        last[q] = 0;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[q][c] = 0.f;
+    }
 
     for (int b0 = 0; b0 < n; b0 += kBlock) {
-        if (__syncthreads_count(done) == kBlock) break;
-        const int k = b0 + threadIdx.x;
-        if (k < n) {
-            const float4* r = splat + (size_t)ids[rg.x + k] * 5;
+        bool all_done = true;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
+        for (int q = 0; q < PPT; ++q) all_done = all_done && done[q];
+        if (__syncthreads_count(all_done) == NT) break;
+#pragma unroll
+        for (int l = 0; l < PPT; ++l) {
+            const int i = threadIdx.x + l * NT;
+            const int k = b0 + i;
+            if (k < n) {
+                const float4* r = splat + (size_t)ids[rg.x + k] * 5;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) rec[c][i] = __ldg(r + c);
+            }
         }
         __syncthreads();
         const int cnt = min(kBlock, n - b0);
-        for (int j = 0; !done && j < cnt; ++j) {
+        for (int j = 0; j < cnt; ++j) {
+            all_done = true;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) all_done = all_done && done[q];
+            if (all_done) break;
             const float4 g0 = rec[0][j], g1 = rec[1][j];
-            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
-            const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
-            if (power > 0.f) continue;
-            const float alpha = fminf(0.99f, splat_alpha0(g1.y, power));
-            if (alpha < (1.f / 255.f)) continue;
-            const float test = T * (1.f - alpha);
-            if (test < 1e-4f) {
-                done = true;
-                break;
+            const float dx = __fsub_rn(g0.x, fpx);
+            float w[PPT];
+            bool need = false;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                w[q] = 0.f;
+                if (done[q]) continue;
+                const float dy = __fsub_rn(g0.y, (float)py[q]);
+                const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
+                if (power > 0.f) continue;
+                const float alpha = fminf(0.99f, splat_alpha0(g1.y, power));
+                if (alpha < (1.f / 255.f)) continue;
+                const float test = T[q] * (1.f - alpha);
+                if (test < 1e-4f) {
+                    done[q] = true;
+                    continue;
+                }
+                w[q] = alpha * T[q];
+                T[q] = test;
+                last[q] = b0 + j + 1;
+                need = true;
             }
-            const float w = alpha * T;
+            if (!need) continue;
             const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
-            acc[0] = fmaf(g1.z, w, acc[0]);
-            acc[1] = fmaf(g1.w, w, acc[1]);
-            acc[2] = fmaf(g2.x, w, acc[2]);
-            acc[3] = fmaf(g2.y, w, acc[3]);     // uncertainty
-            acc[4] = fmaf(g2.z, w, acc[4]);     // feature 0..7
-            acc[5] = fmaf(g2.w, w, acc[5]);
-            acc[6] = fmaf(g3.x, w, acc[6]);
-            acc[7] = fmaf(g3.y, w, acc[7]);
-            acc[8] = fmaf(g3.z, w, acc[8]);
-            acc[9] = fmaf(g3.w, w, acc[9]);
-            acc[10] = fmaf(g4.x, w, acc[10]);
-            acc[11] = fmaf(g4.y, w, acc[11]);
-            T = test;
-            last = b0 + j + 1;
+            const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
+#pragma unroll
+            for (int q = 0; q < PPT; ++q)
+#pragma unroll
+                for (int c = 0; c < 12; ++c) acc[q][c] = fmaf(f[c], w[q], acc[q][c]);
         }
     }
-    if (!inside) return;
-    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
-    out_rgb[o] = acc[0] + T * cam.bg[0];
-    out_rgb[P + o] = acc[1] + T * cam.bg[1];
-    out_rgb[2 * P + o] = acc[2] + T * cam.bg[2];
-    out_unc[o] = acc[3];
+    const size_t P = (size_t)cam.W * cam.H;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[4 + c];
-    T_final[o] = T;
-    n_contrib[o] = last;
+    for (int q = 0; q < PPT; ++q) {
+        if (!(px < cam.W && py[q] < cam.H)) continue;
+        const size_t o = (size_t)py[q] * cam.W + px;
+        out_rgb[o] = acc[q][0] + T[q] * cam.bg[0];
+        out_rgb[P + o] = acc[q][1] + T[q] * cam.bg[1];
+        out_rgb[2 * P + o] = acc[q][2] + T[q] * cam.bg[2];
+        out_unc[o] = acc[q][3];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[q][4 + c];
+        T_final[o] = T[q];
+        n_contrib[o] = last[q];
+    }
 }
 
 // One stage of a recursive-halving ("transpose") reduction of N values held by
@@ -155,47 +187,51 @@ __device__ __forceinline__ int field_of_lane(int lane)
     return valid >= 1 ? base : -1;
 }
 
-__global__ void __launch_bounds__(kBlock) render_bwd_kernel(
+template <int PPT>
+__global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
     CamParams cam, const float4* __restrict__ splat, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
     const float* __restrict__ T_final, const int* __restrict__ n_contrib, const float* __restrict__ dL_drgb,
     const float* __restrict__ dL_dfeat, const float* __restrict__ dL_dunc, float4* __restrict__ grad2d)
 {
+    constexpr int NT = kBlock / PPT;
     __shared__ float4 rec[5][kBlock];
     __shared__ uint32_t sid[kBlock];
     __shared__ int s_max;
     const int tile = blockIdx.x;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
-    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
-    const bool inside = px < cam.W && py < cam.H;
+    const int px = tx * LE_TILE + (threadIdx.x & 15);
     const uint2 rg = ranges[tile];
-    const float fpx = (float)px, fpy = (float)py;
-    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
+    const float fpx = (float)px;
+    const size_t P = (size_t)cam.W * cam.H;
 
-    float dC[12];
-    float T = 0.f;
-    int last = 0;
-    if (inside) {
-        T = T_final[o];
-        last = n_contrib[o];
-        dC[0] = dL_drgb[o];
-        dC[1] = dL_drgb[P + o];
-        dC[2] = dL_drgb[2 * P + o];
-        dC[3] = dL_dunc[o];
+    float py[PPT], dC[PPT][12], T[PPT], Tf[PPT], S[PPT], bgdot[PPT];
+    int last[PPT];
+    int lmax = 0;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) dC[4 + c] = dL_dfeat[c * P + o];
-    } else {
+    for (int q = 0; q < PPT; ++q) {
+        const int y = ty * LE_TILE + (threadIdx.x >> 4) + q * (LE_TILE / PPT);
+        py[q] = (float)y;
+        const bool inside = px < cam.W && y < cam.H;
+        const size_t o = (size_t)y * cam.W + px;
+        T[q] = inside ? T_final[o] : 0.f;
+        last[q] = inside ? n_contrib[o] : 0;
+        dC[q][0] = inside ? dL_drgb[o] : 0.f;
+        dC[q][1] = inside ? dL_drgb[P + o] : 0.f;
+        dC[q][2] = inside ? dL_drgb[2 * P + o] : 0.f;
+        dC[q][3] = inside ? dL_dunc[o] : 0.f;
 #pragma unroll
-        for (int c = 0; c < 12; ++c) dC[c] = 0.f;
+        for (int c = 0; c < 8; ++c) dC[q][4 + c] = inside ? dL_dfeat[c * P + o] : 0.f;
+        Tf[q] = T[q];
+        // S = sum_c acc_c dL/dC_c, the "colour behind" seen through this pixel's
+        // upstream gradient; it obeys the blending recurrence of acc itself.
+        S[q] = 0.f;
+        bgdot[q] = cam.bg[0] * dC[q][0] + cam.bg[1] * dC[q][1] + cam.bg[2] * dC[q][2];
+        lmax = max(lmax, last[q]);
     }
-    const float Tf = T;
-    const float bgdot = cam.bg[0] * dC[0] + cam.bg[1] * dC[1] + cam.bg[2] * dC[2];
-    // S = sum_c acc_c dL/dC_c, the "colour behind" seen through this pixel's
-    // upstream gradient; it obeys the blending recurrence of acc itself.
-    float S = 0.f;
 
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    const int wmax = __reduce_max_sync(0xffffffffu, last);
+    const int wmax = __reduce_max_sync(0xffffffffu, lmax);
     if ((threadIdx.x & 31) == 0) atomicMax(&s_max, wmax);
     __syncthreads();
     const int nproc = s_max;
@@ -205,50 +241,65 @@ __global__ void __launch_bounds__(kBlock) render_bwd_kernel(
     for (int b_end = nproc; b_end > 0; b_end -= kBlock) {
         const int b_start = max(0, b_end - kBlock);
         __syncthreads();
-        const int k = b_start + threadIdx.x;
-        if (k < b_end) {
-            const uint32_t gid = ids[rg.x + k];
-            sid[threadIdx.x] = gid;
-            const float4* r = splat + (size_t)gid * 5;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
+        for (int l = 0; l < PPT; ++l) {
+            const int i = threadIdx.x + l * NT;
+            const int k = b_start + i;
+            if (k < b_end) {
+                const uint32_t gid = ids[rg.x + k];
+                sid[i] = gid;
+                const float4* r = splat + (size_t)gid * 5;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) rec[c][i] = __ldg(r + c);
+            }
         }
         __syncthreads();
         for (int j = min(b_end, wmax) - b_start - 1; j >= 0; --j) {
             const int pos = b_start + j;
             const float4 g0 = rec[0][j], g1 = rec[1][j];
-            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
-            const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
-            const float G = __expf(power);
-            const float a0 = __fmul_rn(g1.y, G);
-            const float alpha = fminf(0.99f, a0);
-            const bool contrib = pos < last && power <= 0.f && alpha >= (1.f / 255.f);
-            if (!__any_sync(0xffffffffu, contrib)) continue;
+            const float dx = __fsub_rn(g0.x, fpx);
+            float dy[PPT], G[PPT], a0[PPT], alpha[PPT];
+            bool contrib[PPT], any_mine = false;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                dy[q] = __fsub_rn(g0.y, py[q]);
+                const float power = splat_power(g0.z, g0.w, g1.x, dx, dy[q]);
+                G[q] = __expf(power);
+                a0[q] = __fmul_rn(g1.y, G[q]);
+                alpha[q] = fminf(0.99f, a0[q]);
+                contrib[q] = pos < last[q] && power <= 0.f && alpha[q] >= (1.f / 255.f);
+                any_mine = any_mine || contrib[q];
+            }
+            if (!__any_sync(0xffffffffu, any_mine)) continue;
             float gr[18];
 #pragma unroll
-            for (int q = 0; q < 18; ++q) gr[q] = 0.f;
-            if (contrib) {
-                const float inv1ma = __fdividef(1.f, 1.f - alpha);
-                T *= inv1ma;
-                const float w = alpha * T;
+            for (int c = 0; c < 18; ++c) gr[c] = 0.f;
+            if (any_mine) {
                 const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
                 const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
-                float fdc = 0.f;
 #pragma unroll
-                for (int c = 0; c < 12; ++c) {
-                    gr[6 + c] = w * dC[c];                  // rgb (6..8), unc (9), feat (10..17)
-                    fdc = fmaf(f[c], dC[c], fdc);
-                }
-                const float dalpha = T * (fdc - S) - Tf * inv1ma * bgdot;
-                S = fmaf(alpha, fdc - S, S);
-                if (a0 < 0.99f) {
-                    const float dpow = dalpha * alpha;
-                    gr[5] = dalpha * G;
-                    gr[2] = -0.5f * dpow * dx * dx;
-                    gr[3] = -dpow * dx * dy;
-                    gr[4] = -0.5f * dpow * dy * dy;
-                    gr[0] = dpow * (-g0.z * dx - g0.w * dy);
-                    gr[1] = dpow * (-g1.x * dy - g0.w * dx);
+                for (int q = 0; q < PPT; ++q) {
+                    if (!contrib[q]) continue;
+                    const float inv1ma = __fdividef(1.f, 1.f - alpha[q]);
+                    T[q] *= inv1ma;
+                    const float w = alpha[q] * T[q];
+                    float fdc = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) {
+                        gr[6 + c] = fmaf(w, dC[q][c], gr[6 + c]);      // rgb (6..8), unc (9), feat (10..17)
+                        fdc = fmaf(f[c], dC[q][c], fdc);
+                    }
+                    const float dalpha = T[q] * (fdc - S[q]) - Tf[q] * inv1ma * bgdot[q];
+                    S[q] = fmaf(alpha[q], fdc - S[q], S[q]);
+                    if (a0[q] < 0.99f) {
+                        const float dpow = dalpha * alpha[q];
+                        gr[5] = fmaf(dalpha, G[q], gr[5]);
+                        gr[2] = fmaf(-0.5f * dpow * dx, dx, gr[2]);
+                        gr[3] = fmaf(-dpow * dx, dy[q], gr[3]);
+                        gr[4] = fmaf(-0.5f * dpow * dy[q], dy[q], gr[4]);
+                        gr[0] = fmaf(dpow, -g0.z * dx - g0.w * dy[q], gr[0]);
+                        gr[1] = fmaf(dpow, -g1.x * dy[q] - g0.w * dx, gr[1]);
+                    }
                 }
             }
             warp_sum18(gr, lane);
@@ -273,7 +324,7 @@ extern "C" le_status le_render_fwd(const le_camera* cam, int32_t n, const float*
     LE_CHECK_ARG(n == 0 || (splat && aligned16(splat)), "splat must be non-null and 16-byte aligned");
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(tile_ranges) & 7u) == 0, "tile_ranges must be 8-byte aligned");
     const CamParams cp = cam_params(cam);
-    render_fwd_kernel<<<cp.TX * cp.TY, kBlock, 0, as_stream(stream)>>>(
+    render_fwd_kernel<1><<<cp.TX * cp.TY, kBlock, 0, as_stream(stream)>>>(
         cp, reinterpret_cast<const float4*>(splat), sorted_ids, reinterpret_cast<const uint2*>(tile_ranges), out_rgb,
         out_feat, out_unc, T_final, n_contrib);
     LE_LAUNCHED();
@@ -295,11 +346,12 @@ extern "C" le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, 
     LE_CHECK_ARG(grad2d && aligned16(grad2d), "grad2d must be non-null and 16-byte aligned");
     LE_CHECK_ARG(out->means && out->log_scales && out->quats && out->opacity_raw && out->sh && out->feat && out->unc,
                  "null gradient pointer");
-    LE_CHECK_ARG(aligned16(out->quats) && aligned16(out->feat), "quats/feat gradients must be 16-byte aligned");
+    LE_CHECK_ARG(aligned16(out->quats) && aligned16(out->feat) && aligned16(out->sh),
+                 "quats/sh/feat gradients must be 16-byte aligned");
     cudaStream_t s = as_stream(stream);
     const CamParams cp = cam_params(cam);
     LE_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * LE_SPLAT_STRIDE * (size_t)g->n, s));
-    render_bwd_kernel<<<cp.TX * cp.TY, kBlock, 0, s>>>(cp, reinterpret_cast<const float4*>(pr->splat), sorted_ids,
+    render_bwd_kernel<2><<<cp.TX * cp.TY, kBlock / 2, 0, s>>>(cp, reinterpret_cast<const float4*>(pr->splat), sorted_ids,
                                                         reinterpret_cast<const uint2*>(tile_ranges), T_final,
                                                         n_contrib, dL_drgb, dL_dfeat, dL_dunc,
                                                         reinterpret_cast<float4*>(grad2d));

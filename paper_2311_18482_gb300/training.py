@@ -88,6 +88,17 @@ class TrainState:
         self.K = 0
         self.events = None
 
+    def state_dict(self):
+        """Everything a resumed run needs: parameters, Adam moments, step count."""
+        return {"params": self.params.detach().cpu().clone(), "m": self.m.detach().cpu().clone(),
+                "v": self.v.detach().cpu().clone(), "step": self.step_count}
+
+    def load_state_dict(self, sd):
+        self.params.copy_(sd["params"])
+        self.m.copy_(sd["m"])
+        self.v.copy_(sd["v"])
+        self.step_count = int(sd["step"])
+
     def _mark(self, name):
         if self.events is not None:
             ev = torch.cuda.Event(enable_timing=True)
