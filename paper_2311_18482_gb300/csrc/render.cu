@@ -39,109 +39,79 @@ __device__ __forceinline__ float splat_alpha0(float opacity, float power)
     return __fmul_rn(opacity, __expf(power));
 }
 
-// PPT pixels per thread: thread t serves column t % 16 of rows t / 16 + q * (16 / PPT),
-// so every staged record read and loop step is shared by PPT pixels.
-template <int PPT>
-__global__ void __launch_bounds__(kBlock / PPT) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
-                                                                  const uint32_t* __restrict__ ids,
-                                                                  const uint2* __restrict__ ranges,
-                                                                  float* __restrict__ out_rgb,
-                                                                  float* __restrict__ out_feat,
-                                                                  float* __restrict__ out_unc,
-                                                                  float* __restrict__ T_final,
-                                                                  int* __restrict__ n_contrib)
+__global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
+                                                            const uint32_t* __restrict__ ids,
+                                                            const uint2* __restrict__ ranges,
+                                                            float* __restrict__ out_rgb, float* __restrict__ out_feat,
+                                                            float* __restrict__ out_unc, float* __restrict__ T_final,
+                                                            int* __restrict__ n_contrib)
 {
-    constexpr int NT = kBlock / PPT;
     __shared__ float4 rec[5][kBlock];
     const int tile = blockIdx.x;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
-    const int px = tx * LE_TILE + (threadIdx.x & 15);
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
+    const bool inside = px < cam.W && py < cam.H;
     const uint2 rg = ranges[tile];
     const int n = (int)(rg.y - rg.x);
-    const float fpx = (float)px;
+    const float fpx = (float)px, fpy = (float)py;
 
-    int py[PPT];
-    bool done[PPT];
-    float T[PPT], acc[PPT][12];
-    int last[PPT];
+    bool done = !inside;
+    float T = 1.f;
+    float acc[12];
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        py[q] = ty * LE_TILE + (threadIdx.x >> 4) + q * (LE_TILE / PPT);
-        done[q] = !(px < cam.W && py[q] < cam.H);
-        T[q] = 1.f;
-        last[q] = 0;
-#pragma unroll
-        for (int c = 0; c < 12; ++c) acc[q][c] = 0.f;
-    }
+    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
+    int last = 0;
 
     for (int b0 = 0; b0 < n; b0 += kBlock) {
-        bool all_done = true;
+        if (__syncthreads_count(done) == kBlock) break;
+        const int k = b0 + threadIdx.x;
+        if (k < n) {
+            const float4* r = splat + (size_t)ids[rg.x + k] * 5;
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) all_done = all_done && done[q];
-        if (__syncthreads_count(all_done) == NT) break;
-#pragma unroll
-        for (int l = 0; l < PPT; ++l) {
-            const int i = threadIdx.x + l * NT;
-            const int k = b0 + i;
-            if (k < n) {
-                const float4* r = splat + (size_t)ids[rg.x + k] * 5;
-#pragma unroll
-                for (int c = 0; c < 5; ++c) rec[c][i] = __ldg(r + c);
-            }
+            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
         }
         __syncthreads();
         const int cnt = min(kBlock, n - b0);
-        for (int j = 0; j < cnt; ++j) {
-            all_done = true;
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) all_done = all_done && done[q];
-            if (all_done) break;
+        for (int j = 0; !done && j < cnt; ++j) {
             const float4 g0 = rec[0][j], g1 = rec[1][j];
-            const float dx = __fsub_rn(g0.x, fpx);
-            float w[PPT];
-            bool need = false;
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                w[q] = 0.f;
-                if (done[q]) continue;
-                const float dy = __fsub_rn(g0.y, (float)py[q]);
-                const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
-                if (power > 0.f) continue;
-                const float alpha = fminf(0.99f, splat_alpha0(g1.y, power));
-                if (alpha < (1.f / 255.f)) continue;
-                const float test = T[q] * (1.f - alpha);
-                if (test < 1e-4f) {
-                    done[q] = true;
-                    continue;
-                }
-                w[q] = alpha * T[q];
-                T[q] = test;
-                last[q] = b0 + j + 1;
-                need = true;
+            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
+            const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
+            if (power > 0.f) continue;
+            const float alpha = fminf(0.99f, splat_alpha0(g1.y, power));
+            if (alpha < (1.f / 255.f)) continue;
+            const float test = T * (1.f - alpha);
+            if (test < 1e-4f) {
+                done = true;
+                break;
             }
-            if (!need) continue;
+            const float w = alpha * T;
             const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
-            const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
-#pragma unroll
-            for (int q = 0; q < PPT; ++q)
-#pragma unroll
-                for (int c = 0; c < 12; ++c) acc[q][c] = fmaf(f[c], w[q], acc[q][c]);
+            acc[0] = fmaf(g1.z, w, acc[0]);
+            acc[1] = fmaf(g1.w, w, acc[1]);
+            acc[2] = fmaf(g2.x, w, acc[2]);
+            acc[3] = fmaf(g2.y, w, acc[3]);     // uncertainty
+            acc[4] = fmaf(g2.z, w, acc[4]);     // feature 0..7
+            acc[5] = fmaf(g2.w, w, acc[5]);
+            acc[6] = fmaf(g3.x, w, acc[6]);
+            acc[7] = fmaf(g3.y, w, acc[7]);
+            acc[8] = fmaf(g3.z, w, acc[8]);
+            acc[9] = fmaf(g3.w, w, acc[9]);
+            acc[10] = fmaf(g4.x, w, acc[10]);
+            acc[11] = fmaf(g4.y, w, acc[11]);
+            T = test;
+            last = b0 + j + 1;
         }
     }
-    const size_t P = (size_t)cam.W * cam.H;
+    if (!inside) return;
+    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
+    out_rgb[o] = acc[0] + T * cam.bg[0];
+    out_rgb[P + o] = acc[1] + T * cam.bg[1];
+    out_rgb[2 * P + o] = acc[2] + T * cam.bg[2];
+    out_unc[o] = acc[3];
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        if (!(px < cam.W && py[q] < cam.H)) continue;
-        const size_t o = (size_t)py[q] * cam.W + px;
-        out_rgb[o] = acc[q][0] + T[q] * cam.bg[0];
-        out_rgb[P + o] = acc[q][1] + T[q] * cam.bg[1];
-        out_rgb[2 * P + o] = acc[q][2] + T[q] * cam.bg[2];
-        out_unc[o] = acc[q][3];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[q][4 + c];
-        T_final[o] = T[q];
-        n_contrib[o] = last[q];
-    }
+    for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[4 + c];
+    T_final[o] = T;
+    n_contrib[o] = last;
 }
 
 // One stage of a recursive-halving ("transpose") reduction of N values held by
@@ -324,7 +294,7 @@ extern "C" le_status le_render_fwd(const le_camera* cam, int32_t n, const float*
     LE_CHECK_ARG(n == 0 || (splat && aligned16(splat)), "splat must be non-null and 16-byte aligned");
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(tile_ranges) & 7u) == 0, "tile_ranges must be 8-byte aligned");
     const CamParams cp = cam_params(cam);
-    render_fwd_kernel<1><<<cp.TX * cp.TY, kBlock, 0, as_stream(stream)>>>(
+    render_fwd_kernel<<<cp.TX * cp.TY, kBlock, 0, as_stream(stream)>>>(
         cp, reinterpret_cast<const float4*>(splat), sorted_ids, reinterpret_cast<const uint2*>(tile_ranges), out_rgb,
         out_feat, out_unc, T_final, n_contrib);
     LE_LAUNCHED();
