@@ -126,8 +126,8 @@ def stage_bytes(N, n_vis, K, P, T, nc, total_scalars):
     par = 4 * (3 + 3 + 4 + 1 + 3 * nc + 8 + 1)          # all per-Gaussian parameters
     geo = 4 * (3 + 3 + 4 + 1 + 3 * nc)                  # parameters the projection reads
     return {
-        "preprocess": N * par + N * (80 + 4 + 4 + 8 + 4 + 1),
-        "bin_sort": N * (4 + 4 + 8) + 4 * K + 8 * T,
+        "preprocess": N * par + N * (80 + 4 + 4 + 8 + 4 + 1 + 32),
+        "bin_sort": N * (4 + 4) + n_vis * (8 + 32) + 4 * K + 8 * T,
         "render_fwd": 4 * K + 80 * n_vis + 56 * P,
         "decoder": (36 + 4 + 36) * P,
         "render_bwd": 4 * K + 80 * n_vis + 104 * P + 80 * N + geo * N + 80 * N + par * N + 5 * N,

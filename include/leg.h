@@ -95,6 +95,7 @@ typedef struct le_projected {
     uint16_t* rect;           /* [n,4] tile rectangle x0,y0,x1,y1 (half-open) */
     int32_t* tiles_touched;   /* [n]  (x1-x0)(y1-y0), 0 = culled */
     uint8_t* clamp_mask;      /* [n]  bit c set when colour channel c was clamped at 0 */
+    float* tile_ellipse;      /* [n,8] tile ellipse for binning (see le_preprocess), 16-byte aligned */
 } le_projected;
 
 /* ---------------------------------------------------------------------------
@@ -107,23 +108,38 @@ typedef struct le_projected {
  * Depth, screen mean, Sigma2, radius and rect are computed by a fixed
  * sequence of IEEE FP32 operations (explicit FMA chains, exp by Cody-Waite
  * reduction + degree-7 Taylor) so that binning is reproducible bit for bit.
+ * The same fixed sequence writes tile_ellipse, which is not in the paper: a
+ * conservative form of the ellipse where o exp(-q/2) >= 1/255, used by
+ * le_bin_sort to skip the rect tiles no pixel of which the Gaussian can
+ * reach.  With Sigma2 = [[a,b],[b,c]], t = (2 lnu(255 o) + 1/16)(1 + 2^-10)
+ * (lnu an upper bound of ln from the exponent and (m-1)/sqrt(m)), r the
+ * radius: {mx, my, b/c, det/c^2, c t, b sqrt(t/a), 1/4 + 2^-12(|mx| + 2r),
+ * 1/4 + 2^-12(|my| + 2r)} (c t = -1 when t <= 0).
+ * tiles_touched is the rect's tile count, an upper bound of the copies.
  * Culled Gaussians get radius = tiles_touched = 0 and a zero splat record.
  * Errors: LE_ERR_INVALID_ARG for n < 0, sh_degree outside 0..3, null or
  * misaligned pointers. */
 le_status le_preprocess(const le_gaussians* g, const le_camera* cam, le_projected* out, void* stream);
 
 /* ---------------------------------------------------------------------------
- * le_bin_sort -- duplicate each visible Gaussian once per tile of its rect,
- * key each copy (tile_id << 32) | float_bits(depth), tile_id = ty*TX + tx,
- * order the copies by key with ties kept in emission order (Gaussian index),
- * and cut the order into per-tile ranges (the 3DGS binning of Sec. 4; tie
- * rule and empty range (0,0) are readings).  The K copies are never sorted:
+ * le_bin_sort -- duplicate each visible Gaussian once per tile of its rect
+ * that its tile ellipse reaches, key each copy (tile_id << 32) |
+ * float_bits(depth), tile_id = ty*TX + tx, order the copies by key with ties
+ * kept in emission order (Gaussian index), and cut the order into per-tile
+ * ranges (the 3DGS binning of Sec. 4; tie rule and empty range (0,0) are
+ * readings).  Tile ellipse (not in the paper; see le_preprocess): in rect row
+ * ty, with lo/hi = 16 ty (+15) - my -/+ pady, dR = clamp(ystar, lo, hi), dL =
+ * clamp(-ystar, lo, hi), the row keeps tiles [ceil((mx + s dL - sqrt(k (mm -
+ * dL^2)) - padx - 15)/16), floor((mx + s dR + sqrt(k (mm - dR^2)) + padx)/16)
+ * + 1) clipped to the rect, none if mm < dR^2 or mm < dL^2; the left-out
+ * tiles hold no pixel where the renderer's alpha reaches 1/255, so images and
+ * gradients equal those of whole-rect binning.  The K copies are never sorted:
  * the Gaussians are radix-sorted by depth, per-(tile, chunk-of-Gaussians)
- * copy counts come from 2-D difference arrays of the rects, one exclusive scan
- * of those counts in tile-major order gives every chunk's offset inside every
- * tile's range, and each chunk writes its copies in depth order -- the same
- * order as a stable sort of the full keys.
- *   depth, rect, tiles_touched: from le_preprocess (n entries)
+ * copy counts come from per-row difference arrays of those spans, one
+ * exclusive scan of the counts in tile-major order gives every chunk's offset
+ * inside every tile's range, and each chunk writes its copies in depth order
+ * -- the same order as a stable sort of the full keys.
+ *   depth, rect, tile_ellipse, tiles_touched: from le_preprocess (n entries)
  *   workspace: le_bin_sort_workspace(n, k_cap) bytes, 256-byte aligned (it
  *     depends on n only; k_cap bounds the outputs)
  *   sorted_ids:  [k_cap] out, Gaussian id of each copy in key order
@@ -135,7 +151,8 @@ le_status le_preprocess(const le_gaussians* g, const le_camera* cam, le_projecte
  * LE_ERR_UNSUPPORTED for more than 16384 screen tiles or 256 tile columns. */
 le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* bytes);
 le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
-                      const int32_t* tiles_touched, void* workspace, size_t workspace_bytes, int64_t k_cap,
+                      const float* tile_ellipse, const int32_t* tiles_touched, void* workspace,
+                      size_t workspace_bytes, int64_t k_cap,
                       uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
                       void* stream);
 
@@ -147,7 +164,7 @@ le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const
  * budgeted by someone else, or a per-frame path where the implicit
  * synchronisation of cudaMalloc/cudaFree is not acceptable.  It calls no
  * cudaMalloc, cudaFree or other allocating routine; its scratch is a
- * statically sized device array inside this library (about 9.4 MB), which
+ * statically sized device array inside this library (about 11.5 MB), which
  * every GPU that loads the library holds until the process exits.
  *   Limits: n <= LE_STATIC_MAX_GAUSSIANS, and at most LE_STATIC_MAX_INSTANCES
  *   tile copies (k_cap is clamped to it).  Larger n -> LE_ERR_INVALID_ARG;
@@ -162,8 +179,9 @@ le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const
 #define LE_STATIC_MAX_GAUSSIANS 65536
 #define LE_STATIC_MAX_INSTANCES 524288
 le_status le_bin_sort_static(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
-                             const int32_t* tiles_touched, int64_t k_cap, uint32_t* sorted_ids,
-                             uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out, void* stream);
+                             const float* tile_ellipse, const int32_t* tiles_touched, int64_t k_cap,
+                             uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
+                             void* stream);
 
 /* ---------------------------------------------------------------------------
  * le_render_fwd -- per pixel, front to back over its tile's range:

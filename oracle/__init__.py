@@ -45,7 +45,10 @@ def lib():
         _lib = C.CDLL(LIB)
         _lib.orc_exp_f32.restype = C.c_float
         _lib.orc_exp_f32.argtypes = [C.c_float]
+        _lib.orc_ln_up_f32.restype = C.c_float
+        _lib.orc_ln_up_f32.argtypes = [C.c_float]
         _lib.orc_bin.restype = C.c_int64
+        _lib.orc_bin_count.restype = C.c_int64
         _lib.orc_tile_list.restype = C.c_int
         _lib.orc_l1.restype = C.c_double
         _lib.orc_sh_count.restype = C.c_int
@@ -85,6 +88,10 @@ def exp_f32(x: float) -> float:
     return lib().orc_exp_f32(float(x))
 
 
+def ln_up_f32(x: float) -> float:
+    return lib().orc_ln_up_f32(float(x))
+
+
 def sh_basis(deg: int, d):
     n = (deg + 1) ** 2
     d = _f64(d)
@@ -98,12 +105,21 @@ def keypath(scene, cam) -> dict:
     N = scene.N
     out = dict(depth=np.zeros(N, np.float32), mean2d=np.zeros((N, 2), np.float32),
                cov2d=np.zeros((N, 3), np.float32), radius=np.zeros(N, np.int32),
-               rect=np.zeros((N, 4), np.int32), tiles=np.zeros(N, np.int32))
+               rect=np.zeros((N, 4), np.int32), tiles=np.zeros(N, np.int32), ell=np.zeros((N, 8), np.float32))
     cs = cam_struct(cam)
-    m, ls, q = _f32(scene.means), _f32(scene.log_scales), _f32(scene.quats)
-    lib().orc_keypath(C.c_int(N), _p(m), _p(ls), _p(q), C.byref(cs), _p(out["depth"]), _p(out["mean2d"]),
-                      _p(out["cov2d"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]))
+    m, ls, q, o = _f32(scene.means), _f32(scene.log_scales), _f32(scene.quats), _f32(scene.opacity_raw)
+    lib().orc_keypath(C.c_int(N), _p(m), _p(ls), _p(q), _p(o), C.byref(cs), _p(out["depth"]), _p(out["mean2d"]),
+                      _p(out["cov2d"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]), _p(out["ell"]))
     return out
+
+
+def row_span(kp, i: int, ty: int):
+    """Tiles [xl, xr) of row ty of Gaussian i's rectangle that meet its tile ellipse."""
+    xl, xr = C.c_int(), C.c_int()
+    e = np.ascontiguousarray(kp["ell"][i], np.float32)
+    r = np.ascontiguousarray(kp["rect"][i], np.int32)
+    lib().orc_row_span(_p(e), _p(r), C.c_int(ty), C.byref(xl), C.byref(xr))
+    return xl.value, xr.value
 
 
 def project(scene, cam, tiles) -> dict:
@@ -134,30 +150,41 @@ def project_bwd(scene, cam, tiles, d_mean2d, d_conic, d_opacity, d_rgb) -> dict:
     return out
 
 
-def bin(cam, kp):
-    """Keys, sorted Gaussian ids and per-tile ranges (stable sort of 64-bit keys)."""
+def _ell(kp, ellipse: bool):
+    return _p(kp["ell"]) if ellipse else None
+
+
+def bin(cam, kp, ellipse: bool = True):
+    """Keys, sorted Gaussian ids and per-tile ranges (stable sort of 64-bit keys).
+    ellipse=False bins whole rectangles (the plain 3DGS assignment)."""
     N = kp["tiles"].shape[0]
-    K = int(kp["tiles"].astype(np.int64).sum())
-    keys = np.zeros(max(K, 1), np.uint64)
-    vals = np.zeros(max(K, 1), np.uint32)
+    cap = int(kp["tiles"].astype(np.int64).sum())
+    keys = np.zeros(max(cap, 1), np.uint64)
+    vals = np.zeros(max(cap, 1), np.uint32)
     ntiles = cam.tiles_x * cam.tiles_y
     ranges = np.zeros((ntiles, 2), np.uint32)
     cs = cam_struct(cam)
-    K2 = lib().orc_bin(C.c_int(N), C.byref(cs), _p(kp["depth"]), _p(kp["rect"]), _p(kp["tiles"]),
-                       _p(keys), _p(vals), _p(ranges))
-    assert K2 == K
+    K = lib().orc_bin(C.c_int(N), C.byref(cs), _p(kp["depth"]), _p(kp["rect"]), _p(kp["tiles"]),
+                      _ell(kp, ellipse), _p(keys), _p(vals), _p(ranges))
+    assert 0 <= K <= cap
     return keys[:K], vals[:K], ranges
 
 
-def tile_list(kp, tx: int, ty: int) -> np.ndarray:
+def bin_count(kp, ellipse: bool = True) -> int:
+    """The number of tile copies bin() emits."""
+    N = kp["tiles"].shape[0]
+    return int(lib().orc_bin_count(C.c_int(N), _p(kp["rect"]), _p(kp["tiles"]), _ell(kp, ellipse)))
+
+
+def tile_list(kp, tx: int, ty: int, ellipse: bool = True) -> np.ndarray:
     N = kp["tiles"].shape[0]
     out = np.zeros(max(N, 1), np.uint32)
-    n = lib().orc_tile_list(C.c_int(N), _p(kp["depth"]), _p(kp["rect"]), _p(kp["tiles"]), C.c_int(tx),
-                            C.c_int(ty), _p(out))
+    n = lib().orc_tile_list(C.c_int(N), _p(kp["depth"]), _p(kp["rect"]), _p(kp["tiles"]), _ell(kp, ellipse),
+                            C.c_int(tx), C.c_int(ty), _p(out))
     return out[:n].copy()
 
 
-def lists_for_tiles(cam, kp, tiles_xy):
+def lists_for_tiles(cam, kp, tiles_xy, ellipse: bool = True):
     """Brute-force per-tile lists packed as (vals, ranges) for the given tiles only
     (all other tiles empty).  Used for crops of scenes too large to bin fully."""
     ntiles = cam.tiles_x * cam.tiles_y
@@ -165,7 +192,7 @@ def lists_for_tiles(cam, kp, tiles_xy):
     chunks = []
     pos = 0
     for tx, ty in tiles_xy:
-        ids = tile_list(kp, tx, ty)
+        ids = tile_list(kp, tx, ty, ellipse)
         t = ty * cam.tiles_x + tx
         ranges[t] = (pos, pos + len(ids))
         pos += len(ids)

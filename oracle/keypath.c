@@ -18,6 +18,22 @@
  *   low-pass dilation: +0.3 px^2 on the diagonal of the 2D covariance
  *   radius: ceil(3 * sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det))
  *   rectangle: [floor((mu - r)/16), floor((mu + r + 15)/16)) clamped to the tile grid
+ *
+ * Tile ellipse (an addition of this implementation, not of the paper): inside
+ * its rectangle a Gaussian is binned only to the tiles whose pixel centres can
+ * reach alpha >= 1/255.  With Sigma2 = [[a, b], [b, c]] and o its opacity, the
+ * pixels where o exp(-q/2) >= 1/255, q = d^T Sigma2^-1 d, form the ellipse
+ * q <= 2 ln(255 o).  The key path stores, per Gaussian, a conservative version
+ * of that ellipse from which every tile row's span of tiles follows (see
+ * orc_row_span in binning.c):
+ *   t      = (2 lnu(255 o) + 1/16) (1 + 2^-10),   lnu(x) >= ln(x) (orc_ln_up_f32)
+ *   mm     = c t                 (the ellipse's squared half-height)
+ *   ystar  = b sqrt(t / a)       (row offset of its right-most point)
+ *   s, k   = b / c, det / c^2    (row dy spans dx in s dy +- sqrt(k (mm - dy^2)))
+ *   padx/y = 1/4 + 2^-12 (|mu| + 2 r)   (rounding allowance, pixels)
+ * The 1/16 and 2^-10 margins absorb the rounding of o, of the conic and of
+ * the renderer's exponent, so a tile left out could never have passed the
+ * renderer's alpha test: images and gradients are those of rectangle binning.
  */
 #include <math.h>
 #include <string.h>
@@ -60,14 +76,32 @@ float orc_exp_f32(float x)
     return p * pow2i((int)n);
 }
 
+/*
+ * Upper bound of ln(x) for normal x > 0, exact to within 0.0141:
+ *   x = m 2^e with m in [1, 2) read from the bit pattern (exact), and
+ *   ln m <= (m - 1) / sqrt(m)  for m >= 1
+ * (the difference has derivative (sqrt(m) - 1)^2 / (2 m^1.5) >= 0 and is 0 at
+ * m = 1; at m = 2 it is 1/sqrt(2) - ln 2 = 0.0140).
+ */
+float orc_ln_up_f32(float x)
+{
+    uint32_t bits;
+    memcpy(&bits, &x, 4);
+    const int e = (int)(bits >> 23) - 127;
+    const uint32_t mb = (bits & 0x7fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    return (float)e * 0x1.62e430p-1f + (m - 1.0f) / sqrtf(m);
+}
+
 static float fclampf(float v, float lo, float hi)
 {
     return fminf(fmaxf(v, lo), hi);
 }
 
 void orc_keypath(int N, const float* means, const float* log_scales, const float* quats,
-                 const orc_cam* cam, float* depth, float* mean2d, float* cov2d,
-                 int32_t* radius, int32_t* rect, int32_t* tiles)
+                 const float* opacity_raw, const orc_cam* cam, float* depth, float* mean2d, float* cov2d,
+                 int32_t* radius, int32_t* rect, int32_t* tiles, float* ell)
 {
     const float* V = cam->view;
     const int TX = (cam->W + ORC_TILE - 1) / ORC_TILE;
@@ -87,6 +121,7 @@ void orc_keypath(int N, const float* means, const float* log_scales, const float
         radius[i] = 0;
         rect[4 * i] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
         tiles[i] = 0;
+        for (int k = 0; k < 8; ++k) ell[8 * i + k] = 0.f;
         if (!(tz > cam->near_z)) continue;
 
         /* scales and unit quaternion (w, x, y, z) */
@@ -173,5 +208,22 @@ void orc_keypath(int N, const float* means, const float* log_scales, const float
         rect[4 * i + 2] = x1;
         rect[4 * i + 3] = y1;
         tiles[i] = nt;
+
+        /* tile ellipse */
+        const float o = 1.0f / (1.0f + orc_exp_f32(-opacity_raw[i]));
+        const float t = (2.0f * orc_ln_up_f32(255.0f * o) + 0.0625f) * 1.0009765625f;
+        float* E = ell + 8 * i;
+        E[0] = mx;
+        E[1] = my;
+        if (t > 0.f) {
+            E[2] = b / c;
+            E[3] = det / (c * c);
+            E[4] = c * t;
+            E[5] = b * sqrtf(t / a);
+        } else {
+            E[4] = -1.0f;   /* alpha < 1/255 everywhere: no tile */
+        }
+        E[6] = 0.25f + (fabsf(mx) + 2.0f * rf) * 0x1p-12f;
+        E[7] = 0.25f + (fabsf(my) + 2.0f * rf) * 0x1p-12f;
     }
 }

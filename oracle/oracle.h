@@ -44,9 +44,10 @@ typedef struct {
 
 /* keypath.c */
 float orc_exp_f32(float x);
+float orc_ln_up_f32(float x);
 void orc_keypath(int N, const float* means, const float* log_scales, const float* quats,
-                 const orc_cam* cam, float* depth, float* mean2d, float* cov2d,
-                 int32_t* radius, int32_t* rect, int32_t* tiles);
+                 const float* opacity_raw, const orc_cam* cam, float* depth, float* mean2d, float* cov2d,
+                 int32_t* radius, int32_t* rect, int32_t* tiles, float* ell /* [N][8] */);
 
 /* sh.c */
 int orc_sh_count(int deg);
@@ -64,10 +65,13 @@ void orc_project_bwd(int N, int deg, const double* means, const double* log_scal
                      double* d_opacity_raw, double* d_sh);
 
 /* binning.c */
+void orc_row_span(const float* E, const int32_t* r, int ty, int* xl, int* xr);
 int64_t orc_bin(int N, const orc_cam* cam, const float* depth, const int32_t* rect, const int32_t* tiles,
-                uint64_t* keys, uint32_t* vals, uint32_t* ranges);
+                const float* ell /* nullable: whole rectangles */, uint64_t* keys, uint32_t* vals,
+                uint32_t* ranges);
+int64_t orc_bin_count(int N, const int32_t* rect, const int32_t* tiles, const float* ell /* nullable */);
 int orc_tile_list(int N, const float* depth, const int32_t* rect, const int32_t* tiles,
-                  int tx, int ty, uint32_t* out);
+                  const float* ell /* nullable */, int tx, int ty, uint32_t* out);
 
 /* composite.c */
 void orc_render(const orc_cam* cam, int N, const uint32_t* vals, const uint32_t* ranges,

@@ -43,8 +43,11 @@ class LeGaussianGrads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat", "unc")]
 
 
+_PROJ_FIELDS = ("splat", "depth", "radius", "rect", "tiles_touched", "clamp_mask", "tile_ellipse")
+
+
 class LeProjected(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("splat", "depth", "radius", "rect", "tiles_touched", "clamp_mask")]
+    _fields_ = [(k, C.c_void_p) for k in _PROJ_FIELDS]
 
 
 class LeDecoder(C.Structure):
@@ -61,9 +64,9 @@ _P = C.c_void_p
 _SIG = {
     "le_preprocess": [C.POINTER(LeGaussians), C.POINTER(LeCamera), C.POINTER(LeProjected), _P],
     "le_bin_sort_workspace": [C.c_int32, C.c_int64, C.POINTER(C.c_size_t)],
-    "le_bin_sort": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, C.c_size_t, C.c_int64, _P, _P, _P,
+    "le_bin_sort": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, _P, C.c_size_t, C.c_int64, _P, _P, _P,
                     C.POINTER(C.c_int64), _P],
-    "le_bin_sort_static": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, C.c_int64, _P, _P, _P,
+    "le_bin_sort_static": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, C.c_int64, _P, _P, _P,
                            C.POINTER(C.c_int64), _P],
     "le_render_fwd": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "le_render_bwd": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P, _P, _P,
@@ -199,6 +202,7 @@ class Projected:
     rect: torch.Tensor           # [n,4] i16 (uint16 contents)
     tiles_touched: torch.Tensor  # [n] i32
     clamp_mask: torch.Tensor     # [n] u8
+    tile_ellipse: torch.Tensor   # [n,8] f32
 
     @staticmethod
     def empty(n: int, device="cuda") -> "Projected":
@@ -207,11 +211,12 @@ class Projected:
                          torch.empty(n, dtype=torch.int32, device=device),
                          torch.empty((n, 4), dtype=torch.int16, device=device),
                          torch.empty(n, dtype=torch.int32, device=device),
-                         torch.empty(n, dtype=torch.uint8, device=device))
+                         torch.empty(n, dtype=torch.uint8, device=device),
+                         torch.empty((n, 8), dtype=torch.float32, device=device))
 
     def struct(self) -> LeProjected:
         s = LeProjected()
-        for k in ("splat", "depth", "radius", "rect", "tiles_touched", "clamp_mask"):
+        for k in _PROJ_FIELDS:
             setattr(s, k, getattr(self, k).data_ptr())
         return s
 
@@ -267,8 +272,8 @@ def le_bin_sort(cam, proj: Projected, buffers: BinSortBuffers | None = None, k_c
     for _ in range(2):
         buffers.ensure(n, k_cap, ntiles, proj.depth.device, want_keys)
         K = C.c_int64()
-        st = load().le_bin_sort(C.byref(cs), n, _ptr(proj.depth), _ptr(proj.rect), _ptr(proj.tiles_touched),
-                                _ptr(buffers.ws), buffers.ws.numel(), buffers.k_cap, _ptr(buffers.ids),
+        st = load().le_bin_sort(C.byref(cs), n, _ptr(proj.depth), _ptr(proj.rect), _ptr(proj.tile_ellipse),
+                                _ptr(proj.tiles_touched), _ptr(buffers.ws), buffers.ws.numel(), buffers.k_cap, _ptr(buffers.ids),
                                 _ptr(buffers.keys) if want_keys else None, _ptr(buffers.ranges), C.byref(K),
                                 _stream())
         if st == LE_ERR_CAPACITY:
@@ -286,7 +291,8 @@ def le_bin_sort_static(cam, proj: Projected, sorted_ids, tile_ranges, sorted_key
     The caller provides the outputs; returns K."""
     K = C.c_int64()
     _check(load().le_bin_sort_static(C.byref(camera_struct(cam)), proj.depth.shape[0], _ptr(proj.depth),
-                                     _ptr(proj.rect), _ptr(proj.tiles_touched), sorted_ids.numel(),
+                                     _ptr(proj.rect), _ptr(proj.tile_ellipse), _ptr(proj.tiles_touched),
+                                     sorted_ids.numel(),
                                      _ptr(sorted_ids), _ptr(sorted_keys), _ptr(tile_ranges), C.byref(K), _stream()))
     return K.value
 

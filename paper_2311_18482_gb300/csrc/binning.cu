@@ -1,6 +1,11 @@
 // Tile binning: 64-bit (tile | depth) keys, their stable order and the per-tile
 // ranges of the 3DGS rasterizer the paper reuses (Sec. 4).
 //
+// A Gaussian is copied to the tiles of its rectangle that its tile ellipse
+// reaches (row_span below; the ellipse comes from the key path of
+// le_preprocess and is not in the paper): the renderer would skip it on every
+// pixel of the other tiles, so they only cost time.
+//
 // The order is that of a stable sort of key = (tile_id << 32) | bits(depth)
 // over the copies emitted Gaussian by Gaussian: inside each tile, copies are
 // ordered by depth, ties by Gaussian index.  It is computed without sorting the
@@ -8,7 +13,7 @@
 //   1. e[i] = bits(depth_i) << 32 | i          (culled: 0xFFFFFFFF, sorted last)
 //   2. stable LSD radix sort of e on bits 32..63 (4 passes over the N Gaussians)
 //   3. split the depth-sorted Gaussians into chunks; per chunk, the number of
-//      copies in every tile from a 2-D difference array of the rectangles
+//      copies in every tile from per-row difference arrays of the row spans
 //   4. one exclusive scan of those counts in tile-major order: entry (t, c) is
 //      where chunk c's copies of tile t start; the total is K; consecutive
 //      tiles' first entries are the tile ranges
@@ -286,49 +291,80 @@ __global__ void depth_elems_kernel(int n, const float* __restrict__ depth, const
     e[i] = ((uint64_t)hi << 32) | (uint32_t)i;
 }
 
-// Rectangles in depth order (zero for culled Gaussians), so the kernels below
-// stage them with coalesced loads.
+// Tiles [xl, xr) of rectangle row ty that the tile ellipse {e0, e1} reaches.
+// The ellipse is convex, so its tiles in a row are contiguous.  For the row's
+// band of pixel-centre offsets dy in [lo, hi], the right end s dy + sqrt(k (mm -
+// dy^2)) of a row is concave in dy with its peak at ystar, so the band's
+// right-most point is at clamp(ystar, lo, hi), its left-most (mirror image) at
+// clamp(-ystar, lo, hi).  Every operation is an explicit IEEE FP32 one, in a
+// fixed order, so that every implementation gets the same integers.
+__device__ __forceinline__ void row_span(const float4 e0, const float4 e1, const ushort4 r, int ty, int& xl, int& xr)
+{
+    xl = xr = r.x;
+    const float yc = __fsub_rn((float)(16 * ty), e0.y);
+    const float lo = __fsub_rn(yc, e1.w);
+    const float hi = __fadd_rn(__fadd_rn(yc, 15.0f), e1.w);
+    const float dR = fminf(fmaxf(e1.y, lo), hi);
+    const float dL = fminf(fmaxf(-e1.y, lo), hi);
+    const float vR = __fsub_rn(e1.x, __fmul_rn(dR, dR));
+    const float vL = __fsub_rn(e1.x, __fmul_rn(dL, dL));
+    if (!(vR >= 0.0f) || !(vL >= 0.0f)) return;
+    const float R = __fadd_rn(__fmul_rn(e0.z, dR), __fsqrt_rn(__fmul_rn(e0.w, vR)));
+    const float L = __fsub_rn(__fmul_rn(e0.z, dL), __fsqrt_rn(__fmul_rn(e0.w, vL)));
+    const float fl = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(__fadd_rn(e0.x, L), e1.z), 15.0f), 0.0625f));
+    const float fr = __fadd_rn(floorf(__fmul_rn(__fadd_rn(__fadd_rn(e0.x, R), e1.z), 0.0625f)), 1.0f);
+    const float x0 = (float)r.x, x1 = (float)r.z;
+    xl = (int)fminf(fmaxf(fl, x0), x1);
+    xr = (int)fminf(fmaxf(fr, x0), x1);
+    if (xr < xl) xr = xl;
+}
+
+// Rectangles and tile ellipses in depth order (zero for culled Gaussians), so
+// the kernels below read them with coalesced loads.
 __global__ void gather_rect_kernel(int n, const uint64_t* __restrict__ dsorted, const int* __restrict__ tiles,
-                                   const ushort4* __restrict__ rect, ushort4* __restrict__ drect)
+                                   const ushort4* __restrict__ rect, const float4* __restrict__ ell,
+                                   ushort4* __restrict__ drect, float4* __restrict__ dell)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint32_t gid = (uint32_t)dsorted[j];
-    drect[j] = tiles[gid] > 0 ? rect[gid] : make_ushort4(0, 0, 0, 0);
+    const bool vis = tiles[gid] > 0;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    drect[j] = vis ? rect[gid] : make_ushort4(0, 0, 0, 0);
+    dell[2 * j] = vis ? ell[2 * (size_t)gid] : z;
+    dell[2 * j + 1] = vis ? ell[2 * (size_t)gid + 1] : z;
 }
 
 // Copies of chunk c (depth-sorted Gaussians [c*chunk, (c+1)*chunk)) per tile,
-// via a 2-D difference array in shared memory: +1 / -1 at the four corners of
-// every rectangle, then prefix sums along x and y.  Written tile-major:
+// via per-row difference arrays in shared memory: +1 / -1 at both ends of every
+// row span, then a prefix sum along each row.  Written tile-major:
 // counts[t * nchunks + c].
-__global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* __restrict__ drect, int TX, int TY,
+__global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* __restrict__ drect,
+                                                          const float4* __restrict__ dell, int TX, int TY,
                                                           int chunk, int nchunks, uint32_t* __restrict__ counts)
 {
     extern __shared__ int diff[];
-    const int W1 = TX + 1, cells = W1 * (TY + 1);
+    const int W1 = TX + 1, cells = W1 * TY;
     for (int i = threadIdx.x; i < cells; i += blockDim.x) diff[i] = 0;
     __syncthreads();
     const int j0 = blockIdx.x * chunk, j1 = min(n, j0 + chunk);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         const ushort4 r = drect[j];
         if (r.z <= r.x) continue;
-        atomicAdd(&diff[r.y * W1 + r.x], 1);
-        atomicAdd(&diff[r.y * W1 + r.z], -1);
-        atomicAdd(&diff[r.w * W1 + r.x], -1);
-        atomicAdd(&diff[r.w * W1 + r.z], 1);
+        const float4 e0 = dell[2 * j], e1 = dell[2 * j + 1];
+        for (int ty = r.y; ty < r.w; ++ty) {
+            int xl, xr;
+            row_span(e0, e1, r, ty, xl, xr);
+            if (xr > xl) {
+                atomicAdd(&diff[ty * W1 + xl], 1);
+                atomicAdd(&diff[ty * W1 + xr], -1);
+            }
+        }
     }
     __syncthreads();
     for (int y = threadIdx.x; y < TY; y += blockDim.x) {
         int run = 0;
         for (int x = 0; x < TX; ++x) {
-            run += diff[y * W1 + x];
-            diff[y * W1 + x] = run;
-        }
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < TX; x += blockDim.x) {
-        int run = 0;
-        for (int y = 0; y < TY; ++y) {
             run += diff[y * W1 + x];
             diff[y * W1 + x] = run;
         }
@@ -344,9 +380,10 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
 // tile (row, tx) starts at base[t * nchunks + C*cs] -- the exclusive scan of the
 // counts in tile-major order -- and lives in a register of lane tx % 32 of the
 // row's warp, so no two threads share a cursor and no barrier is needed between
-// Gaussians.  A warp takes the super-chunk's Gaussians 32 at a time, keeps (by
-// ballot) those whose rectangle covers its row and, for each in depth order,
-// every lane whose tiles fall in the rectangle writes them.  Only one cursor per
+// Gaussians.  A warp takes the super-chunk's Gaussians 32 at a time; each lane
+// computes the row span of its Gaussian (when its rectangle covers the row), a
+// ballot keeps the non-empty ones and, for each in depth order, every lane
+// whose tiles fall in the span writes them.  Only one cursor per
 // (tile, block) advances at a time, so the partly written output sectors stay
 // few enough to remain in L2.
 constexpr int kPlaceThreads = 256;
@@ -355,6 +392,7 @@ constexpr int kPlaceRows = kPlaceThreads / 32;
 template <int NK>
 __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint64_t* __restrict__ dsorted,
                                                               const ushort4* __restrict__ drect,
+                                                              const float4* __restrict__ dell,
                                                               const float* __restrict__ depth, int TX, int TY,
                                                               int super_chunk, int cstride, int nchunks,
                                                               const uint32_t* __restrict__ base,
@@ -384,22 +422,25 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
         if (!row_ok) continue;
         const int m = min(kPlaceThreads, j1 - jb);
         for (int q0 = 0; q0 < m; q0 += 32) {
-            bool mine = false;
+            int xl = 0, xr = 0;
             if (q0 + lane < m) {
                 const ushort4 r = sr[q0 + lane];
-                mine = r.z > r.x && r.y <= row && row < r.w;
+                if (r.z > r.x && r.y <= row && row < r.w) {
+                    const size_t jj = (size_t)(jb + q0 + lane);
+                    row_span(__ldg(dell + 2 * jj), __ldg(dell + 2 * jj + 1), r, row, xl, xr);
+                }
             }
-            uint32_t mask = __ballot_sync(0xffffffffu, mine);
+            uint32_t mask = __ballot_sync(0xffffffffu, xr > xl);
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const ushort4 r = sr[q0 + b];
+                const int bl = __shfl_sync(0xffffffffu, xl, b), br = __shfl_sync(0xffffffffu, xr, b);
                 const uint32_t gid = sg[q0 + b];
                 const uint32_t dbits = keys ? __float_as_uint(depth[gid]) : 0u;
 #pragma unroll
                 for (int k = 0; k < NK; ++k) {
                     const int tx = lane + 32 * k;
-                    if (tx >= r.x && tx < r.z) {
+                    if (tx >= bl && tx < br) {
                         const uint32_t pos = ctr[k];
                         ids[pos] = gid;
                         if (keys) keys[pos] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | dbits;
@@ -426,6 +467,7 @@ constexpr int kMaxTiles = 16384;
 struct SortWs {
     uint64_t *eA, *eB;
     ushort4* drect;
+    float4* dell;
     uint32_t *counts, *base, *partials, *misc;
     int nchunks, chunk;
     size_t bytes;
@@ -443,7 +485,7 @@ __host__ __device__ constexpr size_t seg(size_t bytes) { return (bytes + 255) / 
 // Scratch layout of le_bin_sort for n Gaussians (independent of the copy count).
 __host__ __device__ constexpr size_t sort_ws_bytes(int n)
 {
-    return seg(8ull * n) * 3 + seg(4ull * (256ull * ((n + kTile - 1) / kTile) + 1)) +
+    return seg(8ull * n) * 3 + seg(32ull * n) + seg(4ull * (256ull * ((n + kTile - 1) / kTile) + 1)) +
            seg(4ull * ((size_t)kMaxTiles * chunks_for(n) + 1)) +
            seg(4ull * (((size_t)kMaxTiles * chunks_for(n) + 1 > 256ull * ((n + kTile - 1) / kTile) + 1
                             ? (size_t)kMaxTiles * chunks_for(n) + 1
@@ -470,6 +512,7 @@ SortWs sort_ws_layout(char* base, int32_t n)
     w.eA = (uint64_t*)take(8ull * n);
     w.eB = (uint64_t*)take(8ull * n);
     w.drect = (ushort4*)take(8ull * n);
+    w.dell = (float4*)take(32ull * n);
     w.counts = (uint32_t*)take(4ull * radix_len);
     w.base = (uint32_t*)take(4ull * count_len);
     w.partials = (uint32_t*)take(4ull * (scan_max / kTile + 2));
@@ -514,7 +557,8 @@ extern "C" le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* byt
 }
 
 extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
-                                 const int32_t* tiles_touched, void* workspace, size_t workspace_bytes, int64_t k_cap,
+                                 const float* tile_ellipse, const int32_t* tiles_touched, void* workspace,
+                                 size_t workspace_bytes, int64_t k_cap,
                                  uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
                                  void* stream)
 {
@@ -522,11 +566,12 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     if (st != LE_OK) return st;
     LE_CHECK_ARG(n >= 0 && k_cap >= 0 && k_cap < (int64_t)1 << 31, "n or k_cap out of range");
     LE_CHECK_ARG(k_out != nullptr && tile_ranges != nullptr, "k_out and tile_ranges are required");
-    LE_CHECK_ARG(n == 0 || (depth && rect && tiles_touched), "null input pointer");
+    LE_CHECK_ARG(n == 0 || (depth && rect && tile_ellipse && tiles_touched), "null input pointer");
     LE_CHECK_ARG(k_cap == 0 || sorted_ids, "sorted_ids is null");
     LE_CHECK_ARG(workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u) == 0,
                  "workspace must be non-null and 256-byte aligned");
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(rect) & 7u) == 0, "rect must be 8-byte aligned");
+    LE_CHECK_ARG((reinterpret_cast<uintptr_t>(tile_ellipse) & 15u) == 0, "tile_ellipse must be 16-byte aligned");
     const SortWs w = sort_ws_layout(static_cast<char*>(workspace), n);
     LE_CHECK_ARG(workspace_bytes >= w.bytes, "workspace too small: %zu < %zu", workspace_bytes, w.bytes);
     cudaStream_t s = as_stream(stream);
@@ -545,14 +590,15 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     LE_LAUNCHED();
     uint64_t *cur = w.eA, *alt = w.eB;
     if ((st = radix_sort(cur, alt, n, 32, 32, w, s)) != LE_OK) return st;
-    // 3: rectangles in depth order; copies per (tile, chunk of depth-sorted Gaussians)
+    // 3: rectangles and ellipses in depth order; copies per (tile, chunk of depth-sorted Gaussians)
     gather_rect_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cur, tiles_touched, reinterpret_cast<const ushort4*>(rect),
-                                                       w.drect);
+                                                       reinterpret_cast<const float4*>(tile_ellipse), w.drect,
+                                                       w.dell);
     LE_LAUNCHED();
-    const size_t diff_smem = sizeof(int) * (TX + 1) * (TY + 1);
+    const size_t diff_smem = sizeof(int) * (TX + 1) * TY;
     if (diff_smem > 48 * 1024)
         LE_CUDA(cudaFuncSetAttribute(chunk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diff_smem));
-    chunk_count_kernel<<<w.nchunks, 256, diff_smem, s>>>(n, w.drect, TX, TY, w.chunk, w.nchunks, w.base);
+    chunk_count_kernel<<<w.nchunks, 256, diff_smem, s>>>(n, w.drect, w.dell, TX, TY, w.chunk, w.nchunks, w.base);
     LE_LAUNCHED();
     // 4: one exclusive scan in tile-major order gives every (tile, chunk) base and K
     const int len = ntiles * w.nchunks;
@@ -577,7 +623,8 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     const dim3 grid(ngroups, nsuper);
     const int nk = (TX + 31) / 32;
 #define LE_PLACE(NK)                                                                                             \
-    place_kernel<NK><<<grid, kPlaceThreads, 0, s>>>(n, cur, w.drect, depth, TX, TY, w.chunk * cs, cs, w.nchunks, \
+    place_kernel<NK><<<grid, kPlaceThreads, 0, s>>>(n, cur, w.drect, w.dell, depth, TX, TY, w.chunk * cs, cs,     \
+                                                    w.nchunks,                                                 \
                                                     w.base, sorted_ids, sorted_keys)
     switch (nk) {
         case 1: LE_PLACE(1); break;
@@ -635,8 +682,9 @@ le_status static_scratch(void** out)
 }  // namespace leg
 
 extern "C" le_status le_bin_sort_static(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
-                                        const int32_t* tiles_touched, int64_t k_cap, uint32_t* sorted_ids,
-                                        uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out, void* stream)
+                                        const float* tile_ellipse, const int32_t* tiles_touched, int64_t k_cap,
+                                        uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges,
+                                        int64_t* k_out, void* stream)
 {
     LE_CHECK_ARG(n >= 0 && n <= kStaticMaxN, "n = %d exceeds the static-scratch limit of %d Gaussians", n,
                  kStaticMaxN);
@@ -651,8 +699,8 @@ extern "C" le_status le_bin_sort_static(const le_camera* cam, int32_t n, const f
     }
     void* ws = nullptr;
     if ((st = static_scratch(&ws)) != LE_OK) return st;
-    st = le_bin_sort(cam, n, depth, rect, tiles_touched, ws, sizeof(g_static_scratch), k_cap, sorted_ids, sorted_keys,
-                     tile_ranges, k_out, stream);
+    st = le_bin_sort(cam, n, depth, rect, tile_ellipse, tiles_touched, ws, sizeof(g_static_scratch), k_cap,
+                     sorted_ids, sorted_keys, tile_ranges, k_out, stream);
     if (st == LE_ERR_CAPACITY && k_out && *k_out > kStaticMaxK)
         set_error("instance count K = %lld exceeds the static-scratch limit of %lld tile copies",
                   (long long)*k_out, (long long)kStaticMaxK);

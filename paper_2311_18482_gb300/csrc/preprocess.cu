@@ -48,7 +48,7 @@ __device__ __forceinline__ float dot3(float a0, float b0, float a1, float b1, fl
 struct KeyGeom {
     float tx, ty, tz, xn, yn, xc, yc, inv_tz;
     float s[3], q[4], qnorm_inv, R[3][3], M[3][3], S[3][3], T0[3], T1[3];
-    float a, b, c, det, mx, my;
+    float a, b, c, det, mx, my, rf;
     float limx, limy;
     int radius, x0, y0, x1, y1;
     bool visible;
@@ -141,7 +141,44 @@ __device__ __forceinline__ void key_geometry(const CamParams& cam, float px, flo
     g.y1 = (int)fminf(fmaxf(floorf(__fmul_rn(__fadd_rn(__fadd_rn(g.my, rf), 15.0f), 0.0625f)), 0.f), TYf);
     if ((g.x1 - g.x0) * (g.y1 - g.y0) <= 0) return;
     g.radius = (int)rf;
+    g.rf = rf;
     g.visible = true;
+}
+
+// Upper bound of ln(x), normal x > 0, within 0.0141 of it: x = m 2^e with m in
+// [1, 2) taken from the bit pattern, and ln m <= (m - 1)/sqrt(m) for m >= 1
+// (equality at m = 1; the gap grows to 1/sqrt(2) - ln 2 at m = 2).
+__device__ __forceinline__ float kp_ln_up(float x)
+{
+    const uint32_t bits = __float_as_uint(x);
+    const int e = (int)(bits >> 23) - 127;
+    const float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+    return __fadd_rn(__fmul_rn((float)e, 0x1.62e430p-1f), __fdiv_rn(__fsub_rn(m, 1.0f), __fsqrt_rn(m)));
+}
+
+// Tile ellipse of a visible Gaussian (key path; binning uses it to skip the
+// rect tiles it cannot reach).  Pixels with o exp(-q/2) >= 1/255 satisfy
+// q <= 2 ln(255 o); t bounds that from above with a margin of 1/16 and a factor
+// 1 + 2^-10 that absorb the rounding of o, the conic and the renderer's exp.
+// Stored as {mx, my, s, k} {mm, ystar, padx, pady}: a row at offset dy spans
+// dx in s dy -+ sqrt(k (mm - dy^2)), mm = c t is the squared half-height and
+// ystar = b sqrt(t/a) the row offset of the right-most point; the pads (in
+// pixels) cover the rounding of the span arithmetic.
+__device__ __forceinline__ void key_ellipse(const KeyGeom& g, float opacity_raw, float4& e0, float4& e1)
+{
+    const float o = __fdiv_rn(1.0f, __fadd_rn(1.0f, kp_exp(-opacity_raw)));
+    const float t = __fmul_rn(__fadd_rn(__fmul_rn(2.0f, kp_ln_up(__fmul_rn(255.0f, o))), 0.0625f), 1.0009765625f);
+    e0 = make_float4(g.mx, g.my, 0.f, 0.f);
+    e1 = make_float4(-1.0f, 0.f, 0.f, 0.f);
+    if (t > 0.f) {
+        e0.z = __fdiv_rn(g.b, g.c);
+        e0.w = __fdiv_rn(g.det, __fmul_rn(g.c, g.c));
+        e1.x = __fmul_rn(g.c, t);
+        e1.y = __fmul_rn(g.b, __fsqrt_rn(__fdiv_rn(t, g.a)));
+    }
+    const float r2 = __fmul_rn(2.0f, g.rf);
+    e1.z = __fadd_rn(0.25f, __fmul_rn(__fadd_rn(fabsf(g.mx), r2), 0x1p-12f));
+    e1.w = __fadd_rn(0.25f, __fmul_rn(__fadd_rn(fabsf(g.my), r2), 0x1p-12f));
 }
 
 // ----------------------------------------------------------------------------
@@ -235,7 +272,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(int n, const float* __r
                                                          const float* __restrict__ unc, CamParams cam,
                                                          float4* __restrict__ splat, float* __restrict__ depth,
                                                          int* __restrict__ radius, ushort4* __restrict__ rect,
-                                                         int* __restrict__ tiles, uint8_t* __restrict__ clamp)
+                                                         int* __restrict__ tiles, uint8_t* __restrict__ clamp,
+                                                         float4* __restrict__ ellipse)
 {
     constexpr int NC = (DEG + 1) * (DEG + 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,7 +294,15 @@ __global__ void __launch_bounds__(256) preprocess_kernel(int n, const float* __r
         rect[i] = make_ushort4(0, 0, 0, 0);
         tiles[i] = 0;
         clamp[i] = 0;
+        ellipse[2 * i] = z4;
+        ellipse[2 * i + 1] = z4;
         return;
+    }
+    {
+        float4 e0, e1;
+        key_ellipse(g, __ldg(opacity_raw + i), e0, e1);
+        ellipse[2 * i] = e0;
+        ellipse[2 * i + 1] = e1;
     }
     const float inv_det = 1.0f / g.det;
     const float A = g.c * inv_det, B = -g.b * inv_det, C = g.a * inv_det;
@@ -488,9 +534,11 @@ extern "C" le_status le_preprocess(const le_gaussians* g, const le_camera* cam, 
     if ((st = check_camera(cam)) != LE_OK) return st;
     LE_CHECK_ARG(out != nullptr, "projected is null");
     if (g->n == 0) return LE_OK;
-    LE_CHECK_ARG(out->splat && out->depth && out->radius && out->rect && out->tiles_touched && out->clamp_mask,
+    LE_CHECK_ARG(out->splat && out->depth && out->radius && out->rect && out->tiles_touched && out->clamp_mask &&
+                     out->tile_ellipse,
                  "null projected pointer");
-    LE_CHECK_ARG(aligned16(out->splat), "splat must be 16-byte aligned");
+    LE_CHECK_ARG(aligned16(out->splat) && aligned16(out->tile_ellipse),
+                 "splat and tile_ellipse must be 16-byte aligned");
     LE_CHECK_ARG(aligned16(out->rect) || (reinterpret_cast<uintptr_t>(out->rect) & 7u) == 0,
                  "rect must be 8-byte aligned");
     const CamParams cp = cam_params(cam);
@@ -501,7 +549,8 @@ extern "C" le_status le_preprocess(const le_gaussians* g, const le_camera* cam, 
                                                       g->sh, g->feat, g->unc, cp,                            \
                                                       reinterpret_cast<float4*>(out->splat), out->depth,     \
                                                       out->radius, reinterpret_cast<ushort4*>(out->rect),    \
-                                                      out->tiles_touched, out->clamp_mask)
+                                                      out->tiles_touched, out->clamp_mask,                   \
+                                                      reinterpret_cast<float4*>(out->tile_ellipse))
     switch (g->sh_degree) {
         case 0: LE_PRE(0); break;
         case 1: LE_PRE(1); break;

@@ -276,17 +276,21 @@ def test_binning_invariants(orc):
     sc, cam = c["scene"], c["camera"]
     kp = orc.keypath(sc, cam)
     keys, vals, ranges = orc.bin(cam, kp)
-    assert len(keys) == kp["tiles"].sum()
     assert np.all(keys[1:] >= keys[:-1])
-    # multiset of (tile, id) equals the rectangle enumeration
+    # multiset of (tile, id) equals the enumeration of every rectangle row's span
     want = []
     for i in np.nonzero(kp["tiles"] > 0)[0]:
         x0, y0, x1, y1 = kp["rect"][i]
         for ty in range(y0, y1):
-            for tx in range(x0, x1):
-                want.append((ty * cam.tiles_x + tx, i))
+            xl, xr = orc.row_span(kp, i, ty)
+            assert x0 <= xl <= xr <= x1
+            want.extend((ty * cam.tiles_x + tx, i) for tx in range(xl, xr))
     got = sorted(zip((keys >> np.uint64(32)).astype(np.int64).tolist(), vals.tolist()))
     assert got == sorted(want)
+    # without the ellipse: the whole rectangles
+    keys_r, vals_r, _ = orc.bin(cam, kp, ellipse=False)
+    assert len(keys_r) == kp["tiles"].sum() > len(keys)
+    assert orc.bin_count(kp) == len(keys) and orc.bin_count(kp, ellipse=False) == len(keys_r)
     # low word is the depth's float bits
     assert np.array_equal((keys & np.uint64(0xFFFFFFFF)).astype(np.uint32), kp["depth"].view(np.uint32)[vals])
     # ranges partition the sorted list by tile id
@@ -304,6 +308,88 @@ def test_binning_invariants(orc):
         v = vals[s:e]
         same = k[1:] == k[:-1]
         assert np.all(v[1:][same] > v[:-1][same])
+
+
+# --------------------------------------------------------------------------- tile ellipse
+def test_ln_up_bounds_ln(orc):
+    xs = np.concatenate([np.geomspace(1e-3, 300.0, 20001), 2.0 ** np.arange(-9, 9),
+                         np.nextafter(2.0 ** np.arange(-9, 9), 0)]).astype(np.float32)
+    got = np.array([orc.ln_up_f32(float(x)) for x in xs], np.float64)
+    ref = np.log(xs.astype(np.float64))
+    assert np.all(got >= ref - 2e-6)                 # an upper bound up to FP32 rounding
+    assert np.max(got - ref) < 0.0141                # and within 1/sqrt(2) - ln 2
+    assert abs(orc.ln_up_f32(1.0)) == 0.0
+
+
+def _aniso_scene(n, seed):
+    rng = np.random.default_rng(seed)
+    means = np.stack([rng.uniform(-1.2, 1.2, n), rng.uniform(-0.9, 0.9, n), rng.uniform(2.0, 4.0, n)], 1)
+    ls = np.stack([rng.normal(-2.2, 0.6, n), rng.normal(-3.5, 0.6, n), rng.normal(-3.0, 0.5, n)], 1)
+    q = rng.standard_normal((n, 4))
+    o = np.concatenate([rng.uniform(0.003, 0.999, n - 8), [1 / 255 * 0.9, 1 / 255 * 1.01, 0.999, 0.9995,
+                                                          0.01, 0.02, 0.5, 0.99]])
+    sc = tiny_scene(means, ls, quats=q / np.linalg.norm(q, axis=1, keepdims=True), opacity=o)
+    return sc
+
+
+def test_tile_ellipse_complete_and_tight(orc):
+    """Every tile with a pixel at alpha >= 1/255 (FP64) is binned; every binned
+    tile's box, widened by half a pixel, reaches q <= 2 ln(255 o) + 0.2 (0.25 px grid)."""
+    W, H = 160, 128
+    cam = ident_camera(W, H, f=110.0)
+    sc = _aniso_scene(400, 3)
+    kp = orc.keypath(sc, cam)
+    pr = orc.project(sc, cam, kp["tiles"])
+    keys, vals, _ = orc.bin(cam, kp)
+    binned = set(zip((keys >> np.uint64(32)).astype(np.int64).tolist(), vals.tolist()))
+    TX = cam.tiles_x
+    n_rect = n_kept = 0
+    gx = np.arange(-0.5, 16.0, 0.25)
+    for i in np.nonzero(kp["tiles"] > 0)[0]:
+        A, B, Cc = pr["conic"][i]
+        mx, my = pr["mean2d"][i]
+        o = pr["opacity"][i]
+        lim = 2 * math.log(255 * o)
+        x0, y0, x1, y1 = kp["rect"][i]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                n_rect += 1
+                kept = (ty * TX + tx, i) in binned
+                n_kept += kept
+                px, py = np.meshgrid(np.arange(16.0) + 16 * tx, np.arange(16.0) + 16 * ty)
+                dx, dy = mx - px, my - py
+                alpha = o * np.exp(-0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy)
+                if alpha.max() >= 1 / 255:
+                    assert kept, (i, tx, ty, alpha.max())
+                if kept:
+                    qx, qy = np.meshgrid(gx + 16 * tx, gx + 16 * ty)
+                    ex, ey = mx - qx, my - qy
+                    qmin = (A * ex * ex + 2 * B * ex * ey + Cc * ey * ey).min()
+                    assert qmin <= lim + 0.2, (i, tx, ty, qmin, lim)
+    assert n_kept < 0.8 * n_rect
+
+
+def test_ellipse_binning_renders_like_rectangles(orc):
+    """Left-out tiles hold no pixel with alpha >= 1/255, so images, transmittance
+    and all gradients equal those of whole-rectangle binning exactly (FP64)."""
+    W, H = 160, 128
+    cam = ident_camera(W, H, f=110.0, bg=(0.1, 0.2, 0.3))
+    sc = _aniso_scene(400, 4)
+    kp = orc.keypath(sc, cam)
+    pr = orc.project(sc, cam, kp["tiles"])
+    _, ve, re_ = orc.bin(cam, kp)
+    _, vr, rr = orc.bin(cam, kp, ellipse=False)
+    assert len(ve) < len(vr)
+    ie, ir = orc.render(cam, sc, pr, ve, re_), orc.render(cam, sc, pr, vr, rr)
+    for k in ("rgb", "feat", "unc", "T", "flip"):
+        assert np.array_equal(ie[k], ir[k]), k
+    assert np.all(ie["n_contrib"] <= ir["n_contrib"])
+    rng = np.random.default_rng(1)
+    dr, df, du = rng.standard_normal((3, H, W)), rng.standard_normal((8, H, W)), rng.standard_normal((H, W))
+    ge = orc.render_bwd(cam, sc, pr, ve, re_, dr, df, du)
+    gr = orc.render_bwd(cam, sc, pr, vr, rr, dr, df, du)
+    for k in ge:
+        assert np.array_equal(ge[k], gr[k]), k
 
 
 # --------------------------------------------------------------------------- backward: finite differences
