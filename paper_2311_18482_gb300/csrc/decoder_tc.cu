@@ -302,211 +302,496 @@ __global__ void __launch_bounds__(128 * NWG, 1) dec_fwd_kernel(DecArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Training.  One CTA per SM, persistent over tiles; 256 threads: the two
-// warpgroups serve the same 128 rows (TMEM lanes) and split each epilogue by
-// columns.  TMEM: working 128 columns + the three weight-gradient accumulators.
-constexpr uint32_t kAcc3 = 128, kAcc2 = 288, kAcc1 = 384;   // TMEM columns (32-aligned)
-constexpr int kC1 = 16, kCH1 = 80, kCH2 = 144, kCD = 128;   // buffer widths (with ones columns)
+// Training.  One CTA per SM, persistent over tiles and warp-specialised: warp
+// 16 issues every MMA; warpgroups 0-3 run the epilogues of two tiles in flight
+// (slot s = warpgroups 2s and 2s+1, which serve the same 128 rows and split
+// every epilogue by columns), so the tensor core works on one slot while the
+// CUDA cores finish the other.  Per tile, six MMA stages alternate with six
+// epilogues (z = logits, dz = dL/dz etc.):
+//   S1  h1 = X1 W1^T                                E1  bias, ReLU -> H1; ReLU mask kept in registers
+//   S2  h2 = H1 W2^T                                E2  bias, ReLU -> H2; mask
+//   S3  z  = H2 W3^T                                E3  softmax, CE (Eqs. 9-12) -> dz into D
+//   S4  dh2 = dz W3;  dW3 += dz^T h2;  db3 += dz^T 1   E4  mask -> dh2 into H2's buffer
+//   S5  dh1 = dh2 W2; dW2 += dh2^T h1; db2 += dh2^T 1  E5  mask -> dh1 into D
+//   S6  dx  = dh1 W1; [dW1 | db1] += dh1^T [x | 1]     E6  dx -> d_feat
+// dz, dh2 and dh1 are stored pixel-major: the input-gradient MMAs read them
+// K-major and the weight-gradient MMAs MN-major (contracting over the tile's
+// pixels).  Handshake per slot: its 256 epilogue threads arrive on ready[s]
+// once their operand is in shared memory and their TMEM reads are done; the
+// MMA thread waits, issues, and commits to done[s].  All MMAs come from one
+// thread, so the weight-gradient accumulations of both slots are ordered.
+// TMEM (512 columns): working accumulators [0,128) and [128,256); dW3
+// [256,384); dW2 [384,448); block P [448,464) holds db2 (column 0, again in 9)
+// and db3 (column 8); block Q [480,496) holds dW1 (columns 0-7) and db1 (8).
+// The ones operand E (128 pixels x 24, ones in columns 8 and 17) read from
+// column 0 sums over pixels into output column 8, read from column 8 into
+// columns 0 and 9 -- so db3 and db2 share block P without overlapping.
+constexpr int kTrainThreads = 4 * 128 + 32;
+constexpr uint32_t kTW3 = 256, kTW2 = 384, kTP = 448, kTQ = 480;
+constexpr int kEC = 24;
+
+// Shared-memory addresses of one slot's buffers (column counts 16, 64, 128, 128):
+// X1; H1; H2, later dh2; D: dz (and the softmax exchange), later dh1.
+constexpr uint32_t kSX1 = 0, kSH1 = sbuf_bytes(128, 16), kSH2 = kSH1 + sbuf_bytes(128, kH1),
+                   kSD = kSH2 + sbuf_bytes(128, 128), kSlotBytes = kSD + sbuf_bytes(128, 128);
+
+__host__ __device__ constexpr size_t train_slot_bytes() { return kSlotBytes; }
 
 __host__ constexpr size_t train_smem(int ncb)
 {
-    return weights_bytes(ncb) + sbuf_bytes(128, kC1) + sbuf_bytes(128, kCH1) + sbuf_bytes(128, kCH2) +
-           3 * sbuf_bytes(128, kCD) + 2 * 128 * 16 + 128;
+    return weights_bytes(ncb) + sbuf_bytes(128, kEC) + 2 * train_slot_bytes() + 128;
 }
 
-__global__ void __launch_bounds__(256, 1) dec_train_kernel(DecArgs a)
+// Issue MMA stage `st` (0-5) of the slot whose buffers start at shared address
+// q.  `init`: the first tile of this CTA, whose weight-gradient MMAs overwrite
+// their accumulators.
+__device__ __forceinline__ void train_stage(int st, int ncb, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t e,
+                                            uint32_t q, uint32_t tw, uint32_t tb, bool init)
 {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    Front f;
-    unsigned char* p = load_weights(sm, a, f);
-    f.X1 = SBuf{p, kC1};
-    p += sbuf_bytes(128, kC1);
-    f.H1 = SBuf{p, kCH1};
-    p += sbuf_bytes(128, kCH1);
-    f.H2 = SBuf{p, kCH2};
-    p += sbuf_bytes(128, kCH2);
-    const SBuf DZ{p, kCD}, DH2{p + sbuf_bytes(128, kCD), kCD}, DH1{p + 2 * sbuf_bytes(128, kCD), kCD};
-    p += 3 * sbuf_bytes(128, kCD);
-    f.xch = reinterpret_cast<float4*>(p);
-    p += 2 * 128 * 16;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);
-    uint32_t* slot = reinterpret_cast<uint32_t*>(p + 8);
-    f.mbar = mbar;
-    f.phase = 0;
-    f.tid = threadIdx.x & 127;
-    f.half = threadIdx.x >> 7;
-    f.nhalf = 2;
-    f.bar_id = 0;
-    f.nthreads = blockDim.x;
-    const int row = f.tid;
-    const bool leader = threadIdx.x == 0;
-    // constant columns of this row: ones for the bias gradients, zero padding
-    {
-        const float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (f.half == 0) {
-            sbuf_store8(f.H1, row, 64, one);
-            sbuf_store8(f.H1, row, 72, zero);
-            sbuf_store8(f.H2, row, 128, one);
-            sbuf_store8(f.H2, row, 136, zero);
-        } else {
-            for (int c = a.ncb; c < kCD; c += 8) sbuf_store8(DZ, row, c, zero);
-            for (int c = 64; c < kCD; c += 8) sbuf_store8(DH1, row, c, zero);
-        }
+    const uint32_t keep = init ? 0u : 1u;
+    const uint32_t x1 = q + kSX1, h1 = q + kSH1, h2 = q + kSH2, d = q + kSD;
+    switch (st) {
+        case 0:
+            mma(tw, kdesc_at(x1, 16, 0, 0), kdesc_at(w1, 16, 0, 0), idesc_bf16(kH1, false, false), 0);
+            break;
+        case 1:
+#pragma unroll
+            for (int k = 0; k < kH1 / 16; ++k)
+                mma(tw, kdesc_at(h1, kH1, 0, 16 * k), kdesc_at(w2, kH1, 0, 16 * k), idesc_bf16(kH2, false, false),
+                    k > 0);
+            break;
+        case 2:
+#pragma unroll
+            for (int k = 0; k < kH2 / 16; ++k)
+                mma(tw, kdesc_at(h2, 128, 0, 16 * k), kdesc_at(w3, 128, 0, 16 * k), idesc_bf16(ncb, false, false),
+                    k > 0);
+            break;
+        case 3:
+            for (int k = 0; k < ncb / 16; ++k)
+                mma(tw, kdesc_at(d, 128, 0, 16 * k), mndesc_at(w3, 128, 16 * k, 0), idesc_bf16(kH2, false, true),
+                    k > 0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                mma(tb + kTW3, mndesc_at(d, 128, 16 * k, 0), mndesc_at(h2, 128, 16 * k, 0),
+                    idesc_bf16(kH2, true, true), k > 0 ? 1u : keep);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                mma(tb + kTP, mndesc_at(d, 128, 16 * k, 0), mndesc_at(e, kEC, 16 * k, 0), idesc_bf16(16, true, true),
+                    k > 0 ? 1u : keep);
+            break;
+        case 4:
+#pragma unroll
+            for (int k = 0; k < kH2 / 16; ++k)
+                mma(tw, kdesc_at(h2, 128, 0, 16 * k), mndesc_at(w2, kH1, 16 * k, 0), idesc_bf16(kH1, false, true),
+                    k > 0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                mma(tb + kTW2, mndesc_at(h2, 128, 16 * k, 0), mndesc_at(h1, kH1, 16 * k, 0),
+                    idesc_bf16(kH1, true, true), k > 0 ? 1u : keep);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                mma(tb + kTP, mndesc_at(h2, 128, 16 * k, 0), mndesc_at(e, kEC, 16 * k, 8), idesc_bf16(16, true, true),
+                    1u);
+            break;
+        default:
+#pragma unroll
+            for (int k = 0; k < kH1 / 16; ++k)
+                mma(tw, kdesc_at(d, 128, 0, 16 * k), mndesc_at(w1, 16, 16 * k, 0), idesc_bf16(16, false, true), k > 0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                mma(tb + kTQ, mndesc_at(d, 128, 16 * k, 0), mndesc_at(x1, 16, 16 * k, 0), idesc_bf16(16, true, true),
+                    k > 0 ? 1u : keep);
+            break;
     }
-    if (leader) mbar_init(mbar, 1);
-    if (threadIdx.x < 32) tmem_alloc(slot, 512);
+}
+
+// The MMA thread: tile pairs in order, stage by stage, slot 0 then slot 1.
+__device__ __forceinline__ bool train_mma_loop(int ncb, const Front& f, uint32_t e, uint32_t slots,
+                                               uint64_t* ready, uint64_t* done, uint32_t tb, int ntiles)
+{
+    uint32_t ph[2] = {0u, 0u};
+    const uint32_t w1 = smem_u32(f.W1s.p), w2 = smem_u32(f.W2s.p), w3 = smem_u32(f.W3s.p);
+    for (int it = 0;; ++it) {
+        const int t0 = blockIdx.x + 2 * it * gridDim.x;
+        if (t0 >= ntiles) break;
+        const int nsl = t0 + (int)gridDim.x < ntiles ? 2 : 1;
+        for (int st = 0; st < 6; ++st)
+            for (int s = 0; s < nsl; ++s) {
+                if (!mbar_wait(ready + s, ph[s])) return false;
+                ph[s] ^= 1u;
+                fence_after();
+                train_stage(st, ncb, opaque(w1), opaque(w2), opaque(w3), opaque(e), opaque(slots + kSlotBytes * s),
+                            tb + 128u * s, tb, it == 0 && s == 0);
+                commit(done + s);
+            }
+    }
+    return true;
+}
+
+// Epilogue thread state: slot s (buffers at shared address sb), half h of the
+// columns, tile row `row`.
+struct EpiCtx {
+    uint32_t sb;
+    uint64_t *ready, *done;
+    uint32_t tw, lanef, ph;
+    int s, h, row, bar_id;
+};
+
+__device__ __forceinline__ void epi_signal(const EpiCtx& e)
+{
     fence_proxy_async();
     fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(slot);
-    f.tw = tbase;
-    f.lane = (uint32_t)(32 * (row >> 5)) << 16;
+    mbar_arrive(e.ready);
+}
 
-    const int ntiles = (a.P + 127) / 128;
-    float acc_ce = 0.f, acc_u = 0.f;
-    bool any = false;
-    int c0, c1;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+// Wait for the slot's MMAs; the outcome is made uniform over the slot's 256
+// threads, so a timeout never leaves part of them at the exchange barrier.
+__device__ __forceinline__ bool epi_wait(EpiCtx& e)
+{
+    const bool ok = !bar_any(e.bar_id, 256, !mbar_wait(e.done, e.ph));
+    e.ph ^= 1u;
+    fence_after();
+    return ok;
+}
+
+// Byte offset of exchange entry i (0-255) in the 128-column canonical buffer D:
+// the 16-byte chunk (row 8 (i/16) + i%8, columns 8 ((i/8)%2) ...), i.e. every
+// entry lies in columns [0, 16).
+__device__ __forceinline__ uint32_t xch_off(int i)
+{
+    return (uint32_t)((i >> 4) * 2048 + ((i >> 3) & 1) * 128 + (i & 7) * 16);
+}
+
+__device__ __forceinline__ float4 ld_bias4(const float* b, int c) { return *reinterpret_cast<const float4*>(b + c); }
+
+// bias + ReLU over 16 columns starting at c: v <- relu(v + b); bit j of the
+// result = (v_j > 0)
+__device__ __forceinline__ uint32_t bias_relu16(float* v, const float* b, int c)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < 16; j += 4) {
+        const float4 bb = ld_bias4(b, c + j);
+        const float bj[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float x = v[j + i] + bj[i];
+            m |= (x > 0.f ? 1u : 0u) << (j + i);
+            v[j + i] = fmaxf(x, 0.f);
+        }
+    }
+    return m;
+}
+
+__device__ __forceinline__ void mask16(float* v, uint32_t m)
+{
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = (m >> j) & 1u ? v[j] : 0.f;
+}
+
+// 16 columns [c, c + 16) of row `row` of the C-column buffer at shared address b.
+__device__ __forceinline__ void store16(uint32_t b, int C, int row, int c, const float* v)
+{
+    sts_bf16x8(b + sbuf_off(row, c, C), v);
+    sts_bf16x8(b + sbuf_off(row, c + 8, C), v + 8);
+}
+
+// v[idx] for a runtime idx in [0, 16), by a select tree over the index bits
+// (keeps v in registers).
+__device__ __forceinline__ float select16(const float* v, int idx)
+{
+    float t8[8], t4[4], t2[2];
+    const bool b0 = idx & 1, b1 = idx & 2, b2 = idx & 4, b3 = idx & 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t8[i] = b0 ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t4[i] = b1 ? t8[2 * i + 1] : t8[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) t2[i] = b2 ? t4[2 * i + 1] : t4[2 * i];
+    return b3 ? t2[1] : t2[0];
+}
+
+__device__ __forceinline__ void add_bias16(float* v, const float* b, int c)
+{
+#pragma unroll
+    for (int j = 0; j < 16; j += 4) {
+        const float4 bb = ld_bias4(b, c + j);
+        v[j] += bb.x;
+        v[j + 1] += bb.y;
+        v[j + 2] += bb.z;
+        v[j + 3] += bb.w;
+    }
+}
+
+__device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bias, EpiCtx& e, int ntiles,
+                                               float& acc_ce, float& acc_u)
+{
+    constexpr float kL2E = 1.4426950408889634f;
+    const int row = e.row, h = e.h;
+    const float *b1s = bias, *b2s = bias + kH1, *b3s = bias + kH1 + kH2;
+    const uint32_t tl = e.tw + e.lanef;
+    const int nu = a.ncb / 16, per = (nu + 1) / 2;
+    const int c0 = min(nu, h * per) * 16, c1 = min(nu, (h + 1) * per) * 16;   // this half's logit columns
+    float v[16];
+    for (int it = 0;; ++it) {
+        const int tile = blockIdx.x + (2 * it + e.s) * gridDim.x;
+        if (tile >= ntiles) break;
         const int px = tile * 128 + row;
         const bool valid = px < a.P;
-        if (!mlp_forward(f, a, px, valid)) { any = false; break; }
-        // softmax cross-entropy with uncertainty weighting (Eqs. 9-12)
+        const uint32_t sb = opaque(e.sb);
+        const uint32_t X1 = sb + kSX1, H1 = sb + kSH1, H2 = sb + kSH2, D = sb + kSD;
+        // X1 = [feat | 1 | 0]: the ones column gives db1
+        if (h == 0) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] = valid ? a.feat[(size_t)c * a.P + px] : 0.f;
+            sts_bf16x8(X1 + sbuf_off(row, 0, 16), v);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] = c == 0 ? 1.f : 0.f;
+            sts_bf16x8(X1 + sbuf_off(row, 8, 16), v);
+        }
         const float u = valid ? a.unc[px] : 0.f;
         const int t = valid ? a.target[px] : -1;
-        float lse, zt;
-        int am;
-        logits_lse(f, a.ncb, lse, am, t, zt);
+        epi_signal(e);
+        if (!epi_wait(e)) return false;
+        // E1: h1 columns [32h, 32h + 32), bits of the ReLU mask in m1
+        uint32_t m1 = 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            tmem_ld16(tl + 32 * h + 16 * k, v);
+            m1 |= bias_relu16(v, b1s, 32 * h + 16 * k) << (16 * k);
+            store16(H1, kH1, row, 32 * h + 16 * k, v);
+        }
+        epi_signal(e);
+        if (!epi_wait(e)) return false;
+        // E2: h2 columns [64h, 64h + 64), mask bits in m2a (first 32) and m2b
+        uint32_t m2a = 0, m2b = 0;
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            tmem_ld16(tl + 64 * h + 16 * k, v);
+            const uint32_t mk = bias_relu16(v, b2s, 64 * h + 16 * k);
+            if (k < 2) m2a |= mk << (16 * k);
+            else m2b |= mk << (16 * (k - 2));
+            store16(H2, 128, row, 64 * h + 16 * k, v);
+        }
+        epi_signal(e);
+        if (!epi_wait(e)) return false;
+        // E3: softmax over this half's logit columns [c0, c1).  Pass 1: max (and
+        // the target's logit); pass 2: e = exp(z - max), their sum, e parked in
+        // the free TMEM columns; exchange with the other half; pass 3: dz.
+        const int jt = t - c0;
+        const bool own_t = jt >= 0 && t < c1;
+        float mh = -INFINITY, zt_h = 0.f;
+#pragma unroll 1
+        for (int uu = 0; uu < 4; ++uu)
+            if (c0 + 16 * uu < c1) {
+                tmem_ld16(tl + c0 + 16 * uu, v);
+                add_bias16(v, b3s, c0 + 16 * uu);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) mh = fmaxf(mh, v[j]);
+                if (own_t && (jt >> 4) == uu) zt_h = select16(v, jt & 15);
+            }
+        const float mhl = mh * kL2E;
+        float sh = 0.f;
+#pragma unroll 1
+        for (int uu = 0; uu < 4; ++uu)
+            if (c0 + 16 * uu < c1) {
+                tmem_ld16(tl + c0 + 16 * uu, v);
+                add_bias16(v, b3s, c0 + 16 * uu);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = ex2_approx(fmaf(v[j], kL2E, -mhl));
+                    sh += v[j];
+                }
+                tmem_st16(tl + c0 + 16 * uu, v);
+            }
+        tmem_wait_st();
+        // the halves exchange (max, sum, target logit) through D's columns [0, 16),
+        // which pass 3 then overwrites with dz: no stale FP32 bits stay in D to
+        // reach an MMA (as bf16 they can be Inf or NaN)
+        float4 o;
+        asm volatile("st.shared.v4.f32 [%0], {%1,%2,%3,%4};" ::"r"(D + xch_off(h * 128 + row)), "f"(mh), "f"(sh),
+                     "f"(zt_h), "f"(0.f)
+                     : "memory");
+        asm volatile("bar.sync %0, 256;" ::"r"(e.bar_id) : "memory");
+        asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                     : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
+                     : "r"(D + xch_off((1 - h) * 128 + row))
+                     : "memory");
+        asm volatile("bar.sync %0, 256;" ::"r"(e.bar_id) : "memory");
+        const float m = fmaxf(mh, o.x);
+        const float ssum = (c0 < c1 ? sh * ex2_approx((mh - m) * kL2E) : 0.f) +
+                           (o.y > 0.f ? o.y * ex2_approx((o.x - m) * kL2E) : 0.f);
+        const float lse = m + __logf(ssum);
+        const float zt = own_t ? zt_h : o.z;
         const float ce = lse - zt;
-        // dL/dz * P (1/P applied when the gradients are written)
         const float w = valid ? a.lambda_ce * (1.f - u) : 0.f;
-        if (valid && f.half == 0) {
+        if (valid && h == 0) {
             a.d_unc[px] = (a.lambda_u - a.lambda_ce * ce) * a.invP;
             acc_ce += ce * (1.f - u);
             acc_u += u;
         }
-        float v[16], h[16];
-        my_cols(f, a.ncb, c0, c1);
-        for (int c = c0; c < c1; c += 16) {
-            tmem_ld16(f.tw + f.lane + c, v);
+        // dz * P (1/P is applied when the gradients are written)
+        const float scale = c0 < c1 ? w * ex2_approx((mh - m) * kL2E) / ssum : 0.f;
+#pragma unroll 1
+        for (int uu = 0; uu < 4; ++uu)
+            if (c0 + 16 * uu < c1) {
+                tmem_ld16(tl + c0 + 16 * uu, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = w * (__expf(v[j] + f.b3s[c + j] - lse) - (c + j == t ? 1.f : 0.f));
-            sbuf_store8(DZ, row, c, v);
-            sbuf_store8(DZ, row, c + 8, v + 8);
+                for (int j = 0; j < 16; ++j) v[j] *= scale;
+                store16(D, 128, row, c0 + 16 * uu, v);
+            }
+        if (own_t && valid) {
+            const float et = ex2_approx(fmaf(zt_h, kL2E, -mhl));
+            const __nv_bfloat16 bv = __float2bfloat16_rn(et * scale - w);
+            asm volatile("st.shared.b16 [%0], %1;" ::"r"(D + sbuf_off(row, t, 128)),
+                         "h"(*reinterpret_cast<const unsigned short*>(&bv))
+                         : "memory");
         }
-        wg_publish(f);
-        const uint32_t acc = any ? 1u : 0u;
-        if (leader) {
-            // dh2 = dz W3   (A = DZ K-major, B = W3 read MN-major)
-            for (int s = 0; s < a.ncb / 16; ++s)
-                mma(f.tw, kdesc(DZ, 0, 16 * s), mndesc(f.W3s, 16 * s, 0), idesc_bf16(kH2, false, true), s > 0);
-            // dW3 | db3 += dz^T [h2 | 1]   (both read MN-major, contraction over pixels)
-#pragma unroll
-            for (int s = 0; s < 8; ++s)
-                mma(tbase + kAcc3, mndesc(DZ, 16 * s, 0), mndesc(f.H2, 16 * s, 0), idesc_bf16(kCH2, true, true),
-                    s > 0 ? 1u : acc);
-            commit(f.mbar);
+        epi_signal(e);
+        if (!epi_wait(e)) return false;
+        // E4: dh2 = (dz W3) * [h2 > 0] into H2's buffer
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            tmem_ld16(tl + 64 * h + 16 * k, v);
+            mask16(v, (k < 2 ? m2a : m2b) >> (16 * (k & 1)));
+            store16(H2, 128, row, 64 * h + 16 * k, v);
         }
-        if (!wg_wait(f)) { any = false; break; }
-        // dh2 * [h2 > 0]
-        my_cols(f, kH2, c0, c1);
-        for (int c = c0; c < c1; c += 16) {
-            tmem_ld16(f.tw + f.lane + c, v);
-            sbuf_load8(f.H2, row, c, h);
-            sbuf_load8(f.H2, row, c + 8, h + 8);
+        epi_signal(e);
+        if (!epi_wait(e)) return false;
+        // E5: dh1 = (dh2 W2) * [h1 > 0] into D
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
-            sbuf_store8(DH2, row, c, v);
-            sbuf_store8(DH2, row, c + 8, v + 8);
+        for (int k = 0; k < 2; ++k) {
+            tmem_ld16(tl + 32 * h + 16 * k, v);
+            mask16(v, m1 >> (16 * k));
+            store16(D, 128, row, 32 * h + 16 * k, v);
         }
-        wg_publish(f);
-        if (leader) {
-#pragma unroll
-            for (int s = 0; s < kH2 / 16; ++s)
-                mma(f.tw, kdesc(DH2, 0, 16 * s), mndesc(f.W2s, 16 * s, 0), idesc_bf16(kH1, false, true), s > 0);
-#pragma unroll
-            for (int s = 0; s < 8; ++s)
-                mma(tbase + kAcc2, mndesc(DH2, 16 * s, 0), mndesc(f.H1, 16 * s, 0), idesc_bf16(kCH1, true, true),
-                    s > 0 ? 1u : acc);
-            commit(f.mbar);
-        }
-        if (!wg_wait(f)) { any = false; break; }
-        // dh1 * [h1 > 0]
-        my_cols(f, kH1, c0, c1);
-        for (int c = c0; c < c1; c += 16) {
-            tmem_ld16(f.tw + f.lane + c, v);
-            sbuf_load8(f.H1, row, c, h);
-            sbuf_load8(f.H1, row, c + 8, h + 8);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = h[j] > 0.f ? v[j] : 0.f;
-            sbuf_store8(DH1, row, c, v);
-            sbuf_store8(DH1, row, c + 8, v + 8);
-        }
-        wg_publish(f);
-        if (leader) {
-#pragma unroll
-            for (int s = 0; s < kH1 / 16; ++s)
-                mma(f.tw, kdesc(DH1, 0, 16 * s), mndesc(f.W1s, 16 * s, 0), idesc_bf16(16, false, true), s > 0);
-#pragma unroll
-            for (int s = 0; s < 8; ++s)
-                mma(tbase + kAcc1, mndesc(DH1, 16 * s, 0), mndesc(f.X1, 16 * s, 0), idesc_bf16(16, true, true),
-                    s > 0 ? 1u : acc);
-            commit(f.mbar);
-        }
-        if (!wg_wait(f)) { any = false; break; }
-        any = true;
-        if (f.half == 0) {
-            tmem_ld16(f.tw + f.lane, v);
+        epi_signal(e);
+        if (!epi_wait(e)) return false;
+        // E6: dx = dh1 W1 -> d_feat
+        if (h == 0) {
+            tmem_ld16(tl, v);
             if (valid)
 #pragma unroll
                 for (int c = 0; c < kD; ++c) a.d_feat[(size_t)c * a.P + px] = v[c] * a.invP;
         }
-        fence_before();
-        __syncthreads();
     }
-    // flush the weight-gradient accumulators (row = this thread's TMEM lane, columns split by half)
-    if (any) {
-        float v[16];
-        my_cols(f, kCH2, c0, c1);
-        for (int c = c0; c < c1; c += 16) {
-            tmem_ld16(tbase + kAcc3 + f.lane + c, v);
-            if (row < a.ncb)
-                for (int j = 0; j < 16; ++j) {
-                    const int col = c + j;
-                    if (col < kH2) atomicAdd(a.dW3 + (size_t)row * kH2 + col, v[j] * a.invP);
-                    else if (col == kH2) atomicAdd(a.db3 + row, v[j] * a.invP);
-                }
-        }
-        my_cols(f, kCH1, c0, c1);
-        for (int c = c0; c < c1; c += 16) {
-            tmem_ld16(tbase + kAcc2 + f.lane + c, v);
-            for (int j = 0; j < 16; ++j) {
-                const int col = c + j;
-                if (col < kH1) atomicAdd(a.dW2 + (size_t)row * kH1 + col, v[j] * a.invP);
-                else if (col == kH1) atomicAdd(a.db2 + row, v[j] * a.invP);
+    return true;
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1) dec_train_kernel(DecArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    Front f;
+    unsigned char* p = load_weights(sm, a, f);
+    const SBuf E{p, kEC};
+    p += sbuf_bytes(128, kEC);
+    unsigned char* slots = p;
+    const uint32_t slots_a = smem_u32(slots);
+    p += 2 * train_slot_bytes();
+    uint64_t* ready = reinterpret_cast<uint64_t*>(p);
+    uint64_t* done = ready + 2;
+    uint64_t* fin = ready + 4;
+    uint32_t* slot_addr = reinterpret_cast<uint32_t*>(ready + 5);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the slots start zeroed (padding columns feed MMA rows that are never read,
+    // and must hold finite values); E has ones in columns 8 and 17
+    for (size_t i = threadIdx.x; i < 2 * train_slot_bytes() / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(slots)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = threadIdx.x; i < 128 * (kEC / 8); i += blockDim.x) {
+        const int r = i / (kEC / 8), cb = i % (kEC / 8);
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (cb == 1) v[0] = 1.f;
+        if (cb == 2) v[1] = 1.f;
+        sbuf_store8(E, r, 8 * cb, v);
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(ready, 256);
+        mbar_init(ready + 1, 256);
+        mbar_init(done, 1);
+        mbar_init(done + 1, 1);
+        mbar_init(fin, 1);
+    }
+    if (warp == 0) tmem_alloc(slot_addr, 512);
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tb = *reinterpret_cast<volatile uint32_t*>(slot_addr);
+    const int ntiles = (a.P + 127) / 128;
+    bool ok = true;
+    float acc_ce = 0.f, acc_u = 0.f;
+    if (warp == 16) {
+        if (lane == 0) {
+            ok = train_mma_loop(a.ncb, f, smem_u32(E.p), slots_a, ready, done, tb, ntiles);
+            if (ok) {
+                commit(fin);
+                ok = mbar_wait(fin, 0);
             }
         }
-        if (f.half == 0) {
-            tmem_ld16(tbase + kAcc1 + f.lane, v);
+    } else {
+        EpiCtx e;
+        e.s = warp >> 3;
+        e.h = (warp >> 2) & 1;
+        e.row = threadIdx.x & 127;
+        e.sb = slots_a + kSlotBytes * e.s;
+        e.ready = ready + e.s;
+        e.done = done + e.s;
+        e.tw = tb + 128u * e.s;
+        e.lanef = (uint32_t)(32 * (warp & 3)) << 16;
+        e.ph = 0;
+        e.bar_id = 1 + e.s;
+        ok = train_epilogue(a, f.b1s, e, ntiles, acc_ce, acc_u);
+    }
+    fence_before();
+    const bool bad = __syncthreads_or(!ok);
+    fence_after();
+    if (bad) {
+        if (threadIdx.x == 0) atomicExch(&g_tc_error, 1);
+    } else if (warp < 16) {
+        // flush the weight-gradient accumulators: TMEM lane = this thread's row
+        const int row = threadIdx.x & 127, wg = warp >> 2;
+        const uint32_t lanef = (uint32_t)(32 * (warp & 3)) << 16;
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            tmem_ld16(tb + kTW3 + lanef + 32 * wg + 16 * k, v);
+            if (row < a.ncb)
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    atomicAdd(a.dW3 + (size_t)row * kH2 + 32 * wg + 16 * k + j, v[j] * a.invP);
+        }
+        tmem_ld16(tb + kTW2 + lanef + 16 * wg, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) atomicAdd(a.dW2 + (size_t)row * kH1 + 16 * wg + j, v[j] * a.invP);
+        if (wg == 0) {
+            tmem_ld16(tb + kTP + lanef, v);
+            atomicAdd(a.db2 + row, v[0] * a.invP);
+            if (row < a.ncb) atomicAdd(a.db3 + row, v[8] * a.invP);
+        } else if (wg == 1) {
+            tmem_ld16(tb + kTQ + lanef, v);
             if (row < kH1) {
+#pragma unroll
                 for (int j = 0; j < kD; ++j) atomicAdd(a.dW1 + (size_t)row * kD + j, v[j] * a.invP);
                 atomicAdd(a.db1 + row, v[kD] * a.invP);
             }
         }
     }
+    if (warp < 16) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        acc_ce += __shfl_xor_sync(0xffffffffu, acc_ce, o);
-        acc_u += __shfl_xor_sync(0xffffffffu, acc_u, o);
-    }
-    if ((threadIdx.x & 31) == 0 && f.half == 0) {
-        atomicAdd(a.loss, acc_ce * a.invP);
-        atomicAdd(a.loss + 1, acc_u * a.invP);
+        for (int o = 16; o > 0; o >>= 1) {
+            acc_ce += __shfl_xor_sync(0xffffffffu, acc_ce, o);
+            acc_u += __shfl_xor_sync(0xffffffffu, acc_u, o);
+        }
+        if (lane == 0 && ((warp >> 2) & 1) == 0) {
+            atomicAdd(a.loss, acc_ce * a.invP);
+            atomicAdd(a.loss + 1, acc_u * a.invP);
+        }
     }
     fence_before();
     __syncthreads();
     fence_after();
-    if (threadIdx.x < 32) tmem_dealloc(tbase, 512);
+    if (warp == 0) tmem_dealloc(tb, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -738,7 +1023,7 @@ le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_
         le_status st = set_smem(dec_train_kernel, smem);
         if (st != LE_OK) return st;
         const int grid = ntiles < sm_count() ? ntiles : sm_count();
-        dec_train_kernel<<<grid, 256, smem, s>>>(a);
+        dec_train_kernel<<<grid, kTrainThreads, smem, s>>>(a);
         LE_LAUNCHED();
         return LE_OK;
     }
