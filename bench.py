@@ -114,15 +114,18 @@ STAGE_CALLS = {"preprocess": "le_preprocess (preprocess_kernel)",
                "bin_sort": "le_bin_sort (depth radix sort, chunk_count, scan, place_kernel)",
                "render_fwd": "le_render_fwd (render_fwd_kernel)",
                "decoder": "le_decode fused (dec_train_kernel)",
-               "render_bwd": "le_render_bwd (render_bwd_kernel + preprocess_bwd_kernel)",
-               "adam": "le_adam (adam_kernel x2)"}
+               "render_bwd": "le_render_bwd_adam (render_bwd_kernel + preprocess_bwd_kernel with the Gaussians' "
+                             "Adam step fused in)",
+               "adam": "le_adam (adam_kernel, decoder parameters)"}
 STAGE_SOURCES = {"preprocess": ["preprocess.cu"], "bin_sort": ["binning.cu"], "render_fwd": ["render.cu"],
-                 "decoder": ["decoder_tc.cu", "tc_common.cuh"], "render_bwd": ["render.cu", "preprocess.cu"],
-                 "adam": ["train.cu"]}
+                 "decoder": ["decoder_tc.cu", "tc_common.cuh"],
+                 "render_bwd": ["render.cu", "preprocess.cu", "common.cuh"], "adam": ["train.cu", "common.cuh"]}
 
 
 def stage_bytes(N, n_vis, K, P, T, nc, total_scalars):
-    """Compulsory HBM bytes per call of each stage (each input read once, each output written once)."""
+    """Compulsory HBM bytes per call of each stage (each input read once, each output written once).
+    render_bwd includes the Gaussians' Adam step fused into it: read m, v and the
+    parameters the projection does not read, write parameters, m and v."""
     par = 4 * (3 + 3 + 4 + 1 + 3 * nc + 8 + 1)          # all per-Gaussian parameters
     geo = 4 * (3 + 3 + 4 + 1 + 3 * nc)                  # parameters the projection reads
     return {
@@ -130,8 +133,9 @@ def stage_bytes(N, n_vis, K, P, T, nc, total_scalars):
         "bin_sort": N * (4 + 4) + n_vis * (8 + 32) + 4 * K + 8 * T,
         "render_fwd": 4 * K + 80 * n_vis + 56 * P,
         "decoder": (36 + 4 + 36) * P,
-        "render_bwd": 4 * K + 80 * n_vis + 104 * P + 80 * N + geo * N + 80 * N + par * N + 5 * N,
-        "adam": 28 * total_scalars,
+        "render_bwd": 4 * K + 80 * n_vis + 104 * P + 80 * N + geo * N + 80 * N + (par - geo) * N + 5 * par * N
+                      + 5 * N,
+        "adam": 28 * (total_scalars - par // 4 * N),
     }
 
 

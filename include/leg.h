@@ -215,6 +215,28 @@ le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, const le_pr
                         const float* dL_dunc, float* grad2d, const le_gaussian_grads* out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * le_render_bwd_adam -- le_render_bwd fused with the Adam step of Sec. 4 on
+ * the Gaussian parameters: the gradient of each parameter is applied where it
+ * is computed and never written to memory.  The arrays of g are updated in
+ * place (they must be writable device memory); m and v are the first and
+ * second moments, one array per field in the parameters' own layout; u is
+ * clamped to [0, 1] (Sec. 3.4.2), the other fields are not clamped.  The
+ * result equals le_render_bwd followed by le_adam on every field with the
+ * same hyperparameters, bit for bit.
+ *   adam: step >= 1 (bias corrections 1 - beta^step), lr, beta1, beta2, eps
+ * Errors: LE_ERR_INVALID_ARG (null/misaligned pointers, step < 1). */
+typedef struct le_adam_config {
+    int32_t step;
+    float lr, beta1, beta2, eps;
+} le_adam_config;
+
+le_status le_render_bwd_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                             const uint32_t* sorted_ids, const uint32_t* tile_ranges, const float* T_final,
+                             const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
+                             const float* dL_dunc, float* grad2d, const le_gaussian_grads* m,
+                             const le_gaussian_grads* v, const le_adam_config* adam, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Semantic decoder D_MLP (Eq. 8, eq:lem_dec; supp. Tab. dmlp): per-pixel MLP
  * d_in(=8) -> h1 -> h2 -> n_cb, ReLU, ReLU, linear.  FP32 device weights
  * [out][in] row-major (a 1x1 convolution's weight), 16-byte aligned. */

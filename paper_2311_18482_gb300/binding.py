@@ -43,6 +43,11 @@ class LeGaussianGrads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat", "unc")]
 
 
+class LeAdamConfig(C.Structure):
+    _fields_ = [("step", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float)]
+
+
 _PROJ_FIELDS = ("splat", "depth", "radius", "rect", "tiles_touched", "clamp_mask", "tile_ellipse")
 
 
@@ -71,6 +76,9 @@ _SIG = {
     "le_render_fwd": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "le_render_bwd": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P, _P, _P,
                       _P, _P, C.POINTER(LeGaussianGrads), _P],
+    "le_render_bwd_adam": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P, _P,
+                           _P, _P, _P, C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads),
+                           C.POINTER(LeAdamConfig), _P],
     "le_decode_workspace": [C.c_int32, C.c_int32, C.POINTER(LeDecoder), C.POINTER(C.c_size_t)],
     "le_decode": [C.c_int32, C.c_int32, _P, _P, C.POINTER(LeDecoder), _P, C.c_float, C.c_float, _P, _P, _P,
                   C.POINTER(LeDecoderGrads), _P, _P, _P, _P, C.c_size_t, _P],
@@ -330,6 +338,22 @@ def le_render_bwd(cam, g: Gaussians, proj: Projected, ids, ranges, img: Image, d
                                 _ptr(img.n_contrib), _ptr(dL_drgb.contiguous()), _ptr(dL_dfeat.contiguous()),
                                 _ptr(dL_dunc.contiguous()), _ptr(grad2d), C.byref(os_), _stream()))
     return grads, grad2d
+
+
+def le_render_bwd_adam(cam, g: Gaussians, proj: Projected, ids, ranges, img: Image, dL_drgb, dL_dfeat, dL_dunc,
+                       m: Gaussians, v: Gaussians, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                       grad2d=None):
+    """le_render_bwd with the Adam step fused in: updates g's tensors (and m, v) in place."""
+    grad2d = grad2d if grad2d is not None else torch.empty((g.n, SPLAT_STRIDE), dtype=torch.float32,
+                                                           device=g.means.device)
+    cs, gs, ps = camera_struct(cam), g.struct(), proj.struct()
+    ms, vs = grads_struct(m), grads_struct(v)
+    cfg = LeAdamConfig(int(step), lr, beta1, beta2, eps)
+    _check(load().le_render_bwd_adam(C.byref(cs), C.byref(gs), C.byref(ps), _ptr(ids), _ptr(ranges), _ptr(img.T),
+                                     _ptr(img.n_contrib), _ptr(dL_drgb.contiguous()), _ptr(dL_dfeat.contiguous()),
+                                     _ptr(dL_dunc.contiguous()), _ptr(grad2d), C.byref(ms), C.byref(vs),
+                                     C.byref(cfg), _stream()))
+    return grad2d
 
 
 def decoder_struct(W1, b1, W2, b2, W3, b3) -> LeDecoder:

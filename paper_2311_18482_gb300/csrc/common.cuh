@@ -48,6 +48,26 @@ inline int tiles_x(const le_camera* c) { return (c->width + LE_TILE - 1) / LE_TI
 inline int tiles_y(const le_camera* c) { return (c->height + LE_TILE - 1) / LE_TILE; }
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Adam (Kingma & Ba; Sec. 4 trains with it) with both bias corrections folded
+// in: step_size = lr / (1 - b1^t), inv_sqrt_c2 = 1 / sqrt(1 - b2^t).
+struct AdamParams {
+    float b1, b2, step_size, inv_sqrt_c2, eps;
+};
+
+// One element: m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+// p <- clamp(p - step_size m / (sqrt(v) inv_sqrt_c2 + eps), lo, hi).  A fixed
+// sequence of IEEE operations, so every kernel that applies it agrees bit for bit.
+__device__ __forceinline__ float adam_step(float p, float g, float& m, float& v, const AdamParams& h, float lo,
+                                           float hi)
+{
+    m = __fmaf_rn(h.b1, m, __fmul_rn(1.f - h.b1, g));
+    v = __fmaf_rn(h.b2, v, __fmul_rn(__fmul_rn(1.f - h.b2, g), g));
+    const float den = __fmaf_rn(__fsqrt_rn(v), h.inv_sqrt_c2, h.eps);
+    return fminf(fmaxf(__fsub_rn(p, __fdiv_rn(__fmul_rn(h.step_size, m), den)), lo), hi);
+}
+
+AdamParams adam_params(int32_t step, float lr, float beta1, float beta2, float eps);
+
 // Camera values the kernels need, passed by value.
 struct CamParams {
     float view[12];

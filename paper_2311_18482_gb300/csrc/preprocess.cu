@@ -245,20 +245,22 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
 
 // SH coefficients of Gaussian i into registers ([k][3]); 16-byte vector loads
 // when the per-Gaussian stride allows it (degrees 1 and 3).
+// RO: through the read-only data path (only where nothing writes sh during the kernel).
+template <bool RO = true>
 __device__ __forceinline__ void load_sh(const float* sh, int i, int nc, float* out)
 {
     const size_t base = (size_t)i * nc * 3;
     if ((nc * 3) % 4 == 0) {
         const float4* p = reinterpret_cast<const float4*>(sh + base);
         for (int v = 0; v < nc * 3 / 4; ++v) {
-            const float4 t = __ldg(p + v);
+            const float4 t = RO ? __ldg(p + v) : p[v];
             out[4 * v] = t.x;
             out[4 * v + 1] = t.y;
             out[4 * v + 2] = t.z;
             out[4 * v + 3] = t.w;
         }
     } else {
-        for (int k = 0; k < nc * 3; ++k) out[k] = __ldg(sh + base + k);
+        for (int k = 0; k < nc * 3; ++k) out[k] = RO ? __ldg(sh + base + k) : sh[base + k];
     }
 }
 
@@ -342,31 +344,148 @@ __global__ void __launch_bounds__(256) preprocess_kernel(int n, const float* __r
 }
 
 // ----------------------------------------------------------------------------
-// Adjoint of preprocess_kernel.  Reads the screen-space gradient record
-// (same layout as the splat record) and writes every parameter gradient.
+// Backward of the projection.  Each thread computes the parameter gradients of
+// one Gaussian into a per-warp staging area in shared memory (Gaussian-major,
+// in each field's own layout; the SH gradient Y_k dL/drgb_c is kept factored
+// as the basis Y and the colour gradient).  Each warp then hands the
+// contiguous ranges of its 32 Gaussians to the sink with coalesced 16-byte
+// accesses: GradSink stores the gradients, AdamSink applies one Adam step to
+// parameters and moments in place, so the gradients never reach memory.
+template <int NC>
+struct GradStage {
+    float means[32 * 3], scales[32 * 3], quats[32 * 4], opacity[32], feat[32 * 8], unc[32];
+    float Y[32 * NC], gcol[32 * 3];
+};
+
+enum { kFMeans, kFScales, kFQuats, kFOpacity, kFSH, kFFeat, kFUnc };
+
+// Gradient of element e of the warp's sh range.
+template <int NC>
+__device__ __forceinline__ float sh_grad(const GradStage<NC>& S, int e)
+{
+    const int gi = e / (NC * 3), r = e - gi * (NC * 3), k = r / 3;
+    return S.Y[gi * NC + k] * S.gcol[gi * 3 + (r - 3 * k)];
+}
+
+// Elements [0, len) of the warp's range of one field, starting at flat index
+// base of that field; grad(e) gives element e's gradient.  16-byte accesses
+// where the sink's arrays are 16-byte aligned at base (base is a multiple of
+// 4), two of them in flight per lane; the n % 4 tail element by element.
+template <class Sink, class GradOf>
+__device__ __forceinline__ void warp_apply(const Sink& sk, int f, size_t base, int len, int lane, float lo, float hi,
+                                           const GradOf& grad)
+{
+    int e0 = 0;
+    if (sk.aligned(f, base)) {
+        const int len4 = len & ~3;
+        for (int e = 4 * lane; e < len4; e += 256) {
+            const float4 ga = make_float4(grad(e), grad(e + 1), grad(e + 2), grad(e + 3));
+            if (e + 128 < len4) {
+                const int e2 = e + 128;
+                const float4 gb = make_float4(grad(e2), grad(e2 + 1), grad(e2 + 2), grad(e2 + 3));
+                sk.put4x2(f, (base + e) >> 2, 32, ga, gb, lo, hi);
+            } else {
+                sk.put4(f, (base + e) >> 2, ga, lo, hi);
+            }
+        }
+        e0 = len4;
+    }
+    for (int e = e0 + lane; e < len; e += 32) sk.put1(f, base + e, grad(e), lo, hi);
+}
+
+struct GradSink {
+    float* d[7];
+    __device__ __forceinline__ bool aligned(int f, size_t base) const
+    {
+        return ((reinterpret_cast<uintptr_t>(d[f] + base)) & 15u) == 0;
+    }
+    __device__ __forceinline__ void put1(int f, size_t i, float g, float, float) const { d[f][i] = g; }
+    __device__ __forceinline__ void put4(int f, size_t i4, float4 g, float, float) const
+    {
+        reinterpret_cast<float4*>(d[f])[i4] = g;
+    }
+    __device__ __forceinline__ void put4x2(int f, size_t i4, int step4, float4 ga, float4 gb, float, float) const
+    {
+        reinterpret_cast<float4*>(d[f])[i4] = ga;
+        reinterpret_cast<float4*>(d[f])[i4 + step4] = gb;
+    }
+};
+
+struct AdamSink {
+    float *p[7], *m[7], *v[7];
+    AdamParams h;
+    __device__ __forceinline__ bool aligned(int f, size_t base) const
+    {
+        return ((reinterpret_cast<uintptr_t>(p[f] + base) | reinterpret_cast<uintptr_t>(m[f] + base) |
+                 reinterpret_cast<uintptr_t>(v[f] + base)) & 15u) == 0;
+    }
+    __device__ __forceinline__ void put1(int f, size_t i, float g, float lo, float hi) const
+    {
+        float mm = m[f][i], vv = v[f][i];
+        p[f][i] = adam_step(p[f][i], g, mm, vv, h, lo, hi);
+        m[f][i] = mm;
+        v[f][i] = vv;
+    }
+    __device__ __forceinline__ void put4(int f, size_t i4, float4 g, float lo, float hi) const
+    {
+        float4 pp = reinterpret_cast<float4*>(p[f])[i4], mm = reinterpret_cast<float4*>(m[f])[i4];
+        float4 vv = reinterpret_cast<float4*>(v[f])[i4];
+        pp.x = adam_step(pp.x, g.x, mm.x, vv.x, h, lo, hi);
+        pp.y = adam_step(pp.y, g.y, mm.y, vv.y, h, lo, hi);
+        pp.z = adam_step(pp.z, g.z, mm.z, vv.z, h, lo, hi);
+        pp.w = adam_step(pp.w, g.w, mm.w, vv.w, h, lo, hi);
+        reinterpret_cast<float4*>(p[f])[i4] = pp;
+        reinterpret_cast<float4*>(m[f])[i4] = mm;
+        reinterpret_cast<float4*>(v[f])[i4] = vv;
+    }
+    // quads i4 and i4 + step4: all six loads issued before any store (the
+    // three arrays are distinct, and nothing else touches them here)
+    __device__ __forceinline__ void put4x2(int f, size_t i4, int step4, float4 ga, float4 gb, float lo,
+                                           float hi) const
+    {
+        float4* __restrict__ P = reinterpret_cast<float4*>(p[f]);
+        float4* __restrict__ M = reinterpret_cast<float4*>(m[f]);
+        float4* __restrict__ V = reinterpret_cast<float4*>(v[f]);
+        float4 pa = P[i4], ma = M[i4], va = V[i4];
+        float4 pb = P[i4 + step4], mb = M[i4 + step4], vb = V[i4 + step4];
+        pa.x = adam_step(pa.x, ga.x, ma.x, va.x, h, lo, hi);
+        pa.y = adam_step(pa.y, ga.y, ma.y, va.y, h, lo, hi);
+        pa.z = adam_step(pa.z, ga.z, ma.z, va.z, h, lo, hi);
+        pa.w = adam_step(pa.w, ga.w, ma.w, va.w, h, lo, hi);
+        pb.x = adam_step(pb.x, gb.x, mb.x, vb.x, h, lo, hi);
+        pb.y = adam_step(pb.y, gb.y, mb.y, vb.y, h, lo, hi);
+        pb.z = adam_step(pb.z, gb.z, mb.z, vb.z, h, lo, hi);
+        pb.w = adam_step(pb.w, gb.w, mb.w, vb.w, h, lo, hi);
+        P[i4] = pa;
+        M[i4] = ma;
+        V[i4] = va;
+        P[i4 + step4] = pb;
+        M[i4 + step4] = mb;
+        V[i4 + step4] = vb;
+    }
+};
+
+// Adjoint of preprocess_kernel for Gaussian i, written into stage slot `lane`.
+// Reads the screen-space gradient record (same layout as the splat record).
 template <int DEG>
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(
-    int n, const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
-    const float* __restrict__ opacity_raw, const float* __restrict__ sh, CamParams cam,
-    const int* __restrict__ tiles, const uint8_t* __restrict__ clamp, const float4* __restrict__ grad2d,
-    float* __restrict__ d_means, float* __restrict__ d_log_scales, float* __restrict__ d_quats,
-    float* __restrict__ d_opacity_raw, float* __restrict__ d_sh, float* __restrict__ d_feat,
-    float* __restrict__ d_unc)
+__device__ __forceinline__ void gaussian_grads(int i, int lane, const float* means, const float* log_scales,
+                                               const float* quats, const float* opacity_raw, const float* sh,
+                                               const CamParams& cam, const int* __restrict__ tiles,
+                                               const uint8_t* __restrict__ clamp, const float4* __restrict__ grad2d,
+                                               GradStage<(DEG + 1) * (DEG + 1)>& S)
 {
     constexpr int NC = (DEG + 1) * (DEG + 1);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const float4 g0 = grad2d[5 * (size_t)i], g1 = grad2d[5 * (size_t)i + 1], g2 = grad2d[5 * (size_t)i + 2];
     const float4 g3 = grad2d[5 * (size_t)i + 3], g4 = grad2d[5 * (size_t)i + 4];
     // semantic feature and uncertainty pass straight through
-    reinterpret_cast<float4*>(d_feat)[2 * i] = make_float4(g2.z, g2.w, g3.x, g3.y);
-    reinterpret_cast<float4*>(d_feat)[2 * i + 1] = make_float4(g3.z, g3.w, g4.x, g4.y);
-    d_unc[i] = g2.y;
+    reinterpret_cast<float4*>(S.feat)[2 * lane] = make_float4(g2.z, g2.w, g3.x, g3.y);
+    reinterpret_cast<float4*>(S.feat)[2 * lane + 1] = make_float4(g3.z, g3.w, g4.x, g4.y);
+    S.unc[lane] = g2.y;
     if (tiles[i] <= 0) {
-        for (int k = 0; k < 3; ++k) d_means[3 * i + k] = d_log_scales[3 * i + k] = 0.f;
-        reinterpret_cast<float4*>(d_quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        d_opacity_raw[i] = 0.f;
-        for (int k = 0; k < NC * 3; ++k) d_sh[(size_t)i * NC * 3 + k] = 0.f;
+        for (int k = 0; k < 3; ++k) S.means[3 * lane + k] = S.scales[3 * lane + k] = S.gcol[3 * lane + k] = 0.f;
+        for (int k = 0; k < NC; ++k) S.Y[NC * lane + k] = 0.f;
+        reinterpret_cast<float4*>(S.quats)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.opacity[lane] = 0.f;
         return;
     }
     const float gmx = g0.x, gmy = g0.y, gA = g0.z, gB = g0.w, gC = g1.x, gop = g1.y;
@@ -382,7 +501,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
 
     // opacity
     const float op = 1.0f / (1.0f + expf(-opacity_raw[i]));
-    d_opacity_raw[i] = gop * op * (1.f - op);
+    S.opacity[lane] = gop * op * (1.f - op);
 
     // colour through SH and the view direction
     const uint8_t cm = clamp[i];
@@ -394,7 +513,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
     float Y[16], dY[16][3];
     sh_basis<true>(DEG, dx, dy, dz, Y, dY);
     float coef[NC * 3];
-    load_sh(sh, i, NC, coef);
+    load_sh<false>(sh, i, NC, coef);
     float gdir[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
@@ -405,22 +524,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
         gdir[1] = fmaf(w, dY[k][1], gdir[1]);
         gdir[2] = fmaf(w, dY[k][2], gdir[2]);
     }
-    // dL/dsh_kc = Y_k dL/drgb_c, written with 16-byte stores where the stride allows
-    {
-        float* dsh = d_sh + (size_t)i * NC * 3;
-        if ((NC * 3) % 4 == 0) {
 #pragma unroll
-            for (int v = 0; v < NC * 3 / 4; ++v) {
-                float o[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) o[e] = Y[(4 * v + e) / 3] * gcol[(4 * v + e) % 3];
-                reinterpret_cast<float4*>(dsh)[v] = make_float4(o[0], o[1], o[2], o[3]);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < NC * 3; ++e) dsh[e] = Y[e / 3] * gcol[e % 3];
-        }
-    }
+    for (int k = 0; k < NC; ++k) S.Y[NC * lane + k] = Y[k];
+    for (int ch = 0; ch < 3; ++ch) S.gcol[3 * lane + ch] = gcol[ch];
     const float dd = dx * gdir[0] + dy * gdir[1] + dz * gdir[2];
     float Gp[3] = {(gdir[0] - dx * dd) * il, (gdir[1] - dy * dd) * il, (gdir[2] - dz * dd) * il};
 
@@ -470,7 +576,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
     // t = R_c p + t_c
 #pragma unroll
     for (int k = 0; k < 3; ++k) Gp[k] += V[k] * Gtx + V[4 + k] * Gty + V[8 + k] * Gtz;
-    for (int k = 0; k < 3; ++k) d_means[3 * i + k] = Gp[k];
+    for (int k = 0; k < 3; ++k) S.means[3 * lane + k] = Gp[k];
 
     // Sigma = M M^T: dL/dM = (GS + GS^T) M with GS = ga T0T0' + gb T0T1' + gc T1T1'
     float Gsym[3][3];
@@ -490,7 +596,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
             GR[r][j] = gm * g.s[j];
             gs += gm * g.R[r][j];
         }
-        d_log_scales[3 * i + j] = gs * g.s[j];
+        S.scales[3 * lane + j] = gs * g.s[j];
     }
     // R(q), q = (w, x, y, z) normalised
     const float w = g.q[0], x = g.q[1], y = g.q[2], z = g.q[3];
@@ -504,8 +610,39 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(
             4.f * z * (GR[0][0] + GR[1][1]);
     const float qg = w * Gq[0] + x * Gq[1] + y * Gq[2] + z * Gq[3];
     const float qi = g.qnorm_inv;
-    reinterpret_cast<float4*>(d_quats)[i] =
+    reinterpret_cast<float4*>(S.quats)[lane] =
         make_float4((Gq[0] - w * qg) * qi, (Gq[1] - x * qg) * qi, (Gq[2] - y * qg) * qi, (Gq[3] - z * qg) * qi);
+}
+
+// One thread per Gaussian, then one warp per 32 Gaussians for the sink.  The
+// parameter pointers are not __restrict__: with AdamSink the kernel updates
+// them (after the warp has read every value it needs: __syncwarp below).
+template <int DEG, class Sink>
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(
+    int n, const float* means, const float* log_scales, const float* quats, const float* opacity_raw, const float* sh,
+    CamParams cam, const int* __restrict__ tiles, const uint8_t* __restrict__ clamp,
+    const float4* __restrict__ grad2d, Sink sk)
+{
+    constexpr int NC = (DEG + 1) * (DEG + 1);
+    constexpr float kInf = INFINITY;
+    __shared__ GradStage<NC> stage[4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    GradStage<NC>& S = stage[w];
+    const int gw = blockIdx.x * 128 + 32 * w;
+    if (gw >= n) return;
+    const int i = gw + lane;
+    if (i < n) gaussian_grads<DEG>(i, lane, means, log_scales, quats, opacity_raw, sh, cam, tiles, clamp, grad2d, S);
+    __syncwarp();
+    const int cnt = min(32, n - gw);
+    const size_t g = (size_t)gw;
+    warp_apply(sk, kFMeans, 3 * g, 3 * cnt, lane, -kInf, kInf, [&](int e) { return S.means[e]; });
+    warp_apply(sk, kFScales, 3 * g, 3 * cnt, lane, -kInf, kInf, [&](int e) { return S.scales[e]; });
+    warp_apply(sk, kFQuats, 4 * g, 4 * cnt, lane, -kInf, kInf, [&](int e) { return S.quats[e]; });
+    warp_apply(sk, kFOpacity, g, cnt, lane, -kInf, kInf, [&](int e) { return S.opacity[e]; });
+    warp_apply(sk, kFSH, (size_t)NC * 3 * g, NC * 3 * cnt, lane, -kInf, kInf,
+               [&](int e) { return sh_grad<NC>(S, e); });
+    warp_apply(sk, kFFeat, 8 * g, 8 * cnt, lane, -kInf, kInf, [&](int e) { return S.feat[e]; });
+    warp_apply(sk, kFUnc, g, cnt, lane, 0.f, 1.f, [&](int e) { return S.unc[e]; });
 }
 
 }  // namespace
@@ -563,17 +700,17 @@ extern "C" le_status le_preprocess(const le_gaussians* g, const le_camera* cam, 
 }
 
 namespace leg {
-le_status preprocess_backward(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
-                              const float* grad2d, const le_gaussian_grads* out, cudaStream_t s)
+template <class Sink>
+static le_status launch_preprocess_backward(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                            const float* grad2d, const Sink& sk, cudaStream_t s)
 {
     const CamParams cp = cam_params(cam);
     const int threads = 128, blocks = (g->n + threads - 1) / threads;
 #define LE_PREB(DEG)                                                                                               \
-    preprocess_bwd_kernel<DEG><<<blocks, threads, 0, s>>>(g->n, g->means, g->log_scales, g->quats, g->opacity_raw, \
-                                                          g->sh, cp, pr->tiles_touched, pr->clamp_mask,             \
-                                                          reinterpret_cast<const float4*>(grad2d), out->means,      \
-                                                          out->log_scales, out->quats, out->opacity_raw, out->sh,   \
-                                                          out->feat, out->unc)
+    preprocess_bwd_kernel<DEG, Sink><<<blocks, threads, 0, s>>>(g->n, g->means, g->log_scales, g->quats,           \
+                                                                g->opacity_raw, g->sh, cp, pr->tiles_touched,      \
+                                                                pr->clamp_mask,                                    \
+                                                                reinterpret_cast<const float4*>(grad2d), sk)
     switch (g->sh_degree) {
         case 0: LE_PREB(0); break;
         case 1: LE_PREB(1); break;
@@ -583,5 +720,31 @@ le_status preprocess_backward(const le_camera* cam, const le_gaussians* g, const
 #undef LE_PREB
     LE_LAUNCHED();
     return LE_OK;
+}
+
+le_status preprocess_backward(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                              const float* grad2d, const le_gaussian_grads* out, cudaStream_t s)
+{
+    const GradSink sk{{out->means, out->log_scales, out->quats, out->opacity_raw, out->sh, out->feat, out->unc}};
+    return launch_preprocess_backward(cam, g, pr, grad2d, sk, s);
+}
+
+le_status preprocess_backward_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                   const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
+                                   const AdamParams& h, cudaStream_t s)
+{
+    AdamSink sk;
+    float* const p[7] = {const_cast<float*>(g->means), const_cast<float*>(g->log_scales), const_cast<float*>(g->quats),
+                         const_cast<float*>(g->opacity_raw), const_cast<float*>(g->sh), const_cast<float*>(g->feat),
+                         const_cast<float*>(g->unc)};
+    float* const mm[7] = {m->means, m->log_scales, m->quats, m->opacity_raw, m->sh, m->feat, m->unc};
+    float* const vv[7] = {v->means, v->log_scales, v->quats, v->opacity_raw, v->sh, v->feat, v->unc};
+    for (int f = 0; f < 7; ++f) {
+        sk.p[f] = p[f];
+        sk.m[f] = mm[f];
+        sk.v[f] = vv[f];
+    }
+    sk.h = h;
+    return launch_preprocess_backward(cam, g, pr, grad2d, sk, s);
 }
 }  // namespace leg

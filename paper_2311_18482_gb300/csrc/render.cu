@@ -20,6 +20,9 @@
 namespace leg {
 le_status preprocess_backward(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
                               const float* grad2d, const le_gaussian_grads* out, cudaStream_t s);
+le_status preprocess_backward_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                   const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
+                                   const AdamParams& h, cudaStream_t s);
 le_status check_gaussians(const le_gaussians* g);
 
 namespace {
@@ -301,24 +304,16 @@ extern "C" le_status le_render_fwd(const le_camera* cam, int32_t n, const float*
     return LE_OK;
 }
 
-extern "C" le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
-                                   const uint32_t* sorted_ids, const uint32_t* tile_ranges, const float* T_final,
-                                   const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
-                                   const float* dL_dunc, float* grad2d, const le_gaussian_grads* out, void* stream)
+namespace leg {
+namespace {
+
+// Arguments shared by le_render_bwd and le_render_bwd_adam; launches the
+// screen-space backward (grad2d).
+le_status render_backward_2d(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                             const uint32_t* sorted_ids, const uint32_t* tile_ranges, const float* T_final,
+                             const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
+                             const float* dL_dunc, float* grad2d, cudaStream_t s)
 {
-    le_status st = check_camera(cam);
-    if (st != LE_OK) return st;
-    if ((st = check_gaussians(g)) != LE_OK) return st;
-    LE_CHECK_ARG(pr && out, "null projected / grads struct");
-    LE_CHECK_ARG(tile_ranges && T_final && n_contrib && dL_drgb && dL_dfeat && dL_dunc, "null input pointer");
-    if (g->n == 0) return LE_OK;
-    LE_CHECK_ARG(pr->splat && pr->tiles_touched && pr->clamp_mask && aligned16(pr->splat), "bad projected pointers");
-    LE_CHECK_ARG(grad2d && aligned16(grad2d), "grad2d must be non-null and 16-byte aligned");
-    LE_CHECK_ARG(out->means && out->log_scales && out->quats && out->opacity_raw && out->sh && out->feat && out->unc,
-                 "null gradient pointer");
-    LE_CHECK_ARG(aligned16(out->quats) && aligned16(out->feat) && aligned16(out->sh),
-                 "quats/sh/feat gradients must be 16-byte aligned");
-    cudaStream_t s = as_stream(stream);
     const CamParams cp = cam_params(cam);
     LE_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * LE_SPLAT_STRIDE * (size_t)g->n, s));
     render_bwd_kernel<2><<<cp.TX * cp.TY, kBlock / 2, 0, s>>>(cp, reinterpret_cast<const float4*>(pr->splat), sorted_ids,
@@ -326,5 +321,69 @@ extern "C" le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, 
                                                         n_contrib, dL_drgb, dL_dfeat, dL_dunc,
                                                         reinterpret_cast<float4*>(grad2d));
     LE_LAUNCHED();
+    return LE_OK;
+}
+
+le_status check_render_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                           const uint32_t* tile_ranges, const float* T_final, const int32_t* n_contrib,
+                           const float* dL_drgb, const float* dL_dfeat, const float* dL_dunc, const float* grad2d)
+{
+    le_status st = check_camera(cam);
+    if (st != LE_OK) return st;
+    if ((st = check_gaussians(g)) != LE_OK) return st;
+    LE_CHECK_ARG(pr != nullptr, "null projected struct");
+    LE_CHECK_ARG(tile_ranges && T_final && n_contrib && dL_drgb && dL_dfeat && dL_dunc, "null input pointer");
+    if (g->n == 0) return LE_OK;
+    LE_CHECK_ARG(pr->splat && pr->tiles_touched && pr->clamp_mask && aligned16(pr->splat), "bad projected pointers");
+    LE_CHECK_ARG(grad2d && aligned16(grad2d), "grad2d must be non-null and 16-byte aligned");
+    return LE_OK;
+}
+
+le_status check_field_set(const le_gaussian_grads* o, const char* what)
+{
+    LE_CHECK_ARG(o != nullptr, "null %s struct", what);
+    LE_CHECK_ARG(o->means && o->log_scales && o->quats && o->opacity_raw && o->sh && o->feat && o->unc,
+                 "null %s pointer", what);
+    LE_CHECK_ARG(aligned16(o->quats) && aligned16(o->feat) && aligned16(o->sh),
+                 "%s: quats/sh/feat must be 16-byte aligned", what);
+    return LE_OK;
+}
+
+}  // namespace
+}  // namespace leg
+
+extern "C" le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                   const uint32_t* sorted_ids, const uint32_t* tile_ranges, const float* T_final,
+                                   const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
+                                   const float* dL_dunc, float* grad2d, const le_gaussian_grads* out, void* stream)
+{
+    le_status st = check_render_bwd(cam, g, pr, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc, grad2d);
+    if (st != LE_OK || g->n == 0) return st;
+    if ((st = check_field_set(out, "gradient")) != LE_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    if ((st = render_backward_2d(cam, g, pr, sorted_ids, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc,
+                                 grad2d, s)) != LE_OK)
+        return st;
     return preprocess_backward(cam, g, pr, grad2d, out, s);
+}
+
+extern "C" le_status le_render_bwd_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                        const uint32_t* sorted_ids, const uint32_t* tile_ranges,
+                                        const float* T_final, const int32_t* n_contrib, const float* dL_drgb,
+                                        const float* dL_dfeat, const float* dL_dunc, float* grad2d,
+                                        const le_gaussian_grads* m, const le_gaussian_grads* v,
+                                        const le_adam_config* adam, void* stream)
+{
+    le_status st = check_render_bwd(cam, g, pr, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc, grad2d);
+    if (st != LE_OK) return st;
+    LE_CHECK_ARG(adam != nullptr && adam->step >= 1, "adam config is null or step < 1");
+    if (g->n == 0) return LE_OK;
+    if ((st = check_field_set(m, "first-moment")) != LE_OK) return st;
+    if ((st = check_field_set(v, "second-moment")) != LE_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    if ((st = render_backward_2d(cam, g, pr, sorted_ids, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc,
+                                 grad2d, s)) != LE_OK)
+        return st;
+    return preprocess_backward_adam(cam, g, pr, grad2d, m, v,
+                                    adam_params(adam->step, adam->lr, adam->beta1, adam->beta2, adam->eps), s);
 }

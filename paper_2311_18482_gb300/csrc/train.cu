@@ -27,19 +27,10 @@ __global__ void __launch_bounds__(256) l1_kernel(int64_t n, const float* __restr
     }
 }
 
-// Adam (Kingma & Ba) with bias correction folded into the step size, then a clamp.
-__device__ __forceinline__ float adam_one(float p, float g, float& m, float& v, float b1, float b2, float step_size,
-                                          float inv_sqrt_c2, float eps, float lo, float hi)
-{
-    m = b1 * m + (1.f - b1) * g;
-    v = b2 * v + (1.f - b2) * g * g;
-    return fminf(fmaxf(p - step_size * m / (sqrtf(v) * inv_sqrt_c2 + eps), lo), hi);
-}
-
 // float4 body over the first n/4 quads; the n % 4 tail elements scalar.
 __global__ void __launch_bounds__(256) adam_kernel(int64_t n, float* __restrict__ p, const float* __restrict__ g,
-                                                   float* __restrict__ m, float* __restrict__ v, float b1, float b2,
-                                                   float step_size, float inv_sqrt_c2, float eps, float lo, float hi)
+                                                   float* __restrict__ m, float* __restrict__ v, AdamParams h,
+                                                   float lo, float hi)
 {
     const int64_t n4 = n / 4;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
@@ -47,19 +38,26 @@ __global__ void __launch_bounds__(256) adam_kernel(int64_t n, float* __restrict_
         float4 pp = reinterpret_cast<float4*>(p)[i], mm = reinterpret_cast<float4*>(m)[i];
         float4 vv = reinterpret_cast<float4*>(v)[i];
         const float4 gg = reinterpret_cast<const float4*>(g)[i];
-        pp.x = adam_one(pp.x, gg.x, mm.x, vv.x, b1, b2, step_size, inv_sqrt_c2, eps, lo, hi);
-        pp.y = adam_one(pp.y, gg.y, mm.y, vv.y, b1, b2, step_size, inv_sqrt_c2, eps, lo, hi);
-        pp.z = adam_one(pp.z, gg.z, mm.z, vv.z, b1, b2, step_size, inv_sqrt_c2, eps, lo, hi);
-        pp.w = adam_one(pp.w, gg.w, mm.w, vv.w, b1, b2, step_size, inv_sqrt_c2, eps, lo, hi);
+        pp.x = adam_step(pp.x, gg.x, mm.x, vv.x, h, lo, hi);
+        pp.y = adam_step(pp.y, gg.y, mm.y, vv.y, h, lo, hi);
+        pp.z = adam_step(pp.z, gg.z, mm.z, vv.z, h, lo, hi);
+        pp.w = adam_step(pp.w, gg.w, mm.w, vv.w, h, lo, hi);
         reinterpret_cast<float4*>(p)[i] = pp;
         reinterpret_cast<float4*>(m)[i] = mm;
         reinterpret_cast<float4*>(v)[i] = vv;
     }
     const int64_t t = 4 * n4 + tid;
-    if (t < n) p[t] = adam_one(p[t], g[t], m[t], v[t], b1, b2, step_size, inv_sqrt_c2, eps, lo, hi);
+    if (t < n) p[t] = adam_step(p[t], g[t], m[t], v[t], h, lo, hi);
 }
 
 }  // namespace
+
+AdamParams adam_params(int32_t step, float lr, float beta1, float beta2, float eps)
+{
+    const double c1 = 1.0 - pow((double)beta1, step), c2 = 1.0 - pow((double)beta2, step);
+    return AdamParams{beta1, beta2, (float)(lr / c1), (float)(1.0 / sqrt(c2)), eps};
+}
+
 }  // namespace leg
 
 using namespace leg;
@@ -85,11 +83,10 @@ extern "C" le_status le_adam(int64_t n, float* param, const float* grad, float* 
     LE_CHECK_ARG(param && grad && m && v, "null pointer");
     LE_CHECK_ARG(aligned16(param) && aligned16(grad) && aligned16(m) && aligned16(v),
                  "Adam buffers must be 16-byte aligned");
-    const double c1 = 1.0 - pow((double)beta1, step), c2 = 1.0 - pow((double)beta2, step);
     const int64_t n4 = n / 4 + 1;
     const int blocks = (int)((n4 + 255) / 256 < 152 * 16 ? (n4 + 255) / 256 : 152 * 16);
-    adam_kernel<<<blocks, 256, 0, as_stream(stream)>>>(n, param, grad, m, v, beta1, beta2, (float)(lr / c1),
-                                                        (float)(1.0 / sqrt(c2)), eps, clamp_lo, clamp_hi);
+    adam_kernel<<<blocks, 256, 0, as_stream(stream)>>>(n, param, grad, m, v,
+                                                        adam_params(step, lr, beta1, beta2, eps), clamp_lo, clamp_hi);
     LE_LAUNCHED();
     return LE_OK;
 }

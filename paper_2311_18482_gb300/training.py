@@ -3,9 +3,12 @@ driven entirely through the C ABI with preallocated device buffers:
 
   le_preprocess -> le_bin_sort -> le_render_fwd -> le_rgb_l1 (RGB loss, Sec. 4)
   -> le_decode (D_MLP + uncertainty-weighted CE + L_u, Eqs. 8-12, training mode)
-  -> le_render_bwd (all Gaussian parameter gradients)
-  -> le_adam (Gaussians + decoder; u clamped to [0,1], Sec. 3.4.2)
+  -> le_render_bwd_adam (all Gaussian parameter gradients, each applied by
+     Adam where it is computed; u clamped to [0,1], Sec. 3.4.2)
+  -> le_adam (decoder parameters)
 
+With fused_adam=False the Gaussian gradients are written out by le_render_bwd
+and le_adam runs over them (bit-identical result, more memory traffic).
 All parameters live in one flat FP32 buffer (each tensor a 16-byte aligned
 view), so Adam is two launches over contiguous memory.  The loss weights are
 the paper's (all lambda = 1, Sec. 4).
@@ -52,7 +55,7 @@ class FlatParams:
 
 
 class TrainState:
-    def __init__(self, scene, dec, W, H, device="cuda", decoder_mode=B.FUSED_BF16, lr=1e-3):
+    def __init__(self, scene, dec, W, H, device="cuda", decoder_mode=B.FUSED_BF16, lr=1e-3, fused_adam=True):
         self.layout = FlatParams(scene, dec, device)
         L = self.layout
         self.params = torch.zeros(L.total, dtype=torch.float32, device=device)
@@ -70,6 +73,12 @@ class TrainState:
         self.gg = B.grads_struct(B.Gaussians(*(self.gv[k] for k in list(_FIELDS) + ["unc"]), scene.sh_degree))
         self.dec = B.decoder_struct(*(pv[k] for k in _DEC))
         self.dgrad = B.decoder_grads_struct([self.gv[k] for k in _DEC])
+        mv, vv = L.views(self.m), L.views(self.v)
+        gfields = list(_FIELDS) + ["unc"]
+        self.gm = B.Gaussians(*(mv[k] for k in gfields), scene.sh_degree)
+        self.gvv = B.Gaussians(*(vv[k] for k in gfields), scene.sh_degree)
+        self.fused_adam = fused_adam
+        self.dec_lo = L.offsets["W1"][0]
         N, P = scene.N, W * H
         self.W, self.H, self.P = W, H, P
         self.proj = B.Projected.empty(N, device)
@@ -118,17 +127,24 @@ class TrainState:
         B.le_decode_raw(self.mode, self.P, self.img.feat, self.img.unc, self.dec, idx_target, 1.0, 1.0,
                         self.loss[1:3], self.d_feat, self.d_unc, self.dgrad, None, None, None, self.dec_ws)
         self._mark("decoder")
-        cs, gs, ps = B.camera_struct(cam), self.g.struct(), self.proj.struct()
-        import ctypes as C
-        B._check(B.load().le_render_bwd(C.byref(cs), C.byref(gs), C.byref(ps), B._ptr(ids), B._ptr(ranges),
-                                        B._ptr(self.img.T), B._ptr(self.img.n_contrib), B._ptr(self.d_rgb),
-                                        B._ptr(self.d_feat), B._ptr(self.d_unc), B._ptr(self.grad2d),
-                                        C.byref(self.gg), B._stream()))
-        self._mark("render_bwd")
         self.step_count += 1
-        u0 = self.layout.unc_offset
-        B.le_adam(self.params[:u0], self.grads[:u0], self.m[:u0], self.v[:u0], self.step_count, lr=self.lr)
-        B.le_adam(self.params[u0:], self.grads[u0:], self.m[u0:], self.v[u0:], self.step_count, lr=self.lr,
-                  clamp_lo=0.0, clamp_hi=1.0)
+        u0, d0 = self.layout.unc_offset, self.dec_lo
+        if self.fused_adam:
+            B.le_render_bwd_adam(cam, self.g, self.proj, ids, ranges, self.img, self.d_rgb, self.d_feat, self.d_unc,
+                                 self.gm, self.gvv, self.step_count, lr=self.lr, grad2d=self.grad2d)
+            self._mark("render_bwd")
+            B.le_adam(self.params[d0:u0], self.grads[d0:u0], self.m[d0:u0], self.v[d0:u0], self.step_count,
+                      lr=self.lr)
+        else:
+            cs, gs, ps = B.camera_struct(cam), self.g.struct(), self.proj.struct()
+            import ctypes as C
+            B._check(B.load().le_render_bwd(C.byref(cs), C.byref(gs), C.byref(ps), B._ptr(ids), B._ptr(ranges),
+                                            B._ptr(self.img.T), B._ptr(self.img.n_contrib), B._ptr(self.d_rgb),
+                                            B._ptr(self.d_feat), B._ptr(self.d_unc), B._ptr(self.grad2d),
+                                            C.byref(self.gg), B._stream()))
+            self._mark("render_bwd")
+            B.le_adam(self.params[:u0], self.grads[:u0], self.m[:u0], self.v[:u0], self.step_count, lr=self.lr)
+            B.le_adam(self.params[u0:], self.grads[u0:], self.m[u0:], self.v[u0:], self.step_count, lr=self.lr,
+                      clamp_lo=0.0, clamp_hi=1.0)
         self._mark("adam")
         return self.loss

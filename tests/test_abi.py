@@ -54,6 +54,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     cam.width = 10
     g.sh_degree = 4
     assert lib.le_preprocess(C.byref(g), C.byref(cam), C.byref(p), None) == b.LE_ERR_INVALID_ARG
+    # fused backward + Adam: null camera / config rejected before any GPU work
+    assert lib.le_render_bwd_adam(None, None, None, None, None, None, None, None, None, None, None, None, None,
+                                  None, None) == b.LE_ERR_INVALID_ARG
     # misaligned Adam buffers
     assert lib.le_adam(C.c_int64(8), C.c_void_p(3), C.c_void_p(16), C.c_void_p(32), C.c_void_p(48), 1,
                        C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999), C.c_float(1e-8), C.c_float(0),
