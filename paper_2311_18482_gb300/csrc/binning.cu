@@ -91,13 +91,15 @@ __global__ void __launch_bounds__(kThreads) scan_reduce_kernel(In in, int n, uin
     }
 }
 
-// Single block: exclusive scan of nb partials in place (nb <= 1024 * 16), total -> *total.
+// Single block: exclusive scan of nb values in place (each thread a contiguous
+// segment of ceil(nb / 1024)), total -> *total.
 __global__ void __launch_bounds__(1024) scan_partials_kernel(uint32_t* partials, int nb, uint32_t* total)
 {
     __shared__ uint32_t ws[32];
     const int per = (nb + 1023) / 1024;
     const int lo = threadIdx.x * per, hi = min(nb, lo + per);
     uint32_t s = 0;
+#pragma unroll 8
     for (int i = lo; i < hi; ++i) s += partials[i];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t x = s;
@@ -380,14 +382,17 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
 // tile (row, tx) starts at base[t * nchunks + C*cs] -- the exclusive scan of the
 // counts in tile-major order -- and lives in a register of lane tx % 32 of the
 // row's warp, so no two threads share a cursor and no barrier is needed between
-// Gaussians.  A warp takes the super-chunk's Gaussians 32 at a time; each lane
-// computes the row span of its Gaussian (when its rectangle covers the row), a
-// ballot keeps the non-empty ones and, for each in depth order, every lane
-// whose tiles fall in the span writes them.  Only one cursor per
+// Gaussians.  The block first compacts, 1024 at a time and in depth order, the
+// super-chunk's Gaussians whose rectangle meets its 8 rows; a warp then takes
+// those 32 at a time: each lane computes the row span of its Gaussian (when its
+// rectangle covers the row), a ballot keeps the non-empty ones and, for each in
+// depth order, every lane whose tiles fall in the span writes them.  Only one cursor per
 // (tile, block) advances at a time, so the partly written output sectors stay
 // few enough to remain in L2.
 constexpr int kPlaceThreads = 256;
 constexpr int kPlaceRows = kPlaceThreads / 32;
+
+constexpr int kPlaceBatch = 4 * kPlaceThreads;   // Gaussians examined per compaction round
 
 template <int NK>
 __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint64_t* __restrict__ dsorted,
@@ -398,11 +403,13 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
                                                               const uint32_t* __restrict__ base,
                                                               uint32_t* __restrict__ ids, uint64_t* __restrict__ keys)
 {
-    __shared__ uint32_t sg[kPlaceThreads];
-    __shared__ ushort4 sr[kPlaceThreads];
+    __shared__ uint32_t sg[kPlaceBatch], sj[kPlaceBatch];
+    __shared__ ushort4 sr[kPlaceBatch];
+    __shared__ uint32_t ws[kWarps];
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * kPlaceRows + (threadIdx.x >> 5);
     const bool row_ok = row < TY;
+    const int rb = blockIdx.x * kPlaceRows, re = min(TY, rb + kPlaceRows);
     const int C = blockIdx.y;
     uint32_t ctr[NK];
 #pragma unroll
@@ -411,22 +418,37 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
         ctr[k] = (row_ok && tx < TX) ? base[(size_t)(row * TX + tx) * nchunks + (size_t)C * cstride] : 0u;
     }
     const int j0 = C * super_chunk, j1 = min(n, j0 + super_chunk);
-    for (int jb = j0; jb < j1; jb += kPlaceThreads) {
+    for (int jb = j0; jb < j1; jb += kPlaceBatch) {
+        // compaction: the batch's Gaussians whose rectangle meets this block's
+        // rows, in depth order (thread t examines 4 consecutive ones)
         __syncthreads();
-        const int j = jb + threadIdx.x;
-        if (j < j1) {
-            sg[threadIdx.x] = (uint32_t)dsorted[j];
-            sr[threadIdx.x] = drect[j];
+        ushort4 rr[4];
+        uint32_t flags = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = jb + 4 * threadIdx.x + k;
+            rr[k] = j < j1 ? drect[j] : make_ushort4(0, 0, 0, 0);
+            if (rr[k].z > rr[k].x && rr[k].y < re && rr[k].w > rb) flags |= 1u << k;
         }
+        uint32_t m = 0;
+        uint32_t pos = block_exclusive_scan((uint32_t)__popc(flags), ws, &m);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (flags & (1u << k)) {
+                const int j = jb + 4 * threadIdx.x + k;
+                sr[pos] = rr[k];
+                sg[pos] = (uint32_t)dsorted[j];
+                sj[pos] = (uint32_t)j;
+                ++pos;
+            }
         __syncthreads();
         if (!row_ok) continue;
-        const int m = min(kPlaceThreads, j1 - jb);
-        for (int q0 = 0; q0 < m; q0 += 32) {
+        for (int q0 = 0; q0 < (int)m; q0 += 32) {
             int xl = 0, xr = 0;
-            if (q0 + lane < m) {
+            if (q0 + lane < (int)m) {
                 const ushort4 r = sr[q0 + lane];
-                if (r.z > r.x && r.y <= row && row < r.w) {
-                    const size_t jj = (size_t)(jb + q0 + lane);
+                if (r.y <= row && row < r.w) {
+                    const size_t jj = sj[q0 + lane];
                     row_span(__ldg(dell + 2 * jj), __ldg(dell + 2 * jj + 1), r, row, xl, xr);
                 }
             }
@@ -441,10 +463,10 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
                 for (int k = 0; k < NK; ++k) {
                     const int tx = lane + 32 * k;
                     if (tx >= bl && tx < br) {
-                        const uint32_t pos = ctr[k];
-                        ids[pos] = gid;
-                        if (keys) keys[pos] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | dbits;
-                        ctr[k] = pos + 1;
+                        const uint32_t p = ctr[k];
+                        ids[p] = gid;
+                        if (keys) keys[p] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | dbits;
+                        ctr[k] = p + 1;
                     }
                 }
             }
