@@ -57,9 +57,10 @@ struct DecArgs {
     float* rel;
 };
 
-// Per-warpgroup state of the shared MLP front end.  With nhalf = 2 two
-// warpgroups serve the same 128 TMEM lanes (rows) and split every epilogue
-// by columns; `xch` is their shared-memory exchange for row-wide statistics.
+// Per-warpgroup state of the shared MLP front end.  With nhalf = 2 or 4,
+// that many warpgroups serve the same 128 TMEM lanes (rows) and split every
+// epilogue by columns; `xch` is their shared-memory exchange for row-wide
+// statistics ([nhalf][128] float4).
 struct Front {
     SBuf W1s, W2s, W3s, X1, H1, H2;
     const float *b1s, *b2s, *b3s;
@@ -70,7 +71,7 @@ struct Front {
     int tid;           // row of the tile (TMEM lane) this thread serves
     int bar_id, nthreads;
     int half, nhalf;
-    float4* xch;       // [2][128] (nhalf = 2 only)
+    float4* xch;       // [nhalf][128] (nhalf > 1 only)
 };
 
 // Columns [c0, c1) of an N-column epilogue handled by this thread's half (units of 16).
@@ -166,8 +167,8 @@ __device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
 }
 
 // Online max / argmax / log-sum-exp over the ncb logits in TMEM (+ b3); with
-// two halves, each covers its columns and the pair combine through f.xch.
-// Ties go to the lowest index.  zt = logit of class t (if t >= 0).
+// several parts, each covers its columns and they combine through f.xch in
+// column order.  Ties go to the lowest index.  zt = logit of class t (if t >= 0).
 __device__ __forceinline__ void logits_lse(const Front& f, int ncb, float& lse, int& am, int t, float& zt)
 {
     float m = -INFINITY, s = 0.f, v[16];
@@ -190,19 +191,25 @@ __device__ __forceinline__ void logits_lse(const Front& f, int ncb, float& lse, 
             }
         }
     }
-    if (f.nhalf == 2) {
+    if (f.nhalf > 1) {
         f.xch[f.half * 128 + f.tid] = make_float4(m, s, __int_as_float(am), zt);
         wg_sync(f);
-        const float4 o = f.xch[(1 - f.half) * 128 + f.tid];
+        float mt = -INFINITY, st = 0.f, zsum = 0.f;
+        int at = 0;
+        for (int h = 0; h < f.nhalf; ++h) {
+            const float4 o = f.xch[h * 128 + f.tid];
+            if (o.x == -INFINITY) continue;           // a part without columns
+            const float mn = fmaxf(mt, o.x);
+            st = (mt == -INFINITY ? 0.f : st * __expf(mt - mn)) + o.y * __expf(o.x - mn);
+            if (o.x > mt) at = __float_as_int(o.z);
+            mt = mn;
+            zsum += o.w;                             // only the part holding class t has it
+        }
         wg_sync(f);
-        const float m0 = f.half == 0 ? m : o.x, s0 = f.half == 0 ? s : o.y;
-        const float m1 = f.half == 0 ? o.x : m, s1 = f.half == 0 ? o.y : s;
-        const int a0 = f.half == 0 ? am : __float_as_int(o.z), a1 = f.half == 0 ? __float_as_int(o.z) : am;
-        const bool t_mine = t >= c0 && t < c1;
-        zt = t_mine ? zt : o.w;
-        m = fmaxf(m0, m1);
-        s = (m0 == -INFINITY ? 0.f : s0 * __expf(m0 - m)) + (m1 == -INFINITY ? 0.f : s1 * __expf(m1 - m));
-        am = m1 > m0 ? a1 : a0;
+        m = mt;
+        s = st;
+        am = at;
+        zt = zsum;
     }
     lse = m + __logf(s);
 }
@@ -795,11 +802,15 @@ __global__ void __launch_bounds__(kTrainThreads, 1) dec_train_kernel(DecArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Query: decode, softmax, relevancy.  One warpgroup per CTA; TMEM: logits in
-// [0, ncb) (later the 16 text/negative projections in [0, 16)), p^T G in
-// [256, 256 + ncb).  The activations X1/H1/H2 and the BF16 softmax P share one
-// region (P is written after the last MMA that reads H2 has completed).
+// Query: decode, softmax, relevancy.  Four warpgroups per CTA serve the same
+// 128 rows and split every epilogue by columns; TMEM: logits in [0, ncb)
+// (later the 16 text/negative projections in [0, 16) and the four parts'
+// partial p^T G p in columns 16-19), p^T G in [256, 256 + ncb).  The
+// activations X1/H1/H2, the parts' softmax exchange and the BF16 softmax P
+// share one region (each is written after the last reader of the previous
+// one has finished).
 constexpr uint32_t kTG = 256;
+constexpr int kQueryParts = 4;
 
 __host__ constexpr size_t query_smem(int ncb)
 {
@@ -807,7 +818,7 @@ __host__ constexpr size_t query_smem(int ncb)
            (sbuf_bytes(128, ncb) > kFwdWgBytes ? sbuf_bytes(128, ncb) : kFwdWgBytes) + 2 * sbuf_bytes(ncb, 64) + 128;
 }
 
-__global__ void __launch_bounds__(128, 1) query_fused_kernel(DecArgs a)
+__global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     Front f;
@@ -818,6 +829,7 @@ __global__ void __launch_bounds__(128, 1) query_fused_kernel(DecArgs a)
     f.H1 = SBuf{p + sbuf_bytes(128, 16), 64};
     f.H2 = SBuf{p + sbuf_bytes(128, 16) + sbuf_bytes(128, 64), 128};
     const SBuf Ps{p, a.ncb};
+    f.xch = reinterpret_cast<float4*>(p);
     p += sbuf_bytes(128, a.ncb) > kFwdWgBytes ? sbuf_bytes(128, a.ncb) : kFwdWgBytes;
     const uint32_t chunk_bytes = sbuf_bytes(a.ncb, 64);
     const SBuf Gs[2] = {SBuf{p, 64}, SBuf{p + chunk_bytes, 64}};
@@ -828,12 +840,11 @@ __global__ void __launch_bounds__(128, 1) query_fused_kernel(DecArgs a)
     sbuf_fill(Aqs, 16, a.Aq, a.ncb, 16, a.ncb);
     f.mbar = mbar;
     f.phase = 0;
-    f.tid = tid;
+    f.tid = tid & 127;
     f.bar_id = 0;
     f.nthreads = blockDim.x;
-    f.half = 0;
-    f.nhalf = 1;
-    f.xch = nullptr;
+    f.half = tid >> 7;
+    f.nhalf = kQueryParts;
     if (tid == 0)
         for (int i = 0; i < 3; ++i) mbar_init(mbar + i, 1);
     if (tid < 32) tmem_alloc(slot, 512);
@@ -843,7 +854,10 @@ __global__ void __launch_bounds__(128, 1) query_fused_kernel(DecArgs a)
     fence_after();
     const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(slot);
     f.tw = tbase;
-    f.lane = (uint32_t)(32 * (tid >> 5)) << 16;
+    f.lane = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+    const int row = f.tid;
+    int c0, c1;
+    my_cols(f, a.ncb, c0, c1);                  // this part's class columns
     const int nch = a.ncb / 64;                 // G chunks (64 K-columns each)
     uint32_t gphase[2] = {0u, 0u};
     bool pending[2] = {false, false};          // a load into the slot is in flight (thread 0 only)
@@ -857,18 +871,18 @@ __global__ void __launch_bounds__(128, 1) query_fused_kernel(DecArgs a)
     if (tid == 0 && blockIdx.x < ntiles)
         for (int s = 0; s < 2 && s < nch; ++s) load_chunk(s, s);
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int px = tile * 128 + tid;
+        const int px = tile * 128 + row;
         const bool valid = px < a.P;
         if (!mlp_forward(f, a, px, valid)) break;
         float lse, zt, v[16];
         int am;
         logits_lse(f, a.ncb, lse, am, -1, zt);
-        for (int c = 0; c < a.ncb; c += 16) {
+        for (int c = c0; c < c1; c += 16) {
             tmem_ld16(f.tw + f.lane + c, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = __expf(v[j] + f.b3s[c + j] - lse);
-            sbuf_store8(Ps, tid, c, v);
-            sbuf_store8(Ps, tid, c + 8, v + 8);
+            sbuf_store8(Ps, row, c, v);
+            sbuf_store8(Ps, row, c + 8, v + 8);
         }
         wg_publish(f);
         // p . (S_c [q; n]) into [0, 16), p^T G into [256, 256 + ncb), G chunk by chunk
@@ -904,21 +918,32 @@ __global__ void __launch_bounds__(128, 1) query_fused_kernel(DecArgs a)
             }
         }
         if (!ok) break;
-        // relevancy
+        // relevancy: each part sums p^T G p over its columns into TMEM column 16 + part
         float ptgp = 0.f, pp[16];
-        for (int c = 0; c < a.ncb; c += 16) {
+        for (int c = c0; c < c1; c += 16) {
             tmem_ld16(tbase + kTG + f.lane + c, v);
-            sbuf_load8(Ps, tid, c, pp);
-            sbuf_load8(Ps, tid, c + 8, pp + 8);
+            sbuf_load8(Ps, row, c, pp);
+            sbuf_load8(Ps, row, c + 8, pp + 8);
 #pragma unroll
             for (int j = 0; j < 16; ++j) ptgp = fmaf(pp[j], v[j], ptgp);
         }
-        tmem_ld16(tbase + f.lane, v);
-        const float inv = rsqrtf(fmaxf(ptgp, 1e-30f));
-        float smax = -INFINITY;
-        for (int j = a.Q; j < a.Q + a.n_neg; ++j) smax = fmaxf(smax, v[j] * inv);
-        if (valid)
-            for (int j = 0; j < a.Q; ++j) a.rel[(size_t)j * a.P + px] = 1.f / (1.f + __expf(smax - v[j] * inv));
+        tmem_st1(tbase + f.lane + 16 + f.half, ptgp);
+        tmem_wait_st();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (f.half == 0) {
+            tmem_ld16(tbase + f.lane, v);        // the 16 projections and the parts' partial sums
+            float tot = 0.f, w[16];
+            tmem_ld16(tbase + f.lane + 16, w);
+#pragma unroll
+            for (int h = 0; h < kQueryParts; ++h) tot += w[h];
+            const float inv = rsqrtf(fmaxf(tot, 1e-30f));
+            float smax = -INFINITY;
+            for (int j = a.Q; j < a.Q + a.n_neg; ++j) smax = fmaxf(smax, v[j] * inv);
+            if (valid)
+                for (int j = 0; j < a.Q; ++j) a.rel[(size_t)j * a.P + px] = 1.f / (1.f + __expf(smax - v[j] * inv));
+        }
         fence_before();
         __syncthreads();
     }
@@ -1087,7 +1112,7 @@ le_status query_fused(int32_t P, const float* feat, const le_decoder* d, const f
     if ((st = set_smem(query_fused_kernel, smem)) != LE_OK) return st;
     const int ntiles = (P + 127) / 128;
     const int grid = ntiles < sm_count() ? ntiles : sm_count();
-    query_fused_kernel<<<grid, 128, smem, s>>>(a);
+    query_fused_kernel<<<grid, 128 * kQueryParts, smem, s>>>(a);
     LE_LAUNCHED();
     return LE_OK;
 }

@@ -163,6 +163,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v)
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// Store one FP32 value to a column of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, float v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(__float_as_uint(v)) : "memory");
+}
+
 // Single arrival on an mbarrier (release semantics at CTA scope).
 __device__ __forceinline__ void mbar_arrive(uint64_t* m)
 {
