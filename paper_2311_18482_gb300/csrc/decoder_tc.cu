@@ -10,20 +10,23 @@
 //   dec_fwd_kernel    inference (supp. Sec. "Inference"): argmax and/or
 //                     M_infer = softmax(logits), two tiles in flight per CTA.
 //   dec_train_kernel  training step (Eqs. 9-12): uncertainty-weighted CE,
-//                     dL/dR_u, and the whole backward on the tensor cores.
-//                     dL/dz, dL/dh2 and dL/dh1 are written once, pixel-major;
-//                     the input-gradient MMAs read them K-major and the
-//                     weight-gradient MMAs read the same buffers MN-major
-//                     (contracting over the tile's pixels), with a ones column
-//                     appended to each activation so the bias gradients come
-//                     out of the same MMAs.  Weight gradients accumulate in
-//                     TMEM over all tiles of a CTA and are flushed once.
+//                     dL/dR_u, and the whole backward on the tensor cores,
+//                     warp-specialised with two tiles in flight (one MMA
+//                     warp, four epilogue warpgroups).  dL/dz, dL/dh2 and
+//                     dL/dh1 are written once, pixel-major; the input-gradient
+//                     MMAs read them K-major and the weight-gradient MMAs read
+//                     the same buffers MN-major (contracting over the tile's
+//                     pixels); bias gradients are MMAs against a ones operand.
+//                     Weight gradients accumulate in TMEM over all tiles of a
+//                     CTA and are flushed once.
 //   query_fused_kernel relevancy (supp. Sec. "Inference", LERF): with
-//                     p = softmax(z), |F_clip|^2 = p^T (S_c S_c^T) p and
-//                     phi.q_j = p.(S_c q_j)/|F_clip|, so the 896-dim feature
-//                     map F is never formed; S_c S_c^T (N x N) is streamed
-//                     through shared memory in 64-column chunks with 1-D bulk
-//                     async copies, S_c [q; n] sits in shared memory.
+//                     p proportional to e = exp(z - max z), |F_clip|^2 =
+//                     p^T (S_c S_c^T) p and phi.q_j = p.(S_c q_j)/|F_clip|; the
+//                     relevancy does not depend on the scale of p, so neither
+//                     the softmax normaliser nor the 896-dim feature map F is
+//                     ever formed; S_c S_c^T (N x N) is streamed through shared
+//                     memory in 64-column chunks with 1-D bulk async copies,
+//                     S_c [q; n] sits in shared memory.
 //
 // Every mbarrier wait is bounded (about a second); on timeout the kernel
 // records it in g_tc_error, stops issuing work, frees its TMEM and returns.
@@ -802,7 +805,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) dec_train_kernel(DecArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Query: decode, softmax, relevancy.  Four warpgroups per CTA serve the same
+// Query: decode, softmax (unnormalised), relevancy.  Four warpgroups per CTA serve the same
 // 128 rows and split every epilogue by columns; TMEM: logits in [0, ncb)
 // (later the 16 text/negative projections in [0, 16) and the four parts'
 // partial p^T G p in columns 16-19), p^T G in [256, 256 + ncb).  The
@@ -874,13 +877,26 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
         const int px = tile * 128 + row;
         const bool valid = px < a.P;
         if (!mlp_forward(f, a, px, valid)) break;
-        float lse, zt, v[16];
-        int am;
-        logits_lse(f, a.ncb, lse, am, -1, zt);
+        // e = exp(z - max z) in BF16.  The relevancy phi.q / |phi| with
+        // phi = sum_c p_c s_c does not depend on the scale of p, so the
+        // softmax normaliser 1 / sum e is never needed.
+        float v[16], mh = -INFINITY;
         for (int c = c0; c < c1; c += 16) {
             tmem_ld16(f.tw + f.lane + c, v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __expf(v[j] + f.b3s[c + j] - lse);
+            for (int j = 0; j < 16; ++j) mh = fmaxf(mh, v[j] + f.b3s[c + j]);
+        }
+        f.xch[f.half * 128 + row].x = mh;
+        wg_sync(f);
+        float m = -INFINITY;
+#pragma unroll
+        for (int h = 0; h < kQueryParts; ++h) m = fmaxf(m, f.xch[h * 128 + row].x);
+        wg_sync(f);
+        const float ml = m * 1.4426950408889634f;
+        for (int c = c0; c < c1; c += 16) {
+            tmem_ld16(f.tw + f.lane + c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = ex2_approx(fmaf(v[j] + f.b3s[c + j], 1.4426950408889634f, -ml));
             sbuf_store8(Ps, row, c, v);
             sbuf_store8(Ps, row, c + 8, v + 8);
         }
@@ -918,7 +934,7 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
             }
         }
         if (!ok) break;
-        // relevancy: each part sums p^T G p over its columns into TMEM column 16 + part
+        // relevancy: each part sums e^T G e over its columns into TMEM column 16 + part
         float ptgp = 0.f, pp[16];
         for (int c = c0; c < c1; c += 16) {
             tmem_ld16(tbase + kTG + f.lane + c, v);
