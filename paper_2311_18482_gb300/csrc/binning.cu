@@ -11,7 +11,8 @@
 // ordered by depth, ties by Gaussian index.  It is computed without sorting the
 // K copies at all:
 //   1. e[i] = bits(depth_i) << 32 | i          (culled: 0xFFFFFFFF, sorted last)
-//   2. stable LSD radix sort of e on bits 32..63 (4 passes over the N Gaussians)
+//   2. stable LSD radix sort of e on bits 32..63 (4 passes over the N Gaussians,
+//      one kernel each, see depth_sort)
 //   3. split the depth-sorted Gaussians into chunks; per chunk, the number of
 //      copies in every tile from per-row difference arrays of the row spans
 //   4. one exclusive scan of those counts in tile-major order: entry (t, c) is
@@ -20,10 +21,8 @@
 //   5. blocks of (8 tile rows x a super-chunk of Gaussians) write the copies in
 //      depth order through per-tile cursors held in registers (one warp per
 //      row, one lane per 32nd tile of the row).
-// Each radix pass of step 2 is reduce-then-scan: per-block digit histograms,
-// one global exclusive scan (digit-major), then a stable block-local scatter
-// staged in shared memory.  No kernel waits on another block, so nothing can
-// spin.
+// Only the depth sort's look-back waits on other blocks (bounded, see
+// onesweep_kernel).
 #include <mutex>
 
 #include "common.cuh"
@@ -181,54 +180,93 @@ le_status exclusive_scan(In in, int n, uint32_t* out, uint32_t* partials, uint32
 }
 
 // ----------------------------------------------------------------------------
-// One stable LSD radix pass over u64 elements on digit (e >> shift) & (2^bits - 1).
+// Depth sort: stable LSD radix sort of e = bits(depth) << 32 | index on bits
+// 32-63 in four 8-bit passes, one kernel per pass.  The digit histograms of
+// all four passes are counted once, while the keys are built (they do not
+// depend on the order); each pass's blocks then find their offsets by
+// decoupled look-back: a block takes a virtual index in launch order,
+// publishes its per-digit counts, and adds up its predecessors' counts until
+// it meets one that has published its inclusive prefix.  A block only waits
+// for blocks that started before it, which publish their counts without
+// waiting; every wait is still bounded (about a second) and reports a timeout.
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kCountMask = (1u << 30) - 1u;
+constexpr int kSortPasses = 4;
 
-__device__ __forceinline__ uint32_t digit_of(uint64_t e, int shift, uint32_t mask)
+__device__ __forceinline__ uint32_t digit_of(uint64_t e, int shift) { return (uint32_t)(e >> shift) & 255u; }
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v)
 {
-    return (uint32_t)(e >> shift) & mask;
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t* __restrict__ in, int n, int shift,
-                                                              int bits, uint32_t* __restrict__ counts, int nb)
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p)
 {
-    __shared__ uint32_t hist[256];
-    const uint32_t radix = 1u << bits, mask = radix - 1;
-    for (uint32_t d = threadIdx.x; d < radix; d += kThreads) hist[d] = 0;
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// e[i] (culled: 0xFFFFFFFF in the high word, sorted last) and the histograms of
+// the four digits of the high word, hist[pass][digit].
+__global__ void __launch_bounds__(256) depth_elems_kernel(int n, const float* __restrict__ depth,
+                                                          const int* __restrict__ tiles, uint64_t* __restrict__ e,
+                                                          uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kSortPasses * 256];
+    for (int k = threadIdx.x; k < kSortPasses * 256; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    const int base = blockIdx.x * kTile;
-    for (int k = 0; k < kItems; ++k) {
-        const int i = base + k * kThreads + threadIdx.x;
-        if (i < n) atomicAdd(&hist[digit_of(in[i], shift, mask)], 1u);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = blockIdx.x * 1024 + r * 256 + threadIdx.x;
+        if (i < n) {
+            const uint32_t hi = tiles[i] > 0 ? __float_as_uint(depth[i]) : 0xFFFFFFFFu;
+            e[i] = ((uint64_t)hi << 32) | (uint32_t)i;
+#pragma unroll
+            for (int q = 0; q < kSortPasses; ++q) atomicAdd(&h[q * 256 + ((hi >> (8 * q)) & 255u)], 1u);
+        }
     }
     __syncthreads();
-    for (uint32_t d = threadIdx.x; d < radix; d += kThreads) counts[(size_t)d * nb + blockIdx.x] = hist[d];
+    for (int k = threadIdx.x; k < kSortPasses * 256; k += blockDim.x)
+        if (h[k]) atomicAdd(hist + k, h[k]);
 }
 
-// offs = exclusive scan of the digit-major counts, with offs[radix*nb] = n.
-__global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t* __restrict__ in,
-                                                                 uint64_t* __restrict__ out, int n, int shift,
-                                                                 int bits, const uint32_t* __restrict__ offs, int nb)
+// Exclusive scan of each pass's 256 digit counts, in place.
+__global__ void __launch_bounds__(kSortPasses * 256) digit_base_kernel(uint32_t* hist)
+{
+    __shared__ uint32_t sm[kSortPasses * 256];
+    const int t = threadIdx.x, d = t & 255;
+    const uint32_t v = hist[t];
+    sm[t] = v;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const uint32_t add = d >= o ? sm[t - o] : 0u;
+        __syncthreads();
+        sm[t] += add;
+        __syncthreads();
+    }
+    hist[t] = sm[t] - v;
+}
+
+// One pass on digit (e >> shift) & 255 from in to out.  dbase: the pass's
+// exclusive digit offsets; status: [blocks][256] look-back words (zeroed);
+// vctr: the pass's virtual-block counter (zeroed); err: set on a timed-out wait.
+__global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t* __restrict__ in,
+                                                            uint64_t* __restrict__ out, int n, int shift,
+                                                            const uint32_t* __restrict__ dbase, uint32_t* status,
+                                                            uint32_t* vctr, uint32_t* err)
 {
     __shared__ uint64_t stage[kTile];
     __shared__ uint32_t warp_cnt[kWarps][256];
     __shared__ uint32_t gbase[256], lbase[256];
     __shared__ uint32_t ws[kWarps];
-    const uint32_t radix = 1u << bits, mask = radix - 1;
+    __shared__ int s_vb;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int base = blockIdx.x * kTile;
-    const int cnt = min(kTile, n - base);
-
-    // block's digit counts from the scanned offsets, local exclusive prefix over digits
-    uint32_t c = 0;
-    if (threadIdx.x < (int)radix) {
-        const size_t k = (size_t)threadIdx.x * nb + blockIdx.x;
-        gbase[threadIdx.x] = offs[k];
-        c = offs[k + 1] - offs[k];
-    }
-    const uint32_t lb = block_exclusive_scan(c, ws, nullptr);
-    if (threadIdx.x < (int)radix) lbase[threadIdx.x] = lb;
+    if (threadIdx.x == 0) s_vb = (int)atomicAdd(vctr, 1u);
     for (int j = threadIdx.x; j < kWarps * 256; j += kThreads) (&warp_cnt[0][0])[j] = 0;
     __syncthreads();
+    const int vb = s_vb;
+    const int base = vb * kTile;
+    const int cnt = min(kTile, n - base);
 
     // each warp owns the contiguous sub-range [w*512, (w+1)*512) of the block
     const uint32_t lt = (1u << lane) - 1u;
@@ -239,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t*
         const int j = w * (kTile / kWarps) + k * 32 + lane;
         const bool valid = j < cnt;
         e[k] = valid ? in[base + j] : 0ull;
-        dg[k] = valid ? digit_of(e[k], shift, mask) : 0xFFFFFFFFu;
+        dg[k] = valid ? digit_of(e[k], shift) : 0xFFFFFFFFu;
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
         if (valid) {
             const uint32_t peers = __match_any_sync(vm, dg[k]);
@@ -248,16 +286,45 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t*
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps per digit
-    for (uint32_t d = threadIdx.x; d < radix; d += kThreads) {
-        uint32_t run = 0;
+    // per digit (thread d): exclusive prefix over warps and the block's count;
+    // publish the count, look back for the offset, publish the inclusive prefix
+    uint32_t tot = 0;
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;
         for (int ww = 0; ww < kWarps; ++ww) {
             const uint32_t v = warp_cnt[ww][d];
-            warp_cnt[ww][d] = run;
-            run += v;
+            warp_cnt[ww][d] = tot;
+            tot += v;
         }
+        uint32_t* mine = status + (size_t)vb * 256 + d;
+        uint32_t excl = 0;
+        if (vb == 0) {
+            st_release(mine, kFlagPre | tot);
+        } else {
+            st_release(mine, kFlagAgg | tot);
+            const long long t0 = clock64();
+            for (int b = vb - 1; b >= 0;) {
+                const uint32_t sv = ld_acquire(status + (size_t)b * 256 + d);
+                const uint32_t flag = sv & ~kCountMask;
+                if (flag == 0u) {
+                    if (clock64() - t0 > (1ll << 31)) {
+                        atomicExch(err, 1u);
+                        break;
+                    }
+                    continue;
+                }
+                excl += sv & kCountMask;
+                if (flag == kFlagPre) break;
+                --b;
+            }
+            st_release(mine, kFlagPre | (excl + tot));
+        }
+        gbase[d] = dbase[d] + excl;
     }
+    const uint32_t lb = block_exclusive_scan(tot, ws, nullptr);
+    if (threadIdx.x < 256) lbase[threadIdx.x] = lb;
     __syncthreads();
+    // stage the block's elements in digit order (stable), then write them out
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int j = w * (kTile / kWarps) + k * 32 + lane;
@@ -278,19 +345,9 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t*
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += kThreads) {
         const uint64_t v = stage[j];
-        const uint32_t d = digit_of(v, shift, mask);
+        const uint32_t d = digit_of(v, shift);
         out[gbase[d] + (j - lbase[d])] = v;
     }
-}
-
-// ----------------------------------------------------------------------------
-__global__ void depth_elems_kernel(int n, const float* __restrict__ depth, const int* __restrict__ tiles,
-                                   uint64_t* __restrict__ e)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t hi = tiles[i] > 0 ? __float_as_uint(depth[i]) : 0xFFFFFFFFu;
-    e[i] = ((uint64_t)hi << 32) | (uint32_t)i;
 }
 
 // Tiles [xl, xr) of rectangle row ty that the tile ellipse {e0, e1} reaches.
@@ -491,6 +548,7 @@ struct SortWs {
     ushort4* drect;
     float4* dell;
     uint32_t *counts, *base, *partials, *misc;
+    uint32_t* sort_state;   // [passes][256] digit counts / offsets, then [passes][blocks][256] look-back words
     int nchunks, chunk;
     size_t bytes;
 };
@@ -504,7 +562,13 @@ __host__ __device__ constexpr int chunks_for(int n)
 
 __host__ __device__ constexpr size_t seg(size_t bytes) { return (bytes + 255) / 256 * 256; }
 
+__host__ __device__ constexpr size_t sort_state_words(int n)
+{
+    return (size_t)kSortPasses * 256 * (1 + (size_t)((n + kTile - 1) / kTile));
+}
+
 // Scratch layout of le_bin_sort for n Gaussians (independent of the copy count).
+// misc: [0, 4) the passes' virtual-block counters, [4] the sort's timeout flag.
 __host__ __device__ constexpr size_t sort_ws_bytes(int n)
 {
     return seg(8ull * n) * 3 + seg(32ull * n) + seg(4ull * (256ull * ((n + kTile - 1) / kTile) + 1)) +
@@ -514,7 +578,7 @@ __host__ __device__ constexpr size_t sort_ws_bytes(int n)
                             : 256ull * ((n + kTile - 1) / kTile) + 1) /
                            kTile +
                        2)) +
-           seg(4ull * 64);
+           seg(4ull * 64) + seg(4ull * sort_state_words(n));
 }
 
 SortWs sort_ws_layout(char* base, int32_t n)
@@ -539,24 +603,22 @@ SortWs sort_ws_layout(char* base, int32_t n)
     w.base = (uint32_t*)take(4ull * count_len);
     w.partials = (uint32_t*)take(4ull * (scan_max / kTile + 2));
     w.misc = (uint32_t*)take(4ull * 64);
+    w.sort_state = (uint32_t*)take(4ull * sort_state_words(n));
     w.bytes = off;
     return w;
 }
 
-// Sort n u64 elements by bits [lo_bit, lo_bit + nbits) (stable, LSD).  Result in *cur.
-le_status radix_sort(uint64_t*& cur, uint64_t*& alt, int n, int lo_bit, int nbits, const SortWs& w, cudaStream_t s)
+// The four passes (the histograms are in w.sort_state, counted by
+// depth_elems_kernel).  Result in *cur.
+le_status depth_sort(uint64_t*& cur, uint64_t*& alt, int n, const SortWs& w, cudaStream_t s)
 {
-    if (n <= 0) return LE_OK;
     const int nb = nblocks(n);
-    for (int b = 0; b < nbits; b += 8) {
-        const int bits = nbits - b < 8 ? nbits - b : 8;
-        const int shift = lo_bit + b;
-        const int len = (1 << bits) * nb;
-        radix_hist_kernel<<<nb, kThreads, 0, s>>>(cur, n, shift, bits, w.counts, nb);
-        LE_LAUNCHED();
-        le_status st = exclusive_scan(DirectIn{w.counts}, len, w.counts, w.partials, w.counts + len, s);
-        if (st != LE_OK) return st;
-        radix_scatter_kernel<<<nb, kThreads, 0, s>>>(cur, alt, n, shift, bits, w.counts, nb);
+    digit_base_kernel<<<1, kSortPasses * 256, 0, s>>>(w.sort_state);
+    LE_LAUNCHED();
+    for (int q = 0; q < kSortPasses; ++q) {
+        uint32_t* status = w.sort_state + kSortPasses * 256 + (size_t)q * nb * 256;
+        onesweep_kernel<<<nb, kThreads, 0, s>>>(cur, alt, n, 32 + 8 * q, w.sort_state + q * 256, status,
+                                                w.misc + q, w.misc + 4);
         LE_LAUNCHED();
         uint64_t* t = cur;
         cur = alt;
@@ -608,10 +670,12 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     if (n == 0) return LE_OK;
 
     // 1-2: sort the Gaussians by depth (stable: equal depths keep index order; culled last)
-    depth_elems_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, depth, tiles_touched, w.eA);
+    LE_CUDA(cudaMemsetAsync(w.misc, 0, 4 * 64, s));
+    LE_CUDA(cudaMemsetAsync(w.sort_state, 0, 4 * sort_state_words(n), s));
+    depth_elems_kernel<<<(n + 1023) / 1024, 256, 0, s>>>(n, depth, tiles_touched, w.eA, w.sort_state);
     LE_LAUNCHED();
     uint64_t *cur = w.eA, *alt = w.eB;
-    if ((st = radix_sort(cur, alt, n, 32, 32, w, s)) != LE_OK) return st;
+    if ((st = depth_sort(cur, alt, n, w, s)) != LE_OK) return st;
     // 3: rectangles and ellipses in depth order; copies per (tile, chunk of depth-sorted Gaussians)
     gather_rect_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cur, tiles_touched, reinterpret_cast<const ushort4*>(rect),
                                                        reinterpret_cast<const float4*>(tile_ellipse), w.drect,
@@ -625,9 +689,14 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     // 4: one exclusive scan in tile-major order gives every (tile, chunk) base and K
     const int len = ntiles * w.nchunks;
     if ((st = exclusive_scan(DirectIn{w.base}, len, w.base, w.partials, w.base + len, s)) != LE_OK) return st;
-    uint32_t K32 = 0;
+    uint32_t K32 = 0, sort_err = 0;
     LE_CUDA(cudaMemcpyAsync(&K32, w.base + len, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LE_CUDA(cudaMemcpyAsync(&sort_err, w.misc + 4, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     LE_CUDA(cudaStreamSynchronize(s));
+    if (sort_err) {
+        set_error("the depth sort gave up on a bounded wait");
+        return LE_ERR_TIMEOUT;
+    }
     *k_out = K32;
     if ((int64_t)K32 > k_cap) {
         set_error("instance count K = %u exceeds k_cap = %lld", K32, (long long)k_cap);
