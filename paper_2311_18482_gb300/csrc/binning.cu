@@ -199,12 +199,17 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p)
+// Look-back words hold flag and count in one 32-bit word and guard no other
+// data, so relaxed (but coherent) loads suffice, and a window of them can be
+// in flight at once.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p)
 {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+
+constexpr int kLookWindow = 16;
 
 // e[i] (culled: 0xFFFFFFFF in the high word, sorted last) and the histograms of
 // the four digits of the high word, hist[pass][digit].
@@ -303,19 +308,33 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t* __re
         } else {
             st_release(mine, kFlagAgg | tot);
             const long long t0 = clock64();
+            // predecessors b, b-1, ... read kLookWindow at a time; stop at the first
+            // inclusive prefix, re-read from the first one not yet published
             for (int b = vb - 1; b >= 0;) {
-                const uint32_t sv = ld_acquire(status + (size_t)b * 256 + d);
-                const uint32_t flag = sv & ~kCountMask;
-                if (flag == 0u) {
-                    if (clock64() - t0 > (1ll << 31)) {
-                        atomicExch(err, 1u);
-                        break;
+                uint32_t sv[kLookWindow];
+#pragma unroll
+                for (int k = 0; k < kLookWindow; ++k)
+                    sv[k] = b - k >= 0 ? ld_relaxed(status + (size_t)(b - k) * 256 + d) : kFlagPre;
+                int used = kLookWindow;
+                bool found = false, waiting = false;
+#pragma unroll
+                for (int k = 0; k < kLookWindow; ++k) {
+                    if (found || waiting) continue;
+                    const uint32_t flag = sv[k] & ~kCountMask;
+                    if (flag == 0u) {
+                        waiting = true;
+                        used = k;
+                    } else {
+                        excl += sv[k] & kCountMask;
+                        if (flag == kFlagPre) found = true;
                     }
-                    continue;
                 }
-                excl += sv & kCountMask;
-                if (flag == kFlagPre) break;
-                --b;
+                if (found) break;
+                b -= used;
+                if (waiting && clock64() - t0 > (1ll << 31)) {
+                    atomicExch(err, 1u);
+                    break;
+                }
             }
             st_release(mine, kFlagPre | (excl + tot));
         }
