@@ -85,9 +85,12 @@ typedef struct le_gaussian_grads {
 
 /* Screen-space state produced by le_preprocess.  Host struct of device pointers.
  * splat record, 20 floats per Gaussian (80 bytes, the unit the renderer reads):
- *   [0,1] mean2d x,y  [2,3,4] conic A,B,C (inverse 2D covariance)  [5] opacity
- *   [6,7,8] rgb  [9] u  [10..17] s_G  [18,19] unused
- * grad2d records (le_render_bwd) use the same layout for dL/d of each field. */
+ *   [0,1] mean2d x,y  [2,3,4] the conic (A, B, C) = inverse 2D covariance, stored
+ *   in base-2 exponent units as (A log2(e)/2, B log2(e), C log2(e)/2), so that
+ *   alpha = o 2^-(A' dx^2 + B' dx dy + C' dy^2)  [5] opacity  [6,7,8] rgb  [9] u
+ *   [10..17] s_G  [18,19] unused
+ * grad2d records (le_render_bwd) use the same layout for dL/d of each field,
+ * the conic slots holding dL/dA, dL/dB, dL/dC of the unscaled conic. */
 typedef struct le_projected {
     float* splat;             /* [n,20] */
     float* depth;             /* [n]  view-space z (sort key) */

@@ -48,6 +48,20 @@ inline int tiles_x(const le_camera* c) { return (c->width + LE_TILE - 1) / LE_TI
 inline int tiles_y(const le_camera* c) { return (c->height + LE_TILE - 1) / LE_TILE; }
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// 2^x on the special-function unit (approximate, flush-to-zero).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The splat record stores the conic in base-2 exponent units, so that
+// alpha = o 2^-q with q = A' dx^2 + B' dx dy + C' dy^2 (kConicScale*: A' = A log2(e)/2,
+// B' = B log2(e), C' = C log2(e)/2).  kConicUnscale* undo it.
+constexpr float kConicScaleAC = 0.72134752044448170f, kConicScaleB = 1.4426950408889634f;
+constexpr float kConicUnscaleAC = 1.3862943611198906f, kConicUnscaleB = 0.69314718055994531f;
+
 // Adam (Kingma & Ba; Sec. 4 trains with it) with both bias corrections folded
 // in: step_size = lr / (1 - b1^t), inv_sqrt_c2 = 1 / sqrt(1 - b2^t).
 struct AdamParams {

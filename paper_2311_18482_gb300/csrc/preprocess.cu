@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(int n, const float* __r
     }
     const float4 f0 = __ldg(reinterpret_cast<const float4*>(feat) + 2 * i);
     const float4 f1 = __ldg(reinterpret_cast<const float4*>(feat) + 2 * i + 1);
-    rec[0] = make_float4(g.mx, g.my, A, B);
-    rec[1] = make_float4(C, op, col[0], col[1]);
+    rec[0] = make_float4(g.mx, g.my, A * kConicScaleAC, B * kConicScaleB);
+    rec[1] = make_float4(C * kConicScaleAC, op, col[0], col[1]);
     rec[2] = make_float4(col[2], __ldg(unc + i), f0.x, f0.y);
     rec[3] = make_float4(f0.z, f0.w, f1.x, f1.y);
     rec[4] = make_float4(f1.z, f1.w, 0.f, 0.f);

@@ -29,17 +29,21 @@ namespace {
 
 constexpr int kBlock = LE_TILE * LE_TILE;
 
-// power = -(A dx^2 + C dy^2)/2 - B dx dy with a fixed operation order, so the
-// forward and backward kernels take identical skip decisions.
-__device__ __forceinline__ float splat_power(float A, float B, float C, float dx, float dy)
+// q = A' dx^2 + B' dx dy + C' dy^2 in base-2 exponent units (the record's scaled
+// conic; alpha = o 2^-q), with a fixed operation order: the forward and the
+// backward kernel take identical skip decisions.  ax = A' dx^2 and bx = B' dx
+// depend on the column only, so the backward computes them once for its two
+// pixels of a column.
+__device__ __forceinline__ float splat_ax(float Ap, float dx) { return __fmul_rn(Ap, __fmul_rn(dx, dx)); }
+__device__ __forceinline__ float splat_bx(float Bp, float dx) { return __fmul_rn(Bp, dx); }
+__device__ __forceinline__ float splat_q(float ax, float bx, float Cp, float dy)
 {
-    const float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+    return __fmaf_rn(Cp, __fmul_rn(dy, dy), __fmaf_rn(bx, dy, ax));
 }
 
-__device__ __forceinline__ float splat_alpha0(float opacity, float power)
+__device__ __forceinline__ float splat_alpha0(float opacity, float q)
 {
-    return __fmul_rn(opacity, __expf(power));
+    return __fmul_rn(opacity, ex2_approx(-q));
 }
 
 __global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
@@ -78,9 +82,9 @@ __global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const
         for (int j = 0; !done && j < cnt; ++j) {
             const float4 g0 = rec[0][j], g1 = rec[1][j];
             const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
-            const float power = splat_power(g0.z, g0.w, g1.x, dx, dy);
-            if (power > 0.f) continue;
-            const float alpha = fminf(0.99f, splat_alpha0(g1.y, power));
+            const float q = splat_q(splat_ax(g0.z, dx), splat_bx(g0.w, dx), g1.x, dy);
+            if (q < 0.f) continue;
+            const float alpha = fminf(0.99f, splat_alpha0(g1.y, q));
             if (alpha < (1.f / 255.f)) continue;
             const float test = T * (1.f - alpha);
             if (test < 1e-4f) {
@@ -231,16 +235,17 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
             const int pos = b_start + j;
             const float4 g0 = rec[0][j], g1 = rec[1][j];
             const float dx = __fsub_rn(g0.x, fpx);
+            const float ax = splat_ax(g0.z, dx), bx = splat_bx(g0.w, dx);
             float dy[PPT], G[PPT], a0[PPT], alpha[PPT];
             bool contrib[PPT], any_mine = false;
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
                 dy[q] = __fsub_rn(g0.y, py[q]);
-                const float power = splat_power(g0.z, g0.w, g1.x, dx, dy[q]);
-                G[q] = __expf(power);
+                const float qq = splat_q(ax, bx, g1.x, dy[q]);
+                G[q] = ex2_approx(-qq);
                 a0[q] = __fmul_rn(g1.y, G[q]);
                 alpha[q] = fminf(0.99f, a0[q]);
-                contrib[q] = pos < last[q] && power <= 0.f && alpha[q] >= (1.f / 255.f);
+                contrib[q] = pos < last[q] && qq >= 0.f && alpha[q] >= (1.f / 255.f);
                 any_mine = any_mine || contrib[q];
             }
             if (!__any_sync(0xffffffffu, any_mine)) continue;
@@ -249,6 +254,8 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
             for (int c = 0; c < 18; ++c) gr[c] = 0.f;
             if (any_mine) {
                 const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
+                // the conic itself, for the mean gradient (dL/dpower is per unit of the natural exponent)
+                const float cA = g0.z * kConicUnscaleAC, cB = g0.w * kConicUnscaleB, cC = g1.x * kConicUnscaleAC;
                 const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
@@ -270,8 +277,8 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
                         gr[2] = fmaf(-0.5f * dpow * dx, dx, gr[2]);
                         gr[3] = fmaf(-dpow * dx, dy[q], gr[3]);
                         gr[4] = fmaf(-0.5f * dpow * dy[q], dy[q], gr[4]);
-                        gr[0] = fmaf(dpow, -g0.z * dx - g0.w * dy[q], gr[0]);
-                        gr[1] = fmaf(dpow, -g1.x * dy[q] - g0.w * dx, gr[1]);
+                        gr[0] = fmaf(dpow, -cA * dx - cB * dy[q], gr[0]);
+                        gr[1] = fmaf(dpow, -cC * dy[q] - cB * dx, gr[1]);
                     }
                 }
             }

@@ -175,13 +175,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* m)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
 }
 
-// 2^x on the special-function unit (approximate, flush-to-zero).
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // ---------------------------------------------------------------------------
 // Canonical no-swizzle bf16 buffer in shared memory.

@@ -39,7 +39,8 @@ def _check_preprocess(proj, sc, kp, pr):
     assert np.array_equal(to_np(proj.tile_ellipse).view(np.uint32), kp["ell"].view(np.uint32))
     sp = to_np(proj.splat)
     assert np.array_equal(sp[vis, 0:2].view(np.uint32), kp["mean2d"][vis].view(np.uint32))
-    assert rel_err(sp[vis, 2:5], pr["conic"][vis]) < 1e-5
+    l2e = np.log2(np.e)
+    assert rel_err(sp[vis, 2:5] / np.array([l2e / 2, l2e, l2e / 2]), pr["conic"][vis]) < 1e-5   # base-2 units
     assert rel_err(sp[vis, 5], pr["opacity"][vis]) < 1e-5
     assert rel_err(sp[vis, 6:9], pr["rgb"][vis]) < 1e-5
     assert np.array_equal(sp[vis, 9], sc.unc[vis])

@@ -6,9 +6,11 @@ code is compiled once per path, and the compiler may contract a multiply-add
 differently in each copy, so a gradient can differ in its last bits.
   1. Gradients: one step with lr = 0 leaves the parameters unchanged and the
      first moment is (1 - beta1) g on both paths; per field, |dm| must stay
-     within 1e-5 of the field's largest |m| (the screen-space gradients are
-     summed with atomic adds, whose order varies from run to run; sums with
-     cancellation then differ by ~1e-6 of the field's scale), and the
+     within 1e-4 of the field's largest |m| -- the bar of the rasterizer's
+     gradient parity (the screen-space gradients are summed with atomic adds
+     whose order varies from run to run, and the quaternion gradient's
+     tangent projection cancels, so runs differ by up to ~1e-5 of the field's
+     scale; a wrong element or field would differ by O(1)) -- and the
      parameters must be identical.
   2. Training: three steps on both paths; the losses of every step agree to
      1e-4 relative (small differences change later renders a little), u stays
@@ -48,7 +50,7 @@ def test_fused_adam_gradients_match(leg):
         d = (va[k] - vb[k]).abs()
         scale = va[k].abs().max().clamp_min(1e-30)
         print(f"m.{k}: max |diff| / max |m| {float(d.max() / scale):.2e}, identical {float((d == 0).float().mean()):.4f}")
-        assert float(d.max()) <= 1e-5 * float(scale), k
+        assert float(d.max()) <= 1e-4 * float(scale), k
     assert float(va["means"].abs().max()) > 0
 
 
