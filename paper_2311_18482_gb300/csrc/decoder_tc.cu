@@ -354,7 +354,10 @@ __host__ constexpr size_t train_smem(int ncb)
 
 // Issue MMA stage `st` (0-5) of the slot whose buffers start at shared address
 // q.  `init`: the first tile of this CTA, whose weight-gradient MMAs overwrite
-// their accumulators.
+// their accumulators.  Each operand's descriptor is built once per stage; the
+// next 16-wide K step only moves the start address, by 16 (K-major: one pair
+// of core matrices, 256 B) or by 2C (MN-major over a C-column buffer: two
+// 8-row groups, 32 C bytes) in descriptor units of 16 B.
 __device__ __forceinline__ void train_stage(int st, int ncb, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t e,
                                             uint32_t q, uint32_t tw, uint32_t tb, bool init)
 {
@@ -364,54 +367,57 @@ __device__ __forceinline__ void train_stage(int st, int ncb, uint32_t w1, uint32
         case 0:
             mma(tw, kdesc_at(x1, 16, 0, 0), kdesc_at(w1, 16, 0, 0), idesc_bf16(kH1, false, false), 0);
             break;
-        case 1:
+        case 1: {
+            const uint64_t a = kdesc_at(h1, kH1, 0, 0), b = kdesc_at(w2, kH1, 0, 0);
 #pragma unroll
-            for (int k = 0; k < kH1 / 16; ++k)
-                mma(tw, kdesc_at(h1, kH1, 0, 16 * k), kdesc_at(w2, kH1, 0, 16 * k), idesc_bf16(kH2, false, false),
-                    k > 0);
+            for (int k = 0; k < kH1 / 16; ++k) mma(tw, a + 16 * k, b + 16 * k, idesc_bf16(kH2, false, false), k > 0);
             break;
-        case 2:
+        }
+        case 2: {
+            const uint64_t a = kdesc_at(h2, 128, 0, 0), b = kdesc_at(w3, 128, 0, 0);
+            const uint32_t id = idesc_bf16(ncb, false, false);
 #pragma unroll
-            for (int k = 0; k < kH2 / 16; ++k)
-                mma(tw, kdesc_at(h2, 128, 0, 16 * k), kdesc_at(w3, 128, 0, 16 * k), idesc_bf16(ncb, false, false),
-                    k > 0);
+            for (int k = 0; k < kH2 / 16; ++k) mma(tw, a + 16 * k, b + 16 * k, id, k > 0);
             break;
-        case 3:
+        }
+        case 3: {
+            const uint64_t ak = kdesc_at(d, 128, 0, 0), w3m = mndesc_at(w3, 128, 0, 0);
             for (int k = 0; k < ncb / 16; ++k)
-                mma(tw, kdesc_at(d, 128, 0, 16 * k), mndesc_at(w3, 128, 16 * k, 0), idesc_bf16(kH2, false, true),
-                    k > 0);
+                mma(tw, ak + 16 * k, w3m + 256 * k, idesc_bf16(kH2, false, true), k > 0);
+            const uint64_t am = mndesc_at(d, 128, 0, 0), h2m = mndesc_at(h2, 128, 0, 0), em = mndesc_at(e, kEC, 0, 0);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                mma(tb + kTW3, mndesc_at(d, 128, 16 * k, 0), mndesc_at(h2, 128, 16 * k, 0),
-                    idesc_bf16(kH2, true, true), k > 0 ? 1u : keep);
+                mma(tb + kTW3, am + 256 * k, h2m + 256 * k, idesc_bf16(kH2, true, true), k > 0 ? 1u : keep);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                mma(tb + kTP, mndesc_at(d, 128, 16 * k, 0), mndesc_at(e, kEC, 16 * k, 0), idesc_bf16(16, true, true),
-                    k > 0 ? 1u : keep);
+                mma(tb + kTP, am + 256 * k, em + 2 * kEC * k, idesc_bf16(16, true, true), k > 0 ? 1u : keep);
             break;
-        case 4:
+        }
+        case 4: {
+            const uint64_t ak = kdesc_at(h2, 128, 0, 0), w2m = mndesc_at(w2, kH1, 0, 0);
 #pragma unroll
             for (int k = 0; k < kH2 / 16; ++k)
-                mma(tw, kdesc_at(h2, 128, 0, 16 * k), mndesc_at(w2, kH1, 16 * k, 0), idesc_bf16(kH1, false, true),
-                    k > 0);
+                mma(tw, ak + 16 * k, w2m + 2 * kH1 * k, idesc_bf16(kH1, false, true), k > 0);
+            const uint64_t am = mndesc_at(h2, 128, 0, 0), h1m = mndesc_at(h1, kH1, 0, 0),
+                           em = mndesc_at(e, kEC, 0, 8);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                mma(tb + kTW2, mndesc_at(h2, 128, 16 * k, 0), mndesc_at(h1, kH1, 16 * k, 0),
-                    idesc_bf16(kH1, true, true), k > 0 ? 1u : keep);
+                mma(tb + kTW2, am + 256 * k, h1m + 2 * kH1 * k, idesc_bf16(kH1, true, true), k > 0 ? 1u : keep);
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                mma(tb + kTP, mndesc_at(h2, 128, 16 * k, 0), mndesc_at(e, kEC, 16 * k, 8), idesc_bf16(16, true, true),
-                    1u);
+            for (int k = 0; k < 8; ++k) mma(tb + kTP, am + 256 * k, em + 2 * kEC * k, idesc_bf16(16, true, true), 1u);
             break;
-        default:
+        }
+        default: {
+            const uint64_t ak = kdesc_at(d, 128, 0, 0), w1m = mndesc_at(w1, 16, 0, 0);
 #pragma unroll
             for (int k = 0; k < kH1 / 16; ++k)
-                mma(tw, kdesc_at(d, 128, 0, 16 * k), mndesc_at(w1, 16, 16 * k, 0), idesc_bf16(16, false, true), k > 0);
+                mma(tw, ak + 16 * k, w1m + 2 * 16 * k, idesc_bf16(16, false, true), k > 0);
+            const uint64_t am = mndesc_at(d, 128, 0, 0), x1m = mndesc_at(x1, 16, 0, 0);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                mma(tb + kTQ, mndesc_at(d, 128, 16 * k, 0), mndesc_at(x1, 16, 16 * k, 0), idesc_bf16(16, true, true),
-                    k > 0 ? 1u : keep);
+                mma(tb + kTQ, am + 256 * k, x1m + 2 * 16 * k, idesc_bf16(16, true, true), k > 0 ? 1u : keep);
             break;
+        }
     }
 }
 
