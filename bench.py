@@ -111,18 +111,18 @@ def measured_peaks():
 
 # ---------------------------------------------------------------------------
 STAGE_CALLS = {"preprocess": "le_preprocess (preprocess_kernel)",
-               "bin_sort": "le_bin_sort (depth radix sort, chunk_count, scan, place_kernel)",
-               "render_fwd": "le_render_fwd (render_fwd_kernel)",
+               "bin_render": "le_bin_render_fwd (depth radix sort, chunk counts, scan, lazily placed copies "
+                             "and compositing)",
                "decoder": "le_decode fused (dec_train_kernel)",
                "render_bwd": "le_render_bwd_adam (render_bwd_kernel + preprocess_bwd_kernel with the Gaussians' "
                              "Adam step fused in)",
                "adam": "le_adam (adam_kernel, decoder parameters)"}
-STAGE_SOURCES = {"preprocess": ["preprocess.cu"], "bin_sort": ["binning.cu"], "render_fwd": ["render.cu"],
+STAGE_SOURCES = {"preprocess": ["preprocess.cu"], "bin_render": ["binning.cu", "render.cu"],
                  "decoder": ["decoder_tc.cu", "tc_common.cuh"],
                  "render_bwd": ["render.cu", "preprocess.cu", "common.cuh"], "adam": ["train.cu", "common.cuh"]}
 
 
-def stage_bytes(N, n_vis, K, P, T, nc, total_scalars):
+def stage_bytes(N, n_vis, K, P, T, nc, total_scalars, K_read):
     """Compulsory HBM bytes per call of each stage (each input read once, each output written once).
     render_bwd includes the Gaussians' Adam step fused into it: read m, v and the
     parameters the projection does not read, write parameters, m and v."""
@@ -130,10 +130,10 @@ def stage_bytes(N, n_vis, K, P, T, nc, total_scalars):
     geo = 4 * (3 + 3 + 4 + 1 + 3 * nc)                  # parameters the projection reads
     return {
         "preprocess": N * par + N * (80 + 4 + 4 + 8 + 4 + 1 + 32),
-        "bin_sort": N * (4 + 4) + n_vis * (8 + 32) + 4 * K + 8 * T,
-        "render_fwd": 4 * K + 80 * n_vis + 56 * P,
+        # binning inputs, the list entries the compositing reads (written once, read once), records, images
+        "bin_render": N * (4 + 4) + n_vis * (8 + 32) + 8 * T + 8 * K_read + 80 * n_vis + 56 * P,
         "decoder": (36 + 4 + 36) * P,
-        "render_bwd": 4 * K + 80 * n_vis + 104 * P + 80 * N + geo * N + 80 * N + (par - geo) * N + 5 * par * N
+        "render_bwd": 4 * K_read + 80 * n_vis + 104 * P + 80 * N + geo * N + 80 * N + (par - geo) * N + 5 * par * N
                       + 5 * N,
         "adam": 28 * (total_scalars - par // 4 * N),
     }
@@ -274,6 +274,7 @@ def run_ours(args, rank, world):
            "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12},
            "gpu_launches": launches, "clocks": clk, "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
            "instances_K": K_mean}
+    # (instances_read is added with the roofline below)
 
     # --- roofline of the dominant stage: compulsory HBM bytes (every datum read or
     # written once) / event-timed stage duration, against the measured copy bandwidth
@@ -281,7 +282,10 @@ def run_ours(args, rank, world):
     nc = (scene.sh_degree + 1) ** 2
     N = args.n
     n_vis = int((st.proj.tiles_touched > 0).sum().item())
-    alg_bytes = stage_bytes(N, n_vis, K_mean, P, ((W + 15) // 16) * ((H + 15) // 16), nc, st.layout.total)
+    # list entries any pixel reads: per tile, the largest n_contrib (last view)
+    ncb = torch.nn.functional.pad(st.img.n_contrib.float(), (0, (-W) % 16, 0, (-H) % 16))
+    K_read = int(torch.nn.functional.max_pool2d(ncb[None, None], 16).sum().item())
+    alg_bytes = stage_bytes(N, n_vis, K_mean, P, ((W + 15) // 16) * ((H + 15) // 16), nc, st.layout.total, K_read)
     dom = max((k for k in stage_ms if k in alg_bytes), key=lambda k: stage_ms[k])
     ach = alg_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
     out["roofline"] = {"kernel": STAGE_CALLS[dom], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
@@ -292,6 +296,7 @@ def run_ours(args, rank, world):
     out["stage_hbm_frac"] = {k: round(alg_bytes[k] / (stage_ms[k] * 1e-3) / 1e9 / hbm_peak, 4)
                              for k in stage_ms if k in alg_bytes}
     out["visible_gaussians"] = n_vis
+    out["instances_read"] = K_read
 
     if not args.no_extras and rank == 0:
         out["fused_vs_plain"] = compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, args)
@@ -358,8 +363,7 @@ def query_leg(leg, synth, scene, cams, args):
 
             def once(k):
                 leg.le_preprocess(g, cams[k], proj)
-                ids, ranges, K, _ = leg.le_bin_sort(cams[k], proj, bins)
-                leg.le_render_fwd(cams[k], proj, ids, ranges, img)
+                ids, ranges, K, _ = leg.le_bin_render_fwd(cams[k], proj, bins, img)
                 if mode == leg.UNFUSED_FP32:
                     leg.le_decode_raw(mode, P, img.feat, None, decs, None, 1.0, 1.0, None, None, None, None, None,
                                       prob, None, ws_d)

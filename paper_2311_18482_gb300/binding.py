@@ -74,6 +74,8 @@ _SIG = {
     "le_bin_sort_static": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, C.c_int64, _P, _P, _P,
                            C.POINTER(C.c_int64), _P],
     "le_render_fwd": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "le_bin_render_fwd": [C.POINTER(LeCamera), C.c_int32, _P, _P, _P, _P, _P, _P, C.c_size_t, C.c_int64, _P, _P,
+                          C.POINTER(C.c_int64), _P, _P, _P, _P, _P, _P],
     "le_render_bwd": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P, _P, _P,
                       _P, _P, C.POINTER(LeGaussianGrads), _P],
     "le_render_bwd_adam": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P, _P,
@@ -326,6 +328,34 @@ def le_render_fwd(cam, proj: Projected, ids, ranges, out: Image | None = None) -
                                 _ptr(out.rgb), _ptr(out.feat), _ptr(out.unc), _ptr(out.T), _ptr(out.n_contrib),
                                 _stream()))
     return out
+
+
+def le_bin_render_fwd(cam, proj: Projected, buffers: BinSortBuffers | None = None, out: Image | None = None,
+                      k_cap: int | None = None):
+    """le_bin_sort + le_render_fwd with lazy placement (see leg.h).  Returns
+    (sorted_ids, tile_ranges, K, image); ids are written up to every tile's
+    last reached entry.  Retries once with a larger capacity on LE_ERR_CAPACITY."""
+    n = proj.depth.shape[0]
+    ntiles = ((cam.W + TILE - 1) // TILE) * ((cam.H + TILE - 1) // TILE)
+    buffers = buffers or BinSortBuffers()
+    out = out or Image.empty(cam.H, cam.W, proj.splat.device)
+    k_cap = k_cap if k_cap is not None else max(buffers.k_cap, 16 * n, 1024)
+    cs = camera_struct(cam)
+    for _ in range(2):
+        buffers.ensure(n, k_cap, ntiles, proj.depth.device)
+        K = C.c_int64()
+        st = load().le_bin_render_fwd(C.byref(cs), n, _ptr(proj.splat), _ptr(proj.depth), _ptr(proj.rect),
+                                      _ptr(proj.tile_ellipse), _ptr(proj.tiles_touched), _ptr(buffers.ws),
+                                      buffers.ws.numel(), buffers.k_cap, _ptr(buffers.ids), _ptr(buffers.ranges),
+                                      C.byref(K), _ptr(out.rgb), _ptr(out.feat), _ptr(out.unc), _ptr(out.T),
+                                      _ptr(out.n_contrib), _stream())
+        if st == LE_ERR_CAPACITY:
+            k_cap = int(K.value * 1.25) + 1024
+            continue
+        _check(st)
+        k = K.value
+        return buffers.ids[:k], buffers.ranges[:ntiles], k, out
+    raise LegError(LE_ERR_CAPACITY, "capacity retry failed")
 
 
 def le_render_bwd(cam, g: Gaussians, proj: Projected, ids, ranges, img: Image, dL_drgb, dL_dfeat, dL_dunc,

@@ -470,6 +470,9 @@ constexpr int kPlaceRows = kPlaceThreads / 32;
 
 constexpr int kPlaceBatch = 4 * kPlaceThreads;   // Gaussians examined per compaction round
 
+// tile_act / rows_act (nullable): only tiles with a non-zero flag get copies,
+// blocks of row groups without one return at once; super-chunk blockIdx.y is
+// super_base + blockIdx.y.
 template <int NK>
 __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint64_t* __restrict__ dsorted,
                                                               const ushort4* __restrict__ drect,
@@ -477,8 +480,11 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
                                                               const float* __restrict__ depth, int TX, int TY,
                                                               int super_chunk, int cstride, int nchunks,
                                                               const uint32_t* __restrict__ base,
-                                                              uint32_t* __restrict__ ids, uint64_t* __restrict__ keys)
+                                                              uint32_t* __restrict__ ids, uint64_t* __restrict__ keys,
+                                                              const uint8_t* __restrict__ tile_act,
+                                                              const uint8_t* __restrict__ rows_act, int super_base)
 {
+    if (rows_act && !rows_act[blockIdx.x]) return;
     __shared__ uint32_t sg[kPlaceBatch], sj[kPlaceBatch];
     __shared__ ushort4 sr[kPlaceBatch];
     __shared__ uint32_t ws[kWarps];
@@ -486,12 +492,15 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
     const int row = blockIdx.x * kPlaceRows + (threadIdx.x >> 5);
     const bool row_ok = row < TY;
     const int rb = blockIdx.x * kPlaceRows, re = min(TY, rb + kPlaceRows);
-    const int C = blockIdx.y;
+    const int C = super_base + blockIdx.y;
     uint32_t ctr[NK];
+    uint32_t act = 0;   // bit k: this lane's tile lane + 32 k takes copies
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         const int tx = lane + 32 * k;
-        ctr[k] = (row_ok && tx < TX) ? base[(size_t)(row * TX + tx) * nchunks + (size_t)C * cstride] : 0u;
+        const bool ok = row_ok && tx < TX;
+        ctr[k] = ok ? base[(size_t)(row * TX + tx) * nchunks + (size_t)C * cstride] : 0u;
+        if (ok && (!tile_act || tile_act[row * TX + tx])) act |= 1u << k;
     }
     const int j0 = C * super_chunk, j1 = min(n, j0 + super_chunk);
     for (int jb = j0; jb < j1; jb += kPlaceBatch) {
@@ -538,7 +547,7 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
 #pragma unroll
                 for (int k = 0; k < NK; ++k) {
                     const int tx = lane + 32 * k;
-                    if (tx >= bl && tx < br) {
+                    if (tx >= bl && tx < br && ((act >> k) & 1u)) {
                         const uint32_t p = ctr[k];
                         ids[p] = gid;
                         if (keys) keys[p] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | dbits;
@@ -568,6 +577,7 @@ struct SortWs {
     float4* dell;
     uint32_t *counts, *base, *partials, *misc;
     uint32_t* sort_state;   // [passes][256] digit counts / offsets, then [passes][blocks][256] look-back words
+    uint8_t* flags;         // lazy placement: two tile-activity arrays [kMaxTiles], two row-group arrays [64]
     int nchunks, chunk;
     size_t bytes;
 };
@@ -597,7 +607,7 @@ __host__ __device__ constexpr size_t sort_ws_bytes(int n)
                             : 256ull * ((n + kTile - 1) / kTile) + 1) /
                            kTile +
                        2)) +
-           seg(4ull * 64) + seg(4ull * sort_state_words(n));
+           seg(4ull * 64) + seg(4ull * sort_state_words(n)) + seg(2ull * (kMaxTiles + 64));
 }
 
 SortWs sort_ws_layout(char* base, int32_t n)
@@ -623,6 +633,7 @@ SortWs sort_ws_layout(char* base, int32_t n)
     w.partials = (uint32_t*)take(4ull * (scan_max / kTile + 2));
     w.misc = (uint32_t*)take(4ull * 64);
     w.sort_state = (uint32_t*)take(4ull * sort_state_words(n));
+    w.flags = (uint8_t*)take(2ull * (kMaxTiles + 64));
     w.bytes = off;
     return w;
 }
@@ -659,25 +670,29 @@ extern "C" le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* byt
     return LE_OK;
 }
 
-extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
-                                 const float* tile_ellipse, const int32_t* tiles_touched, void* workspace,
-                                 size_t workspace_bytes, int64_t k_cap,
-                                 uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
-                                 void* stream)
+namespace leg {
+namespace {
+
+// Steps 1-4 of the binning (depth sort, counts, tile-major scan, K, ranges):
+// everything except placing the copies.  Returns with *K = 0 and nothing
+// launched beyond the range reset when n == 0.
+le_status bin_prepare(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
+                      const float* tile_ellipse, const int32_t* tiles_touched, void* workspace,
+                      size_t workspace_bytes, int64_t k_cap, bool need_ids, uint32_t* tile_ranges, int64_t* k_out,
+                      cudaStream_t s, SortWs& w, uint64_t*& cur)
 {
     le_status st = check_camera(cam);
     if (st != LE_OK) return st;
     LE_CHECK_ARG(n >= 0 && k_cap >= 0 && k_cap < (int64_t)1 << 31, "n or k_cap out of range");
     LE_CHECK_ARG(k_out != nullptr && tile_ranges != nullptr, "k_out and tile_ranges are required");
     LE_CHECK_ARG(n == 0 || (depth && rect && tile_ellipse && tiles_touched), "null input pointer");
-    LE_CHECK_ARG(k_cap == 0 || sorted_ids, "sorted_ids is null");
+    LE_CHECK_ARG(k_cap == 0 || need_ids, "sorted_ids is null");
     LE_CHECK_ARG(workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u) == 0,
                  "workspace must be non-null and 256-byte aligned");
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(rect) & 7u) == 0, "rect must be 8-byte aligned");
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(tile_ellipse) & 15u) == 0, "tile_ellipse must be 16-byte aligned");
-    const SortWs w = sort_ws_layout(static_cast<char*>(workspace), n);
+    w = sort_ws_layout(static_cast<char*>(workspace), n);
     LE_CHECK_ARG(workspace_bytes >= w.bytes, "workspace too small: %zu < %zu", workspace_bytes, w.bytes);
-    cudaStream_t s = as_stream(stream);
     const int TX = tiles_x(cam), TY = tiles_y(cam);
     const int ntiles = TX * TY;
     if (ntiles > kMaxTiles || TX > 256) {
@@ -693,7 +708,8 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     LE_CUDA(cudaMemsetAsync(w.sort_state, 0, 4 * sort_state_words(n), s));
     depth_elems_kernel<<<(n + 1023) / 1024, 256, 0, s>>>(n, depth, tiles_touched, w.eA, w.sort_state);
     LE_LAUNCHED();
-    uint64_t *cur = w.eA, *alt = w.eB;
+    cur = w.eA;
+    uint64_t* alt = w.eB;
     if ((st = depth_sort(cur, alt, n, w, s)) != LE_OK) return st;
     // 3: rectangles and ellipses in depth order; copies per (tile, chunk of depth-sorted Gaussians)
     gather_rect_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cur, tiles_touched, reinterpret_cast<const ushort4*>(rect),
@@ -724,19 +740,41 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     if (K32 == 0) return LE_OK;
     ranges_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(ntiles, w.nchunks, w.base, tile_ranges);
     LE_LAUNCHED();
-    // 5: place every copy; super-chunks of `cs` count chunks, small enough for about
-    //    eight waves of blocks (row groups differ a lot in work; many short blocks balance them)
-    const int ngroups = (TY + kPlaceRows - 1) / kPlaceRows;
-    const int want = (8 * 1216 + ngroups - 1) / ngroups;
-    const int cs = w.nchunks / want > 1 ? w.nchunks / want : 1;
-    const int nsuper = (w.nchunks + cs - 1) / cs;
-    const dim3 grid(ngroups, nsuper);
-    const int nk = (TX + 31) / 32;
+    return LE_OK;
+}
+
+// Placement geometry: super-chunks of `cs` count chunks, small enough for about
+// eight waves of blocks (row groups differ a lot in work; many short blocks
+// balance them).
+struct PlaceGrid {
+    int ngroups, cs, nsuper, nk;
+};
+
+PlaceGrid place_grid(const le_camera* cam, const SortWs& w)
+{
+    PlaceGrid g;
+    const int TY = tiles_y(cam);
+    g.ngroups = (TY + kPlaceRows - 1) / kPlaceRows;
+    const int want = (8 * 1216 + g.ngroups - 1) / g.ngroups;
+    g.cs = w.nchunks / want > 1 ? w.nchunks / want : 1;
+    g.nsuper = (w.nchunks + g.cs - 1) / g.cs;
+    g.nk = (tiles_x(cam) + 31) / 32;
+    return g;
+}
+
+// Step 5 for super-chunks [s0, s1): place the copies of the active tiles.
+le_status place(const le_camera* cam, int32_t n, const float* depth, const SortWs& w, const uint64_t* cur,
+                const PlaceGrid& g, int s0, int s1, const uint8_t* tile_act, const uint8_t* rows_act,
+                uint32_t* sorted_ids, uint64_t* sorted_keys, cudaStream_t s)
+{
+    if (s1 <= s0) return LE_OK;
+    const dim3 grid(g.ngroups, s1 - s0);
+    const int TX = tiles_x(cam), TY = tiles_y(cam);
 #define LE_PLACE(NK)                                                                                             \
-    place_kernel<NK><<<grid, kPlaceThreads, 0, s>>>(n, cur, w.drect, w.dell, depth, TX, TY, w.chunk * cs, cs,     \
-                                                    w.nchunks,                                                 \
-                                                    w.base, sorted_ids, sorted_keys)
-    switch (nk) {
+    place_kernel<NK><<<grid, kPlaceThreads, 0, s>>>(n, cur, w.drect, w.dell, depth, TX, TY, w.chunk * g.cs, g.cs, \
+                                                    w.nchunks, w.base, sorted_ids, sorted_keys, tile_act,      \
+                                                    rows_act, s0)
+    switch (g.nk) {
         case 1: LE_PLACE(1); break;
         case 2: LE_PLACE(2); break;
         case 3: LE_PLACE(3); break;
@@ -748,6 +786,88 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     }
 #undef LE_PLACE
     LE_LAUNCHED();
+    return LE_OK;
+}
+
+}  // namespace
+
+le_status render_fwd_phase(const le_camera* cam, const float* splat, const uint32_t* ids, const uint32_t* base,
+                           int nchunks, int c_lo, int c_hi, const uint8_t* act, uint8_t* next_act,
+                           uint8_t* next_rows, float* out_rgb, float* out_feat, float* out_unc, float* T_final,
+                           int32_t* n_contrib, cudaStream_t s);
+}  // namespace leg
+
+extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const uint16_t* rect,
+                                 const float* tile_ellipse, const int32_t* tiles_touched, void* workspace,
+                                 size_t workspace_bytes, int64_t k_cap,
+                                 uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
+                                 void* stream)
+{
+    cudaStream_t s = as_stream(stream);
+    SortWs w;
+    uint64_t* cur = nullptr;
+    le_status st = bin_prepare(cam, n, depth, rect, tile_ellipse, tiles_touched, workspace, workspace_bytes, k_cap,
+                               sorted_ids != nullptr, tile_ranges, k_out, s, w, cur);
+    if (st != LE_OK || n == 0 || *k_out == 0) return st;
+    const PlaceGrid g = place_grid(cam, w);
+    return place(cam, n, depth, w, cur, g, 0, g.nsuper, nullptr, nullptr, sorted_ids, sorted_keys, s);
+}
+
+extern "C" le_status le_bin_render_fwd(const le_camera* cam, int32_t n, const float* splat, const float* depth,
+                                       const uint16_t* rect, const float* tile_ellipse,
+                                       const int32_t* tiles_touched, void* workspace, size_t workspace_bytes,
+                                       int64_t k_cap, uint32_t* sorted_ids, uint32_t* tile_ranges, int64_t* k_out,
+                                       float* out_rgb, float* out_feat, float* out_unc, float* T_final,
+                                       int32_t* n_contrib, void* stream)
+{
+    LE_CHECK_ARG(out_rgb && out_feat && out_unc && T_final && n_contrib, "null output pointer");
+    LE_CHECK_ARG(n == 0 || (splat && aligned16(splat)), "splat must be non-null and 16-byte aligned");
+    cudaStream_t s = as_stream(stream);
+    SortWs w;
+    uint64_t* cur = nullptr;
+    le_status st = bin_prepare(cam, n, depth, rect, tile_ellipse, tiles_touched, workspace, workspace_bytes, k_cap,
+                               sorted_ids != nullptr, tile_ranges, k_out, s, w, cur);
+    if (st != LE_OK) return st;
+    const int ntiles = tiles_x(cam) * tiles_y(cam);
+    if (n == 0 || *k_out == 0) {
+        // nothing to place: one render pass over empty lists writes the background
+        LE_CUDA(cudaMemsetAsync(w.flags, 0, 2 * (kMaxTiles + 64), s));
+        if (n == 0) {
+            LE_CUDA(cudaMemsetAsync(w.base, 0, sizeof(uint32_t) * ((size_t)ntiles * w.nchunks + 1), s));
+        }
+        return render_fwd_phase(cam, splat, sorted_ids, w.base, w.nchunks, 0, w.nchunks, nullptr, w.flags,
+                                w.flags + 2 * kMaxTiles, out_rgb, out_feat, out_unc, T_final, n_contrib, s);
+    }
+    // Lazy placement: only 1-2 % of the copies are ever read -- every pixel
+    // stops once its transmittance falls below 1e-4, long before the end of its
+    // tile's depth-ordered list.  So the depth chunks are placed and rendered
+    // in phases [0, 16), [16, 64), [64, 256), [256, all), each phase only for
+    // the tiles with a pixel still blending; a tile's later chunks are never
+    // written.  The result equals placing everything and rendering once, bit
+    // for bit (the same entries are blended in the same order).
+    const PlaceGrid g = place_grid(cam, w);
+    const int bounds[5] = {0, 16, 64, 256, 1 << 30};
+    uint8_t* act[2] = {w.flags, w.flags + kMaxTiles};
+    uint8_t* rows[2] = {w.flags + 2 * kMaxTiles, w.flags + 2 * kMaxTiles + 64};
+    int lo = 0, phase = 0;
+    for (int b = 1; b < 5 && lo < w.nchunks; ++b) {
+        int hi = bounds[b] >= w.nchunks ? w.nchunks : (bounds[b] + g.cs - 1) / g.cs * g.cs;
+        if (hi > w.nchunks) hi = w.nchunks;
+        if (hi <= lo) continue;
+        const uint8_t* a = phase == 0 ? nullptr : act[phase & 1];
+        const uint8_t* r = phase == 0 ? nullptr : rows[phase & 1];
+        uint8_t* na = act[(phase + 1) & 1];
+        uint8_t* nr = rows[(phase + 1) & 1];
+        LE_CUDA(cudaMemsetAsync(na, 0, ntiles, s));
+        LE_CUDA(cudaMemsetAsync(nr, 0, 64, s));
+        const int s0 = lo / g.cs, s1 = (hi + g.cs - 1) / g.cs;
+        if ((st = place(cam, n, depth, w, cur, g, s0, s1, a, r, sorted_ids, nullptr, s)) != LE_OK) return st;
+        if ((st = render_fwd_phase(cam, splat, sorted_ids, w.base, w.nchunks, lo, hi, a, na, nr, out_rgb, out_feat,
+                                   out_unc, T_final, n_contrib, s)) != LE_OK)
+            return st;
+        lo = hi;
+        ++phase;
+    }
     return LE_OK;
 }
 

@@ -111,14 +111,122 @@ __global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const
     }
     if (!inside) return;
     const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
-    out_rgb[o] = acc[0] + T * cam.bg[0];
-    out_rgb[P + o] = acc[1] + T * cam.bg[1];
-    out_rgb[2 * P + o] = acc[2] + T * cam.bg[2];
+    out_rgb[o] = __fmaf_rn(T, cam.bg[0], acc[0]);
+    out_rgb[P + o] = __fmaf_rn(T, cam.bg[1], acc[1]);
+    out_rgb[2 * P + o] = __fmaf_rn(T, cam.bg[2], acc[2]);
     out_unc[o] = acc[3];
 #pragma unroll
     for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[4 + c];
     T_final[o] = T;
     n_contrib[o] = last;
+}
+
+// One phase of the lazily placed forward render (le_bin_render_fwd): tile t
+// blends its list entries [base(t, c_lo), base(t, c_hi)) -- depth chunks
+// [c_lo, c_hi) -- where base(t, c) = base[t nchunks + c] (the next tile's start
+// for c = nchunks) comes from the tile-major scan of the per-(tile, chunk)
+// copy counts.  Phase c_lo > 0 resumes each pixel from the state the previous
+// phase left in the outputs (colour sums without background, T, last list
+// position, bit 30 of n_contrib = the pixel has stopped).  A tile whose pixels
+// have all stopped, or whose list ends with this phase, writes its final
+// outputs; any other tile saves the state and sets its flag in next_act (and
+// its 8-row group's in next_rows) for the next phase.  act (nullable = all):
+// the tiles active in this phase.
+constexpr int kStopped = 1 << 30;
+
+__global__ void __launch_bounds__(kBlock) render_fwd_phase_kernel(
+    CamParams cam, const float4* __restrict__ splat, const uint32_t* __restrict__ ids,
+    const uint32_t* __restrict__ base, int nchunks, int c_lo, int c_hi, const uint8_t* __restrict__ act,
+    uint8_t* __restrict__ next_act, uint8_t* __restrict__ next_rows, float* __restrict__ out_rgb,
+    float* __restrict__ out_feat, float* __restrict__ out_unc, float* __restrict__ T_final, int* __restrict__ n_contrib)
+{
+    __shared__ float4 rec[5][kBlock];
+    const int tile = blockIdx.x;
+    if (act && !act[tile]) return;
+    const int tx = tile % cam.TX, ty = tile / cam.TX;
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
+    const bool inside = px < cam.W && py < cam.H;
+    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
+    const uint32_t tstart = base[(size_t)tile * nchunks], tend = base[(size_t)(tile + 1) * nchunks];
+    const uint32_t s0 = c_lo == 0 ? tstart : base[(size_t)tile * nchunks + c_lo];
+    const uint32_t s1 = c_hi >= nchunks ? tend : base[(size_t)tile * nchunks + c_hi];
+    const int n = (int)(s1 - s0), off = (int)(s0 - tstart);
+    const float fpx = (float)px, fpy = (float)py;
+
+    bool done = !inside;
+    float T = 1.f;
+    float acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
+    int last = 0;
+    if (c_lo > 0 && inside) {
+        T = T_final[o];
+        acc[0] = out_rgb[o];
+        acc[1] = out_rgb[P + o];
+        acc[2] = out_rgb[2 * P + o];
+        acc[3] = out_unc[o];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[4 + c] = out_feat[c * P + o];
+        const int nc = n_contrib[o];
+        last = nc & (kStopped - 1);
+        done = (nc & kStopped) != 0;
+    }
+
+    for (int b0 = 0; b0 < n; b0 += kBlock) {
+        if (__syncthreads_count(done) == kBlock) break;
+        const int k = b0 + threadIdx.x;
+        if (k < n) {
+            const float4* r = splat + (size_t)ids[s0 + k] * 5;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
+        }
+        __syncthreads();
+        const int cnt = min(kBlock, n - b0);
+        for (int j = 0; !done && j < cnt; ++j) {
+            const float4 g0 = rec[0][j], g1 = rec[1][j];
+            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
+            const float q = splat_q(splat_ax(g0.z, dx), splat_bx(g0.w, dx), g1.x, dy);
+            if (q < 0.f) continue;
+            const float alpha = fminf(0.99f, splat_alpha0(g1.y, q));
+            if (alpha < (1.f / 255.f)) continue;
+            const float test = T * (1.f - alpha);
+            if (test < 1e-4f) {
+                done = true;
+                break;
+            }
+            const float w = alpha * T;
+            const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
+            acc[0] = fmaf(g1.z, w, acc[0]);
+            acc[1] = fmaf(g1.w, w, acc[1]);
+            acc[2] = fmaf(g2.x, w, acc[2]);
+            acc[3] = fmaf(g2.y, w, acc[3]);
+            acc[4] = fmaf(g2.z, w, acc[4]);
+            acc[5] = fmaf(g2.w, w, acc[5]);
+            acc[6] = fmaf(g3.x, w, acc[6]);
+            acc[7] = fmaf(g3.y, w, acc[7]);
+            acc[8] = fmaf(g3.z, w, acc[8]);
+            acc[9] = fmaf(g3.w, w, acc[9]);
+            acc[10] = fmaf(g4.x, w, acc[10]);
+            acc[11] = fmaf(g4.y, w, acc[11]);
+            T = test;
+            last = off + b0 + j + 1;
+        }
+    }
+    const bool complete = __syncthreads_count(done) == kBlock || s1 == tend;
+    if (!complete && threadIdx.x == 0) {
+        next_act[tile] = 1;
+        next_rows[ty / 8] = 1;
+    }
+    if (!inside) return;
+    // the background only once the pixel is final (the same FMA as render_fwd_kernel)
+    out_rgb[o] = complete ? __fmaf_rn(T, cam.bg[0], acc[0]) : acc[0];
+    out_rgb[P + o] = complete ? __fmaf_rn(T, cam.bg[1], acc[1]) : acc[1];
+    out_rgb[2 * P + o] = complete ? __fmaf_rn(T, cam.bg[2], acc[2]) : acc[2];
+    out_unc[o] = acc[3];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[4 + c];
+    T_final[o] = T;
+    n_contrib[o] = complete ? last : (last | (done ? kStopped : 0));
 }
 
 // One stage of a recursive-halving ("transpose") reduction of N values held by
@@ -292,6 +400,21 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
 }  // namespace leg
 
 using namespace leg;
+
+namespace leg {
+le_status render_fwd_phase(const le_camera* cam, const float* splat, const uint32_t* ids, const uint32_t* base,
+                           int nchunks, int c_lo, int c_hi, const uint8_t* act, uint8_t* next_act,
+                           uint8_t* next_rows, float* out_rgb, float* out_feat, float* out_unc, float* T_final,
+                           int32_t* n_contrib, cudaStream_t s)
+{
+    const CamParams cp = cam_params(cam);
+    render_fwd_phase_kernel<<<cp.TX * cp.TY, kBlock, 0, s>>>(cp, reinterpret_cast<const float4*>(splat), ids, base,
+                                                            nchunks, c_lo, c_hi, act, next_act, next_rows, out_rgb,
+                                                            out_feat, out_unc, T_final, n_contrib);
+    LE_LAUNCHED();
+    return LE_OK;
+}
+}  // namespace leg
 
 extern "C" le_status le_render_fwd(const le_camera* cam, int32_t n, const float* splat, const uint32_t* sorted_ids,
                                    const uint32_t* tile_ranges, float* out_rgb, float* out_feat, float* out_unc,

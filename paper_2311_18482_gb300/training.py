@@ -1,7 +1,8 @@
 """One training step of the Language Embedded 3D Gaussians hot path on one GPU,
 driven entirely through the C ABI with preallocated device buffers:
 
-  le_preprocess -> le_bin_sort -> le_render_fwd -> le_rgb_l1 (RGB loss, Sec. 4)
+  le_preprocess -> le_bin_render_fwd (binning + compositing, lazily placed)
+  -> le_rgb_l1 (RGB loss, Sec. 4)
   -> le_decode (D_MLP + uncertainty-weighted CE + L_u, Eqs. 8-12, training mode)
   -> le_render_bwd_adam (all Gaussian parameter gradients, each applied by
      Adam where it is computed; u clamped to [0,1], Sec. 3.4.2)
@@ -119,10 +120,8 @@ class TrainState:
         self._mark("start")
         B.le_preprocess(self.g, cam, self.proj)
         self._mark("preprocess")
-        ids, ranges, self.K, _ = B.le_bin_sort(cam, self.proj, self.bins)
-        self._mark("bin_sort")
-        B.le_render_fwd(cam, self.proj, ids, ranges, self.img)
-        self._mark("render_fwd")
+        ids, ranges, self.K, _ = B.le_bin_render_fwd(cam, self.proj, self.bins, self.img)
+        self._mark("bin_render")
         B.le_rgb_l1(self.img.rgb, rgb_target, self.loss[0:1], self.d_rgb)
         B.le_decode_raw(self.mode, self.P, self.img.feat, self.img.unc, self.dec, idx_target, 1.0, 1.0,
                         self.loss[1:3], self.d_feat, self.d_unc, self.dgrad, None, None, None, self.dec_ws)
