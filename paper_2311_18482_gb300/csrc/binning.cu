@@ -453,20 +453,43 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
         counts[(size_t)t * nchunks + blockIdx.x] = (uint32_t)diff[(t / TX) * W1 + (t % TX)];
 }
 
-// Placement.  Block (g, C): tile rows [8g, 8g + 8), one per warp, and the
+// Placement.  Block (g, C): tile rows [R g, R g + R) (R = kPlaceRows), one per warp, and the
 // Gaussians of super-chunk C (count chunks [C*cs, (C+1)*cs)).  The cursor of
 // tile (row, tx) starts at base[t * nchunks + C*cs] -- the exclusive scan of the
 // counts in tile-major order -- and lives in a register of lane tx % 32 of the
 // row's warp, so no two threads share a cursor and no barrier is needed between
-// Gaussians.  The block first compacts, 1024 at a time and in depth order, the
-// super-chunk's Gaussians whose rectangle meets its 8 rows; a warp then takes
+// Gaussians.  The block first compacts, 4 per thread at a time and in depth order, the
+// super-chunk's Gaussians whose rectangle meets its rows; a warp then takes
 // those 32 at a time: each lane computes the row span of its Gaussian (when its
 // rectangle covers the row), a ballot keeps the non-empty ones and, for each in
 // depth order, every lane whose tiles fall in the span writes them.  Only one cursor per
 // (tile, block) advances at a time, so the partly written output sectors stay
 // few enough to remain in L2.
-constexpr int kPlaceThreads = 256;
-constexpr int kPlaceRows = kPlaceThreads / 32;
+constexpr int kPlaceRows = LE_PLACE_ROWS;          // tile rows per block, one warp each
+constexpr int kPlaceThreads = 32 * kPlaceRows;
+
+// Exclusive scan of one value per thread over a block of kPlaceThreads threads.
+__device__ __forceinline__ uint32_t place_block_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int k = 0; k < kPlaceRows; ++k) {
+        const uint32_t t = warp_sums[k];
+        if (k < w) before += t;
+        all += t;
+    }
+    *total = all;
+    return before + x - v;
+}
 
 constexpr int kPlaceBatch = 4 * kPlaceThreads;   // Gaussians examined per compaction round
 
@@ -487,7 +510,7 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
     if (rows_act && !rows_act[blockIdx.x]) return;
     __shared__ uint32_t sg[kPlaceBatch], sj[kPlaceBatch];
     __shared__ ushort4 sr[kPlaceBatch];
-    __shared__ uint32_t ws[kWarps];
+    __shared__ uint32_t ws[kPlaceRows];
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * kPlaceRows + (threadIdx.x >> 5);
     const bool row_ok = row < TY;
@@ -516,7 +539,7 @@ __global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint6
             if (rr[k].z > rr[k].x && rr[k].y < re && rr[k].w > rb) flags |= 1u << k;
         }
         uint32_t m = 0;
-        uint32_t pos = block_exclusive_scan((uint32_t)__popc(flags), ws, &m);
+        uint32_t pos = place_block_scan((uint32_t)__popc(flags), ws, &m);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (flags & (1u << k)) {
@@ -577,7 +600,7 @@ struct SortWs {
     float4* dell;
     uint32_t *counts, *base, *partials, *misc;
     uint32_t* sort_state;   // [passes][256] digit counts / offsets, then [passes][blocks][256] look-back words
-    uint8_t* flags;         // lazy placement: two tile-activity arrays [kMaxTiles], two row-group arrays [64]
+    uint8_t* flags;         // lazy placement: two tile-activity arrays and two row-group arrays, [kMaxTiles] each
     int nchunks, chunk;
     size_t bytes;
 };
@@ -607,7 +630,7 @@ __host__ __device__ constexpr size_t sort_ws_bytes(int n)
                             : 256ull * ((n + kTile - 1) / kTile) + 1) /
                            kTile +
                        2)) +
-           seg(4ull * 64) + seg(4ull * sort_state_words(n)) + seg(2ull * (kMaxTiles + 64));
+           seg(4ull * 64) + seg(4ull * sort_state_words(n)) + seg(4ull * kMaxTiles);
 }
 
 SortWs sort_ws_layout(char* base, int32_t n)
@@ -633,7 +656,7 @@ SortWs sort_ws_layout(char* base, int32_t n)
     w.partials = (uint32_t*)take(4ull * (scan_max / kTile + 2));
     w.misc = (uint32_t*)take(4ull * 64);
     w.sort_state = (uint32_t*)take(4ull * sort_state_words(n));
-    w.flags = (uint8_t*)take(2ull * (kMaxTiles + 64));
+    w.flags = (uint8_t*)take(4ull * kMaxTiles);
     w.bytes = off;
     return w;
 }
@@ -831,7 +854,7 @@ extern "C" le_status le_bin_render_fwd(const le_camera* cam, int32_t n, const fl
     const int ntiles = tiles_x(cam) * tiles_y(cam);
     if (n == 0 || *k_out == 0) {
         // nothing to place: one render pass over empty lists writes the background
-        LE_CUDA(cudaMemsetAsync(w.flags, 0, 2 * (kMaxTiles + 64), s));
+        LE_CUDA(cudaMemsetAsync(w.flags, 0, 4 * kMaxTiles, s));
         if (n == 0) {
             LE_CUDA(cudaMemsetAsync(w.base, 0, sizeof(uint32_t) * ((size_t)ntiles * w.nchunks + 1), s));
         }
@@ -848,7 +871,8 @@ extern "C" le_status le_bin_render_fwd(const le_camera* cam, int32_t n, const fl
     const PlaceGrid g = place_grid(cam, w);
     const int bounds[5] = {0, 16, 64, 256, 1 << 30};
     uint8_t* act[2] = {w.flags, w.flags + kMaxTiles};
-    uint8_t* rows[2] = {w.flags + 2 * kMaxTiles, w.flags + 2 * kMaxTiles + 64};
+    uint8_t* rows[2] = {w.flags + 2 * kMaxTiles, w.flags + 3 * kMaxTiles};
+    const int ngroups = (tiles_y(cam) + kPlaceRows - 1) / kPlaceRows;
     int lo = 0, phase = 0;
     for (int b = 1; b < 5 && lo < w.nchunks; ++b) {
         int hi = bounds[b] >= w.nchunks ? w.nchunks : (bounds[b] + g.cs - 1) / g.cs * g.cs;
@@ -859,7 +883,7 @@ extern "C" le_status le_bin_render_fwd(const le_camera* cam, int32_t n, const fl
         uint8_t* na = act[(phase + 1) & 1];
         uint8_t* nr = rows[(phase + 1) & 1];
         LE_CUDA(cudaMemsetAsync(na, 0, ntiles, s));
-        LE_CUDA(cudaMemsetAsync(nr, 0, 64, s));
+        LE_CUDA(cudaMemsetAsync(nr, 0, ngroups, s));
         const int s0 = lo / g.cs, s1 = (hi + g.cs - 1) / g.cs;
         if ((st = place(cam, n, depth, w, cur, g, s0, s1, a, r, sorted_ids, nullptr, s)) != LE_OK) return st;
         if ((st = render_fwd_phase(cam, splat, sorted_ids, w.base, w.nchunks, lo, hi, a, na, nr, out_rgb, out_feat,

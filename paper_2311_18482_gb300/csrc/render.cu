@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const
 // position, bit 30 of n_contrib = the pixel has stopped).  A tile whose pixels
 // have all stopped, or whose list ends with this phase, writes its final
 // outputs; any other tile saves the state and sets its flag in next_act (and
-// its 8-row group's in next_rows) for the next phase.  act (nullable = all):
+// its placement row group's in next_rows) for the next phase.  act (nullable = all):
 // the tiles active in this phase.
 constexpr int kStopped = 1 << 30;
 
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kBlock) render_fwd_phase_kernel(
     const bool complete = __syncthreads_count(done) == kBlock || s1 == tend;
     if (!complete && threadIdx.x == 0) {
         next_act[tile] = 1;
-        next_rows[ty / 8] = 1;
+        next_rows[ty / LE_PLACE_ROWS] = 1;
     }
     if (!inside) return;
     // the background only once the pixel is final (the same FMA as render_fwd_kernel)
