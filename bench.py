@@ -35,7 +35,7 @@ N_GAUSS, W, H, N_VIEWS = 1_000_000, 1296, 840, 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--decoder", default="auto", choices=["auto", "fused", "unfused"])
@@ -59,7 +59,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -113,30 +113,84 @@ def measured_peaks():
 STAGE_CALLS = {"preprocess": "le_preprocess (preprocess_kernel)",
                "bin_render": "le_bin_render_fwd (depth radix sort, chunk counts, scan, lazily placed copies "
                              "and compositing)",
-               "decoder": "le_decode fused (dec_train_kernel)",
-               "render_bwd": "le_render_bwd_adam (render_bwd_kernel + preprocess_bwd_kernel with the Gaussians' "
-                             "Adam step fused in)",
+               "decoder": "le_rgb_l1 + le_decode fused (l1_kernel, dec_train_kernel)",
+               "render_bwd": "le_render_bwd_screen (render_bwd_kernel)",
+               "project_bwd_adam": "le_project_bwd_adam (preprocess_bwd_kernel with the Gaussians' Adam step "
+                                   "fused in)",
                "adam": "le_adam (adam_kernel, decoder parameters)"}
 STAGE_SOURCES = {"preprocess": ["preprocess.cu"], "bin_render": ["binning.cu", "render.cu"],
-                 "decoder": ["decoder_tc.cu", "tc_common.cuh"],
-                 "render_bwd": ["render.cu", "preprocess.cu", "common.cuh"], "adam": ["train.cu", "common.cuh"]}
+                 "decoder": ["decoder_tc.cu", "tc_common.cuh", "train.cu"],
+                 "render_bwd": ["render.cu", "common.cuh"], "project_bwd_adam": ["preprocess.cu", "common.cuh"],
+                 "adam": ["train.cu", "common.cuh"]}
+
+# FP32 operations (an FMA counts 2) per (pixel, Gaussian) pair of the render
+# backward, from the arithmetic of the compositing adjoint.  Every walked pair
+# (each list position below the pixel's n_contrib): d = mu - pixel (2), the
+# quadratic form q (8), alpha = min(0.99, o 2^-q) (2), the two skip tests (2),
+# plus one exp.  Every contributing pair (q >= 0, alpha >= 1/255) adds: T
+# recovery by division (2), w = alpha T (1), the 12 channel gradients and the
+# dot product f.dL/dC (48), dL/dalpha (5), the colour-behind recurrence (3),
+# opacity and power terms (3), conic (11) and mean (10) terms: 83.
+BWD_FLOP_WALKED, BWD_FLOP_CONTRIB = 14, 83
+DEC_FLOP_PER_PX = 3 * 2 * (8 * 64 + 64 * 128 + 128 * 128)    # forward + input and weight gradients
 
 
 def stage_bytes(N, n_vis, K, P, T, nc, total_scalars, K_read):
     """Compulsory HBM bytes per call of each stage (each input read once, each output written once).
-    render_bwd includes the Gaussians' Adam step fused into it: read m, v and the
-    parameters the projection does not read, write parameters, m and v."""
+    project_bwd_adam applies the Gaussians' Adam step: read grad2d, the parameters, m and v,
+    write parameters, m and v."""
     par = 4 * (3 + 3 + 4 + 1 + 3 * nc + 8 + 1)          # all per-Gaussian parameters
-    geo = 4 * (3 + 3 + 4 + 1 + 3 * nc)                  # parameters the projection reads
     return {
         "preprocess": N * par + N * (80 + 4 + 4 + 8 + 4 + 1 + 32),
         # binning inputs, the list entries the compositing reads (written once, read once), records, images
         "bin_render": N * (4 + 4) + n_vis * (8 + 32) + 8 * T + 8 * K_read + 80 * n_vis + 56 * P,
-        "decoder": (36 + 4 + 36) * P,
-        "render_bwd": 4 * K_read + 80 * n_vis + 104 * P + 80 * N + geo * N + 80 * N + (par - geo) * N + 5 * par * N
-                      + 5 * N,
+        "decoder": (36 + 4 + 36) * P + 36 * P,     # decoder + RGB L1
+        # list entries, records, T_final + n_contrib + upstream gradients, grad2d (zeroed, accumulated)
+        "render_bwd": 4 * K_read + 80 * n_vis + 56 * P + 80 * N,
+        "project_bwd_adam": 80 * N + 5 * N + 6 * par * N,
         "adam": 28 * (total_scalars - par // 4 * N),
     }
+
+
+def pair_counts(img, ids, ranges, splat, TX, sample_tiles=256, seed=0):
+    """(walked, contributing) (pixel, Gaussian) pairs of the render backward.
+    walked = sum of n_contrib (exact); the contributing fraction is measured on
+    a seeded sample of tiles by evaluating the skip tests of the renderer
+    (q >= 0, alpha >= 1/255 with the record's base-2 conic) in torch."""
+    import torch
+    nc = img.n_contrib
+    walked = int(nc.sum().item())
+    H, W = nc.shape
+    ncb = torch.nn.functional.pad(nc.float(), (0, (-W) % 16, 0, (-H) % 16))
+    tmax = torch.nn.functional.max_pool2d(ncb[None, None], 16)[0, 0].flatten().long()
+    live = torch.nonzero(tmax > 0).flatten()
+    if walked == 0 or live.numel() == 0:
+        return walked, 0
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    pick = live[torch.randperm(live.numel(), generator=g)[:sample_tiles].to(live.device)]
+    rg = ranges.view(-1, 2).long()
+    s_walk = s_con = 0
+    for t in pick.tolist():
+        m = int(tmax[t])
+        ty, tx = divmod(t, TX)
+        gid = ids[int(rg[t, 0]):int(rg[t, 0]) + m].long()
+        r = splat[gid]                                                    # [m, 20]
+        ys = torch.arange(ty * 16, ty * 16 + 16, device=r.device)
+        xs = torch.arange(tx * 16, tx * 16 + 16, device=r.device)
+        py, px = torch.meshgrid(ys, xs, indexing="ij")
+        inside = (py < H) & (px < W)
+        py, px = py[inside].float(), px[inside].float()
+        ncp = nc[py.long(), px.long()]
+        dx = r[None, :, 0] - px[:, None]
+        dy = r[None, :, 1] - py[:, None]
+        q = r[None, :, 2] * dx * dx + r[None, :, 3] * dx * dy + r[None, :, 4] * dy * dy
+        alpha = torch.clamp(r[None, :, 5] * torch.exp2(-q), max=0.99)
+        pos = torch.arange(m, device=r.device)[None, :]
+        walk = pos < ncp[:, None].long()
+        con = walk & (q >= 0) & (alpha >= 1.0 / 255.0)
+        s_walk += int(walk.sum().item())
+        s_con += int(con.sum().item())
+    return walked, int(round(walked * s_con / max(s_walk, 1)))
 
 
 def _sources_sha(files):
@@ -276,23 +330,48 @@ def run_ours(args, rank, world):
            "instances_K": K_mean}
     # (instances_read is added with the roofline below)
 
-    # --- roofline of the dominant stage: compulsory HBM bytes (every datum read or
-    # written once) / event-timed stage duration, against the measured copy bandwidth
+    # --- roofline of the dominant kernel (render_bwd_kernel, FP32-ALU bound):
+    # algorithmic FP32 flops of the compositing adjoint per launch / its
+    # event-timed duration, against the FP32 peak of 152 SMs x 128 lanes x 2
+    # flops (FMA) x the maximum SM clock.  The other stages against HBM
+    # (compulsory bytes) and the decoder against the bf16 tensor peak.
     P = W * H
     nc = (scene.sh_degree + 1) ** 2
     N = args.n
+    TX, TY = (W + 15) // 16, (H + 15) // 16
     n_vis = int((st.proj.tiles_touched > 0).sum().item())
     # list entries any pixel reads: per tile, the largest n_contrib (last view)
     ncb = torch.nn.functional.pad(st.img.n_contrib.float(), (0, (-W) % 16, 0, (-H) % 16))
     K_read = int(torch.nn.functional.max_pool2d(ncb[None, None], 16).sum().item())
-    alg_bytes = stage_bytes(N, n_vis, K_mean, P, ((W + 15) // 16) * ((H + 15) // 16), nc, st.layout.total, K_read)
-    dom = max((k for k in stage_ms if k in alg_bytes), key=lambda k: stage_ms[k])
-    ach = alg_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    out["roofline"] = {"kernel": STAGE_CALLS[dom], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
-                       "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": stage_traffic(dom),
-                       "peak_kind": peak_kind, "algorithmic_bytes": round(alg_bytes[dom]),
-                       "note": "render kernels are instruction-issue bound (see profiles/); per-copy record "
-                               "re-reads are served by L2 and not counted"}
+    ids_last, ranges_last = st.bins.ids, st.bins.ranges
+    walked, contrib = pair_counts(st.img, ids_last, ranges_last, st.proj.splat, TX)
+    alg_bytes = stage_bytes(N, n_vis, K_mean, P, TX * TY, nc, st.layout.total, K_read)
+    sm_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    bwd_flop = BWD_FLOP_WALKED * walked + BWD_FLOP_CONTRIB * contrib
+    t_bwd = stage_ms["render_bwd"] * 1e-3
+    ach = bwd_flop / t_bwd / 1e12
+    out["roofline"] = {"kernel": STAGE_CALLS["render_bwd"], "bound": "alu", "achieved": round(ach, 2),
+                       "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                       "traffic": stage_traffic("render_bwd"), "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 "
+                       f"x {sm_mhz:.0f} MHz", "algorithmic_flop": bwd_flop, "pairs_walked": walked,
+                       "pairs_contributing": contrib,
+                       "note": f"{BWD_FLOP_WALKED} flop per walked pair + {BWD_FLOP_CONTRIB} per contributing "
+                               "pair (FMA = 2); traffic is DRAM bytes per launch from ncu"}
+    t_pb = stage_ms["project_bwd_adam"] * 1e-3
+    ach_h = alg_bytes["project_bwd_adam"] / t_pb / 1e9
+    out["roofline_hbm"] = {"kernel": STAGE_CALLS["project_bwd_adam"], "bound": "hbm", "achieved": round(ach_h, 1),
+                           "peak": hbm_peak, "unit": "GB/s", "frac": round(ach_h / hbm_peak, 4),
+                           "traffic": stage_traffic("project_bwd_adam"), "peak_kind": peak_kind,
+                           "algorithmic_bytes": round(alg_bytes["project_bwd_adam"])}
+    if mode_name == "fused":
+        t_dec = stage_ms["decoder"] * 1e-3
+        ach_t = DEC_FLOP_PER_PX * P / t_dec / 1e12
+        out["roofline_tensor"] = {"kernel": STAGE_CALLS["decoder"], "bound": "tensor", "achieved": round(ach_t, 1),
+                                  "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(ach_t / bf16_peak, 4),
+                                  "traffic": stage_traffic("decoder"), "peak_kind": peak_kind + " bf16 burst",
+                                  "algorithmic_flop": DEC_FLOP_PER_PX * P}
     out["stage_hbm_frac"] = {k: round(alg_bytes[k] / (stage_ms[k] * 1e-3) / 1e9 / hbm_peak, 4)
                              for k in stage_ms if k in alg_bytes}
     out["visible_gaussians"] = n_vis

@@ -265,6 +265,29 @@ le_status le_render_bwd_adam(const le_camera* cam, const le_gaussians* g, const 
                              const le_gaussian_grads* v, const le_adam_config* adam, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * The two halves of le_render_bwd / le_render_bwd_adam as separate calls
+ * (same arguments, same results bit for bit), so that a caller can schedule
+ * or time them apart:
+ * le_render_bwd_screen -- the screen-space half: zeroes grad2d and fills it
+ *   with dL/d of every splat record field (the per-pixel back-to-front walk).
+ * le_project_bwd -- the projection half: chains grad2d to every Gaussian
+ *   parameter through le_preprocess (out: overwritten).
+ * le_project_bwd_adam -- the projection half with the Adam step applied where
+ *   each gradient is computed (g updated in place, u clamped to [0, 1]), as in
+ *   le_render_bwd_adam.
+ * grad2d: [n,20], 16-byte aligned, written by le_render_bwd_screen (or by the
+ * caller) and only read by the projection half.  Errors: LE_ERR_INVALID_ARG. */
+le_status le_render_bwd_screen(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                               const uint32_t* sorted_ids, const uint32_t* tile_ranges, const float* T_final,
+                               const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
+                               const float* dL_dunc, float* grad2d, void* stream);
+le_status le_project_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr, const float* grad2d,
+                         const le_gaussian_grads* out, void* stream);
+le_status le_project_bwd_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                              const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
+                              const le_adam_config* adam, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Semantic decoder D_MLP (Eq. 8, eq:lem_dec; supp. Tab. dmlp): per-pixel MLP
  * d_in(=8) -> h1 -> h2 -> n_cb, ReLU, ReLU, linear.  FP32 device weights
  * [out][in] row-major (a 1x1 convolution's weight), 16-byte aligned. */

@@ -81,6 +81,12 @@ _SIG = {
     "le_render_bwd_adam": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P, _P,
                            _P, _P, _P, C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads),
                            C.POINTER(LeAdamConfig), _P],
+    "le_render_bwd_screen": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P, _P, _P, _P,
+                             _P, _P, _P, _P, _P],
+    "le_project_bwd": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P,
+                       C.POINTER(LeGaussianGrads), _P],
+    "le_project_bwd_adam": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P,
+                            C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads), C.POINTER(LeAdamConfig), _P],
     "le_decode_workspace": [C.c_int32, C.c_int32, C.POINTER(LeDecoder), C.POINTER(C.c_size_t)],
     "le_decode": [C.c_int32, C.c_int32, _P, _P, C.POINTER(LeDecoder), _P, C.c_float, C.c_float, _P, _P, _P,
                   C.POINTER(LeDecoderGrads), _P, _P, _P, _P, C.c_size_t, _P],
@@ -384,6 +390,36 @@ def le_render_bwd_adam(cam, g: Gaussians, proj: Projected, ids, ranges, img: Ima
                                      _ptr(dL_dunc.contiguous()), _ptr(grad2d), C.byref(ms), C.byref(vs),
                                      C.byref(cfg), _stream()))
     return grad2d
+
+
+def le_render_bwd_screen(cam, g: Gaussians, proj: Projected, ids, ranges, img: Image, dL_drgb, dL_dfeat, dL_dunc,
+                         grad2d=None):
+    """Screen-space half of le_render_bwd: returns grad2d [n, 20]."""
+    grad2d = grad2d if grad2d is not None else torch.empty((g.n, SPLAT_STRIDE), dtype=torch.float32,
+                                                           device=g.means.device)
+    cs, gs, ps = camera_struct(cam), g.struct(), proj.struct()
+    _check(load().le_render_bwd_screen(C.byref(cs), C.byref(gs), C.byref(ps), _ptr(ids), _ptr(ranges), _ptr(img.T),
+                                       _ptr(img.n_contrib), _ptr(dL_drgb.contiguous()), _ptr(dL_dfeat.contiguous()),
+                                       _ptr(dL_dunc.contiguous()), _ptr(grad2d), _stream()))
+    return grad2d
+
+
+def le_project_bwd(cam, g: Gaussians, proj: Projected, grad2d, grads: Gaussians | None = None) -> Gaussians:
+    """Projection half of le_render_bwd: parameter gradients from grad2d."""
+    grads = grads or g.zeros_like()
+    cs, gs, ps, os_ = camera_struct(cam), g.struct(), proj.struct(), grads_struct(grads)
+    _check(load().le_project_bwd(C.byref(cs), C.byref(gs), C.byref(ps), _ptr(grad2d), C.byref(os_), _stream()))
+    return grads
+
+
+def le_project_bwd_adam(cam, g: Gaussians, proj: Projected, grad2d, m: Gaussians, v: Gaussians, step: int, lr=1e-3,
+                        beta1=0.9, beta2=0.999, eps=1e-8):
+    """Projection half of le_render_bwd_adam: the Adam step on g's tensors (and m, v) in place."""
+    cs, gs, ps = camera_struct(cam), g.struct(), proj.struct()
+    ms, vs = grads_struct(m), grads_struct(v)
+    cfg = LeAdamConfig(int(step), lr, beta1, beta2, eps)
+    _check(load().le_project_bwd_adam(C.byref(cs), C.byref(gs), C.byref(ps), _ptr(grad2d), C.byref(ms),
+                                      C.byref(vs), C.byref(cfg), _stream()))
 
 
 def decoder_struct(W1, b1, W2, b2, W3, b3) -> LeDecoder:

@@ -517,3 +517,47 @@ extern "C" le_status le_render_bwd_adam(const le_camera* cam, const le_gaussians
     return preprocess_backward_adam(cam, g, pr, grad2d, m, v,
                                     adam_params(adam->step, adam->lr, adam->beta1, adam->beta2, adam->eps), s);
 }
+
+extern "C" le_status le_render_bwd_screen(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                          const uint32_t* sorted_ids, const uint32_t* tile_ranges,
+                                          const float* T_final, const int32_t* n_contrib, const float* dL_drgb,
+                                          const float* dL_dfeat, const float* dL_dunc, float* grad2d, void* stream)
+{
+    le_status st = check_render_bwd(cam, g, pr, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc, grad2d);
+    if (st != LE_OK || g->n == 0) return st;
+    return render_backward_2d(cam, g, pr, sorted_ids, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc,
+                              grad2d, as_stream(stream));
+}
+
+extern "C" le_status le_project_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                    const float* grad2d, const le_gaussian_grads* out, void* stream)
+{
+    le_status st = check_camera(cam);
+    if (st != LE_OK) return st;
+    if ((st = check_gaussians(g)) != LE_OK) return st;
+    LE_CHECK_ARG(pr != nullptr, "null projected struct");
+    if (g->n == 0) return LE_OK;
+    LE_CHECK_ARG(pr->tiles_touched && pr->clamp_mask, "bad projected pointers");
+    LE_CHECK_ARG(grad2d && aligned16(grad2d), "grad2d must be non-null and 16-byte aligned");
+    if ((st = check_field_set(out, "gradient")) != LE_OK) return st;
+    return preprocess_backward(cam, g, pr, grad2d, out, as_stream(stream));
+}
+
+extern "C" le_status le_project_bwd_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                         const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
+                                         const le_adam_config* adam, void* stream)
+{
+    le_status st = check_camera(cam);
+    if (st != LE_OK) return st;
+    if ((st = check_gaussians(g)) != LE_OK) return st;
+    LE_CHECK_ARG(pr != nullptr, "null projected struct");
+    LE_CHECK_ARG(adam != nullptr && adam->step >= 1, "adam config is null or step < 1");
+    if (g->n == 0) return LE_OK;
+    LE_CHECK_ARG(pr->tiles_touched && pr->clamp_mask, "bad projected pointers");
+    LE_CHECK_ARG(grad2d && aligned16(grad2d), "grad2d must be non-null and 16-byte aligned");
+    if ((st = check_field_set(m, "first-moment")) != LE_OK) return st;
+    if ((st = check_field_set(v, "second-moment")) != LE_OK) return st;
+    return preprocess_backward_adam(cam, g, pr, grad2d, m, v,
+                                    adam_params(adam->step, adam->lr, adam->beta1, adam->beta2, adam->eps),
+                                    as_stream(stream));
+}

@@ -4,8 +4,9 @@ driven entirely through the C ABI with preallocated device buffers:
   le_preprocess -> le_bin_render_fwd (binning + compositing, lazily placed)
   -> le_rgb_l1 (RGB loss, Sec. 4)
   -> le_decode (D_MLP + uncertainty-weighted CE + L_u, Eqs. 8-12, training mode)
-  -> le_render_bwd_adam (all Gaussian parameter gradients, each applied by
-     Adam where it is computed; u clamped to [0,1], Sec. 3.4.2)
+  -> le_render_bwd_screen (screen-space gradients) -> le_project_bwd_adam
+     (all Gaussian parameter gradients, each applied by Adam where it is
+     computed; u clamped to [0,1], Sec. 3.4.2)
   -> le_adam (decoder parameters)
 
 With fused_adam=False the Gaussian gradients are written out by le_render_bwd
@@ -129,9 +130,13 @@ class TrainState:
         self.step_count += 1
         u0, d0 = self.layout.unc_offset, self.dec_lo
         if self.fused_adam:
-            B.le_render_bwd_adam(cam, self.g, self.proj, ids, ranges, self.img, self.d_rgb, self.d_feat, self.d_unc,
-                                 self.gm, self.gvv, self.step_count, lr=self.lr, grad2d=self.grad2d)
+            # le_render_bwd_adam in its two halves (identical results), so the
+            # stages can be timed apart
+            B.le_render_bwd_screen(cam, self.g, self.proj, ids, ranges, self.img, self.d_rgb, self.d_feat,
+                                   self.d_unc, grad2d=self.grad2d)
             self._mark("render_bwd")
+            B.le_project_bwd_adam(cam, self.g, self.proj, self.grad2d, self.gm, self.gvv, self.step_count, lr=self.lr)
+            self._mark("project_bwd_adam")
             B.le_adam(self.params[d0:u0], self.grads[d0:u0], self.m[d0:u0], self.v[d0:u0], self.step_count,
                       lr=self.lr)
         else:
