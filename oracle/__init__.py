@@ -16,7 +16,8 @@ import sysconfig
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["keypath.c", "sh.c", "project.c", "binning.c", "composite.c", "decoder.c", "query.c", "train.c"]
+SOURCES = ["keypath.c", "sh.c", "project.c", "binning.c", "composite.c", "decoder.c", "query.c", "train.c",
+           "quant.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 TILE = 16
 
@@ -52,6 +53,8 @@ def lib():
         _lib.orc_tile_list.restype = C.c_int
         _lib.orc_l1.restype = C.c_double
         _lib.orc_sh_count.restype = C.c_int
+        _lib.orc_bf16_bits.restype = C.c_uint16
+        _lib.orc_bf16_bits.argtypes = [C.c_float]
     return _lib
 
 
@@ -316,3 +319,34 @@ def forward(scene, cam, window=None, binned=True):
         vals, ranges = lists_for_tiles(cam, kp, tl)
     img = render(cam, scene, proj, vals, ranges, window)
     return dict(kp=kp, proj=proj, keys=keys, vals=vals, ranges=ranges, img=img)
+
+
+def bf16_bits(x) -> np.ndarray:
+    """FP32 values -> BF16 bit patterns (uint16), round to nearest even."""
+    x = _f32(x)
+    out = np.zeros(x.shape, np.uint16)
+    lib().orc_bf16_bits_array(C.c_int64(x.size), _p(x), _p(out))
+    return out
+
+
+def quantize(F_bf16, S, d_clip=512, lambda_d=0.5, lambda_cos=1.0, lambda_lb=0.5, round_codebook=True,
+             want_D=False, want_grad=False) -> dict:
+    """Quantisation of K language features against an N-entry codebook (Sec. 3.3):
+    F_bf16 [K, d] uint16 BF16 bit patterns, S [N, d] codebook (FP32 values, rounded
+    to BF16 when round_codebook, else used as FP64)."""
+    F = np.ascontiguousarray(F_bf16, np.uint16)
+    K, d = F.shape
+    S64 = _f64(S)
+    N = S64.shape[0]
+    out = {"m": np.zeros(K, np.int32), "r": np.zeros(N), "p": np.zeros(N), "loss": np.zeros(3)}
+    D = np.zeros((K, N)) if want_D else None
+    G = np.zeros((N, d)) if want_grad else None
+    lib().orc_quantize(C.c_int(K), C.c_int(N), C.c_int(d), C.c_int(d_clip), _p(F), _p(S64),
+                       C.c_int(int(round_codebook)), C.c_double(lambda_d), C.c_double(lambda_cos),
+                       C.c_double(lambda_lb), _p(D) if D is not None else None, _p(out["m"]), _p(out["r"]),
+                       _p(out["p"]), _p(out["loss"]), _p(G) if G is not None else None)
+    if want_D:
+        out["D"] = D
+    if want_grad:
+        out["grad_S"] = G
+    return out

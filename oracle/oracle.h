@@ -16,6 +16,8 @@
  *   - L_CE with uncertainty weighting, L_u, L_s    Eqs. 10-12 (eq:lem_loss_ce1, _uncer, eq:lem_loss)
  *   - inference M_infer = softmax(D_MLP(R_s)), F = M_infer S, relevancy   supp. Sec. "Inference"
  *   - Adam with lr 1e-3, betas (0.9, 0.999)                          Sec. 4
+ *   - quantisation of language features: mixed cosine argmax, L_cos,
+ *     load balancing L_lb, L_q           Sec. 3.3 (eq:q_dist .. eq:q_loss_cb), supp. Sec. 1
  *
  * Precision: FP64 everywhere except the "key path" (keypath.c), which decides
  * integers (culling, tile rectangle, sort key) and therefore is evaluated in
@@ -105,5 +107,13 @@ void orc_query(int P, int ncb, const double* prob, const float* codebook, int d,
 double orc_l1(int64_t n, const double* img, const float* target, double* grad);
 void orc_adam(int64_t n, double* param, const double* grad, double* m, double* v, int step,
               double lr, double b1, double b2, double eps);
+
+/* quant.c */
+uint16_t orc_bf16_bits(float x);
+void orc_bf16_bits_array(int64_t n, const float* x, uint16_t* out);
+double orc_bf16_value(uint16_t b);
+void orc_quantize(int K, int N, int d, int d_clip, const uint16_t* F_bf16, const double* S_in, int round_codebook,
+                  double lambda_d, double lambda_cos, double lambda_lb, double* D_out, int32_t* m_out, double* r_out,
+                  double* p_out, double* loss_out, double* grad_S);
 
 #endif

@@ -593,3 +593,103 @@ def test_l1(orc):
     loss, g = orc.l1(img, tgt)
     assert loss == (0.25 + 0 + 0.125 + 0.375) / 4
     np.testing.assert_array_equal(g, [0.25, 0, -0.25, 0.25])
+
+
+# ---------------------------------------------------------------------------
+# Quantisation of language features (Sec. 3.3, supp. "Load Balancing Loss")
+
+def _bf16_torch_bits(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(torch.bfloat16).view(torch.int16).numpy() \
+        .view(np.uint16)
+
+
+def test_bf16_rounding_matches_torch(orc):
+    rng = np.random.default_rng(30)
+    x = (rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000)).astype(np.float32)
+    # exact ties between two BF16 neighbours (round half to even; finite values) and signed zeros
+    ties = (rng.integers(0, 0x7F7F, 2000).astype(np.uint32) << 16) | np.uint32(0x8000)
+    x = np.concatenate([x, ties.view(np.float32), -ties.view(np.float32), np.array([0.0, -0.0, 1.0, -3.5], np.float32)])
+    assert x.dtype == np.float32 and np.all(np.isfinite(x))
+    assert np.array_equal(orc.bf16_bits(x), _bf16_torch_bits(x))
+
+
+def _split_cos(A, B, d_clip):
+    from scipy.spatial.distance import cdist
+    return 1.0 - cdist(A[:, :d_clip], B[:, :d_clip], "cosine"), 1.0 - cdist(A[:, d_clip:], B[:, d_clip:], "cosine")
+
+
+def _bf16_value(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def test_quant_distance_vs_library_cosine(orc):
+    rng = np.random.default_rng(31)
+    K, N, d, dc = 300, 32, 896, 512
+    S = rng.standard_normal((N, d)).astype(np.float32)
+    F = orc.bf16_bits(rng.standard_normal((K, d)))
+    o = orc.quantize(F, S, want_D=True)
+    cc, cd = _split_cos(_bf16_value(F), _bf16_value(orc.bf16_bits(S)), dc)
+    D = cc + 0.5 * cd
+    assert np.abs(o["D"] - D).max() < 1e-12
+    assert np.array_equal(o["m"], np.argmax(D, axis=1))
+    best = D[np.arange(K), o["m"]]
+    assert abs(o["loss"][1] - np.mean(1.5 - best)) < 1e-12            # L_cos = 1 + lambda_D - D(F, f_m)
+
+
+def test_quant_feature_equal_to_code(orc):
+    """F_i = f_j exactly: both cosines are 1, D = 1 + lambda_D is the maximum, m_i = j, L_cos = 0."""
+    rng = np.random.default_rng(32)
+    N, d = 64, 896
+    S = rng.standard_normal((N, d)).astype(np.float32)
+    pick = rng.integers(0, N, 500)
+    F = orc.bf16_bits(S)[pick]
+    o = orc.quantize(F, S, want_D=True)
+    assert np.array_equal(o["m"], pick)
+    assert np.abs(o["D"][np.arange(500), pick] - 1.5).max() < 1e-12
+    assert abs(o["loss"][1]) < 1e-12
+
+
+def test_quant_load_balance_closed_form(orc):
+    """Orthonormal codes e_j in both parts and features equal to codes: D = (1 + lambda_D) delta_ij,
+    each softmax row puts a = e^1.5/(e^1.5 + N - 1) on its own code and b = 1/(e^1.5 + N - 1)
+    elsewhere, so with c_j features on code j: r_j = c_j/K, p_j = (c_j a + (K - c_j) b)/K and
+    L_lb = sum_j r_j p_j; a balanced split gives L_lb = 1/N."""
+    N, d, dc = 16, 896, 512
+    S = np.zeros((N, d), np.float32)
+    for j in range(N):
+        S[j, j] = 1.0
+        S[j, dc + j] = 1.0
+    e = np.exp(1.5)
+    a, b = e / (e + N - 1), 1.0 / (e + N - 1)
+    for counts in (np.full(N, 7), np.arange(1, N + 1)):
+        pick = np.repeat(np.arange(N), counts)
+        K = len(pick)
+        o = orc.quantize(orc.bf16_bits(S[pick]), S)
+        r = counts / K
+        p = (counts * a + (K - counts) * b) / K
+        assert np.allclose(o["r"], r, rtol=0, atol=1e-15)
+        assert np.allclose(o["p"], p, rtol=0, atol=1e-14)
+        assert abs(o["loss"][2] - np.sum(r * p)) < 1e-14
+        assert abs(o["loss"][0] - (o["loss"][1] + 0.5 * o["loss"][2])) < 1e-14   # L_q, lambda_cos = 1
+    assert abs(np.sum(np.full(N, 1.0 / N) ** 2) - 1.0 / N) < 1e-15
+
+
+def test_quant_codebook_gradient_fd(orc):
+    """dL_q/dS against central differences of L_q (argmax winners, and with them r, unchanged)."""
+    rng = np.random.default_rng(33)
+    K, N, d, dc = 40, 8, 48, 32
+    S = rng.standard_normal((N, d))
+    F = orc.bf16_bits(S[rng.integers(0, N, K)] + 0.7 * rng.standard_normal((K, d)))
+    o = orc.quantize(F, S, d_clip=dc, round_codebook=False, want_grad=True)
+    G = o["grad_S"]
+    h = 1e-6
+    for j, e in [(int(rng.integers(N)), int(rng.integers(d))) for _ in range(40)]:
+        Sp, Sm = S.copy(), S.copy()
+        Sp[j, e] += h
+        Sm[j, e] -= h
+        op = orc.quantize(F, Sp, d_clip=dc, round_codebook=False)
+        om = orc.quantize(F, Sm, d_clip=dc, round_codebook=False)
+        assert np.array_equal(op["m"], o["m"]) and np.array_equal(om["m"], o["m"])
+        fd = (op["loss"][0] - om["loss"][0]) / (2 * h)
+        assert abs(fd - G[j, e]) <= 1e-6 * max(1.0, np.abs(G).max()), (j, e, fd, G[j, e])
