@@ -380,6 +380,7 @@ def run_ours(args, rank, world):
     if not args.no_extras and rank == 0:
         out["fused_vs_plain"] = compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, args)
         out["query"] = query_leg(leg, synth, scene, cams, args)
+        out["quantize"] = quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(scene, dec, cams[0], rgb_host[0].numpy(), idx_host[0].numpy(),
                                            budget_s=20.0)
@@ -465,6 +466,52 @@ def query_leg(leg, synth, scene, cams, args):
         except leg.LegError as e:
             res[name] = {"unavailable": str(e)[:200]}
     return res
+
+
+def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):
+    """Quantisation stage (Sec. 3.3) on one view's features: 1296x840 = 1,088,640
+    hybrid features of 896 dims (BF16, 1.95 GB, far larger than L2), 128-entry
+    codebook: argmax index map, L_cos, load balancing.  Features are drawn on the
+    GPU (seeded) around 128 hidden codes laid out by a Voronoi map of the view."""
+    import math
+    import numpy as np
+    import torch
+    K, N, dc, dd = W * H, 128, 512, 384
+    d = dc + dd
+    rng = np.random.default_rng(77)
+    centres = np.concatenate([synth.unit_rows(rng, N, dc), synth.unit_rows(rng, N, dd)], axis=1)
+    lab = torch.from_numpy(synth.voronoi_index_map(78, W, H, N, n_seeds=60).reshape(-1).astype(np.int64)).cuda()
+    g = torch.Generator(device="cuda").manual_seed(79)
+    F = torch.from_numpy(centres).cuda()[lab]
+    F += torch.randn(F.shape, generator=g, device="cuda") * (0.6 / math.sqrt(d))
+    Fb = F.to(torch.bfloat16)
+    S = F[torch.randint(0, K, (N,), generator=g, device="cuda")].contiguous()
+    del F, lab
+    out = (torch.empty(K, dtype=torch.int32, device="cuda"), torch.empty(N, device="cuda"),
+           torch.empty(N, device="cuda"), torch.empty(3, device="cuda"))
+    ws = torch.empty(leg.le_quantize_workspace(N, d), dtype=torch.uint8, device="cuda")
+    try:
+        for _ in range(3):
+            leg.le_quantize(Fb, S, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        n = max(5, args.steps // 4)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(n):
+            leg.le_quantize(Fb, S, out=out, workspace=ws)
+        t1.record()
+        torch.cuda.synchronize()
+    except leg.LegError as e:
+        return {"unavailable": str(e)[:200]}
+    ms = t0.elapsed_time(t1) / n
+    byts = K * d * 2 + K * 4 + N * d * 4
+    flop = 2.0 * K * N * d
+    return {"ms": round(ms, 4), "features": K, "dims": d, "codebook": N,
+            "hbm": {"achieved_gbs": round(byts / ms / 1e6, 1), "peak": hbm_peak, "frac": round(byts / ms / 1e6 / hbm_peak, 4),
+                    "peak_kind": peak_kind, "algorithmic_bytes": byts},
+            "tensor": {"achieved_tflops": round(flop / ms / 1e9, 1), "peak": bf16_peak,
+                       "frac": round(flop / ms / 1e9 / bf16_peak, 4)},
+            "loss": [round(float(x), 6) for x in out[3].cpu()]}
 
 
 # ---------------------------------------------------------------------------

@@ -342,6 +342,32 @@ le_status le_query(int32_t mode, int32_t P, const float* feat, const le_decoder*
                    void* stream);
 
 /* ---------------------------------------------------------------------------
+ * le_quantize -- quantisation of K language features against an N-entry
+ * codebook (Sec. 3.3, Eqs. eq:quant, eq:q_dist, eq:q_loss_cos, eq:q_loss_lb,
+ * eq:q_loss_cb; supplementary "Load Balancing Loss"):
+ *   D_ij = cos(F_i^C, f_j^C) + lambda_D cos(F_i^D, f_j^D)
+ *     (C = dims [0, d_clip) of the hybrid CLIP+DINO feature, D = the rest)
+ *   indices[i] = m_i = argmax_j D_ij (ties -> lowest j): the semantic index map
+ *   L_cos = mean_i (1 - cos^C(F_i, f_m)) + lambda_D (1 - cos^D(F_i, f_m))
+ *   r = histogram of m / K (utilisation), p = mean_i softmax_j(D_ij)
+ *   L_lb = sum_j r_j p_j,  L_q = lambda_cos L_cos + lambda_lb L_lb
+ * (the paper: lambda_D = lambda_lb = 0.5, lambda_cos = 1).
+ *   features: [K, d] BF16 bit patterns, row-major, 16-byte aligned
+ *   codebook: [n_cb, d] FP32; the distances use its BF16 rounding (nearest
+ *             even) and the norms of the rounded parts
+ *   indices [K] out; r, p [n_cb] out (nullable); loss [3] out = (L_q, L_cos, L_lb)
+ *   workspace: le_quantize_workspace(n_cb, d) bytes, 256-byte aligned.
+ * Features and codes must have nonzero CLIP and DINO parts.  BF16 operands on
+ * the tensor cores, FP32 accumulation, norms, softmax and sums in FP32.
+ * Errors: LE_ERR_INVALID_ARG (null/misaligned pointers, K < 1, K >= 2^31,
+ * 0 < d_clip < d violated); LE_ERR_UNSUPPORTED unless d and d_clip are
+ * multiples of 64 and n_cb is a multiple of 16 in 16..128. */
+le_status le_quantize_workspace(int32_t n_cb, int32_t d, size_t* bytes);
+le_status le_quantize(int64_t K, int32_t d, int32_t d_clip, const uint16_t* features, int32_t n_cb,
+                      const float* codebook, float lambda_d, float lambda_cos, float lambda_lb, int32_t* indices,
+                      float* r, float* p, float* loss, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Training helpers (Sec. 4).
  * le_rgb_l1: L = mean |img - target| over n values, loss[0] = L (device
  *   scalar, overwritten), grad = sign(img - target)/n (the 3DGS RGB loss's

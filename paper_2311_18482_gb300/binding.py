@@ -93,6 +93,9 @@ _SIG = {
     "le_query_workspace": [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "le_query": [C.c_int32, C.c_int32, _P, C.POINTER(LeDecoder), _P, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P,
                  C.c_int32, _P, _P, C.c_size_t, _P],
+    "le_quantize_workspace": [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
+    "le_quantize": [C.c_int64, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_float, C.c_float, C.c_float, _P, _P, _P,
+                    _P, _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
     "le_selftest_bounded_wait": [_P],
@@ -502,6 +505,32 @@ def le_query(mode: int, P: int, codebook, d_clip: int, text, negs, feat=None, de
                            _ptr(codebook), d, d_clip, _ptr(text), Q, _ptr(negs), negs.shape[0], _ptr(out),
                            _ptr(workspace), workspace.numel(), _stream()))
     return out
+
+
+def le_quantize_workspace(n_cb: int, d: int) -> int:
+    n = C.c_size_t()
+    _check(load().le_quantize_workspace(n_cb, d, C.byref(n)))
+    return n.value
+
+
+def le_quantize(features, codebook, d_clip=512, lambda_d=0.5, lambda_cos=1.0, lambda_lb=0.5, out=None,
+                workspace=None):
+    """Quantisation of language features (Sec. 3.3): features [K, d] torch.bfloat16 (or int16
+    holding BF16 bits), codebook [N, d] float32.  Returns (indices [K] int32, r [N], p [N],
+    loss [3] = (L_q, L_cos, L_lb)), all device tensors."""
+    K, d = features.shape
+    N = codebook.shape[0]
+    dev = features.device
+    if out is None:
+        out = (torch.empty(K, dtype=torch.int32, device=dev), torch.empty(N, dtype=torch.float32, device=dev),
+               torch.empty(N, dtype=torch.float32, device=dev), torch.empty(3, dtype=torch.float32, device=dev))
+    idx, r, p, loss = out
+    if workspace is None:
+        workspace = torch.empty(max(le_quantize_workspace(N, d), 1), dtype=torch.uint8, device=dev)
+    _check(load().le_quantize(K, d, d_clip, _ptr(features), N, _ptr(codebook.contiguous()), lambda_d, lambda_cos,
+                              lambda_lb, _ptr(idx), _ptr(r), _ptr(p), _ptr(loss), _ptr(workspace), workspace.numel(),
+                              _stream()))
+    return idx, r, p, loss
 
 
 def le_rgb_l1(img, target, loss, grad):

@@ -1148,11 +1148,22 @@ extern "C" le_status le_selftest_bounded_wait(void* stream)
     return LE_OK;
 }
 
+namespace leg {
+le_status quant_take_timeout(bool* timed_out);
+}
+
 extern "C" le_status le_device_status(void* stream)
 {
     LE_CUDA(cudaStreamSynchronize(leg::as_stream(stream)));
     int flag = 0;
     LE_CUDA(cudaMemcpyFromSymbol(&flag, leg::g_tc_error, sizeof(int)));
+    bool quant_flag = false;
+    const le_status qs = leg::quant_take_timeout(&quant_flag);
+    if (qs != LE_OK) return qs;
+    if (quant_flag && !flag) {
+        leg::set_error("the quantisation kernel gave up on a bounded wait");
+        return LE_ERR_TIMEOUT;
+    }
     if (flag) {
         const int zero = 0;
         LE_CUDA(cudaMemcpyToSymbol(leg::g_tc_error, &zero, sizeof(int)));

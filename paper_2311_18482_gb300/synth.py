@@ -16,6 +16,10 @@ seeded synthetic scenes with the paper's shapes stand in):
       4 text embeddings and 4 canonical negatives (random unit 512-vectors)
   c5  1M Gaussians, 16 poses on a circle of radius 3, 1296x840, per-view
       Voronoi maps (128-entry codebook), uncertainty initialised to 0
+  quantisation (Sec. 3.3): per-pixel hybrid features F = [CLIP 512 | DINO 384]
+      of one 1296x840 view drawn around the codes of a hidden 128-entry set
+      (one per Voronoi region of the view, Gaussian noise per pixel), stored as
+      BF16; the codebook being optimised starts from 128 random features
 
 Per-Gaussian parameters are FP32 structure-of-arrays:
   means [N,3], log_scales [N,3], quats [N,4] (w,x,y,z), opacity_raw [N]
@@ -263,3 +267,29 @@ def config(name: str, n: int | None = None, W: int | None = None, H: int | None 
                     target_idx=voronoi_index_map(1000 + pose, W, H, 128),
                     rgb_target=smooth_rgb_target(2000 + pose, W, H))
     raise ValueError(f"unknown workload {name!r}")
+
+
+def _bf16_bits(x: np.ndarray) -> np.ndarray:
+    """FP32 -> BF16 bit patterns (round to nearest even), for storing synthetic features."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32)
+    return ((u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) >> np.uint32(16)).astype(np.uint16)
+
+
+def quant_inputs(seed: int, K: int, n_cb: int = 128, d_clip: int = 512, d_dino: int = 384, n_hidden: int = 128,
+                 noise: float = 0.6, W: int | None = None):
+    """Synthetic language features for the quantisation stage: K features
+    [K, d_clip + d_dino] as BF16 bit patterns around n_hidden hidden unit codes
+    (per part), each feature's code chosen by a Voronoi map of the pixel grid of
+    width W (or uniformly at random when W is None), plus N(0, noise^2/d) per
+    dimension; and an n_cb x d FP32 codebook initialised from random features."""
+    rng = np.random.default_rng(seed)
+    d = d_clip + d_dino
+    centres = np.concatenate([unit_rows(rng, n_hidden, d_clip), unit_rows(rng, n_hidden, d_dino)], axis=1)
+    if W is None:
+        lab = rng.integers(0, n_hidden, K)
+    else:
+        H = (K + W - 1) // W
+        lab = voronoi_index_map(seed + 1, W, H, n_hidden, n_seeds=60).reshape(-1)[:K]
+    F = centres[lab] + rng.standard_normal((K, d)).astype(np.float32) * np.float32(noise / math.sqrt(d))
+    S = F[rng.choice(K, n_cb, replace=K < n_cb)].astype(np.float32)
+    return _bf16_bits(F), S

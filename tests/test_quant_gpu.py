@@ -1,0 +1,106 @@
+"""GPU parity of the quantisation stage (le_quantize, Sec. 3.3) against the
+FP64 oracle.
+
+The argmax is decided on the GPU from BF16 products accumulated in FP32, on
+the oracle in FP64.  Both are correct up to that rounding, so the bar is:
+  - every GPU index is a valid maximiser: D_oracle(i, m_gpu) >= max_j D_oracle(i, j) - 1e-4
+    (FP32 accumulation of 512 + 384 exact BF16 products of unit-normalised
+    vectors errs by at most ~(511 + 0.5 * 383) 2^-24 < 5e-5 in D, plus the
+    norms' rounding), and at least 99.9 % of the indices are identical;
+  - r equals the histogram of the GPU's own indices / K (FP32);
+  - p within 2e-5 of the oracle (FP32 softmax and atomic column sums);
+  - L_cos within 1e-5 relative + 2e-6 (a mean of 1 + lambda_D - D_max, each
+    term within the FP32 error of D); L_lb equal to r_gpu . p_oracle within
+    1e-5 relative; L_q = L_cos + 0.5 L_lb.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2311_18482_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(leg, F, S, d_clip=512):
+    Ft = torch.from_numpy(F.view(np.int16)).cuda()
+    St = torch.from_numpy(S).cuda()
+    idx, r, p, loss = leg.le_quantize(Ft, St, d_clip=d_clip)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), r.cpu().numpy(), p.cpu().numpy(), loss.cpu().numpy()
+
+
+def _check(orc, F, S, idx, r, p, loss, d_clip=512, agree=0.999):
+    K = F.shape[0]
+    N = S.shape[0]
+    o = orc.quantize(F, S, d_clip=d_clip, want_D=True)
+    D = o["D"]
+    assert idx.min() >= 0 and idx.max() < N
+    best = D.max(axis=1)
+    assert np.all(D[np.arange(K), idx] >= best - 1e-4)
+    assert np.mean(idx == o["m"]) >= agree
+    cnt = np.bincount(idx, minlength=N)
+    assert np.allclose(r, (cnt / K).astype(np.float32), rtol=1e-6, atol=0)
+    assert np.abs(p - o["p"]).max() <= 2e-5
+    assert abs(loss[1] - o["loss"][1]) <= 1e-5 * abs(o["loss"][1]) + 2e-6
+    lb_ref = float(np.dot(cnt / K, o["p"]))
+    assert abs(loss[2] - lb_ref) <= 1e-5 * lb_ref
+    assert abs(loss[0] - (loss[1] + 0.5 * loss[2])) <= 1e-6 * abs(loss[0])
+    return o
+
+
+@pytest.mark.parametrize("K,N,W", [(20000, 128, 160), (20001, 64, None), (130, 16, None), (1, 32, None),
+                                   (5000, 112, 100)])
+def test_quantize_parity(leg, orc, K, N, W):
+    F, S = synth.quant_inputs(40 + K % 7, K, N, W=W)
+    idx, r, p, loss = _run(leg, F, S)
+    _check(orc, F, S, idx, r, p, loss, agree=0.999 if K >= 1000 else 1.0)
+
+
+def test_quantize_other_split(leg, orc):
+    """A 256-dim feature split 128 / 128 (d and d_clip multiples of 64)."""
+    F, S = synth.quant_inputs(7, 3001, 48, d_clip=128, d_dino=128)
+    idx, r, p, loss = _run(leg, F, S, d_clip=128)
+    _check(orc, F, S, idx, r, p, loss, d_clip=128)
+
+
+def test_quantize_features_equal_codes(leg, orc):
+    """Features that are the (BF16-rounded) codes themselves: m_i = the code, L_cos = 0 up to FP32 rounding."""
+    rng = np.random.default_rng(8)
+    N = 128
+    S = rng.standard_normal((N, 896)).astype(np.float32)
+    pick = rng.integers(0, N, 4096)
+    F = synth._bf16_bits(S)[pick]
+    idx, r, p, loss = _run(leg, F, S)
+    assert np.array_equal(idx, pick)
+    assert abs(loss[1]) < 1e-5
+
+
+def test_quantize_full_view(leg, orc):
+    """The bench's launch configuration: one 1296x840 view of 896-dim features
+    (1,088,640 rows), 128-entry codebook.  Sampled rows against the oracle,
+    global properties on all of them."""
+    K = 1296 * 840
+    F, S = synth.quant_inputs(11, K, 128, W=1296)
+    idx, r, p, loss = _run(leg, F, S)
+    rows = np.random.default_rng(12).choice(K, 3000, replace=False)
+    o = orc.quantize(F[rows], S, want_D=True)
+    D = o["D"]
+    assert np.all(D[np.arange(len(rows)), idx[rows]] >= D.max(axis=1) - 1e-4)
+    assert np.mean(idx[rows] == o["m"]) >= 0.999
+    cnt = np.bincount(idx, minlength=128)
+    assert np.allclose(r, (cnt / K).astype(np.float32), rtol=1e-6, atol=0)
+    assert abs(float(p.sum()) - 1.0) < 1e-4
+    assert abs(loss[0] - (loss[1] + 0.5 * loss[2])) <= 1e-6 * abs(loss[0])
+    # L_cos is a mean over rows: the sample's mean estimates it
+    assert abs(loss[1] - o["loss"][1]) < 0.05 * o["loss"][1] + 1e-3
+
+
+def test_quantize_rejects_unsupported(leg):
+    F = torch.zeros((10, 896), dtype=torch.int16, device="cuda")
+    with pytest.raises(leg.LegError) as e:
+        leg.le_quantize(F, torch.zeros((200, 896), device="cuda"))
+    assert e.value.status == leg.LE_ERR_UNSUPPORTED
+    with pytest.raises(leg.LegError) as e:
+        leg.le_quantize(F, torch.zeros((64, 896), device="cuda"), d_clip=500)
+    assert e.value.status == leg.LE_ERR_UNSUPPORTED
