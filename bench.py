@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--decoder", default="auto", choices=["auto", "fused", "unfused"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussian count (default: the workload's 1M)")
     ap.add_argument("--no-extras", action="store_true", help="skip the query / unfused comparison legs")
+    ap.add_argument("--only", choices=["quantize"], default=None,
+                    help="run one leg alone (quantize: the quantisation stage on --features rows)")
+    ap.add_argument("--features", type=int, default=W * H, help="feature rows for --only quantize")
     return ap.parse_args()
 
 
@@ -476,11 +479,12 @@ def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):
     import math
     import numpy as np
     import torch
-    K, N, dc, dd = W * H, 128, 512, 384
+    K, N, dc, dd = getattr(args, "features", W * H), 128, 512, 384
     d = dc + dd
     rng = np.random.default_rng(77)
     centres = np.concatenate([synth.unit_rows(rng, N, dc), synth.unit_rows(rng, N, dd)], axis=1)
-    lab = torch.from_numpy(synth.voronoi_index_map(78, W, H, N, n_seeds=60).reshape(-1).astype(np.int64)).cuda()
+    Hk = (K + W - 1) // W
+    lab = torch.from_numpy(synth.voronoi_index_map(78, W, Hk, N, n_seeds=60).reshape(-1)[:K].astype(np.int64)).cuda()
     g = torch.Generator(device="cuda").manual_seed(79)
     F = torch.from_numpy(centres).cuda()[lab]
     F += torch.randn(F.shape, generator=g, device="cuda") * (0.6 / math.sqrt(d))
@@ -609,6 +613,17 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.only == "quantize":
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2311_18482_gb300 as leg
+        from paper_2311_18482_gb300 import synth
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        leg.load()
+        hbm, bf16, kind = measured_peaks()
+        print(json.dumps({"leg": "quantize", **quant_leg(leg, synth, args, hbm, bf16, kind)}), flush=True)
+        return
     if world > 1 and args.impl == "ours":
         import torch
         import torch.distributed as dist
