@@ -508,6 +508,19 @@ def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):
     except leg.LegError as e:
         return {"unavailable": str(e)[:200]}
     ms = t0.elapsed_time(t1) / n
+    # the codebook gradient (le_quantize_grad: recompute D and write g / |F|, contraction over the features)
+    gws = torch.empty(leg.le_quantize_grad_workspace(K, N, d), dtype=torch.uint8, device="cuda")
+    grad = torch.empty((N, d), device="cuda")
+    for _ in range(3):
+        leg.le_quantize_grad(Fb, S, out[1], out=grad, workspace=gws)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(n):
+        leg.le_quantize_grad(Fb, S, out[1], out=grad, workspace=gws)
+    t1.record()
+    torch.cuda.synchronize()
+    ms_g = t0.elapsed_time(t1) / n
+    bytes_g = 2 * K * d * 2 + 2 * 2 * K * N * 2       # features twice, g / |F| written and read (two parts)
     byts = K * d * 2 + K * 4 + N * d * 4
     flop = 2.0 * K * N * d
     return {"ms": round(ms, 4), "features": K, "dims": d, "codebook": N,
@@ -515,7 +528,11 @@ def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):
                     "peak_kind": peak_kind, "algorithmic_bytes": byts},
             "tensor": {"achieved_tflops": round(flop / ms / 1e9, 1), "peak": bf16_peak,
                        "frac": round(flop / ms / 1e9 / bf16_peak, 4)},
-            "loss": [round(float(x), 6) for x in out[3].cpu()]}
+            "loss": [round(float(x), 6) for x in out[3].cpu()],
+            "codebook_grad": {"ms": round(ms_g, 4), "hbm_frac": round(bytes_g / ms_g / 1e6 / hbm_peak, 4),
+                              "algorithmic_bytes": bytes_g,
+                              "note": "le_quantize_grad: 4 launches (prep, D recompute + g, split-K tcgen05 "
+                                      "contraction, finalize); the codebook's Adam step is le_adam"}}
 
 
 # ---------------------------------------------------------------------------

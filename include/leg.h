@@ -368,6 +368,29 @@ le_status le_quantize(int64_t K, int32_t d, int32_t d_clip, const uint16_t* feat
                       float* r, float* p, float* loss, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * le_quantize_grad -- gradient of L_q (as le_quantize computes it) with
+ * respect to the codebook, for its optimisation (Sec. 3.3, "Optimization"):
+ *   g_ij = dL_q/dD_ij = lambda_lb/K s_ij (r_j - sum_k s_ik r_k) - lambda_cos/K [j = m_i]
+ *     (s = row softmax of D, r = the utilisation ratio le_quantize returned,
+ *      held constant: argmax counts have no derivative)
+ *   dL/df_j^C = (sum_i g_ij (F_i^C/|F_i^C| - cos^C_ij f_j^C/|f_j^C|)) / |f_j^C|, and the
+ *   same for the DINO part times lambda_D -- with respect to the BF16-rounded
+ *   codebook values the distances use.
+ *   features, codebook, d, d_clip, n_cb, lambdas: as le_quantize (same values)
+ *   r: [n_cb] from le_quantize on the same inputs
+ *   grad_codebook: [n_cb, d] FP32 out (overwritten)
+ *   workspace: le_quantize_grad_workspace(K, n_cb, d) bytes (it holds the
+ *     BF16 matrix g / |F| twice, 4 n_cb K bytes), 256-byte aligned.
+ * The contraction over the K features runs on the tensor cores with g
+ * rounded to BF16 (about 2^-9 relative per term), FP32 accumulation.
+ * Errors: those of le_quantize, and LE_ERR_UNSUPPORTED unless d and d_clip
+ * are multiples of 128. */
+le_status le_quantize_grad_workspace(int64_t K, int32_t n_cb, int32_t d, size_t* bytes);
+le_status le_quantize_grad(int64_t K, int32_t d, int32_t d_clip, const uint16_t* features, int32_t n_cb,
+                           const float* codebook, const float* r, float lambda_d, float lambda_cos, float lambda_lb,
+                           float* grad_codebook, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Training helpers (Sec. 4).
  * le_rgb_l1: L = mean |img - target| over n values, loss[0] = L (device
  *   scalar, overwritten), grad = sign(img - target)/n (the 3DGS RGB loss's

@@ -96,6 +96,9 @@ _SIG = {
     "le_quantize_workspace": [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "le_quantize": [C.c_int64, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_float, C.c_float, C.c_float, _P, _P, _P,
                     _P, _P, C.c_size_t, _P],
+    "le_quantize_grad_workspace": [C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
+    "le_quantize_grad": [C.c_int64, C.c_int32, C.c_int32, _P, C.c_int32, _P, _P, C.c_float, C.c_float, C.c_float,
+                         _P, _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
     "le_selftest_bounded_wait": [_P],
@@ -531,6 +534,27 @@ def le_quantize(features, codebook, d_clip=512, lambda_d=0.5, lambda_cos=1.0, la
                               lambda_lb, _ptr(idx), _ptr(r), _ptr(p), _ptr(loss), _ptr(workspace), workspace.numel(),
                               _stream()))
     return idx, r, p, loss
+
+
+def le_quantize_grad_workspace(K: int, n_cb: int, d: int) -> int:
+    n = C.c_size_t()
+    _check(load().le_quantize_grad_workspace(K, n_cb, d, C.byref(n)))
+    return n.value
+
+
+def le_quantize_grad(features, codebook, r, d_clip=512, lambda_d=0.5, lambda_cos=1.0, lambda_lb=0.5, out=None,
+                     workspace=None):
+    """Gradient of L_q with respect to the codebook (Sec. 3.3): features [K, d] BF16 (or int16
+    bits), codebook [N, d] float32, r [N] from le_quantize.  Returns grad [N, d] float32."""
+    K, d = features.shape
+    N = codebook.shape[0]
+    dev = features.device
+    out = out if out is not None else torch.empty((N, d), dtype=torch.float32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(le_quantize_grad_workspace(K, N, d), dtype=torch.uint8, device=dev)
+    _check(load().le_quantize_grad(K, d, d_clip, _ptr(features), N, _ptr(codebook.contiguous()), _ptr(r), lambda_d,
+                                   lambda_cos, lambda_lb, _ptr(out), _ptr(workspace), workspace.numel(), _stream()))
+    return out
 
 
 def le_rgb_l1(img, target, loss, grad):

@@ -77,6 +77,13 @@ struct QuantArgs {
     float* psum;                 // [N] column sums of the softmax
     unsigned* count;             // [N] argmax counts
     float* lcos;                 // [1] sum of 1 + lambda_D - D_max
+    // gradient mode (quant_kernel<true>)
+    const float* r;              // [N] utilisation ratio from the forward pass
+    __nv_bfloat16* gtc;          // [N][kp] g_ij / |F_i^C|, code-major (feature index contiguous)
+    __nv_bfloat16* gtd;          // [N][kp] g_ij / |F_i^D|
+    long long kp;                // row stride of gtc / gtd (K rounded up to 8)
+    float* u;                    // [2][N] sum_i g_ij cos^C_ij, sum_i g_ij cos^D_ij
+    float cl, cc;                // lambda_lb / K, lambda_cos / K
 };
 
 struct Smem {
@@ -85,7 +92,8 @@ struct Smem {
     uint32_t bstride;
     uint64_t *full, *empty, *acc_full, *acc_empty, *norm_ready, *norm_free, *fin;
     float* norms;                // [2 slots][2][128] inverse feature norms
-    float* xch;                  // [2 slots][2 halves][3][128] epilogue exchange
+    float* xch;                  // [2 slots][2 halves][4][128] epilogue exchange
+    float* rv;                   // [N] utilisation ratio (gradient mode)
     float* inv_s;                // [2][N]
     unsigned* cnt;               // [N]
     uint32_t* tmem_slot;
@@ -93,8 +101,8 @@ struct Smem {
 
 __host__ __device__ constexpr uint32_t quant_smem_bytes(int N)
 {
-    return 1024 + kStages * (kATile + (uint32_t)N * kChunk * 2) + 2 * 2 * kRows * 4 + 2 * 6 * kRows * 4 + 2 * N * 4 +
-           N * 4 + 8 +
+    return 1024 + kStages * (kATile + (uint32_t)N * kChunk * 2) + 2 * 2 * kRows * 4 + 2 * 8 * kRows * 4 + N * 4 +
+           2 * N * 4 + N * 4 + 8 +
            (2 * kStages + 10) * 8;
 }
 
@@ -110,7 +118,9 @@ __device__ Smem carve(unsigned char* base, int N)
     s.norms = reinterpret_cast<float*>(p);
     p += 2 * 2 * kRows * 4;
     s.xch = reinterpret_cast<float*>(p);
-    p += 2 * 6 * kRows * 4;
+    p += 2 * 8 * kRows * 4;
+    s.rv = reinterpret_cast<float*>(p);
+    p += N * 4;
     s.inv_s = reinterpret_cast<float*>(p);
     p += 2 * N * 4;
     s.cnt = reinterpret_cast<unsigned*>(p);
@@ -183,6 +193,7 @@ __device__ __forceinline__ int chunk_at(int i, int nclip, int nchunks, int rot)
     return i < nclip ? (i + rot) % nclip : nclip + (i - nclip + rot) % nd;
 }
 
+template <bool GRAD>
 __global__ void __launch_bounds__(kThreads, 1) quant_kernel(const __grid_constant__ CUtensorMap tmap_f,
                                                             const __grid_constant__ CUtensorMap tmap_s, QuantArgs q)
 {
@@ -191,7 +202,10 @@ __global__ void __launch_bounds__(kThreads, 1) quant_kernel(const __grid_constan
     Smem s = carve(smem_raw, N);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) s.inv_s[i] = q.inv_s[i];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) s.cnt[i] = 0u;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        s.cnt[i] = 0u;
+        if (GRAD) s.rv[i] = q.r[i];
+    }
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(s.full + i, 1);
@@ -347,9 +361,9 @@ __global__ void __launch_bounds__(kThreads, 1) quant_kernel(const __grid_constan
         const uint32_t lanef = (uint32_t)(32 * quad) << 16;
         const int nch = N / 16, nh0 = (nch + 1) / 2;
         const int c_lo = h ? nh0 : 0, c_hi = h ? nch : nh0;
-        float psum[4];
+        float psum[4], usum[4];   // softmax column sums (gradient mode: sums of g cos^C, g cos^D)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) psum[i] = 0.f;
+        for (int i = 0; i < 4; ++i) psum[i] = usum[i] = 0.f;
         float lcos = 0.f;
         int it = 0;
         for (int t = blockIdx.x; t < q.ntiles && ok; t += gridDim.x, ++it) {
@@ -369,71 +383,147 @@ __global__ void __launch_bounds__(kThreads, 1) quant_kernel(const __grid_constan
             const long long row = (long long)t * kRows + r;
             const bool valid = row < q.K;
             const uint32_t acc = tmem + lanef + (uint32_t)(2 * N * slot);
-            // pass 1 over this half's columns: D, argmax (first maximum), sum of
-            // exp(D) (|D| <= 1 + lambda_D: no shift needed); exp(D) replaces the
-            // CLIP dot products in TMEM for pass 2
-            float best = -INFINITY, esum = 0.f;
-            int bi = 0;
-            for (int c = c_lo; c < c_hi; ++c) {
-                const int j0 = 16 * c;
-                float vc[16], vd[16];
-                tmem_ld16(acc + j0, vc);
-                tmem_ld16(acc + N + j0, vd);
+            if constexpr (GRAD) {
+                // pass 1: D, argmax, sum of exp(D) and of exp(D) r_j (for sigma_i = sum_k s_ik r_k)
+                const float aC0 = s.norms[slot * 2 * kRows + r], aD0 = s.norms[slot * 2 * kRows + kRows + r];
+                float best = -INFINITY, esum = 0.f, esr = 0.f;
+                int bi = 0;
+                for (int c = c_lo; c < c_hi; ++c) {
+                    const int j0 = 16 * c;
+                    float vc[16], vd[16];
+                    tmem_ld16(acc + j0, vc);
+                    tmem_ld16(acc + N + j0, vd);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float dv = fmaf(vc[k] * aC, s.inv_s[j0 + k], vd[k] * aD * s.inv_s[N + j0 + k]);
-                    if (dv > best) {
-                        best = dv;
-                        bi = j0 + k;
+                    for (int k = 0; k < 16; ++k) {
+                        const float dv = fmaf(vc[k] * aC, s.inv_s[j0 + k], vd[k] * aD * s.inv_s[N + j0 + k]);
+                        if (dv > best) {
+                            best = dv;
+                            bi = j0 + k;
+                        }
+                        const float e = __expf(dv);
+                        esum += e;
+                        esr = fmaf(e, s.rv[j0 + k], esr);
                     }
-                    vc[k] = __expf(dv);
-                    esum += vc[k];
                 }
-                tmem_st16(acc + j0, vc);
-            }
-            // combine the halves (ties -> half 0, the lower indices)
-            float* x = s.xch + slot * 6 * kRows;
-            x[(3 * h) * kRows + r] = best;
-            x[(3 * h + 1) * kRows + r] = __int_as_float(bi);
-            x[(3 * h + 2) * kRows + r] = esum;
-            named_sync(1 + quad, 64);
-            const float ob = x[(3 * (1 - h)) * kRows + r];
-            const int oi = __float_as_int(x[(3 * (1 - h) + 1) * kRows + r]);
-            esum += x[(3 * (1 - h) + 2) * kRows + r];
-            if (h == 0 ? ob > best : ob >= best) {
-                best = ob;
-                bi = oi;
-            }
-            const float inv_e = valid ? 1.0f / esum : 0.f;
-            tmem_wait_st();
-            // pass 2: softmax column sums of this half's columns over the warp's 32 rows
+                float* x = s.xch + slot * 8 * kRows;
+                x[(4 * h) * kRows + r] = best;
+                x[(4 * h + 1) * kRows + r] = __int_as_float(bi);
+                x[(4 * h + 2) * kRows + r] = esum;
+                x[(4 * h + 3) * kRows + r] = esr;
+                named_sync(1 + quad, 64);
+                const float ob = x[(4 * (1 - h)) * kRows + r];
+                const int oi = __float_as_int(x[(4 * (1 - h) + 1) * kRows + r]);
+                esum += x[(4 * (1 - h) + 2) * kRows + r];
+                esr += x[(4 * (1 - h) + 3) * kRows + r];
+                if (h == 0 ? ob > best : ob >= best) bi = oi;
+                const float inv_e = valid ? 1.0f / esum : 0.f;
+                const float sigma = esr * inv_e;
+                // pass 2: g_ij = lambda_lb/K s_ij (r_j - sigma_i) - lambda_cos/K [j = m_i];
+                // u^C_j += g cos^C_ij, u^D_j += g cos^D_ij; G^T scaled by the inverse feature norms
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int c = c_lo + cc;
-                if (c >= c_hi) break;
-                float e[16];
-                tmem_ld16(acc + 16 * c, e);
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = c_lo + cc;
+                    if (c >= c_hi) break;
+                    const int j0 = 16 * c;
+                    float vc[16], vd[16];
+                    tmem_ld16(acc + j0, vc);
+                    tmem_ld16(acc + N + j0, vd);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) e[k] = valid ? e[k] * inv_e : 0.f;   // rows past K hold NaN
-                psum[cc] += warp_colsum16(e, lane);
-            }
-            fence_before();
-            mbar_arrive(s.acc_empty + slot);
-            if (valid && h == 0) {
-                q.m_out[row] = bi;
-                lcos += 1.0f + q.lambda_d - best;
-                atomicAdd(s.cnt + bi, 1u);
+                    for (int k = 0; k < 16; ++k) {
+                        const float cosc = vc[k] * aC0 * s.inv_s[j0 + k], cosd = vd[k] * aD0 * s.inv_s[N + j0 + k];
+                        const float sv = __expf(fmaf(q.lambda_d, cosd, cosc)) * inv_e;
+                        float g = q.cl * sv * (s.rv[j0 + k] - sigma);
+                        if (j0 + k == bi) g -= q.cc;
+                        g = valid ? g : 0.f;
+                        if (valid) {
+                            q.gtc[(size_t)(j0 + k) * q.kp + row] = __float2bfloat16_rn(g * aC0);
+                            q.gtd[(size_t)(j0 + k) * q.kp + row] = __float2bfloat16_rn(g * aD0);
+                        }
+                        vc[k] = valid ? g * cosc : 0.f;     // rows past K: cos is NaN
+                        vd[k] = valid ? g * cosd : 0.f;
+                    }
+                    psum[cc] += warp_colsum16(vc, lane);
+                    usum[cc] += warp_colsum16(vd, lane);
+                }
+                fence_before();
+                mbar_arrive(s.acc_empty + slot);
+            } else {
+                // pass 1 over this half's columns: D, argmax (first maximum), sum of
+                // exp(D) (|D| <= 1 + lambda_D: no shift needed); exp(D) replaces the
+                // CLIP dot products in TMEM for pass 2
+                float best = -INFINITY, esum = 0.f;
+                int bi = 0;
+                for (int c = c_lo; c < c_hi; ++c) {
+                    const int j0 = 16 * c;
+                    float vc[16], vd[16];
+                    tmem_ld16(acc + j0, vc);
+                    tmem_ld16(acc + N + j0, vd);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float dv = fmaf(vc[k] * aC, s.inv_s[j0 + k], vd[k] * aD * s.inv_s[N + j0 + k]);
+                        if (dv > best) {
+                            best = dv;
+                            bi = j0 + k;
+                        }
+                        vc[k] = __expf(dv);
+                        esum += vc[k];
+                    }
+                    tmem_st16(acc + j0, vc);
+                }
+                // combine the halves (ties -> half 0, the lower indices)
+                float* x = s.xch + slot * 6 * kRows;
+                x[(3 * h) * kRows + r] = best;
+                x[(3 * h + 1) * kRows + r] = __int_as_float(bi);
+                x[(3 * h + 2) * kRows + r] = esum;
+                named_sync(1 + quad, 64);
+                const float ob = x[(3 * (1 - h)) * kRows + r];
+                const int oi = __float_as_int(x[(3 * (1 - h) + 1) * kRows + r]);
+                esum += x[(3 * (1 - h) + 2) * kRows + r];
+                if (h == 0 ? ob > best : ob >= best) {
+                    best = ob;
+                    bi = oi;
+                }
+                const float inv_e = valid ? 1.0f / esum : 0.f;
+                tmem_wait_st();
+                // pass 2: softmax column sums of this half's columns over the warp's 32 rows
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = c_lo + cc;
+                    if (c >= c_hi) break;
+                    float e[16];
+                    tmem_ld16(acc + 16 * c, e);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) e[k] = valid ? e[k] * inv_e : 0.f;   // rows past K hold NaN
+                    psum[cc] += warp_colsum16(e, lane);
+                }
+                fence_before();
+                mbar_arrive(s.acc_empty + slot);
+                if (valid && h == 0) {
+                    q.m_out[row] = bi;
+                    lcos += 1.0f + q.lambda_d - best;
+                    atomicAdd(s.cnt + bi, 1u);
+                }
             }
         }
         // flush this warp's partial sums
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lcos += __shfl_xor_sync(0xffffffffu, lcos, o);
         if (ok) {
-            if (lane == 0 && h == 0) atomicAdd(q.lcos, lcos);
-            if ((lane & 1) == 0)
+            if (GRAD) {
+                if ((lane & 1) == 0)
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
-                    if (c_lo + cc < c_hi) atomicAdd(q.psum + 16 * (c_lo + cc) + (lane >> 1), psum[cc]);
+                    for (int cc = 0; cc < 4; ++cc)
+                        if (c_lo + cc < c_hi) {
+                            atomicAdd(q.u + 16 * (c_lo + cc) + (lane >> 1), psum[cc]);
+                            atomicAdd(q.u + N + 16 * (c_lo + cc) + (lane >> 1), usum[cc]);
+                        }
+            } else {
+                if (lane == 0 && h == 0) atomicAdd(q.lcos, lcos);
+                if ((lane & 1) == 0)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+                        if (c_lo + cc < c_hi) atomicAdd(q.psum + 16 * (c_lo + cc) + (lane >> 1), psum[cc]);
+            }
         }
     }
     fence_before();
@@ -441,11 +531,174 @@ __global__ void __launch_bounds__(kThreads, 1) quant_kernel(const __grid_constan
     fence_after();
     if (bad) {
         if (threadIdx.x == 0) atomicExch(&g_quant_error, 1);
-    } else {
+    } else if (!GRAD) {
         for (int i = threadIdx.x; i < N; i += blockDim.x)
             if (s.cnt[i]) atomicAdd(q.count + i, s.cnt[i]);
     }
     if (warp == 1) tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Codebook gradient, contraction over the features (split-K):
+//   raw[j][e] += sum_i GT[j][i] F[i][e]   (GT = gtc for CLIP dims e, gtd for DINO dims)
+// CTA (x, y): the 128 dims [128 x, 128 x + 128) and the y-th slice of the
+// 64-feature chunks.  A = GT tile [128 codes x 64 features] (K-major, TMA,
+// 128-byte swizzle; codes past N read as zero); B = F tile [64 features x 128
+// dims] as two 64-dim TMA boxes, read MN-major (dims contiguous).  Each MMA
+// covers one 64-dim swizzle atom column (N = 64), so the operand spans one
+// atom along N and only the stride between 8-feature groups (1024 bytes)
+// matters; it is written into both offset fields.  The accumulator (128 lanes
+// = codes x 128 columns = dims) is added into raw with atomics at the end.
+constexpr int kGStages = 4;
+constexpr int kGThreads = 192;
+constexpr uint32_t kGATile = 128 * kChunk * 2;       // 16 KB
+constexpr uint32_t kGBBox = kChunk * kChunk * 2;     // 8 KB: 64 features x 64 dims
+
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(1024 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+struct GemmArgs {
+    int N, d, dclip_tiles;       // codebook size, dims, 128-dim tiles in the CLIP part
+    int nch_total, nch_split;    // 64-feature chunks in all, per split
+    float* raw;                  // [N][d]
+};
+
+__global__ void __launch_bounds__(kGThreads, 1) quant_grad_gemm_kernel(const __grid_constant__ CUtensorMap tmap_gtc,
+                                                                       const __grid_constant__ CUtensorMap tmap_gtd,
+                                                                       const __grid_constant__ CUtensorMap tmap_f,
+                                                                       GemmArgs g)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* A0 = base;                                   // kGStages x 16 KB
+    unsigned char* B0 = base + kGStages * kGATile;              // kGStages x 16 KB
+    uint64_t* full = reinterpret_cast<uint64_t*>(B0 + kGStages * 2 * kGBBox);
+    uint64_t* empty = full + kGStages;
+    uint64_t* done = empty + kGStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int dt = blockIdx.x;
+    const bool clip = dt < g.dclip_tiles;
+    const CUtensorMap* tmap_a = clip ? &tmap_gtc : &tmap_gtd;
+    const int c0 = blockIdx.y * g.nch_split;
+    const int c1 = min(g.nch_total, c0 + g.nch_split);
+    const int nck = max(0, c1 - c0);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kGStages; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tslot, 128);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0;
+            for (int c = 0; c < nck; ++c) {
+                if (!wait_bar(empty + st, ph ^ 1)) {
+                    ok = false;
+                    break;
+                }
+                const int f0 = (c0 + c) * kChunk;
+                mbar_expect_tx(full + st, kGATile + 2 * kGBBox);
+                tma_load_2d(A0 + st * kGATile, tmap_a, f0, 0, full + st);
+                tma_load_2d(B0 + st * 2 * kGBBox, &tmap_f, 128 * dt, f0, full + st);
+                tma_load_2d(B0 + st * 2 * kGBBox + kGBBox, &tmap_f, 128 * dt + 64, f0, full + st);
+                if (++st == kGStages) {
+                    st = 0;
+                    ph ^= 1;
+                }
+            }
+            for (int i = 0; i < kGStages; ++i) {     // nothing may still be landing at exit
+                int k = st - 1 - i;
+                uint32_t kp = ph;
+                if (k < 0) {
+                    k += kGStages;
+                    kp ^= 1;
+                }
+                (void)wait_bar(full + k, kp);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(64, false, true);
+            int st = 0;
+            uint32_t ph = 0;
+            for (int c = 0; c < nck; ++c) {
+                if (!wait_bar(full + st, ph)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint64_t da = desc_sw128(smem_u32(A0 + st * kGATile));
+                const uint64_t db0 = desc_sw128_mn(smem_u32(B0 + st * 2 * kGBBox));
+                const uint64_t db1 = desc_sw128_mn(smem_u32(B0 + st * 2 * kGBBox + kGBBox));
+#pragma unroll
+                for (int k = 0; k < kChunk / 16; ++k) {
+                    const uint32_t accumulate = (c > 0 || k > 0) ? 1u : 0u;
+                    // A: +32 bytes per 16 features (K-major swizzle row); B: +2 x 1024 bytes (two 8-feature groups)
+                    mma(tmem, da + 2u * k, db0 + 128u * k, idesc, accumulate);
+                    mma(tmem + 64, da + 2u * k, db1 + 128u * k, idesc, accumulate);
+                }
+                commit(empty + st);
+                if (++st == kGStages) {
+                    st = 0;
+                    ph ^= 1;
+                }
+            }
+            commit(done);
+        }
+    }
+    // epilogue: warps 2-5 (TMEM lane quadrant warp % 4): codes 32 (warp % 4) + lane
+    if (warp >= 2) {
+        const bool got = wait_bar(done, 0);
+        fence_after();
+        const int j = 32 * (warp & 3) + lane;
+        if (got && nck > 0) {
+            for (int c0c = 0; c0c < 128; c0c += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0c, v);
+                if (j < g.N)
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) atomicAdd(g.raw + (size_t)j * g.d + 128 * dt + c0c + k, v[k]);
+            }
+        }
+        ok = ok && got;
+    } else if (warp == 1 && lane == 0) {
+        ok = ok && wait_bar(done, 0);     // every MMA of ours has completed
+    }
+    fence_before();
+    const bool bad = __syncthreads_or(!ok);
+    fence_after();
+    if (bad && threadIdx.x == 0) atomicExch(&g_quant_error, 1);
+    if (warp == 1) tmem_dealloc(tmem, 128);
+}
+
+// dL/dS_j^C[e] = invS^C_j (raw[j][e] - u^C_j S_j[e] invS^C_j) for CLIP dims, and
+// lambda_D invS^D_j (raw[j][e] - u^D_j S_j[e] invS^D_j) for DINO dims (S the BF16 codebook).
+__global__ void quant_grad_finalize_kernel(const float* __restrict__ raw, const float* __restrict__ u,
+                                           const __nv_bfloat16* __restrict__ Sb, const float* __restrict__ inv_s,
+                                           int N, int d, int d_clip, float lambda_d, float* __restrict__ grad)
+{
+    const size_t n = (size_t)N * d;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i / d), e = (int)(i - (size_t)j * d);
+        const bool cpart = e < d_clip;
+        const float is = inv_s[(cpart ? 0 : N) + j];
+        const float w = cpart ? 1.f : lambda_d;
+        grad[i] = w * is * (raw[i] - u[(cpart ? 0 : N) + j] * __bfloat162float(Sb[i]) * is);
+    }
 }
 
 // BF16 copies of the codebook (round to nearest even; kCopies stacked copies)
@@ -543,14 +796,17 @@ le_status encoder(EncodeTiled* fn)
     return LE_OK;
 }
 
-// 2-D BF16 tensor [rows, cols] row-major, box [box_rows, 64], 128-byte swizzle.
-le_status make_map(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows)
+// 2-D BF16 tensor [rows, cols] row-major (row stride `stride` elements, default
+// cols; cols = 0 means cols = stride), box [box_rows, 64], 128-byte swizzle.
+le_status make_map(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows, long long stride = 0)
 {
     EncodeTiled fn;
     le_status st = encoder(&fn);
     if (st != LE_OK) return st;
+    if (stride == 0) stride = cols;
+    if (cols == 0) cols = (int)stride;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint64_t strides[1] = {(cuuint64_t)stride * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kChunk, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
@@ -645,9 +901,9 @@ extern "C" le_status le_quantize(int64_t K, int32_t d, int32_t d_clip, const uin
     q.count = w.count;
     q.lcos = w.lcos;
     const uint32_t smem = quant_smem_bytes(n_cb);
-    LE_CUDA(cudaFuncSetAttribute(quant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LE_CUDA(cudaFuncSetAttribute(quant_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = q.ntiles < sms ? q.ntiles : sms;
-    quant_kernel<<<grid, kThreads, smem, s>>>(mf, ms, q);
+    quant_kernel<false><<<grid, kThreads, smem, s>>>(mf, ms, q);
     LE_LAUNCHED();
     quant_finalize_kernel<<<1, 128, 0, s>>>(w.psum, w.count, w.lcos, n_cb, K, lambda_cos, lambda_lb, r, p, loss);
     LE_LAUNCHED();
@@ -668,3 +924,108 @@ le_status quant_take_timeout(bool* timed_out)
     return LE_OK;
 }
 }  // namespace leg
+
+namespace leg {
+namespace {
+struct QuantGradWs {
+    QuantWs base;
+    __nv_bfloat16 *gtc, *gtd;
+    float *raw, *u;
+    long long kp;
+    size_t bytes;
+};
+
+QuantGradWs quant_grad_ws(void* p, long long K, int N, int d)
+{
+    QuantGradWs w;
+    w.base = quant_ws(p, N, d);
+    size_t off = w.base.bytes;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off += (b + 255) & ~size_t(255);
+        return reinterpret_cast<unsigned char*>(p) + o;
+    };
+    w.kp = (K + 7) / 8 * 8;
+    w.gtc = reinterpret_cast<__nv_bfloat16*>(take((size_t)N * w.kp * 2));
+    w.gtd = reinterpret_cast<__nv_bfloat16*>(take((size_t)N * w.kp * 2));
+    w.raw = reinterpret_cast<float*>(take((size_t)N * d * 4 + (size_t)2 * N * 4));
+    w.u = w.raw + (size_t)N * d;
+    w.bytes = off;
+    return w;
+}
+}  // namespace
+}  // namespace leg
+
+extern "C" le_status le_quantize_grad_workspace(int64_t K, int32_t n_cb, int32_t d, size_t* bytes)
+{
+    LE_CHECK_ARG(bytes != nullptr, "bytes is null");
+    LE_CHECK_ARG(K >= 1 && n_cb > 0 && d > 0, "bad sizes");
+    *bytes = quant_grad_ws(nullptr, K, n_cb, d).bytes;
+    return LE_OK;
+}
+
+extern "C" le_status le_quantize_grad(int64_t K, int32_t d, int32_t d_clip, const uint16_t* features, int32_t n_cb,
+                                      const float* codebook, const float* r, float lambda_d, float lambda_cos,
+                                      float lambda_lb, float* grad_codebook, void* workspace, size_t workspace_bytes,
+                                      void* stream)
+{
+    le_status st = check_quant(K, d, d_clip, n_cb);
+    if (st != LE_OK) return st;
+    if (d % 128 != 0 || d_clip % 128 != 0)
+        LE_FAIL(LE_ERR_UNSUPPORTED, "codebook gradient: d = %d and d_clip = %d must be multiples of 128", d, d_clip);
+    LE_CHECK_ARG(features && codebook && r && grad_codebook && workspace, "null pointer");
+    LE_CHECK_ARG(aligned16(features), "features must be 16-byte aligned");
+    LE_CHECK_ARG((reinterpret_cast<uintptr_t>(workspace) & 255u) == 0, "workspace must be 256-byte aligned");
+    const QuantGradWs w = quant_grad_ws(workspace, K, n_cb, d);
+    LE_CHECK_ARG(workspace_bytes >= w.bytes, "workspace has %zu bytes, needs %zu", workspace_bytes, w.bytes);
+    cudaStream_t s = as_stream(stream);
+    int dev = 0, sms = 0;
+    LE_CUDA(cudaGetDevice(&dev));
+    LE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUtensorMap mf, ms, mf64, mgc, mgd;
+    if ((st = make_map(&mf, features, K, d, kRows)) != LE_OK) return st;
+    if ((st = make_map(&ms, w.base.sb, (long long)kCopies * n_cb, d, n_cb)) != LE_OK) return st;
+    if ((st = make_map(&mf64, features, K, d, kChunk)) != LE_OK) return st;
+    if ((st = make_map(&mgc, w.gtc, n_cb, (int)K, 128, w.kp)) != LE_OK) return st;   // columns past K read as 0
+    if ((st = make_map(&mgd, w.gtd, n_cb, (int)K, 128, w.kp)) != LE_OK) return st;
+    LE_CUDA(cudaMemsetAsync(w.raw, 0, (size_t)n_cb * d * 4 + (size_t)2 * n_cb * 4, s));
+    codebook_prep_kernel<<<n_cb, 128, 0, s>>>(codebook, d, d_clip, w.base.sb, w.base.inv_s, n_cb);
+    LE_LAUNCHED();
+    QuantArgs q{};
+    q.K = K;
+    q.N = n_cb;
+    q.nchunks = d / kChunk;
+    q.nclip = d_clip / kChunk;
+    q.ntiles = (int)((K + kRows - 1) / kRows);
+    q.lambda_d = lambda_d;
+    q.inv_s = w.base.inv_s;
+    q.r = r;
+    q.gtc = w.gtc;
+    q.gtd = w.gtd;
+    q.kp = w.kp;
+    q.u = w.u;
+    q.cl = lambda_lb / (float)K;
+    q.cc = lambda_cos / (float)K;
+    const uint32_t smem = quant_smem_bytes(n_cb);
+    LE_CUDA(cudaFuncSetAttribute(quant_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = q.ntiles < sms ? q.ntiles : sms;
+    quant_kernel<true><<<grid, kThreads, smem, s>>>(mf, ms, q);
+    LE_LAUNCHED();
+    GemmArgs ga;
+    ga.N = n_cb;
+    ga.d = d;
+    ga.dclip_tiles = d_clip / 128;
+    ga.nch_total = (int)((K + kChunk - 1) / kChunk);
+    const int dtiles = d / 128;
+    const int splits = max(1, min(ga.nch_total, sms / dtiles));
+    ga.nch_split = (ga.nch_total + splits - 1) / splits;
+    ga.raw = w.raw;
+    const uint32_t gsmem = 1024 + kGStages * (kGATile + 2 * kGBBox) + (2 * kGStages + 2) * 8;
+    LE_CUDA(cudaFuncSetAttribute(quant_grad_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+    quant_grad_gemm_kernel<<<dim3(dtiles, splits), kGThreads, gsmem, s>>>(mgc, mgd, mf64, ga);
+    LE_LAUNCHED();
+    quant_grad_finalize_kernel<<<n_cb, 256, 0, s>>>(w.raw, w.u, w.base.sb, w.base.inv_s, n_cb, d, d_clip, lambda_d,
+                                                    grad_codebook);
+    LE_LAUNCHED();
+    return LE_OK;
+}
