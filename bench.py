@@ -342,12 +342,19 @@ def run_ours(args, rank, world):
     nc = (scene.sh_degree + 1) ** 2
     N = args.n
     TX, TY = (W + 15) // 16, (H + 15) // 16
-    n_vis = int((st.proj.tiles_touched > 0).sum().item())
-    # list entries any pixel reads: per tile, the largest n_contrib (last view)
-    ncb = torch.nn.functional.pad(st.img.n_contrib.float(), (0, (-W) % 16, 0, (-H) % 16))
-    K_read = int(torch.nn.functional.max_pool2d(ncb[None, None], 16).sum().item())
-    ids_last, ranges_last = st.bins.ids, st.bins.ranges
-    walked, contrib = pair_counts(st.img, ids_last, ranges_last, st.proj.splat, TX)
+    # per-view work counts (one more step on each view after the timing), each view weighted by
+    # how often the timed loop rendered it: visible Gaussians, list entries any pixel reads (per
+    # tile the largest n_contrib), and the (pixel, Gaussian) pairs of render_bwd_kernel (walked
+    # pairs exact, contributing fraction sampled)
+    per_view = {}
+    for k in range(N_VIEWS):
+        st.step(cams[k], rgb_dev[k], idx_dev[k])
+        ncb = torch.nn.functional.pad(st.img.n_contrib.float(), (0, (-W) % 16, 0, (-H) % 16))
+        per_view[k] = (int((st.proj.tiles_touched > 0).sum().item()),
+                       int(torch.nn.functional.max_pool2d(ncb[None, None], 16).sum().item()),
+                       *pair_counts(st.img, st.bins.ids, st.bins.ranges, st.proj.splat, TX, sample_tiles=96))
+    timed_views = [(args.warmup + i) % N_VIEWS for i in range(args.steps)]
+    n_vis, K_read, walked, contrib = (sum(per_view[k][c] for k in timed_views) / len(timed_views) for c in range(4))
     alg_bytes = stage_bytes(N, n_vis, K_mean, P, TX * TY, nc, st.layout.total, K_read)
     sm_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
@@ -358,10 +365,11 @@ def run_ours(args, rank, world):
     out["roofline"] = {"kernel": STAGE_CALLS["render_bwd"], "bound": "alu", "achieved": round(ach, 2),
                        "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
                        "traffic": stage_traffic("render_bwd"), "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 "
-                       f"x {sm_mhz:.0f} MHz", "algorithmic_flop": bwd_flop, "pairs_walked": walked,
-                       "pairs_contributing": contrib,
+                       f"x {sm_mhz:.0f} MHz", "algorithmic_flop": round(bwd_flop), "pairs_walked": round(walked),
+                       "pairs_contributing": round(contrib),
                        "note": f"{BWD_FLOP_WALKED} flop per walked pair + {BWD_FLOP_CONTRIB} per contributing "
-                               "pair (FMA = 2); traffic is DRAM bytes per launch from ncu"}
+                               "pair (FMA = 2), pairs averaged over the timed steps' views; traffic is DRAM "
+                               "bytes per launch from ncu"}
     t_pb = stage_ms["project_bwd_adam"] * 1e-3
     ach_h = alg_bytes["project_bwd_adam"] / t_pb / 1e9
     out["roofline_hbm"] = {"kernel": STAGE_CALLS["project_bwd_adam"], "bound": "hbm", "achieved": round(ach_h, 1),
@@ -377,8 +385,8 @@ def run_ours(args, rank, world):
                                   "algorithmic_flop": DEC_FLOP_PER_PX * P}
     out["stage_hbm_frac"] = {k: round(alg_bytes[k] / (stage_ms[k] * 1e-3) / 1e9 / hbm_peak, 4)
                              for k in stage_ms if k in alg_bytes}
-    out["visible_gaussians"] = n_vis
-    out["instances_read"] = K_read
+    out["visible_gaussians"] = round(n_vis)
+    out["instances_read"] = round(K_read)
 
     if not args.no_extras and rank == 0:
         out["fused_vs_plain"] = compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, args)

@@ -6,8 +6,9 @@
 // shared memory in batches of 256 splat records (80 B each, 16-byte loads);
 // every thread then reads the batch by broadcast.  The forward runs one pixel
 // per thread (pixels stop at different depths; pairing them costs more than it
-// saves), the backward two (rows y and y + 8), so each staged record read, each
-// loop step and each warp reduction serves two pixels.  The CTA stops fetching once every pixel's
+// saves), the backward four (rows y, y + 4, y + 8, y + 12; 64 threads per
+// tile), so each staged record read, each loop step and each warp reduction
+// serves four pixels.  The CTA stops fetching once every pixel's
 // transmittance has dropped below 1e-4 (__syncthreads_count ballot).
 //
 // The backward walks the same range back to front from each pixel's last
@@ -446,7 +447,7 @@ le_status render_backward_2d(const le_camera* cam, const le_gaussians* g, const 
 {
     const CamParams cp = cam_params(cam);
     LE_CUDA(cudaMemsetAsync(grad2d, 0, sizeof(float) * LE_SPLAT_STRIDE * (size_t)g->n, s));
-    render_bwd_kernel<2><<<cp.TX * cp.TY, kBlock / 2, 0, s>>>(cp, reinterpret_cast<const float4*>(pr->splat), sorted_ids,
+    render_bwd_kernel<4><<<cp.TX * cp.TY, kBlock / 4, 0, s>>>(cp, reinterpret_cast<const float4*>(pr->splat), sorted_ids,
                                                         reinterpret_cast<const uint2*>(tile_ranges), T_final,
                                                         n_contrib, dL_drgb, dL_dfeat, dL_dunc,
                                                         reinterpret_cast<float4*>(grad2d));

@@ -39,17 +39,20 @@ __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count)
 }
 
 // Bounded wait for the phase with the given parity to complete.  Gives up
-// after ~2^31 SM cycles (about a second) and returns false.
+// after ~2^31 SM cycles (about a second) and returns false.  The try_wait
+// carries a suspend-time hint, so the waiting thread sleeps in the barrier
+// until the phase completes instead of spinning on issue slots.
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity)
 {
     const uint32_t a = smem_u32(m);
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done)
-                     : "r"(a), "r"(parity)
-                     : "memory");
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity), "r"(0x989680u)
+            : "memory");
         if (done) return true;
         if (clock64() - t0 > (1ll << 31)) return false;
     }
