@@ -17,7 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["keypath.c", "sh.c", "project.c", "binning.c", "composite.c", "decoder.c", "query.c", "train.c",
-           "quant.c"]
+           "quant.c", "smooth.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 TILE = 16
 
@@ -349,4 +349,25 @@ def quantize(F_bf16, S, d_clip=512, lambda_d=0.5, lambda_cos=1.0, lambda_lb=0.5,
         out["D"] = D
     if want_grad:
         out["grad_S"] = G
+    return out
+
+
+SMOOTH_PARAMS = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
+
+
+def smooth(means, feat, unc, mlp, w_s=0.1, lam=1.0) -> dict:
+    """Adaptive spatial smoothing (Sec. 3.4, Eqs. eq:lem_fmlp, eq:lem_loss_mlp): s_MLP, L_smo and
+    its gradients (d_feat and every MLP parameter).  mlp: object or dict with W1 [128,3], b1,
+    W2 [128,128], b2, W3 [128,128], b3, W4 [8,128], b4."""
+    get = (lambda k: mlp[k]) if isinstance(mlp, dict) else (lambda k: getattr(mlp, k))
+    means, feat, unc = _f64(means), _f64(feat), _f64(unc)
+    n = means.shape[0]
+    P = [_f64(get(k)) for k in SMOOTH_PARAMS]
+    out = {"s_mlp": np.zeros((n, 8)), "loss": np.zeros(1), "d_feat": np.zeros((n, 8))}
+    for k, p in zip(SMOOTH_PARAMS, P):
+        out["d" + k] = np.zeros_like(p)
+    lib().orc_smooth(C.c_int(n), _p(means), _p(feat), _p(unc), *[_p(p) for p in P], C.c_double(w_s),
+                     C.c_double(lam), _p(out["s_mlp"]), _p(out["loss"]), _p(out["d_feat"]),
+                     *[_p(out["d" + k]) for k in SMOOTH_PARAMS])
+    out["loss"] = float(out["loss"][0])
     return out

@@ -16,6 +16,7 @@
  *   - L_CE with uncertainty weighting, L_u, L_s    Eqs. 10-12 (eq:lem_loss_ce1, _uncer, eq:lem_loss)
  *   - inference M_infer = softmax(D_MLP(R_s)), F = M_infer S, relevancy   supp. Sec. "Inference"
  *   - Adam with lr 1e-3, betas (0.9, 0.999)                          Sec. 4
+ *   - adaptive spatial smoothing: MLP(PE(p)), L_smo       Sec. 3.4 (eq:lem_fmlp, eq:lem_loss_mlp)
  *   - quantisation of language features: mixed cosine argmax, L_cos,
  *     load balancing L_lb, L_q           Sec. 3.3 (eq:q_dist .. eq:q_loss_cb), supp. Sec. 1
  *
@@ -115,5 +116,12 @@ double orc_bf16_value(uint16_t b);
 void orc_quantize(int K, int N, int d, int d_clip, const uint16_t* F_bf16, const double* S_in, int round_codebook,
                   double lambda_d, double lambda_cos, double lambda_lb, double* D_out, int32_t* m_out, double* r_out,
                   double* p_out, double* loss_out, double* grad_S);
+
+/* smooth.c */
+void orc_smooth(int n, const double* means, const double* feat, const double* unc, const double* W1,
+                const double* b1, const double* W2, const double* b2, const double* W3, const double* b3,
+                const double* W4, const double* b4, double w_s, double lambda, double* s_mlp, double* loss,
+                double* d_feat, double* dW1, double* db1, double* dW2, double* db2, double* dW3, double* db3,
+                double* dW4, double* db4);
 
 #endif

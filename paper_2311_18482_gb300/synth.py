@@ -293,3 +293,29 @@ def quant_inputs(seed: int, K: int, n_cb: int = 128, d_clip: int = 512, d_dino: 
     F = centres[lab] + rng.standard_normal((K, d)).astype(np.float32) * np.float32(noise / math.sqrt(d))
     S = F[rng.choice(K, n_cb, replace=K < n_cb)].astype(np.float32)
     return _bf16_bits(F), S
+
+
+@dataclass
+class SmoothMLP:
+    """MLP of the adaptive spatial smoothing (supp. Tab. pemlp): 3 -> 128 -> 128 -> 128 -> 8,
+    FP32 weights [out][in]."""
+    W1: np.ndarray
+    b1: np.ndarray
+    W2: np.ndarray
+    b2: np.ndarray
+    W3: np.ndarray
+    b3: np.ndarray
+    W4: np.ndarray
+    b4: np.ndarray
+
+
+def smooth_mlp_init(seed: int) -> SmoothMLP:
+    """Kaiming-uniform weights and small uniform biases (PyTorch's Linear default scheme)."""
+    rng = np.random.default_rng(seed)
+    dims = [(3, 128), (128, 128), (128, 128), (128, 8)]
+    ws = []
+    for fi, fo in dims:
+        bound = 1.0 / math.sqrt(fi)
+        ws.append(rng.uniform(-bound, bound, (fo, fi)).astype(np.float32))
+        ws.append(rng.uniform(-bound, bound, fo).astype(np.float32))
+    return SmoothMLP(*ws)

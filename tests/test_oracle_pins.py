@@ -693,3 +693,89 @@ def test_quant_codebook_gradient_fd(orc):
         assert np.array_equal(op["m"], o["m"]) and np.array_equal(om["m"], o["m"])
         fd = (op["loss"][0] - om["loss"][0]) / (2 * h)
         assert abs(fd - G[j, e]) <= 1e-6 * max(1.0, np.abs(G).max()), (j, e, fd, G[j, e])
+
+
+# ---------------------------------------------------------------------------
+# Adaptive spatial smoothing (Sec. 3.4, Eqs. eq:lem_fmlp, eq:lem_loss_mlp; supp. Tab. pemlp)
+
+def _smooth_case(n=6, seed=40):
+    from paper_2311_18482_gb300 import synth
+    rng = np.random.default_rng(seed)
+    mlp = synth.smooth_mlp_init(seed)
+    P = {k: getattr(mlp, k).astype(np.float64) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")}
+    means = rng.uniform(-1, 1, (n, 3))
+    feat = rng.standard_normal((n, 8))
+    unc = rng.uniform(0, 0.3, n)          # some below w_s = 0.1, some above
+    return P, means, feat, unc
+
+
+def _mlp_np(P, x):
+    h = np.maximum(x @ P["W1"].T + P["b1"], 0)
+    h = np.maximum(h @ P["W2"].T + P["b2"], 0)
+    h = np.maximum(h @ P["W3"].T + P["b3"], 0)
+    return h @ P["W4"].T + P["b4"]
+
+
+def test_smooth_forward_vs_numpy(orc):
+    P, means, feat, unc = _smooth_case(50)
+    o = orc.smooth(means, feat, unc, P, w_s=0.1, lam=0.7)
+    s = _mlp_np(P, means)
+    assert np.abs(o["s_mlp"] - s).max() < 1e-12
+    nrm = np.linalg.norm(s - feat, axis=1)
+    assert abs(o["loss"] - 0.7 * np.mean((1 + np.maximum(unc, 0.1)) * nrm)) < 1e-12
+
+
+def test_smooth_gradients_fd(orc):
+    """The stop-gradients split L_smo into T1 = |s_MLP(W) - s_G*| (MLP parameters) and
+    T2 = max(u*, w_s) |s_MLP* - s_G| (semantic features); each gradient is checked by
+    central differences of its own term."""
+    P, means, feat, unc = _smooth_case(6)
+    lam, ws = 0.9, 0.1
+    o = orc.smooth(means, feat, unc, P, w_s=ws, lam=lam)
+    wgt = np.maximum(unc, ws)
+
+    def t1(Q):
+        return lam * np.mean(np.linalg.norm(_mlp_np(Q, means) - feat, axis=1))
+
+    def t2(f):
+        return lam * np.mean(wgt * np.linalg.norm(o["s_mlp"] - f, axis=1))
+
+    assert abs(o["loss"] - (t1(P) + t2(feat))) < 1e-12
+    rng = np.random.default_rng(41)
+    h = 1e-6
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"):
+        for _ in range(6):
+            idx = tuple(int(rng.integers(s)) for s in P[k].shape)
+            Qp = {kk: v.copy() for kk, v in P.items()}
+            Qm = {kk: v.copy() for kk, v in P.items()}
+            Qp[k][idx] += h
+            Qm[k][idx] -= h
+            fd = (t1(Qp) - t1(Qm)) / (2 * h)
+            assert abs(fd - o["d" + k][idx]) <= 1e-6 * max(1.0, np.abs(o["d" + k]).max()), (k, idx)
+    for _ in range(10):
+        i, c = int(rng.integers(6)), int(rng.integers(8))
+        fp, fm = feat.copy(), feat.copy()
+        fp[i, c] += h
+        fm[i, c] -= h
+        fd = (t2(fp) - t2(fm)) / (2 * h)
+        assert abs(fd - o["d_feat"][i, c]) <= 1e-7
+
+
+def test_smooth_closed_forms(orc):
+    """W4 = 0: s_MLP = b4 for every Gaussian.  With s_G = b4 the loss and all gradients are 0
+    (zero-difference reading); with s_G = b4 - e_c the difference is a unit vector, so
+    L = lam mean(1 + max(u, w_s)), dL/db4 = lam e_c and dL/ds_G = -lam max(u, w_s) e_c / n."""
+    P, means, feat, unc = _smooth_case(7)
+    P["W4"][:] = 0.0
+    f0 = np.tile(P["b4"], (7, 1))
+    o = orc.smooth(means, f0, unc, P, w_s=0.1, lam=1.0)
+    assert o["loss"] == 0.0 and not np.any(o["d_feat"]) and not np.any(o["db4"]) and not np.any(o["dW1"])
+    f1 = f0.copy()
+    f1[:, 3] -= 1.0
+    o = orc.smooth(means, f1, unc, P, w_s=0.1, lam=2.0)
+    wgt = np.maximum(unc, 0.1)
+    assert abs(o["loss"] - 2.0 * np.mean(1 + wgt)) < 1e-12
+    e = np.zeros(8)
+    e[3] = 1.0
+    assert np.abs(o["db4"] - 2.0 * e).max() < 1e-12
+    assert np.abs(o["d_feat"] - (-2.0 / 7) * wgt[:, None] * e).max() < 1e-12
