@@ -391,6 +391,40 @@ le_status le_quantize_grad(int64_t K, int32_t d, int32_t d_clip, const uint16_t*
                            float* grad_codebook, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Adaptive spatial smoothing (Sec. 3.4, Eqs. eq:lem_fmlp, eq:lem_loss_mlp;
+ * supplementary Tab. pemlp): s_MLP = MLP(PE(p)) per Gaussian, PE of frequency
+ * 0 (the position itself), MLP 3 -> 128 -> 128 -> 128 -> 8 with ReLU after
+ * the first three layers.  FP32 device weights [out][in], biases [out]. */
+typedef struct le_smooth_mlp {
+    const float *W1, *b1;     /* [128,3], [128] */
+    const float *W2, *b2;     /* [128,128], [128] */
+    const float *W3, *b3;     /* [128,128], [128] */
+    const float *W4, *b4;     /* [8,128], [8] */
+} le_smooth_mlp;
+
+typedef struct le_smooth_mlp_grads {
+    float *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4;   /* same shapes; overwritten */
+} le_smooth_mlp_grads;
+
+/* le_smooth -- L_smo = lambda_smo mean_i (|s_MLP - s_G*| + max(u*, w_s) |s_MLP* - s_G|)
+ * (* = stop gradient; |.| the plain L2 norm, gradient 0 at a zero difference;
+ * the paper's w_s = 0.1, lambda_smo = 1) and its gradients:
+ *   loss [1] out (overwritten);
+ *   d_feat: dL/ds_G ADDED to d_feat[i * d_feat_stride + c] (c < 8), so that it
+ *     can accumulate into a dense [n,8] array (stride 8) or into the feature
+ *     slots of le_render_bwd_screen's grad2d records (grad2d + 10, stride 20)
+ *     before le_project_bwd_adam applies it;
+ *   dmlp: the MLP parameter gradients (overwritten);
+ *   s_mlp: [n,8] out, nullable.
+ * No gradient reaches the positions or u.  Tensor cores: BF16 operands
+ * (positions, weights, activations and dL/ds_MLP rounded to BF16), FP32
+ * accumulation; loss, norms and d_feat in FP32.
+ * Errors: LE_ERR_INVALID_ARG (null pointers, n < 0, d_feat_stride < 8). */
+le_status le_smooth(int32_t n, const float* means, const float* feat, const float* unc, const le_smooth_mlp* mlp,
+                    float w_s, float lambda_smo, float* loss, float* d_feat, int32_t d_feat_stride,
+                    const le_smooth_mlp_grads* dmlp, float* s_mlp, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Training helpers (Sec. 4).
  * le_rgb_l1: L = mean |img - target| over n values, loss[0] = L (device
  *   scalar, overwritten), grad = sign(img - target)/n (the 3DGS RGB loss's

@@ -60,6 +60,13 @@ class LeDecoder(C.Structure):
         (k, C.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
 
 
+_SMOOTH = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
+
+
+class LeSmoothMlp(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in _SMOOTH]
+
+
 class LeDecoderGrads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
 
@@ -99,6 +106,8 @@ _SIG = {
     "le_quantize_grad_workspace": [C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "le_quantize_grad": [C.c_int64, C.c_int32, C.c_int32, _P, C.c_int32, _P, _P, C.c_float, C.c_float, C.c_float,
                          _P, _P, C.c_size_t, _P],
+    "le_smooth": [C.c_int32, _P, _P, _P, C.POINTER(LeSmoothMlp), C.c_float, C.c_float, _P, _P, C.c_int32,
+                  C.POINTER(LeSmoothMlp), _P, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
     "le_selftest_bounded_wait": [_P],
@@ -555,6 +564,34 @@ def le_quantize_grad(features, codebook, r, d_clip=512, lambda_d=0.5, lambda_cos
     _check(load().le_quantize_grad(K, d, d_clip, _ptr(features), N, _ptr(codebook.contiguous()), _ptr(r), lambda_d,
                                    lambda_cos, lambda_lb, _ptr(out), _ptr(workspace), workspace.numel(), _stream()))
     return out
+
+
+def smooth_struct(params) -> LeSmoothMlp:
+    """params: sequence or dict of the 8 MLP tensors (W1, b1, ..., W4, b4), contiguous FP32."""
+    s = LeSmoothMlp()
+    vals = [params[k] for k in _SMOOTH] if isinstance(params, dict) else list(params)
+    for k, t in zip(_SMOOTH, vals):
+        setattr(s, k, t.data_ptr())
+    return s
+
+
+def le_smooth(means, feat, unc, mlp, w_s=0.1, lambda_smo=1.0, d_feat=None, d_feat_stride=8, grads=None,
+              want_s_mlp=False):
+    """Adaptive spatial smoothing (Sec. 3.4): returns (loss [1], d_feat, grads list, s_mlp or None).
+    d_feat is ADDED to (a zeroed [n, 8] array when not given)."""
+    n = means.shape[0]
+    dev = means.device
+    vals = [mlp[k] for k in _SMOOTH] if isinstance(mlp, dict) else list(mlp)
+    if d_feat is None:
+        d_feat = torch.zeros((n, 8), dtype=torch.float32, device=dev)
+    if grads is None:
+        grads = [torch.empty_like(v) for v in vals]
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    s_mlp = torch.empty((n, 8), dtype=torch.float32, device=dev) if want_s_mlp else None
+    ms, gs = smooth_struct(vals), smooth_struct(grads)
+    _check(load().le_smooth(n, _ptr(means), _ptr(feat), _ptr(unc), C.byref(ms), w_s, lambda_smo, _ptr(loss),
+                            _ptr(d_feat), d_feat_stride, C.byref(gs), _ptr(s_mlp), _stream()))
+    return loss, d_feat, grads, s_mlp
 
 
 def le_rgb_l1(img, target, loss, grad):

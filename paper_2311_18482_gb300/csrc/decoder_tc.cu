@@ -1150,6 +1150,7 @@ extern "C" le_status le_selftest_bounded_wait(void* stream)
 
 namespace leg {
 le_status quant_take_timeout(bool* timed_out);
+le_status smooth_take_timeout(bool* timed_out);
 }
 
 extern "C" le_status le_device_status(void* stream)
@@ -1160,8 +1161,12 @@ extern "C" le_status le_device_status(void* stream)
     bool quant_flag = false;
     const le_status qs = leg::quant_take_timeout(&quant_flag);
     if (qs != LE_OK) return qs;
-    if (quant_flag && !flag) {
-        leg::set_error("the quantisation kernel gave up on a bounded wait");
+    bool smooth_flag = false;
+    const le_status ss = leg::smooth_take_timeout(&smooth_flag);
+    if (ss != LE_OK) return ss;
+    if ((quant_flag || smooth_flag) && !flag) {
+        leg::set_error(quant_flag ? "the quantisation kernel gave up on a bounded wait"
+                                  : "the smoothing kernel gave up on a bounded wait");
         return LE_ERR_TIMEOUT;
     }
     if (flag) {
