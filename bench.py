@@ -41,8 +41,9 @@ def parse():
     ap.add_argument("--decoder", default="auto", choices=["auto", "fused", "unfused"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussian count (default: the workload's 1M)")
     ap.add_argument("--no-extras", action="store_true", help="skip the query / unfused comparison legs")
-    ap.add_argument("--only", choices=["quantize"], default=None,
-                    help="run one leg alone (quantize: the quantisation stage on --features rows)")
+    ap.add_argument("--only", choices=["quantize", "smooth"], default=None,
+                    help="run one leg alone (quantize: the quantisation stage on --features rows; smooth: "
+                         "the adaptive smoothing on --n Gaussians)")
     ap.add_argument("--features", type=int, default=W * H, help="feature rows for --only quantize")
     return ap.parse_args()
 
@@ -392,6 +393,7 @@ def run_ours(args, rank, world):
         out["fused_vs_plain"] = compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, args)
         out["query"] = query_leg(leg, synth, scene, cams, args)
         out["quantize"] = quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind)
+        out["smooth"] = smooth_leg(leg, synth, st, args, bf16_peak)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(scene, dec, cams[0], rgb_host[0].numpy(), idx_host[0].numpy(),
                                            budget_s=20.0)
@@ -477,6 +479,41 @@ def query_leg(leg, synth, scene, cams, args):
         except leg.LegError as e:
             res[name] = {"unavailable": str(e)[:200]}
     return res
+
+
+# forward (3-128-128-128-8), input gradients of layers 4, 3, 2, weight gradients of all four
+SMOOTH_FLOP_PER_GAUSSIAN = 2 * (3 * 128 + 2 * 128 * 128 + 128 * 8) + 2 * (8 * 128 + 2 * 128 * 128) \
+    + 2 * (3 * 128 + 2 * 128 * 128 + 8 * 128)
+
+
+def smooth_leg(leg, synth, st, args, bf16_peak):
+    """Adaptive spatial smoothing (Sec. 3.4) over the training state's Gaussians:
+    MLP(p) forward, L_smo and its backward, d_feat accumulated into grad2d's
+    feature slots as in a training step."""
+    import torch
+    mlp = synth.smooth_mlp_init(5)
+    params = {k: torch.from_numpy(getattr(mlp, k)).cuda() for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")}
+    g = st.g
+    grads = [torch.empty_like(v) for v in params.values()]
+    rec = st.grad2d[:, 10:]
+    try:
+        for _ in range(3):
+            leg.le_smooth(g.means, g.feat, g.unc, params, d_feat=rec, d_feat_stride=20, grads=grads)
+        torch.cuda.synchronize()
+        n = max(5, args.steps // 4)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(n):
+            loss, _, _, _ = leg.le_smooth(g.means, g.feat, g.unc, params, d_feat=rec, d_feat_stride=20, grads=grads)
+        t1.record()
+        torch.cuda.synchronize()
+    except leg.LegError as e:
+        return {"unavailable": str(e)[:200]}
+    ms = t0.elapsed_time(t1) / n
+    flop = SMOOTH_FLOP_PER_GAUSSIAN * g.n
+    return {"ms": round(ms, 4), "gaussians": g.n, "loss": round(float(loss.item()), 6),
+            "tensor": {"achieved_tflops": round(flop / ms / 1e9, 1), "peak": bf16_peak,
+                       "frac": round(flop / ms / 1e9 / bf16_peak, 4), "algorithmic_flop": flop}}
 
 
 def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):
@@ -638,7 +675,7 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if args.only == "quantize":
+    if args.only is not None:
         import torch
         import __graft_entry__
         __graft_entry__.build()
@@ -647,7 +684,13 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         leg.load()
         hbm, bf16, kind = measured_peaks()
-        print(json.dumps({"leg": "quantize", **quant_leg(leg, synth, args, hbm, bf16, kind)}), flush=True)
+        if args.only == "quantize":
+            res = quant_leg(leg, synth, args, hbm, bf16, kind)
+        else:
+            from paper_2311_18482_gb300.training import TrainState
+            c = synth.config("c5", n=args.n)
+            res = smooth_leg(leg, synth, TrainState(c["scene"], c["decoder"], W, H, "cuda"), args, bf16)
+        print(json.dumps({"leg": args.only, **res}), flush=True)
         return
     if world > 1 and args.impl == "ours":
         import torch

@@ -419,7 +419,8 @@ typedef struct le_smooth_mlp_grads {
  * No gradient reaches the positions or u.  Tensor cores: BF16 operands
  * (positions, weights, activations and dL/ds_MLP rounded to BF16), FP32
  * accumulation; loss, norms and d_feat in FP32.
- * Errors: LE_ERR_INVALID_ARG (null pointers, n < 0, d_feat_stride < 8). */
+ * Errors: LE_ERR_INVALID_ARG (null pointers, n < 0, d_feat_stride < 8, feat
+ * not 16-byte aligned). */
 le_status le_smooth(int32_t n, const float* means, const float* feat, const float* unc, const le_smooth_mlp* mlp,
                     float w_s, float lambda_smo, float* loss, float* d_feat, int32_t d_feat_stride,
                     const le_smooth_mlp_grads* dmlp, float* s_mlp, void* stream);

@@ -267,6 +267,20 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
         any = true;
         const int g = t * 128 + c.row;
         const bool valid = g < a.n;
+        // this row's s_G, u and current d_feat, loaded now so that the forward rounds hide their latency
+        float fg[kS], df[kS], ug = 0.f;
+        if (valid) {
+            const float4 f0 = reinterpret_cast<const float4*>(a.feat)[2 * (size_t)g];
+            const float4 f1 = reinterpret_cast<const float4*>(a.feat)[2 * (size_t)g + 1];
+            fg[0] = f0.x; fg[1] = f0.y; fg[2] = f0.z; fg[3] = f0.w;
+            fg[4] = f1.x; fg[5] = f1.y; fg[6] = f1.z; fg[7] = f1.w;
+            ug = a.unc[g];
+#pragma unroll
+            for (int k = 0; k < kS; ++k) df[k] = a.d_feat[(size_t)g * a.d_feat_stride + k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < kS; ++k) fg[k] = df[k] = 0.f;
+        }
         {   // X = [p, 1, 0...]
             float v[8] = {0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (valid) {
@@ -303,11 +317,11 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
             for (int k = 0; k < kS; ++k) {
                 const float s = z[k] + b4[k];
                 if (valid && a.s_mlp) a.s_mlp[(size_t)g * kS + k] = s;
-                diff[k] = valid ? s - a.feat[(size_t)g * kS + k] : 0.f;
+                diff[k] = valid ? s - fg[k] : 0.f;
                 nn = fmaf(diff[k], diff[k], nn);
             }
             nn = sqrtf(nn);
-            const float wgt = valid ? fmaxf(a.unc[g], a.w_s) : 0.f;
+            const float wgt = valid ? fmaxf(ug, a.w_s) : 0.f;
             lsum += (1.f + wgt) * nn;
             const float inv = nn > 0.f ? a.scale / nn : 0.f;
             float dz[16];
@@ -315,7 +329,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
             for (int k = 0; k < 16; ++k) dz[k] = k < kS ? diff[k] * inv : 0.f;
             if (valid)
 #pragma unroll
-                for (int k = 0; k < kS; ++k) a.d_feat[(size_t)g * a.d_feat_stride + k] -= wgt * dz[k];
+                for (int k = 0; k < kS; ++k) a.d_feat[(size_t)g * a.d_feat_stride + k] = df[k] - wgt * dz[k];
             sbuf_store8(SBuf{c.sm + kODZ, 16}, c.row, 0, dz);
             sbuf_store8(SBuf{c.sm + kODZ, 16}, c.row, 8, dz + 8);
             db4acc += colsum16(dz, lane);       // lanes 2k, 2k+1: column k (k < 8)
@@ -409,6 +423,7 @@ extern "C" le_status le_smooth(int32_t n, const float* means, const float* feat,
                  "null MLP gradient");
     LE_CHECK_ARG(n == 0 || (means && feat && unc && d_feat), "null per-Gaussian pointer");
     LE_CHECK_ARG(d_feat_stride >= 8, "d_feat_stride = %d < 8", d_feat_stride);
+    LE_CHECK_ARG(n == 0 || aligned16(feat), "feat must be 16-byte aligned");
     cudaStream_t s = as_stream(stream);
     LE_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), s));
     float* const gz[8] = {dmlp->W1, dmlp->b1, dmlp->W2, dmlp->b2, dmlp->W3, dmlp->b3, dmlp->W4, dmlp->b4};
