@@ -478,6 +478,26 @@ def query_leg(leg, synth, scene, cams, args):
             res[name] = {"ms_per_query_render": round(t0.elapsed_time(t1) / n, 4)}
         except leg.LegError as e:
             res[name] = {"unavailable": str(e)[:200]}
+    # the materialised language feature map F = M_infer S (BF16, [P, 896]) of the last render
+    try:
+        Fm = torch.empty((P, qin.codebook.shape[1]), dtype=torch.bfloat16, device=dev)
+        for _ in range(3):
+            leg.le_feature_map(img.feat.view(8, P), dec_t, cb, out=Fm)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = max(5, args.steps // 4)
+        t0.record()
+        for _ in range(n):
+            leg.le_feature_map(img.feat.view(8, P), dec_t, cb, out=Fm)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / n
+        byts = P * qin.codebook.shape[1] * 2 + P * 8 * 4
+        hbm, _, kind = measured_peaks()
+        res["feature_map"] = {"ms": round(ms, 4), "bytes": byts, "hbm_frac": round(byts / ms / 1e6 / hbm, 4),
+                              "peak_kind": kind, "note": "le_feature_map: decode + softmax + F = p S, BF16 out"}
+    except leg.LegError as e:
+        res["feature_map"] = {"unavailable": str(e)[:200]}
     return res
 
 

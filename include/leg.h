@@ -342,6 +342,21 @@ le_status le_query(int32_t mode, int32_t P, const float* feat, const le_decoder*
                    void* stream);
 
 /* ---------------------------------------------------------------------------
+ * le_feature_map -- the language feature map F = M_infer S (supp. Sec.
+ * "Inference": M_infer = softmax(D_MLP(R_s)), S the [n_cb, d] codebook),
+ * materialised for consumers other than the relevancy query.
+ *   feat [8,P] = R_s; dec: the decoder (fused-path sizes, see le_decode);
+ *   codebook [n_cb, d] FP32; out [P, d] BF16 (bit patterns), pixel-major,
+ *   16-byte aligned; workspace: le_feature_map_workspace(n_cb, d) bytes.
+ * One tcgen05 kernel: decode, softmax (stored in BF16, normalised in FP32 at
+ * the output), F = p S with FP32 accumulation, BF16 out.
+ * Errors: LE_ERR_INVALID_ARG; LE_ERR_UNSUPPORTED unless d is a multiple of
+ * 64 and the decoder has the fused path's sizes. */
+le_status le_feature_map_workspace(int32_t n_cb, int32_t d, size_t* bytes);
+le_status le_feature_map(int32_t P, const float* feat, const le_decoder* dec, const float* codebook, int32_t d,
+                         uint16_t* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * le_quantize -- quantisation of K language features against an N-entry
  * codebook (Sec. 3.3, Eqs. eq:quant, eq:q_dist, eq:q_loss_cos, eq:q_loss_lb,
  * eq:q_loss_cb; supplementary "Load Balancing Loss"):

@@ -286,6 +286,16 @@ def query(prob, qin):
     return rel
 
 
+def feature_map(prob, codebook):
+    """F = M_infer S (supp. Sec. "Inference"): prob [N, P] -> F [P, d] in FP64."""
+    prob = _f64(prob)
+    ncb, P = prob.shape
+    cb = _f32(codebook)
+    F = np.zeros((P, cb.shape[1]))
+    lib().orc_feature_map(C.c_int(P), C.c_int(ncb), _p(prob), _p(cb), C.c_int(cb.shape[1]), _p(F))
+    return F
+
+
 def l1(img, target):
     img = _f64(img)
     target = _f32(target)

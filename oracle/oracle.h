@@ -109,6 +109,9 @@ double orc_l1(int64_t n, const double* img, const float* target, double* grad);
 void orc_adam(int64_t n, double* param, const double* grad, double* m, double* v, int step,
               double lr, double b1, double b2, double eps);
 
+/* query.c: the feature map */
+void orc_feature_map(int P, int ncb, const double* prob, const float* codebook, int d, double* F);
+
 /* quant.c */
 uint16_t orc_bf16_bits(float x);
 void orc_bf16_bits_array(int64_t n, const float* x, uint16_t* out);

@@ -46,3 +46,18 @@ void orc_query(int P, int ncb, const double* prob, const float* codebook, int d,
         free(F);
     }
 }
+
+/* The language feature map itself, F[p] = sum_i prob[i][p] S_i (supp. Sec.
+ * "Inference": F = M_infer S), FP64: F [P][d]. */
+void orc_feature_map(int P, int ncb, const double* prob, const float* codebook, int d, double* F)
+{
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < P; ++p) {
+        double* f = F + (size_t)p * d;
+        for (int e = 0; e < d; ++e) f[e] = 0.0;
+        for (int i = 0; i < ncb; ++i) {
+            const double w = prob[(size_t)i * P + p];
+            for (int e = 0; e < d; ++e) f[e] += w * codebook[(size_t)i * d + e];
+        }
+    }
+}

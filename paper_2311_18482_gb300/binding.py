@@ -108,6 +108,8 @@ _SIG = {
                          _P, _P, C.c_size_t, _P],
     "le_smooth": [C.c_int32, _P, _P, _P, C.POINTER(LeSmoothMlp), C.c_float, C.c_float, _P, _P, C.c_int32,
                   C.POINTER(LeSmoothMlp), _P, _P],
+    "le_feature_map_workspace": [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
+    "le_feature_map": [C.c_int32, _P, C.POINTER(LeDecoder), _P, C.c_int32, _P, _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
     "le_selftest_bounded_wait": [_P],
@@ -592,6 +594,23 @@ def le_smooth(means, feat, unc, mlp, w_s=0.1, lambda_smo=1.0, d_feat=None, d_fea
     _check(load().le_smooth(n, _ptr(means), _ptr(feat), _ptr(unc), C.byref(ms), w_s, lambda_smo, _ptr(loss),
                             _ptr(d_feat), d_feat_stride, C.byref(gs), _ptr(s_mlp), _stream()))
     return loss, d_feat, grads, s_mlp
+
+
+def le_feature_map(feat, dec_t, codebook, out=None, workspace=None):
+    """F = softmax(D_MLP(feat)) S (supp. Sec. "Inference"): feat [8, P], dec_t the six decoder tensors,
+    codebook [N, d] float32.  Returns F [P, d] as torch.bfloat16."""
+    P = feat.shape[1]
+    N, d = codebook.shape
+    dev = feat.device
+    out = out if out is not None else torch.empty((P, d), dtype=torch.bfloat16, device=dev)
+    dec = decoder_struct(*dec_t)
+    if workspace is None:
+        n = C.c_size_t()
+        _check(load().le_feature_map_workspace(N, d, C.byref(n)))
+        workspace = torch.empty(n.value, dtype=torch.uint8, device=dev)
+    _check(load().le_feature_map(P, _ptr(feat.contiguous()), C.byref(dec), _ptr(codebook.contiguous()), d, _ptr(out),
+                                 _ptr(workspace), workspace.numel(), _stream()))
+    return out
 
 
 def le_rgb_l1(img, target, loss, grad):

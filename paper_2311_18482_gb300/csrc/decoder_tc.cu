@@ -58,6 +58,9 @@ struct DecArgs {
     const float* Aq;                // [16, ncb] fp32 = [text; negs] S_c^T
     int Q, n_neg;
     float* rel;
+    // feature-map export
+    int dd;                         // feature dims d (multiple of 64)
+    __nv_bfloat16* fmap;            // [P, dd] out
 };
 
 // Per-warpgroup state of the shared MLP front end.  With nhalf = 2 or 4,
@@ -979,6 +982,180 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
     if (tid < 32) tmem_dealloc(tbase, 512);
 }
 
+// ---------------------------------------------------------------------------
+// Language feature map export F = M_infer S (supp. Sec. "Inference"): per
+// pixel the decoder's softmax p over the n_cb codes times the codebook, in
+// BF16.  Four warpgroups serve the same 128 rows as in the query kernel; e =
+// exp(z - max z) is stored in BF16 and each output row is scaled by 1/sum e.
+// The codebook streams through shared memory in 64-dim chunks ([n_cb x 64]
+// canonical images, two slots, 1-D bulk copies); per chunk one MMA (M = 128
+// pixels, N = 64 dims, K = n_cb) reads the chunk MN-major into one of two
+// 64-column TMEM accumulators, and each warpgroup writes 16 of its columns.
+constexpr uint32_t kTF = 256;      // TMEM columns of the two chunk accumulators
+
+__host__ constexpr size_t export_smem(int ncb)
+{
+    return weights_bytes(ncb) + (sbuf_bytes(128, ncb) > kFwdWgBytes ? sbuf_bytes(128, ncb) : kFwdWgBytes) +
+           2 * sbuf_bytes(ncb, 64) + kQueryParts * 128 * 4 + 128;
+}
+
+__global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    Front f;
+    unsigned char* p = load_weights(sm, a, f);
+    f.X1 = SBuf{p, 16};
+    f.H1 = SBuf{p + sbuf_bytes(128, 16), 64};
+    f.H2 = SBuf{p + sbuf_bytes(128, 16) + sbuf_bytes(128, 64), 128};
+    const SBuf Ps{p, a.ncb};
+    f.xch = reinterpret_cast<float4*>(p);
+    p += sbuf_bytes(128, a.ncb) > kFwdWgBytes ? sbuf_bytes(128, a.ncb) : kFwdWgBytes;
+    const uint32_t chunk_bytes = sbuf_bytes(a.ncb, 64);
+    const SBuf Gs[2] = {SBuf{p, 64}, SBuf{p + chunk_bytes, 64}};
+    p += 2 * chunk_bytes;
+    float* sums = reinterpret_cast<float*>(p);          // [parts][128] partial sums of e
+    p += kQueryParts * 128 * 4;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);     // [0] MMA, [1], [2] codebook slots
+    uint32_t* slot = reinterpret_cast<uint32_t*>(p + 24);
+    const int tid = threadIdx.x;
+    f.mbar = mbar;
+    f.phase = 0;
+    f.tid = tid & 127;
+    f.bar_id = 0;
+    f.nthreads = blockDim.x;
+    f.half = tid >> 7;
+    f.nhalf = kQueryParts;
+    if (tid == 0)
+        for (int i = 0; i < 3; ++i) mbar_init(mbar + i, 1);
+    if (tid < 32) tmem_alloc(slot, 512);
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(slot);
+    f.tw = tbase;
+    f.lane = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+    const int row = f.tid;
+    int c0, c1;
+    my_cols(f, a.ncb, c0, c1);
+    const int nch = a.dd / 64;
+    uint32_t gphase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    auto load_chunk = [&](int kc, int s) {
+        mbar_expect_tx(mbar + 1 + s, chunk_bytes);
+        bulk_g2s(Gs[s].p, a.G_img + (size_t)kc * chunk_bytes, chunk_bytes, mbar + 1 + s);
+        pending[s] = true;
+    };
+    const int ntiles = (a.P + 127) / 128;
+    bool ok = true;
+    if (tid == 0 && blockIdx.x < ntiles)
+        for (int s = 0; s < 2 && s < nch; ++s) load_chunk(s, s);
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int px = tile * 128 + row;
+        const bool valid = px < a.P;
+        if (!mlp_forward(f, a, px, valid)) break;
+        float v[16], mh = -INFINITY;
+        for (int c = c0; c < c1; c += 16) {
+            tmem_ld16(f.tw + f.lane + c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) mh = fmaxf(mh, v[j] + f.b3s[c + j]);
+        }
+        f.xch[f.half * 128 + row].x = mh;
+        wg_sync(f);
+        float m = -INFINITY;
+#pragma unroll
+        for (int h = 0; h < kQueryParts; ++h) m = fmaxf(m, f.xch[h * 128 + row].x);
+        wg_sync(f);
+        const float ml = m * 1.4426950408889634f;
+        float se = 0.f;
+        for (int c = c0; c < c1; c += 16) {
+            tmem_ld16(f.tw + f.lane + c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                v[j] = ex2_approx(fmaf(v[j] + f.b3s[c + j], 1.4426950408889634f, -ml));
+                se += v[j];
+            }
+            sbuf_store8(Ps, row, c, v);
+            sbuf_store8(Ps, row, c + 8, v + 8);
+        }
+        sums[f.half * 128 + row] = se;
+        wg_publish(f);
+        float tot = 0.f;
+#pragma unroll
+        for (int h = 0; h < kQueryParts; ++h) tot += sums[h * 128 + row];
+        const float inv = 1.0f / tot;
+        bool tmo = false;
+        for (int kc0 = 0; kc0 < nch; kc0 += 2) {
+            if (tid == 0) {
+                for (int s = 0; s < 2 && kc0 + s < nch; ++s) {
+                    if (!mbar_wait(mbar + 1 + s, gphase[s])) tmo = true;
+                    gphase[s] ^= 1u;
+                    pending[s] = false;
+                    const uint64_t gm = mndesc(Gs[s], 0, 0);
+                    for (int k = 0; k < a.ncb / 16; ++k)
+                        mma(tbase + kTF + 64 * s, kdesc(Ps, 0, 16 * k), gm + 128 * k, idesc_bf16(64, false, true),
+                            k > 0);
+                }
+                commit(f.mbar);
+            }
+            if (!wg_wait(f) || bar_any(0, blockDim.x, tmo)) {
+                if (tid == 0) atomicExch(&g_tc_error, 1);
+                ok = false;
+                break;
+            }
+            // refill the slots: the next chunk pair of this tile, or the first pair of the next tile
+            if (tid == 0) {
+                const bool more = kc0 + 2 < nch;
+                const bool next_tile = tile + (int)gridDim.x < ntiles;
+                for (int s = 0; s < 2; ++s) {
+                    const int kc = more ? kc0 + 2 + s : s;
+                    if ((more && kc < nch) || (!more && next_tile && kc < nch)) load_chunk(kc, s);
+                }
+            }
+            // this warpgroup's 16 columns of each chunk, scaled by 1 / sum e, as BF16
+            for (int s = 0; s < 2 && kc0 + s < nch; ++s) {
+                tmem_ld16(tbase + kTF + 64 * s + 16 * f.half + f.lane, v);
+                if (valid) {
+                    __nv_bfloat162 h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j] * inv, v[2 * j + 1] * inv);
+                    uint4* dst = reinterpret_cast<uint4*>(a.fmap + (size_t)px * a.dd + 64 * (kc0 + s) + 16 * f.half);
+                    dst[0] = *reinterpret_cast<uint4*>(h);
+                    dst[1] = *reinterpret_cast<uint4*>(h + 4);
+                }
+            }
+            fence_before();
+            __syncthreads();
+            fence_after();
+        }
+    }
+    // drain copies still in flight (only after an early exit) before the shared memory goes away
+    if (tid == 0)
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) mbar_wait(mbar + 1 + s, gphase[s]);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid < 32) tmem_dealloc(tbase, 512);
+}
+
+// Codebook S [ncb x dd] (fp32) -> chunked canonical bf16 image: chunk kc holds
+// dims [64 kc, 64 kc + 64) of every code, as an [ncb x 64] canonical buffer.
+__global__ void codebook_chunks_kernel(const float* __restrict__ S, int ncb, int dd, unsigned char* __restrict__ img)
+{
+    const int n8 = ncb * (dd / 8);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += gridDim.x * blockDim.x) {
+        const int r = i / (dd / 8), c0 = (i % (dd / 8)) * 8;
+        const int kc = c0 / 64, cc = c0 % 64;
+        __nv_bfloat162 h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            h[j] = __floats2bfloat162_rn(S[(size_t)r * dd + c0 + 2 * j], S[(size_t)r * dd + c0 + 2 * j + 1]);
+        unsigned char* dst = img + (size_t)kc * ncb * 64 * 2 + ((r >> 3) * 8 * 128 + (cc >> 3) * 128 + (r & 7) * 16);
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(h);
+    }
+}
+
 // G = S_c S_c^T (fp32) -> chunked canonical bf16 image: chunk kc holds columns
 // [64 kc, 64 kc + 64) of every row, as an [ncb x 64] canonical buffer.
 __global__ void gram_layout_kernel(const float* __restrict__ G, int ncb, unsigned char* __restrict__ img)
@@ -1139,7 +1316,58 @@ le_status query_fused(int32_t P, const float* feat, const le_decoder* d, const f
     return LE_OK;
 }
 
+le_status export_fused(int32_t P, const float* feat, const le_decoder* d, const float* codebook, int32_t dd,
+                       __nv_bfloat16* out, void* ws, cudaStream_t s)
+{
+    le_status st = check_fused_decoder(d, false);
+    if (st != LE_OK) return st;
+    const int ncb = d->n_cb;
+    unsigned char* img = static_cast<unsigned char*>(ws);
+    codebook_chunks_kernel<<<64, 256, 0, s>>>(codebook, ncb, dd, img);
+    LE_LAUNCHED();
+    DecArgs a{};
+    a.P = P;
+    a.ncb = ncb;
+    a.feat = feat;
+    a.W1 = d->W1; a.b1 = d->b1; a.W2 = d->W2; a.b2 = d->b2; a.W3 = d->W3; a.b3 = d->b3;
+    a.G_img = img;
+    a.dd = dd;
+    a.fmap = out;
+    const size_t smem = export_smem(ncb);
+    if ((st = set_smem(export_fused_kernel, smem)) != LE_OK) return st;
+    const int ntiles = (P + 127) / 128;
+    const int grid = ntiles < sm_count() ? ntiles : sm_count();
+    export_fused_kernel<<<grid, 128 * kQueryParts, smem, s>>>(a);
+    LE_LAUNCHED();
+    return LE_OK;
+}
+
 }  // namespace leg
+
+extern "C" le_status le_feature_map_workspace(int32_t n_cb, int32_t d, size_t* bytes)
+{
+    LE_CHECK_ARG(bytes != nullptr, "bytes is null");
+    LE_CHECK_ARG(n_cb > 0 && d > 0, "bad sizes");
+    *bytes = (size_t)n_cb * d * 2;
+    return LE_OK;
+}
+
+extern "C" le_status le_feature_map(int32_t P, const float* feat, const le_decoder* dec, const float* codebook,
+                                    int32_t d, uint16_t* out, void* workspace, size_t workspace_bytes, void* stream)
+{
+    LE_CHECK_ARG(P >= 0, "P = %d < 0", P);
+    LE_CHECK_ARG(dec != nullptr && codebook && out && workspace, "null pointer");
+    LE_CHECK_ARG(P == 0 || feat != nullptr, "null feat");
+    LE_CHECK_ARG(leg::aligned16(out) && leg::aligned16(workspace), "out and workspace must be 16-byte aligned");
+    if (d <= 0 || d % 64 != 0) {
+        leg::set_error("feature map export needs d to be a positive multiple of 64 (got %d)", d);
+        return LE_ERR_UNSUPPORTED;
+    }
+    LE_CHECK_ARG(workspace_bytes >= (size_t)dec->n_cb * d * 2, "workspace too small");
+    if (P == 0) return LE_OK;
+    return leg::export_fused(P, feat, dec, codebook, d, reinterpret_cast<__nv_bfloat16*>(out), workspace,
+                             leg::as_stream(stream));
+}
 
 extern "C" le_status le_selftest_bounded_wait(void* stream)
 {

@@ -779,3 +779,17 @@ def test_smooth_closed_forms(orc):
     e[3] = 1.0
     assert np.abs(o["db4"] - 2.0 * e).max() < 1e-12
     assert np.abs(o["d_feat"] - (-2.0 / 7) * wgt[:, None] * e).max() < 1e-12
+
+
+def test_feature_map_pins(orc):
+    """F = M_infer S (supp. "Inference"): a one-hot distribution returns its code exactly; a
+    general one equals the library matrix product."""
+    rng = np.random.default_rng(50)
+    N, P, d = 32, 40, 896
+    S = rng.standard_normal((N, d)).astype(np.float32)
+    onehot = np.zeros((N, P))
+    m = rng.integers(0, N, P)
+    onehot[m, np.arange(P)] = 1.0
+    assert np.array_equal(orc.feature_map(onehot, S), S[m].astype(np.float64))
+    prob = rng.dirichlet(np.ones(N), P).T
+    assert np.abs(orc.feature_map(prob, S) - prob.T @ S.astype(np.float64)).max() < 1e-12
