@@ -17,7 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["keypath.c", "sh.c", "project.c", "binning.c", "composite.c", "decoder.c", "query.c", "train.c",
-           "quant.c", "smooth.c"]
+           "quant.c", "smooth.c", "ssim.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 TILE = 16
 
@@ -294,6 +294,19 @@ def feature_map(prob, codebook):
     F = np.zeros((P, cb.shape[1]))
     lib().orc_feature_map(C.c_int(P), C.c_int(ncb), _p(prob), _p(cb), C.c_int(cb.shape[1]), _p(F))
     return F
+
+
+def rgb_loss(img, target, lam=0.2, want_grad=True, want_map=False) -> dict:
+    """RGB loss (1 - lam) L1 + lam (1 - SSIM) on [3, H, W] images (3DGS's loss, kept by Sec. 4):
+    loss = (L, L1, SSIM), grad = dL/dimg, smap = the SSIM map."""
+    img, target = _f64(img), _f64(target)
+    _, H, W = img.shape
+    out = {"loss": np.zeros(3)}
+    out["grad"] = np.zeros_like(img) if want_grad else None
+    out["smap"] = np.zeros_like(img) if want_map else None
+    lib().orc_rgb_loss(C.c_int(W), C.c_int(H), _p(img), _p(target), C.c_double(lam), _p(out["loss"]),
+                       _p(out["grad"]) if want_grad else None, _p(out["smap"]) if want_map else None)
+    return out
 
 
 def l1(img, target):

@@ -16,6 +16,7 @@
  *   - L_CE with uncertainty weighting, L_u, L_s    Eqs. 10-12 (eq:lem_loss_ce1, _uncer, eq:lem_loss)
  *   - inference M_infer = softmax(D_MLP(R_s)), F = M_infer S, relevancy   supp. Sec. "Inference"
  *   - Adam with lr 1e-3, betas (0.9, 0.999)                          Sec. 4
+ *   - RGB loss (1 - lambda) L1 + lambda D-SSIM (3DGS's, kept by Sec. 4)
  *   - adaptive spatial smoothing: MLP(PE(p)), L_smo       Sec. 3.4 (eq:lem_fmlp, eq:lem_loss_mlp)
  *   - quantisation of language features: mixed cosine argmax, L_cos,
  *     load balancing L_lb, L_q           Sec. 3.3 (eq:q_dist .. eq:q_loss_cb), supp. Sec. 1
@@ -111,6 +112,10 @@ void orc_adam(int64_t n, double* param, const double* grad, double* m, double* v
 
 /* query.c: the feature map */
 void orc_feature_map(int P, int ncb, const double* prob, const float* codebook, int d, double* F);
+
+/* ssim.c */
+void orc_rgb_loss(int W, int H, const double* img, const double* target, double lambda, double* loss, double* grad,
+                  double* smap);
 
 /* quant.c */
 uint16_t orc_bf16_bits(float x);

@@ -793,3 +793,58 @@ def test_feature_map_pins(orc):
     assert np.array_equal(orc.feature_map(onehot, S), S[m].astype(np.float64))
     prob = rng.dirichlet(np.ones(N), P).T
     assert np.abs(orc.feature_map(prob, S) - prob.T @ S.astype(np.float64)).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# RGB loss with D-SSIM (3DGS's loss, kept by Sec. 4)
+
+def _window11():
+    g = np.exp(-np.arange(-5, 6) ** 2 / (2 * 1.5 ** 2))
+    return np.outer(g, g) / g.sum() ** 2
+
+
+def test_ssim_map_vs_library_filter(orc):
+    """The SSIM map from scipy's correlate with the same window and zero padding."""
+    from scipy.ndimage import correlate
+    rng = np.random.default_rng(60)
+    x, y = rng.uniform(0, 1, (3, 23, 31)), rng.uniform(0, 1, (3, 23, 31))
+    o = orc.rgb_loss(x, y, want_map=True)
+    w = _window11()
+    f = lambda a: correlate(a, w, mode="constant", cval=0.0)
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    for c in range(3):
+        mx, my = f(x[c]), f(y[c])
+        vx, vy, cxy = f(x[c] ** 2) - mx ** 2, f(y[c] ** 2) - my ** 2, f(x[c] * y[c]) - mx * my
+        S = (2 * mx * my + C1) * (2 * cxy + C2) / ((mx ** 2 + my ** 2 + C1) * (vx + vy + C2))
+        assert np.abs(o["smap"][c] - S).max() < 1e-12
+    assert abs(o["loss"][2] - o["smap"].mean()) < 1e-14
+    assert abs(o["loss"][1] - np.abs(x - y).mean()) < 1e-14
+    assert abs(o["loss"][0] - (0.8 * o["loss"][1] + 0.2 * (1 - o["loss"][2]))) < 1e-14
+
+
+def test_ssim_closed_forms(orc):
+    """SSIM(x, x) = 1 everywhere (L = 0, gradient 0); constant images a, b away from the border:
+    S = (2ab + C1)/(a^2 + b^2 + C1)."""
+    rng = np.random.default_rng(61)
+    x = rng.uniform(0, 1, (3, 20, 24))
+    o = orc.rgb_loss(x, x, want_map=True)
+    assert np.abs(o["smap"] - 1).max() < 1e-12 and abs(o["loss"][0]) < 1e-12
+    assert np.abs(o["grad"]).max() < 1e-12
+    a, b = 0.3, 0.7
+    o = orc.rgb_loss(np.full((3, 30, 30), a), np.full((3, 30, 30), b), want_map=True)
+    C1 = 0.01 ** 2
+    assert np.abs(o["smap"][:, 5:-5, 5:-5] - (2 * a * b + C1) / (a * a + b * b + C1)).max() < 1e-12
+
+
+def test_ssim_gradient_fd(orc):
+    rng = np.random.default_rng(62)
+    x, y = rng.uniform(0, 1, (3, 14, 17)), rng.uniform(0, 1, (3, 14, 17))
+    o = orc.rgb_loss(x, y, lam=0.2)
+    h = 1e-6
+    for _ in range(25):
+        c, i, j = int(rng.integers(3)), int(rng.integers(14)), int(rng.integers(17))
+        xp, xm = x.copy(), x.copy()
+        xp[c, i, j] += h
+        xm[c, i, j] -= h
+        fd = (orc.rgb_loss(xp, y, want_grad=False)["loss"][0] - orc.rgb_loss(xm, y, want_grad=False)["loss"][0]) / (2 * h)
+        assert abs(fd - o["grad"][c, i, j]) <= 1e-8 + 1e-6 * abs(fd), (c, i, j, fd, o["grad"][c, i, j])
