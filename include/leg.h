@@ -449,6 +449,19 @@ le_status le_smooth(int32_t n, const float* means, const float* feat, const floa
  *   0.999) in the paper; eps is a reading), step >= 1, then clamp to
  *   [clamp_lo, clamp_hi] (pass -inf/+inf for none; u uses [0,1], Sec. 3.4.2). */
 le_status le_rgb_l1(int64_t n, const float* img, const float* target, float* loss, float* grad, void* stream);
+
+/* le_rgb_loss -- the full RGB loss of 3D Gaussian Splatting, which Sec. 4
+ * keeps ("the same RGB loss"; reading, the paper does not restate it):
+ *   L = (1 - lambda_ssim) L1 + lambda_ssim (1 - SSIM)   (3DGS: lambda_ssim = 0.2)
+ * SSIM per channel with an 11 x 11 Gaussian window (sigma 1.5), zero padding
+ * outside the image, C1 = 0.01^2, C2 = 0.03^2, mean over pixels and channels.
+ *   img, target [3,H,W]; loss [3] out = (L, L1, SSIM); grad [3,H,W] out = dL/dimg;
+ *   workspace: le_rgb_loss_workspace(W, H) bytes (the three per-pixel SSIM
+ *   partial-derivative maps of every channel).
+ * Errors: LE_ERR_INVALID_ARG (null pointers, bad size, lambda outside [0,1]). */
+le_status le_rgb_loss_workspace(int32_t W, int32_t H, size_t* bytes);
+le_status le_rgb_loss(int32_t W, int32_t H, const float* img, const float* target, float lambda_ssim, float* loss,
+                      float* grad, void* workspace, size_t workspace_bytes, void* stream);
 le_status le_adam(int64_t n, float* param, const float* grad, float* m, float* v, int32_t step, float lr,
                   float beta1, float beta2, float eps, float clamp_lo, float clamp_hi, void* stream);
 

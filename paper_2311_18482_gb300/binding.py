@@ -110,6 +110,8 @@ _SIG = {
                   C.POINTER(LeSmoothMlp), _P, _P],
     "le_feature_map_workspace": [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "le_feature_map": [C.c_int32, _P, C.POINTER(LeDecoder), _P, C.c_int32, _P, _P, C.c_size_t, _P],
+    "le_rgb_loss_workspace": [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
+    "le_rgb_loss": [C.c_int32, C.c_int32, _P, _P, C.c_float, _P, _P, _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
     "le_selftest_bounded_wait": [_P],
@@ -611,6 +613,25 @@ def le_feature_map(feat, dec_t, codebook, out=None, workspace=None):
     _check(load().le_feature_map(P, _ptr(feat.contiguous()), C.byref(dec), _ptr(codebook.contiguous()), d, _ptr(out),
                                  _ptr(workspace), workspace.numel(), _stream()))
     return out
+
+
+def le_rgb_loss_workspace(W: int, H: int) -> int:
+    n = C.c_size_t()
+    _check(load().le_rgb_loss_workspace(W, H, C.byref(n)))
+    return n.value
+
+
+def le_rgb_loss(img, target, lambda_ssim=0.2, loss=None, grad=None, workspace=None):
+    """(1 - lambda) L1 + lambda (1 - SSIM) on [3, H, W] images: returns (loss [3] = (L, L1, SSIM), grad)."""
+    _, H, W = img.shape
+    dev = img.device
+    loss = loss if loss is not None else torch.empty(3, dtype=torch.float32, device=dev)
+    grad = grad if grad is not None else torch.empty_like(img)
+    if workspace is None:
+        workspace = torch.empty(le_rgb_loss_workspace(W, H), dtype=torch.uint8, device=dev)
+    _check(load().le_rgb_loss(W, H, _ptr(img.contiguous()), _ptr(target.contiguous()), lambda_ssim, _ptr(loss),
+                              _ptr(grad), _ptr(workspace), workspace.numel(), _stream()))
+    return loss, grad
 
 
 def le_rgb_l1(img, target, loss, grad):
