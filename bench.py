@@ -394,6 +394,7 @@ def run_ours(args, rank, world):
         out["query"] = query_leg(leg, synth, scene, cams, args)
         out["quantize"] = quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind)
         out["smooth"] = smooth_leg(leg, synth, st, args, bf16_peak)
+        out["rgb_dssim"] = rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(scene, dec, cams[0], rgb_host[0].numpy(), idx_host[0].numpy(),
                                            budget_s=20.0)
@@ -534,6 +535,28 @@ def smooth_leg(leg, synth, st, args, bf16_peak):
     return {"ms": round(ms, 4), "gaussians": g.n, "loss": round(float(loss.item()), 6),
             "tensor": {"achieved_tflops": round(flop / ms / 1e9, 1), "peak": bf16_peak,
                        "frac": round(flop / ms / 1e9 / bf16_peak, 4), "algorithmic_flop": flop}}
+
+
+def rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak):
+    """3DGS's RGB loss (1 - 0.2) L1 + 0.2 D-SSIM (le_rgb_loss, forward and gradient) on the last
+    rendered 1296x840 view, in place of the L1 term of the training-loop configuration."""
+    import torch
+    ws = torch.empty(leg.le_rgb_loss_workspace(W, H), dtype=torch.uint8, device="cuda")
+    loss, grad = torch.empty(3, device="cuda"), torch.empty_like(st.img.rgb)
+    for _ in range(3):
+        leg.le_rgb_loss(st.img.rgb, rgb_dev[0], 0.2, loss=loss, grad=grad, workspace=ws)
+    torch.cuda.synchronize()
+    n = max(5, args.steps // 4)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(n):
+        leg.le_rgb_loss(st.img.rgb, rgb_dev[0], 0.2, loss=loss, grad=grad, workspace=ws)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / n
+    byts = W * H * (12 + 12 + 36 + 36 + 12 + 12 + 12)   # fwd: image, target, 3 maps x 3 ch; bwd: maps, image, target, grad
+    return {"ms": round(ms, 4), "hbm_frac": round(byts / ms / 1e6 / hbm_peak, 4), "algorithmic_bytes": byts,
+            "loss": [round(float(x), 6) for x in loss.cpu()]}
 
 
 def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):

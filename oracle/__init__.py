@@ -17,7 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["keypath.c", "sh.c", "project.c", "binning.c", "composite.c", "decoder.c", "query.c", "train.c",
-           "quant.c", "smooth.c", "ssim.c"]
+           "quant.c", "smooth.c", "ssim.c", "densify.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 TILE = 16
 
@@ -53,6 +53,7 @@ def lib():
         _lib.orc_tile_list.restype = C.c_int
         _lib.orc_l1.restype = C.c_double
         _lib.orc_sh_count.restype = C.c_int
+        _lib.orc_densify_plan.restype = C.c_int64
         _lib.orc_bf16_bits.restype = C.c_uint16
         _lib.orc_bf16_bits.argtypes = [C.c_float]
     return _lib
@@ -394,3 +395,60 @@ def smooth(means, feat, unc, mlp, w_s=0.1, lam=1.0) -> dict:
                      *[_p(out["d" + k]) for k in SMOOTH_PARAMS])
     out["loss"] = float(out["loss"][0])
     return out
+
+
+def densify_thresholds(grad_thresh, percent_dense, extent, min_opacity):
+    """(grad_thresh, log_big, logit_min) as FP32 values, derived in double (see densify.c)."""
+    import math
+    return (np.float32(grad_thresh), np.float32(math.log(percent_dense * extent)),
+            np.float32(math.log(min_opacity / (1.0 - min_opacity))))
+
+
+def densify_stats(grad2d, radius, acc, cnt):
+    """In place: acc [n] float32, cnt [n] int32 (adaptive density control statistics)."""
+    g = _f32(grad2d)
+    r = np.ascontiguousarray(radius, np.int32)
+    assert acc.dtype == np.float32 and cnt.dtype == np.int32
+    lib().orc_densify_stats(C.c_int(len(r)), _p(g), _p(r), _p(acc), _p(cnt))
+
+
+def densify(params: dict, m: dict, v: dict, acc, cnt, noise, grad_thresh=0.0002, percent_dense=0.01, extent=1.0,
+            min_opacity=0.005) -> dict:
+    """Adaptive density control (3DGS's, kept by Sec. 4): returns the new parameter and moment
+    dicts (same field names: means, log_scales, quats, opacity_raw, sh, feat, unc) and the plan."""
+    ls = _f32(params["log_scales"])
+    op = _f32(params["opacity_raw"])
+    n = len(op)
+    acc, cnt = _f32(acc), np.ascontiguousarray(cnt, np.int32)
+    gt, lb, lm = densify_thresholds(grad_thresh, percent_dense, extent, min_opacity)
+    kind = np.zeros(n, np.int32)
+    total = lib().orc_densify_plan(C.c_int(n), _p(ls), _p(op), _p(acc), _p(cnt), C.c_float(gt), C.c_float(lb),
+                                   C.c_float(lm), _p(kind))
+    keep = np.nonzero((kind == 1) | (kind == 2))[0]
+    clone = np.nonzero(kind == 2)[0]
+    split = np.nonzero(kind == 3)[0]
+    src = np.concatenate([keep, clone, np.repeat(split, 2)])
+    assert len(src) == total
+    out_p, out_m, out_v = {}, {}, {}
+    for k in params:
+        a = np.asarray(params[k])
+        out_p[k] = a[src].copy()
+        z = np.zeros_like(np.asarray(m[k])[src])
+        z[:len(keep)] = np.asarray(m[k])[keep]
+        out_m[k] = z
+        z = np.zeros_like(np.asarray(v[k])[src])
+        z[:len(keep)] = np.asarray(v[k])[keep]
+        out_v[k] = z
+    base = len(keep) + len(clone)
+    mu = np.zeros((len(split), 2, 3))
+    for j, i in enumerate(split):
+        for c in range(2):
+            o = np.zeros(3)
+            lib().orc_split_mean(_p(_f32(params["means"][i])), _p(_f32(params["log_scales"][i])),
+                                 _p(_f32(params["quats"][i])), _p(_f32(noise[i, c])), _p(o))
+            mu[j, c] = o
+    out_p["means"] = out_p["means"].astype(np.float64)
+    out_p["means"][base:] = mu.reshape(-1, 3)
+    out_p["log_scales"] = out_p["log_scales"].astype(np.float64)
+    out_p["log_scales"][base:] -= np.log(1.6)
+    return {"params": out_p, "m": out_m, "v": out_v, "kind": kind, "n_out": int(total)}

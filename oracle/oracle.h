@@ -17,6 +17,7 @@
  *   - inference M_infer = softmax(D_MLP(R_s)), F = M_infer S, relevancy   supp. Sec. "Inference"
  *   - Adam with lr 1e-3, betas (0.9, 0.999)                          Sec. 4
  *   - RGB loss (1 - lambda) L1 + lambda D-SSIM (3DGS's, kept by Sec. 4)
+ *   - adaptive density control: clone / split / prune (3DGS's, kept by Sec. 4)
  *   - adaptive spatial smoothing: MLP(PE(p)), L_smo       Sec. 3.4 (eq:lem_fmlp, eq:lem_loss_mlp)
  *   - quantisation of language features: mixed cosine argmax, L_cos,
  *     load balancing L_lb, L_q           Sec. 3.3 (eq:q_dist .. eq:q_loss_cb), supp. Sec. 1
@@ -116,6 +117,12 @@ void orc_feature_map(int P, int ncb, const double* prob, const float* codebook, 
 /* ssim.c */
 void orc_rgb_loss(int W, int H, const double* img, const double* target, double lambda, double* loss, double* grad,
                   double* smap);
+
+/* densify.c */
+int64_t orc_densify_plan(int n, const float* log_scales, const float* opacity_raw, const float* acc,
+                         const int32_t* cnt, float grad_thresh, float log_big, float logit_min, int32_t* kind);
+void orc_densify_stats(int n, const float* grad2d, const int32_t* radius, float* acc, int32_t* cnt);
+void orc_split_mean(const float* mu, const float* log_s, const float* q, const float* nz, double* out);
 
 /* quant.c */
 uint16_t orc_bf16_bits(float x);

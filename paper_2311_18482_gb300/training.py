@@ -2,7 +2,7 @@
 driven entirely through the C ABI with preallocated device buffers:
 
   le_preprocess -> le_bin_render_fwd (binning + compositing, lazily placed)
-  -> le_rgb_l1 (RGB loss, Sec. 4)
+  -> le_rgb_l1 (RGB loss, Sec. 4; or le_rgb_loss with D-SSIM)
   -> le_decode (D_MLP + uncertainty-weighted CE + L_u, Eqs. 8-12, training mode)
   -> le_render_bwd_screen (screen-space gradients) -> le_project_bwd_adam
      (all Gaussian parameter gradients, each applied by Adam where it is
@@ -57,7 +57,8 @@ class FlatParams:
 
 
 class TrainState:
-    def __init__(self, scene, dec, W, H, device="cuda", decoder_mode=B.FUSED_BF16, lr=1e-3, fused_adam=True):
+    def __init__(self, scene, dec, W, H, device="cuda", decoder_mode=B.FUSED_BF16, lr=1e-3, fused_adam=True,
+                 rgb_loss="l1", lambda_ssim=0.2):
         self.layout = FlatParams(scene, dec, device)
         L = self.layout
         self.params = torch.zeros(L.total, dtype=torch.float32, device=device)
@@ -96,6 +97,12 @@ class TrainState:
                                   device=device)
         self.step_count = 0
         self.lr = lr
+        # RGB loss: "l1" (the training-loop configuration) or "l1_dssim", 3DGS's (1 - lambda) L1 +
+        # lambda D-SSIM that Sec. 4 keeps; loss[0] then holds the combined value
+        self.rgb_loss, self.lambda_ssim = rgb_loss, lambda_ssim
+        self.rgb_ws = torch.empty(B.le_rgb_loss_workspace(W, H), dtype=torch.uint8, device=device) \
+            if rgb_loss == "l1_dssim" else None
+        self.rgb_terms = torch.empty(3, dtype=torch.float32, device=device)
         self.K = 0
         self.events = None
 
@@ -123,7 +130,12 @@ class TrainState:
         self._mark("preprocess")
         ids, ranges, self.K, _ = B.le_bin_render_fwd(cam, self.proj, self.bins, self.img)
         self._mark("bin_render")
-        B.le_rgb_l1(self.img.rgb, rgb_target, self.loss[0:1], self.d_rgb)
+        if self.rgb_loss == "l1_dssim":
+            B.le_rgb_loss(self.img.rgb, rgb_target, self.lambda_ssim, loss=self.rgb_terms, grad=self.d_rgb,
+                          workspace=self.rgb_ws)
+            self.loss[0:1].copy_(self.rgb_terms[0:1])
+        else:
+            B.le_rgb_l1(self.img.rgb, rgb_target, self.loss[0:1], self.d_rgb)
         B.le_decode_raw(self.mode, self.P, self.img.feat, self.img.unc, self.dec, idx_target, 1.0, 1.0,
                         self.loss[1:3], self.d_feat, self.d_unc, self.dgrad, None, None, None, self.dec_ws)
         self._mark("decoder")

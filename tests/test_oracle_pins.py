@@ -848,3 +848,68 @@ def test_ssim_gradient_fd(orc):
         xm[c, i, j] -= h
         fd = (orc.rgb_loss(xp, y, want_grad=False)["loss"][0] - orc.rgb_loss(xm, y, want_grad=False)["loss"][0]) / (2 * h)
         assert abs(fd - o["grad"][c, i, j]) <= 1e-8 + 1e-6 * abs(fd), (c, i, j, fd, o["grad"][c, i, j])
+
+
+# ---------------------------------------------------------------------------
+# Adaptive density control (3DGS's clone / split / prune, kept by Sec. 4)
+
+def _densify_inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    P = {"means": rng.uniform(-1, 1, (n, 3)).astype(np.float32),
+         "log_scales": rng.normal(-3, 1, (n, 3)).astype(np.float32),
+         "quats": rng.standard_normal((n, 4)).astype(np.float32),
+         "opacity_raw": rng.normal(0, 3, n).astype(np.float32),
+         "sh": rng.standard_normal((n, 16, 3)).astype(np.float32),
+         "feat": rng.standard_normal((n, 8)).astype(np.float32),
+         "unc": rng.uniform(0, 1, n).astype(np.float32)}
+    acc = rng.uniform(0, 0.004, n).astype(np.float32)
+    cnt = rng.integers(0, 10, n).astype(np.int32)
+    return P, acc, cnt
+
+
+def test_densify_plan_matches_definitions(orc):
+    """The FP32 threshold forms take the same decisions as the definitions (sigmoid, mean gradient,
+    exp of the largest log-scale) evaluated in FP64, away from the thresholds."""
+    P, acc, cnt = _densify_inputs(4000, 70)
+    noise = np.zeros((4000, 2, 3), np.float32)
+    o = orc.densify(P, P, P, acc, cnt, noise, grad_thresh=0.0002, percent_dense=0.01, extent=4.0, min_opacity=0.005)
+    op = 1 / (1 + np.exp(-P["opacity_raw"].astype(np.float64)))
+    g = np.where(cnt > 0, acc / np.maximum(cnt, 1), 0.0)
+    big = np.exp(P["log_scales"].astype(np.float64).max(1)) > 0.01 * 4.0
+    want = np.where(op < 0.005, 0, np.where((cnt > 0) & (g >= 0.0002), np.where(big, 3, 2), 1))
+    far = (np.abs(op - 0.005) > 1e-6) & (np.abs(g - 0.0002) > 1e-9) & \
+          (np.abs(np.exp(P["log_scales"].astype(np.float64).max(1)) - 0.04) > 1e-7)
+    assert np.array_equal(o["kind"][far], want[far])
+    assert len(set(o["kind"].tolist())) == 4                    # every kind occurs
+    assert o["n_out"] == int(np.sum(want == 1) + 2 * np.sum(want >= 2))
+
+
+def test_densify_layout_and_children(orc):
+    """Output order (kept, clones, split children), moments carried or zeroed, child means
+    mu + R diag(s) n: with n = +-e_k the child sits at distance s_k along R's k-th column."""
+    P, acc, cnt = _densify_inputs(5, 71)
+    P["opacity_raw"][:] = [5, -9, 5, 5, 5]                      # Gaussian 1 is pruned
+    P["log_scales"][:] = -4.0
+    P["log_scales"][3] = [-1.0, -2.0, -3.0]                      # large: split
+    acc[:] = [0.0, 0.0, 0.01, 0.01, 0.0]
+    cnt[:] = [1, 1, 1, 1, 0]                                     # 2 clone, 3 split, 0 and 4 kept
+    m = {k: np.full_like(v, 7.0) for k, v in P.items()}
+    noise = np.zeros((5, 2, 3), np.float32)
+    noise[3, 0] = [1, 0, 0]
+    noise[3, 1] = [0, -1, 0]
+    o = orc.densify(P, m, m, acc, cnt, noise, extent=4.0)
+    assert list(o["kind"]) == [1, 0, 2, 3, 1] and o["n_out"] == 6      # sources 0, 2, 4 | 2 | 3, 3
+    out_feat = o["params"]["feat"]
+    assert out_feat.shape[0] == 6
+    assert np.array_equal(out_feat[:4], P["feat"][[0, 2, 4, 2]]) and np.array_equal(out_feat[4:], P["feat"][[3, 3]])
+    assert np.all(o["m"]["feat"][:3] == 7.0) and np.all(o["m"]["feat"][3:] == 0.0)
+    q = P["quats"][3].astype(np.float64)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    mu = P["means"][3].astype(np.float64)
+    assert np.abs(o["params"]["means"][4] - (mu + np.exp(-1.0) * R[:, 0])).max() < 1e-12
+    assert np.abs(o["params"]["means"][5] - (mu - np.exp(-2.0) * R[:, 1])).max() < 1e-12
+    assert np.abs(o["params"]["log_scales"][4] - (P["log_scales"][3] - np.log(1.6))).max() < 1e-12

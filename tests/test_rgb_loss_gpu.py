@@ -26,3 +26,17 @@ def test_rgb_loss(leg, orc, W, H, lam):
         assert rel_err(grad.cpu().numpy(), o["grad"]) < 1e-4
     got = loss.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(got - o["loss"]) <= 1e-5 * np.abs(o["loss"]))
+
+
+def test_training_step_with_dssim(leg):
+    """A few training steps with 3DGS's full RGB loss lower it on a fixed view."""
+    from paper_2311_18482_gb300.training import TrainState
+    c = synth.config("c2", n=20000, W=320, H=240)
+    st = TrainState(c["scene"], c["decoder"], 320, 240, rgb_loss="l1_dssim", lr=1e-2)
+    cam = synth.circle_pose(0, 4, 320, 240)
+    rgb = torch.from_numpy(synth.smooth_rgb_target(9, 320, 240)).cuda()
+    idx = torch.from_numpy(synth.voronoi_index_map(10, 320, 240, 128)).cuda()
+    first = float(st.step(cam, rgb, idx)[0])
+    for _ in range(15):
+        last = float(st.step(cam, rgb, idx)[0])
+    assert 0 < last < first
