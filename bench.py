@@ -395,6 +395,7 @@ def run_ours(args, rank, world):
         out["quantize"] = quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind)
         out["smooth"] = smooth_leg(leg, synth, st, args, bf16_peak)
         out["rgb_dssim"] = rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak)
+        out["densify"] = densify_leg(leg, st, args, hbm_peak)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(scene, dec, cams[0], rgb_host[0].numpy(), idx_host[0].numpy(),
                                            budget_s=20.0)
@@ -557,6 +558,38 @@ def rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak):
     byts = W * H * (12 + 12 + 36 + 36 + 12 + 12 + 12)   # fwd: image, target, 3 maps x 3 ch; bwd: maps, image, target, grad
     return {"ms": round(ms, 4), "hbm_frac": round(byts / ms / 1e6 / hbm_peak, 4), "algorithmic_bytes": byts,
             "loss": [round(float(x), 6) for x in loss.cpu()]}
+
+
+def densify_leg(leg, st, args, hbm_peak):
+    """Adaptive density control over the training state's 1M Gaussians: statistics from the last
+    step's screen-space gradients (a synthetic accumulated state: every visible Gaussian seen on
+    10 steps), then one clone/split/prune call into new buffers."""
+    import torch
+    g = st.g
+    n = g.n
+    acc = torch.zeros(n, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    for _ in range(10):
+        leg.le_densify_stats(st.grad2d, st.proj.radius, acc, cnt)
+    noise = torch.randn((n, 2, 3), generator=torch.Generator(device="cuda").manual_seed(5), device="cuda")
+    thresh = float(torch.quantile((acc / cnt.clamp_min(1))[cnt > 0][:1_000_000], 0.9))   # densify ~10 %
+    kw = dict(grad_thresh=thresh, percent_dense=0.01, scene_extent=4.0, min_opacity=0.005, n_cap=2 * n)
+    for _ in range(2):
+        out = leg.le_densify(g, st.gm, st.gvv, acc, cnt, noise, **kw)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    t0.record()
+    for _ in range(reps):
+        out = leg.le_densify(g, st.gm, st.gvv, acc, cnt, noise, **kw)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / reps
+    n2 = out[0].n
+    par = 4 * (3 + 3 + 4 + 1 + 48 + 8 + 1)
+    byts = 3 * par * n + 3 * par * n2 + 12 * n     # read params, m, v; write them for n2; statistics
+    return {"ms": round(ms, 4), "gaussians_in": n, "gaussians_out": n2, "hbm_frac": round(byts / ms / 1e6 / hbm_peak, 4),
+            "note": "one le_densify call (classify, scan, host read of the totals, scatter)"}
 
 
 def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):

@@ -441,6 +441,44 @@ le_status le_smooth(int32_t n, const float* means, const float* feat, const floa
                     const le_smooth_mlp_grads* dmlp, float* s_mlp, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Adaptive density control of 3D Gaussian Splatting, which Sec. 4 keeps
+ * ("enables adaptive density control of 3D Gaussians during the
+ * reconstruction"; reading: 3DGS's clone / split / prune rule).
+ * le_densify_stats -- every step after le_render_bwd_screen: for every
+ *   Gaussian with radius > 0, acc[i] += sqrt(gx^2 + gy^2) (gx, gy = grad2d
+ *   [i][0..1], dL/dmean2d in pixels), cnt[i] += 1.
+ * le_densify -- with g_i = acc_i / cnt_i: pruned if sigmoid(opacity_raw) <
+ *   min_opacity; else split if g_i >= grad_thresh and its largest scale >
+ *   percent_dense * scene_extent; else cloned if g_i >= grad_thresh; else kept.
+ *   The decisions are FP32 comparisons against thresholds computed in double
+ *   (opacity_raw < logit(min_opacity), max log-scale > ln(percent_dense *
+ *   extent), cnt > 0 and acc >= fl(grad_thresh * cnt)), reproducible bit for bit.
+ *   Output (g_out, m_out, v_out, capacity n_cap Gaussians each): the kept and
+ *   cloned Gaussians in index order, then the clones, then two children per
+ *   split Gaussian; a child k copies its parent except mean = mu + R(q)
+ *   diag(exp(log-scale)) noise[i][k] and log-scale - ln(1.6).  Adam moments
+ *   are carried for kept Gaussians and zero for clones and children.
+ *   noise: [n,2,3] standard normal samples (the caller draws them).
+ *   n_out: HOST pointer, the output count (also on LE_ERR_CAPACITY).
+ *   workspace: le_densify_workspace(n) bytes.  Synchronizes `stream` once.
+ * Errors: LE_ERR_INVALID_ARG; LE_ERR_CAPACITY when the output exceeds n_cap. */
+typedef struct le_densify_config {
+    float grad_thresh;       /* mean |dL/dmean2d| in pixels */
+    float percent_dense;     /* 3DGS: 0.01 */
+    float scene_extent;
+    float min_opacity;       /* 3DGS: 0.005 */
+} le_densify_config;
+
+le_status le_densify_stats(int32_t n, const float* grad2d, const int32_t* radius, float* acc, int32_t* cnt,
+                           void* stream);
+le_status le_densify_workspace(int32_t n, size_t* bytes);
+le_status le_densify(const le_densify_config* cfg, const le_gaussians* g, const le_gaussian_grads* m,
+                     const le_gaussian_grads* v, const float* acc, const int32_t* cnt, const float* noise,
+                     int64_t n_cap, const le_gaussian_grads* g_out, const le_gaussian_grads* m_out,
+                     const le_gaussian_grads* v_out, int64_t* n_out, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
+/* ---------------------------------------------------------------------------
  * Training helpers (Sec. 4).
  * le_rgb_l1: L = mean |img - target| over n values, loss[0] = L (device
  *   scalar, overwritten), grad = sign(img - target)/n (the 3DGS RGB loss's

@@ -400,8 +400,8 @@ def smooth(means, feat, unc, mlp, w_s=0.1, lam=1.0) -> dict:
 def densify_thresholds(grad_thresh, percent_dense, extent, min_opacity):
     """(grad_thresh, log_big, logit_min) as FP32 values, derived in double (see densify.c)."""
     import math
-    return (np.float32(grad_thresh), np.float32(math.log(percent_dense * extent)),
-            np.float32(math.log(min_opacity / (1.0 - min_opacity))))
+    pd, ex, mo = (float(np.float32(x)) for x in (percent_dense, extent, min_opacity))   # the FP32 config values
+    return (np.float32(grad_thresh), np.float32(math.log(pd * ex)), np.float32(math.log(mo / (1.0 - mo))))
 
 
 def densify_stats(grad2d, radius, acc, cnt):

@@ -48,6 +48,11 @@ class LeAdamConfig(C.Structure):
                 ("eps", C.c_float)]
 
 
+class LeDensifyConfig(C.Structure):
+    _fields_ = [("grad_thresh", C.c_float), ("percent_dense", C.c_float), ("scene_extent", C.c_float),
+                ("min_opacity", C.c_float)]
+
+
 _PROJ_FIELDS = ("splat", "depth", "radius", "rect", "tiles_touched", "clamp_mask", "tile_ellipse")
 
 
@@ -112,6 +117,11 @@ _SIG = {
     "le_feature_map": [C.c_int32, _P, C.POINTER(LeDecoder), _P, C.c_int32, _P, _P, C.c_size_t, _P],
     "le_rgb_loss_workspace": [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "le_rgb_loss": [C.c_int32, C.c_int32, _P, _P, C.c_float, _P, _P, _P, C.c_size_t, _P],
+    "le_densify_stats": [C.c_int32, _P, _P, _P, _P, _P],
+    "le_densify_workspace": [C.c_int32, C.POINTER(C.c_size_t)],
+    "le_densify": [C.POINTER(LeDensifyConfig), C.POINTER(LeGaussians), C.POINTER(LeGaussianGrads),
+                   C.POINTER(LeGaussianGrads), _P, _P, _P, C.c_int64, C.POINTER(LeGaussianGrads),
+                   C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads), C.POINTER(C.c_int64), _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
     "le_selftest_bounded_wait": [_P],
@@ -632,6 +642,35 @@ def le_rgb_loss(img, target, lambda_ssim=0.2, loss=None, grad=None, workspace=No
     _check(load().le_rgb_loss(W, H, _ptr(img.contiguous()), _ptr(target.contiguous()), lambda_ssim, _ptr(loss),
                               _ptr(grad), _ptr(workspace), workspace.numel(), _stream()))
     return loss, grad
+
+
+def le_densify_stats(grad2d, radius, acc, cnt):
+    """acc [n] float32 += |dL/dmean2d| and cnt [n] int32 += 1 for every visible Gaussian (in place)."""
+    _check(load().le_densify_stats(acc.shape[0], _ptr(grad2d), _ptr(radius), _ptr(acc), _ptr(cnt), _stream()))
+
+
+def le_densify(g: Gaussians, m: Gaussians, v: Gaussians, acc, cnt, noise, grad_thresh=0.0002, percent_dense=0.01,
+               scene_extent=1.0, min_opacity=0.005, n_cap=None):
+    """Adaptive density control: returns (g', m', v') as Gaussians of the new size."""
+    n = g.n
+    n_cap = n_cap if n_cap is not None else 2 * n
+    grow = lambda t: torch.empty((n_cap,) + tuple(t.shape[1:]), dtype=t.dtype, device=t.device)
+    outs = [Gaussians(*(grow(getattr(x, k)) for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat",
+                                                       "unc")), g.sh_degree) for x in (g, g, g)]
+    cfg = LeDensifyConfig(grad_thresh, percent_dense, scene_extent, min_opacity)
+    ws_n = C.c_size_t()
+    _check(load().le_densify_workspace(n, C.byref(ws_n)))
+    ws = torch.empty(max(ws_n.value, 1), dtype=torch.uint8, device=g.means.device)
+    n_out = C.c_int64()
+    gs, ms, vs = g.struct(), grads_struct(m), grads_struct(v)
+    os_ = [grads_struct(o) for o in outs]
+    _check(load().le_densify(C.byref(cfg), C.byref(gs), C.byref(ms), C.byref(vs), _ptr(acc), _ptr(cnt),
+                             _ptr(noise.contiguous()), n_cap, C.byref(os_[0]), C.byref(os_[1]), C.byref(os_[2]),
+                             C.byref(n_out), _ptr(ws), ws.numel(), _stream()))
+    k = n_out.value
+    cut = lambda o: Gaussians(*(getattr(o, f)[:k] for f in ("means", "log_scales", "quats", "opacity_raw", "sh",
+                                                          "feat", "unc")), o.sh_degree)
+    return cut(outs[0]), cut(outs[1]), cut(outs[2])
 
 
 def le_rgb_l1(img, target, loss, grad):
