@@ -552,6 +552,20 @@ __device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bi
     const int nu = a.ncb / 16, per = (nu + 1) / 2;
     const int c0 = min(nu, h * per) * 16, c1 = min(nu, (h + 1) * per) * 16;   // this half's logit columns
     float v[16];
+    // this row's inputs of the slot's next tile, loaded one tile ahead so that
+    // their latency is not on the path from one tile's first MMA to the next
+    float pf[8], pu = 0.f;
+    int pt = -1;
+    auto fetch = [&](int tile_n) {
+        const int pxn = tile_n * 128 + row;
+        const bool vn = tile_n < ntiles && pxn < a.P;
+        if (h == 0)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) pf[c] = vn ? a.feat[(size_t)c * a.P + pxn] : 0.f;
+        pu = vn ? a.unc[pxn] : 0.f;
+        pt = vn ? a.target[pxn] : -1;
+    };
+    fetch(blockIdx.x + e.s * gridDim.x);
     for (int it = 0;; ++it) {
         const int tile = blockIdx.x + (2 * it + e.s) * gridDim.x;
         if (tile >= ntiles) break;
@@ -562,15 +576,16 @@ __device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bi
         // X1 = [feat | 1 | 0]: the ones column gives db1
         if (h == 0) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[c] = valid ? a.feat[(size_t)c * a.P + px] : 0.f;
+            for (int c = 0; c < 8; ++c) v[c] = pf[c];
             sts_bf16x8(X1 + sbuf_off(row, 0, 16), v);
         } else {
 #pragma unroll
             for (int c = 0; c < 8; ++c) v[c] = c == 0 ? 1.f : 0.f;
             sts_bf16x8(X1 + sbuf_off(row, 8, 16), v);
         }
-        const float u = valid ? a.unc[px] : 0.f;
-        const int t = valid ? a.target[px] : -1;
+        const float u = pu;
+        const int t = pt;
+        fetch(tile + 2 * (int)gridDim.x);
         epi_signal(e);
         if (!epi_wait(e)) return false;
         // E1: h1 columns [32h, 32h + 32), bits of the ReLU mask in m1

@@ -143,15 +143,37 @@ struct ScatterArgs {
     float ln16;
 };
 
+// Copies Gaussian src to output slot dst in every field (moments or zeros);
+// 16-byte accesses for the fields whose rows are whole multiples of 16 bytes
+// (quaternions, SH, features) when the arrays allow it, scalar ones otherwise.
 __device__ __forceinline__ void copy_gaussian(const ScatterArgs& a, size_t src, size_t dst, bool moments)
 {
 #pragma unroll
     for (int f = 0; f < 7; ++f) {
         const int w = field_w(f, a.nc);
-        for (int e = 0; e < w; ++e) {
-            a.po.f[f][dst * w + e] = a.p.f[f][src * w + e];
-            a.mo.f[f][dst * w + e] = moments ? a.m.f[f][src * w + e] : 0.f;
-            a.vo.f[f][dst * w + e] = moments ? a.v.f[f][src * w + e] : 0.f;
+        const float* ps = a.p.f[f];
+        const float* ms = a.m.f[f];
+        const float* vs = a.v.f[f];
+        float* pd = a.po.f[f];
+        float* md = a.mo.f[f];
+        float* vd = a.vo.f[f];
+        if ((w & 3) == 0 && ((reinterpret_cast<uintptr_t>(ps) | reinterpret_cast<uintptr_t>(ms) |
+                              reinterpret_cast<uintptr_t>(vs) | reinterpret_cast<uintptr_t>(pd) |
+                              reinterpret_cast<uintptr_t>(md) | reinterpret_cast<uintptr_t>(vd)) & 15u) == 0) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e = 0; e < w; e += 4) {
+                reinterpret_cast<float4*>(pd + dst * w)[e >> 2] = reinterpret_cast<const float4*>(ps + src * w)[e >> 2];
+                reinterpret_cast<float4*>(md + dst * w)[e >> 2] =
+                    moments ? reinterpret_cast<const float4*>(ms + src * w)[e >> 2] : z;
+                reinterpret_cast<float4*>(vd + dst * w)[e >> 2] =
+                    moments ? reinterpret_cast<const float4*>(vs + src * w)[e >> 2] : z;
+            }
+        } else {
+            for (int e = 0; e < w; ++e) {
+                pd[dst * w + e] = ps[src * w + e];
+                md[dst * w + e] = moments ? ms[src * w + e] : 0.f;
+                vd[dst * w + e] = moments ? vs[src * w + e] : 0.f;
+            }
         }
     }
 }
