@@ -16,6 +16,8 @@
  *     errors) or the CUDA error is reported (LE_ERR_CUDA); le_last_error()
  *     returns a message for the calling thread.  The library never aborts and
  *     never traps on the device.
+ *   - Every entry point opens an NVTX range named after itself for the
+ *     duration of the call (visible on profiler timelines; free otherwise).
  *   - Arrays are row-major, FP32 unless stated.  Per-Gaussian data is
  *     structure-of-arrays indexed by Gaussian id; images are planar
  *     [channel][H][W]; pixel (i, j) is sampled at integer coordinates.

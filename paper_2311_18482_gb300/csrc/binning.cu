@@ -687,6 +687,7 @@ using namespace leg;
 
 extern "C" le_status le_bin_sort_workspace(int32_t n, int64_t k_cap, size_t* bytes)
 {
+    LE_TRACE("le_bin_sort_workspace");
     LE_CHECK_ARG(bytes != nullptr, "bytes is null");
     LE_CHECK_ARG(n >= 0 && k_cap >= 0 && k_cap < (int64_t)1 << 31, "n or k_cap out of range");
     *bytes = sort_ws_layout(nullptr, n).bytes;
@@ -826,6 +827,7 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
                                  uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges, int64_t* k_out,
                                  void* stream)
 {
+    LE_TRACE("le_bin_sort");
     cudaStream_t s = as_stream(stream);
     SortWs w;
     uint64_t* cur = nullptr;
@@ -843,6 +845,7 @@ extern "C" le_status le_bin_render_fwd(const le_camera* cam, int32_t n, const fl
                                        float* out_rgb, float* out_feat, float* out_unc, float* T_final,
                                        int32_t* n_contrib, void* stream)
 {
+    LE_TRACE("le_bin_render_fwd");
     LE_CHECK_ARG(out_rgb && out_feat && out_unc && T_final && n_contrib, "null output pointer");
     LE_CHECK_ARG(n == 0 || (splat && aligned16(splat)), "splat must be non-null and 16-byte aligned");
     cudaStream_t s = as_stream(stream);
@@ -940,6 +943,7 @@ extern "C" le_status le_bin_sort_static(const le_camera* cam, int32_t n, const f
                                         uint32_t* sorted_ids, uint64_t* sorted_keys, uint32_t* tile_ranges,
                                         int64_t* k_out, void* stream)
 {
+    LE_TRACE("le_bin_sort_static");
     LE_CHECK_ARG(n >= 0 && n <= kStaticMaxN, "n = %d exceeds the static-scratch limit of %d Gaussians", n,
                  kStaticMaxN);
     LE_CHECK_ARG(k_cap >= 0, "k_cap < 0");

@@ -5,9 +5,22 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/leg.h"
 
 namespace leg {
+
+// Named NVTX range around a C-ABI call (shows up on profiler timelines; a
+// no-op unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+#define LE_TRACE(name) ::leg::TraceRange le_trace_range_(name)
+
 
 // Per-thread error message and launch counter (host side).
 void set_error(const char* fmt, ...);

@@ -215,6 +215,7 @@ using namespace leg;
 
 extern "C" le_status le_decode_workspace(int32_t mode, int32_t P, const le_decoder* dec, size_t* bytes)
 {
+    LE_TRACE("le_decode_workspace");
     LE_CHECK_ARG(bytes && dec && P >= 0, "bad arguments");
     if (mode == LE_DECODE_FUSED_BF16) {
         *bytes = decode_fused_workspace(P, dec);
@@ -230,6 +231,7 @@ extern "C" le_status le_decode(int32_t mode, int32_t P, const float* feat, const
                                float* d_unc, const le_decoder_grads* dgrads, int32_t* argmax, float* prob,
                                float* logits, void* workspace, size_t workspace_bytes, void* stream)
 {
+    LE_TRACE("le_decode");
     le_status st = check_decoder(dec);
     if (st != LE_OK) return st;
     LE_CHECK_ARG(P >= 0, "P < 0");

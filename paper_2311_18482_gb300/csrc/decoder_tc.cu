@@ -1361,6 +1361,7 @@ le_status export_fused(int32_t P, const float* feat, const le_decoder* d, const 
 
 extern "C" le_status le_feature_map_workspace(int32_t n_cb, int32_t d, size_t* bytes)
 {
+    LE_TRACE("le_feature_map_workspace");
     LE_CHECK_ARG(bytes != nullptr, "bytes is null");
     LE_CHECK_ARG(n_cb > 0 && d > 0, "bad sizes");
     *bytes = (size_t)n_cb * d * 2;
@@ -1370,6 +1371,7 @@ extern "C" le_status le_feature_map_workspace(int32_t n_cb, int32_t d, size_t* b
 extern "C" le_status le_feature_map(int32_t P, const float* feat, const le_decoder* dec, const float* codebook,
                                     int32_t d, uint16_t* out, void* workspace, size_t workspace_bytes, void* stream)
 {
+    LE_TRACE("le_feature_map");
     LE_CHECK_ARG(P >= 0, "P = %d < 0", P);
     LE_CHECK_ARG(dec != nullptr && codebook && out && workspace, "null pointer");
     LE_CHECK_ARG(P == 0 || feat != nullptr, "null feat");
@@ -1386,6 +1388,7 @@ extern "C" le_status le_feature_map(int32_t P, const float* feat, const le_decod
 
 extern "C" le_status le_selftest_bounded_wait(void* stream)
 {
+    LE_TRACE("le_selftest_bounded_wait");
     leg::selftest_wait_kernel<<<1, 32, 0, leg::as_stream(stream)>>>();
     LE_LAUNCHED();
     return LE_OK;
@@ -1398,6 +1401,7 @@ le_status smooth_take_timeout(bool* timed_out);
 
 extern "C" le_status le_device_status(void* stream)
 {
+    LE_TRACE("le_device_status");
     LE_CUDA(cudaStreamSynchronize(leg::as_stream(stream)));
     int flag = 0;
     LE_CUDA(cudaMemcpyFromSymbol(&flag, leg::g_tc_error, sizeof(int)));

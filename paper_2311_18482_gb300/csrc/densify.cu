@@ -272,6 +272,7 @@ using namespace leg;
 extern "C" le_status le_densify_stats(int32_t n, const float* grad2d, const int32_t* radius, float* acc, int32_t* cnt,
                                       void* stream)
 {
+    LE_TRACE("le_densify_stats");
     LE_CHECK_ARG(n >= 0, "n = %d < 0", n);
     if (n == 0) return LE_OK;
     LE_CHECK_ARG(grad2d && radius && acc && cnt, "null pointer");
@@ -284,6 +285,7 @@ extern "C" le_status le_densify_stats(int32_t n, const float* grad2d, const int3
 
 extern "C" le_status le_densify_workspace(int32_t n, size_t* bytes)
 {
+    LE_TRACE("le_densify_workspace");
     LE_CHECK_ARG(bytes != nullptr && n >= 0, "bad arguments");
     const size_t nb = ((size_t)n + kDB - 1) / kDB;
     *bytes = ((size_t)n + 255) / 256 * 256 + (3 * nb * 4 + 255) / 256 * 256 + 256;
@@ -296,6 +298,7 @@ extern "C" le_status le_densify(const le_densify_config* cfg, const le_gaussians
                                 const le_gaussian_grads* v_out, int64_t* n_out, void* workspace,
                                 size_t workspace_bytes, void* stream)
 {
+    LE_TRACE("le_densify");
     LE_CHECK_ARG(cfg && g && n_out, "null config / gaussians / n_out");
     LE_CHECK_ARG(g->n >= 0 && g->sh_degree >= 0 && g->sh_degree <= 3, "bad gaussians");
     LE_CHECK_ARG(cfg->min_opacity > 0.f && cfg->min_opacity < 1.f && cfg->percent_dense > 0.f &&

@@ -666,6 +666,7 @@ using namespace leg;
 
 extern "C" le_status le_preprocess(const le_gaussians* g, const le_camera* cam, le_projected* out, void* stream)
 {
+    LE_TRACE("le_preprocess");
     le_status st = check_gaussians(g);
     if (st != LE_OK) return st;
     if ((st = check_camera(cam)) != LE_OK) return st;

@@ -860,6 +860,7 @@ using namespace leg;
 
 extern "C" le_status le_quantize_workspace(int32_t n_cb, int32_t d, size_t* bytes)
 {
+    LE_TRACE("le_quantize_workspace");
     LE_CHECK_ARG(bytes != nullptr, "bytes is null");
     LE_CHECK_ARG(n_cb > 0 && d > 0, "bad sizes");
     *bytes = quant_ws(nullptr, n_cb, d).bytes;
@@ -871,6 +872,7 @@ extern "C" le_status le_quantize(int64_t K, int32_t d, int32_t d_clip, const uin
                                  int32_t* indices, float* r, float* p, float* loss, void* workspace,
                                  size_t workspace_bytes, void* stream)
 {
+    LE_TRACE("le_quantize");
     le_status st = check_quant(K, d, d_clip, n_cb);
     if (st != LE_OK) return st;
     LE_CHECK_ARG(features && codebook && indices && loss && workspace, "null pointer");
@@ -958,6 +960,7 @@ QuantGradWs quant_grad_ws(void* p, long long K, int N, int d)
 
 extern "C" le_status le_quantize_grad_workspace(int64_t K, int32_t n_cb, int32_t d, size_t* bytes)
 {
+    LE_TRACE("le_quantize_grad_workspace");
     LE_CHECK_ARG(bytes != nullptr, "bytes is null");
     LE_CHECK_ARG(K >= 1 && n_cb > 0 && d > 0, "bad sizes");
     *bytes = quant_grad_ws(nullptr, K, n_cb, d).bytes;
@@ -969,6 +972,7 @@ extern "C" le_status le_quantize_grad(int64_t K, int32_t d, int32_t d_clip, cons
                                       float lambda_lb, float* grad_codebook, void* workspace, size_t workspace_bytes,
                                       void* stream)
 {
+    LE_TRACE("le_quantize_grad");
     le_status st = check_quant(K, d, d_clip, n_cb);
     if (st != LE_OK) return st;
     if (d % 128 != 0 || d_clip % 128 != 0)

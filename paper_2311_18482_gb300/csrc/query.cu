@@ -63,6 +63,7 @@ using namespace leg;
 
 extern "C" le_status le_query_workspace(int32_t mode, int32_t P, int32_t n_cb, int32_t d_clip, size_t* bytes)
 {
+    LE_TRACE("le_query_workspace");
     LE_CHECK_ARG(bytes && P >= 0 && n_cb > 0 && d_clip > 0, "bad arguments");
     if (mode == LE_DECODE_FUSED_BF16) {
         *bytes = query_fused_workspace(P, n_cb, d_clip);
@@ -79,6 +80,7 @@ extern "C" le_status le_query(int32_t mode, int32_t P, const float* feat, const 
                               const float* negs, int32_t n_neg, float* relevancy, void* workspace,
                               size_t workspace_bytes, void* stream)
 {
+    LE_TRACE("le_query");
     LE_CHECK_ARG(P >= 0 && d > 0 && d_clip > 0 && d_clip <= d, "bad sizes");
     LE_CHECK_ARG(Q >= 1 && n_neg >= 1 && Q + n_neg <= kMaxEmb, "need 1 <= Q, n_neg and Q + n_neg <= %d", kMaxEmb);
     LE_CHECK_ARG(codebook && text && negs && relevancy, "null pointer");

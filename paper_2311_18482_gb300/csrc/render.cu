@@ -421,6 +421,7 @@ extern "C" le_status le_render_fwd(const le_camera* cam, int32_t n, const float*
                                    const uint32_t* tile_ranges, float* out_rgb, float* out_feat, float* out_unc,
                                    float* T_final, int32_t* n_contrib, void* stream)
 {
+    LE_TRACE("le_render_fwd");
     le_status st = check_camera(cam);
     if (st != LE_OK) return st;
     LE_CHECK_ARG(n >= 0, "n < 0");
@@ -488,6 +489,7 @@ extern "C" le_status le_render_bwd(const le_camera* cam, const le_gaussians* g, 
                                    const int32_t* n_contrib, const float* dL_drgb, const float* dL_dfeat,
                                    const float* dL_dunc, float* grad2d, const le_gaussian_grads* out, void* stream)
 {
+    LE_TRACE("le_render_bwd");
     le_status st = check_render_bwd(cam, g, pr, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc, grad2d);
     if (st != LE_OK || g->n == 0) return st;
     if ((st = check_field_set(out, "gradient")) != LE_OK) return st;
@@ -505,6 +507,7 @@ extern "C" le_status le_render_bwd_adam(const le_camera* cam, const le_gaussians
                                         const le_gaussian_grads* m, const le_gaussian_grads* v,
                                         const le_adam_config* adam, void* stream)
 {
+    LE_TRACE("le_render_bwd_adam");
     le_status st = check_render_bwd(cam, g, pr, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc, grad2d);
     if (st != LE_OK) return st;
     LE_CHECK_ARG(adam != nullptr && adam->step >= 1, "adam config is null or step < 1");
@@ -524,6 +527,7 @@ extern "C" le_status le_render_bwd_screen(const le_camera* cam, const le_gaussia
                                           const float* T_final, const int32_t* n_contrib, const float* dL_drgb,
                                           const float* dL_dfeat, const float* dL_dunc, float* grad2d, void* stream)
 {
+    LE_TRACE("le_render_bwd_screen");
     le_status st = check_render_bwd(cam, g, pr, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc, grad2d);
     if (st != LE_OK || g->n == 0) return st;
     return render_backward_2d(cam, g, pr, sorted_ids, tile_ranges, T_final, n_contrib, dL_drgb, dL_dfeat, dL_dunc,
@@ -533,6 +537,7 @@ extern "C" le_status le_render_bwd_screen(const le_camera* cam, const le_gaussia
 extern "C" le_status le_project_bwd(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
                                     const float* grad2d, const le_gaussian_grads* out, void* stream)
 {
+    LE_TRACE("le_project_bwd");
     le_status st = check_camera(cam);
     if (st != LE_OK) return st;
     if ((st = check_gaussians(g)) != LE_OK) return st;
@@ -548,6 +553,7 @@ extern "C" le_status le_project_bwd_adam(const le_camera* cam, const le_gaussian
                                          const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
                                          const le_adam_config* adam, void* stream)
 {
+    LE_TRACE("le_project_bwd_adam");
     le_status st = check_camera(cam);
     if (st != LE_OK) return st;
     if ((st = check_gaussians(g)) != LE_OK) return st;

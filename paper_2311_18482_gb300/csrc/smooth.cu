@@ -415,6 +415,7 @@ extern "C" le_status le_smooth(int32_t n, const float* means, const float* feat,
                                const le_smooth_mlp* mlp, float w_s, float lambda_smo, float* loss, float* d_feat,
                                int32_t d_feat_stride, const le_smooth_mlp_grads* dmlp, float* s_mlp, void* stream)
 {
+    LE_TRACE("le_smooth");
     LE_CHECK_ARG(n >= 0, "n = %d < 0", n);
     LE_CHECK_ARG(mlp && dmlp && loss, "null mlp / gradient / loss pointer");
     LE_CHECK_ARG(mlp->W1 && mlp->b1 && mlp->W2 && mlp->b2 && mlp->W3 && mlp->b3 && mlp->W4 && mlp->b4,

@@ -172,6 +172,7 @@ using namespace leg;
 
 extern "C" le_status le_rgb_loss_workspace(int32_t W, int32_t H, size_t* bytes)
 {
+    LE_TRACE("le_rgb_loss_workspace");
     LE_CHECK_ARG(bytes != nullptr, "bytes is null");
     LE_CHECK_ARG(W > 0 && H > 0, "bad image size");
     *bytes = ((size_t)9 * W * H + 64) * sizeof(float);
@@ -181,6 +182,7 @@ extern "C" le_status le_rgb_loss_workspace(int32_t W, int32_t H, size_t* bytes)
 extern "C" le_status le_rgb_loss(int32_t W, int32_t H, const float* img, const float* target, float lambda_ssim,
                                  float* loss, float* grad, void* workspace, size_t workspace_bytes, void* stream)
 {
+    LE_TRACE("le_rgb_loss");
     LE_CHECK_ARG(W > 0 && H > 0 && W <= 16384 && H <= 16384, "bad image size %d x %d", W, H);
     LE_CHECK_ARG(img && target && loss && grad && workspace, "null pointer");
     LE_CHECK_ARG(lambda_ssim >= 0.f && lambda_ssim <= 1.f, "lambda_ssim must be in [0, 1]");

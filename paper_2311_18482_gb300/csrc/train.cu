@@ -65,6 +65,7 @@ using namespace leg;
 extern "C" le_status le_rgb_l1(int64_t n, const float* img, const float* target, float* loss, float* grad,
                                void* stream)
 {
+    LE_TRACE("le_rgb_l1");
     LE_CHECK_ARG(n >= 0, "n < 0");
     if (n == 0) return LE_OK;
     LE_CHECK_ARG(img && target && loss && grad, "null pointer");
@@ -78,6 +79,7 @@ extern "C" le_status le_rgb_l1(int64_t n, const float* img, const float* target,
 extern "C" le_status le_adam(int64_t n, float* param, const float* grad, float* m, float* v, int32_t step, float lr,
                              float beta1, float beta2, float eps, float clamp_lo, float clamp_hi, void* stream)
 {
+    LE_TRACE("le_adam");
     LE_CHECK_ARG(n >= 0 && step >= 1, "n < 0 or step < 1");
     if (n == 0) return LE_OK;
     LE_CHECK_ARG(param && grad && m && v, "null pointer");
