@@ -440,11 +440,21 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
         }
     }
     __syncthreads();
-    for (int y = threadIdx.x; y < TY; y += blockDim.x) {
-        int run = 0;
-        for (int x = 0; x < TX; ++x) {
-            run += diff[y * W1 + x];
-            diff[y * W1 + x] = run;
+    // inclusive prefix sum along each row: one warp per row, 32 cells a step
+    const int lane = threadIdx.x & 31;
+    for (int y = threadIdx.x >> 5; y < TY; y += blockDim.x >> 5) {
+        int carry = 0;
+        for (int x0 = 0; x0 < TX; x0 += 32) {
+            const int x = x0 + lane;
+            int v = x < TX ? diff[y * W1 + x] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            v += carry;
+            if (x < TX) diff[y * W1 + x] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
         }
     }
     __syncthreads();

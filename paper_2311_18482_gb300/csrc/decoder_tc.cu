@@ -1171,19 +1171,48 @@ __global__ void codebook_chunks_kernel(const float* __restrict__ S, int ncb, int
     }
 }
 
-// G = S_c S_c^T (fp32) -> chunked canonical bf16 image: chunk kc holds columns
-// [64 kc, 64 kc + 64) of every row, as an [ncb x 64] canonical buffer.
-__global__ void gram_layout_kernel(const float* __restrict__ G, int ncb, unsigned char* __restrict__ img)
+// Query constants in one launch, 16 x 16 outputs per block, k ascending with
+// FMAs (the order of a plain dot product):
+//   block rows y < ncb/16:  G = S_c S_c^T, written straight into its chunked
+//                           canonical BF16 image: chunk kc holds columns
+//                           [64 kc, 64 kc + 64) of every row as an [ncb x 64]
+//                           canonical buffer;
+//   block row y = ncb/16:   Aq[r][j] = [text; negs]_r . S_c[j] (rows r >= Q + n_neg zero).
+__global__ void __launch_bounds__(256) query_prep_kernel(const float* __restrict__ S, int ncb, int dd, int d_clip,
+                                                         const float* __restrict__ text, int Q,
+                                                         const float* __restrict__ negs, int n_neg,
+                                                         unsigned char* __restrict__ img, float* __restrict__ Aq)
 {
-    const int n8 = ncb * (ncb / 8);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += gridDim.x * blockDim.x) {
-        const int r = i / (ncb / 8), c0 = (i % (ncb / 8)) * 8;
-        const int kc = c0 / 64, cc = c0 % 64;
-        __nv_bfloat162 h[4];
+    __shared__ float xs[16][33], ys[16][33];
+    const int j0 = blockIdx.x * 16, i0 = blockIdx.y * 16;
+    const bool gram = i0 < ncb;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc = 0.f;
+    for (int k0 = 0; k0 < d_clip; k0 += 32) {
+        for (int l = threadIdx.x; l < 16 * 32; l += 256) {
+            const int r = l >> 5, c = l & 31, k = k0 + c;
+            float xv = 0.f;
+            if (k < d_clip) {
+                if (gram) xv = S[(size_t)(i0 + r) * dd + k];
+                else if (r < Q) xv = text[(size_t)r * d_clip + k];
+                else if (r < Q + n_neg) xv = negs[(size_t)(r - Q) * d_clip + k];
+            }
+            xs[r][c] = xv;
+            ys[r][c] = k < d_clip ? S[(size_t)(j0 + r) * dd + k] : 0.f;
+        }
+        __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(G[(size_t)r * ncb + c0 + 2 * j], G[(size_t)r * ncb + c0 + 2 * j + 1]);
-        unsigned char* dst = img + (size_t)kc * ncb * 64 * 2 + ((r >> 3) * 8 * 128 + (cc >> 3) * 128 + (r & 7) * 16);
-        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(h);
+        for (int c = 0; c < 32; ++c) acc = fmaf(xs[ty][c], ys[tx][c], acc);
+        __syncthreads();
+    }
+    const int r = i0 + ty, c = j0 + tx;
+    if (gram) {
+        const int kc = c >> 6, cc = c & 63;
+        unsigned char* dst = img + (size_t)kc * ncb * 64 * 2 + ((r >> 3) * 8 * 128 + (cc >> 3) * 128 + (r & 7) * 16) +
+                             (cc & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(acc);
+    } else {
+        Aq[(size_t)ty * ncb + c] = acc;
     }
 }
 
@@ -1294,23 +1323,12 @@ le_status query_fused(int32_t P, const float* feat, const le_decoder* d, const f
         return LE_ERR_UNSUPPORTED;
     }
     char* w = static_cast<char*>(ws);
-    float* G = reinterpret_cast<float*>(w);
     float* Aq = reinterpret_cast<float*>(w + align_up(sizeof(float) * ncb * ncb, 256));
     unsigned char* img = reinterpret_cast<unsigned char*>(w + align_up(sizeof(float) * ncb * ncb, 256) +
                                                           align_up(sizeof(float) * 16 * ncb, 256));
-    // G = S_c S_c^T and Aq = [text; negs] S_c^T, FP32 on CUDA cores (small, once per call)
-    GemmArgs g{};
-    g.M = ncb; g.N = ncb; g.K = d_clip;
-    g.A = codebook; g.lda = dd; g.B = codebook; g.ldb = dd; g.C = G; g.ldc = ncb;
-    if ((st = sgemm(false, true, g, 1, s)) != LE_OK) return st;
-    LE_CUDA(cudaMemsetAsync(Aq, 0, sizeof(float) * 16 * ncb, s));
-    g = GemmArgs{};
-    g.M = Q; g.N = ncb; g.K = d_clip;
-    g.A = text; g.lda = d_clip; g.B = codebook; g.ldb = dd; g.C = Aq; g.ldc = ncb;
-    if ((st = sgemm(false, true, g, 1, s)) != LE_OK) return st;
-    g.M = n_neg; g.A = negs; g.C = Aq + (size_t)Q * ncb;
-    if ((st = sgemm(false, true, g, 1, s)) != LE_OK) return st;
-    gram_layout_kernel<<<64, 256, 0, s>>>(G, ncb, img);
+    // G = S_c S_c^T (as the BF16 image) and Aq = [text; negs] S_c^T, FP32 on CUDA cores, one launch
+    query_prep_kernel<<<dim3(ncb / 16, ncb / 16 + 1), 256, 0, s>>>(codebook, ncb, dd, d_clip, text, Q, negs, n_neg,
+                                                                   img, Aq);
     LE_LAUNCHED();
     DecArgs a{};
     a.P = P;
