@@ -979,10 +979,16 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
 #pragma unroll
             for (int h = 0; h < kQueryParts; ++h) tot += w[h];
             const float inv = rsqrtf(fmaxf(tot, 1e-30f));
+            // unrolled with constant indices: v stays in registers (a runtime
+            // index would put it, and every TMEM load into it, in local memory)
             float smax = -INFINITY;
-            for (int j = a.Q; j < a.Q + a.n_neg; ++j) smax = fmaxf(smax, v[j] * inv);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j >= a.Q && j < a.Q + a.n_neg) smax = fmaxf(smax, v[j] * inv);
             if (valid)
-                for (int j = 0; j < a.Q; ++j) a.rel[(size_t)j * a.P + px] = 1.f / (1.f + __expf(smax - v[j] * inv));
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j < a.Q) a.rel[(size_t)j * a.P + px] = 1.f / (1.f + __expf(smax - v[j] * inv));
         }
         fence_before();
         __syncthreads();
