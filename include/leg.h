@@ -351,7 +351,8 @@ le_status le_query(int32_t mode, int32_t P, const float* feat, const le_decoder*
  *   codebook [n_cb, d] FP32; out [P, d] BF16 (bit patterns), pixel-major,
  *   16-byte aligned; workspace: le_feature_map_workspace(n_cb, d) bytes.
  * One tcgen05 kernel: decode, softmax (stored in BF16, normalised in FP32 at
- * the output), F = p S with FP32 accumulation, BF16 out.
+ * the output), F = p S with FP32 accumulation, BF16 out through TMA tensor
+ * stores.  The workspace holds BF16 images of the codebook and of W3.
  * Errors: LE_ERR_INVALID_ARG; LE_ERR_UNSUPPORTED unless d is a multiple of
  * 64 and the decoder has the fused path's sizes. */
 le_status le_feature_map_workspace(int32_t n_cb, int32_t d, size_t* bytes);

@@ -53,6 +53,10 @@ struct DecArgs {
     float *dW1, *db1, *dW2, *db2, *dW3, *db3;
     int32_t* argmax;
     float* prob;
+    // feature-map export: W3 as the BF16 shared-memory image (reloaded per tile
+    // when the output staging borrows W3's shared memory)
+    const unsigned char* W3_img;
+    int w3_reload;
     // query
     const unsigned char* G_img;     // ncb/64 chunks of [ncb x 64] canonical bf16
     const float* Aq;                // [16, ncb] fp32 = [text; negs] S_c^T
@@ -78,6 +82,11 @@ struct Front {
     int bar_id, nthreads;
     int half, nhalf;
     float4* xch;       // [nhalf][128] (nhalf > 1 only)
+    // W3s reloaded by a bulk copy (thread 0 only): the third layer's MMAs wait
+    // for it first
+    uint64_t* w3bar = nullptr;
+    uint32_t w3phase = 0;
+    bool w3pending = false;
 };
 
 // Columns [c0, c1) of an N-column epilogue handled by this thread's half (units of 16).
@@ -118,14 +127,19 @@ __device__ __forceinline__ void wg_publish(const Front& f)
 // D_MLP forward of one 128-pixel tile: X1 <- feat (col 8 = 1 for the bias
 // gradient), H1 = relu(W1 x + b1), H2 = relu(W2 h1 + b2), logits - b3 left in
 // TMEM columns [tw, tw + ncb).  Returns false on a timed-out wait.
-__device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
+// R_s of pixel p (zeros past the end), for mlp_forward_x.
+__device__ __forceinline__ void load_feat(const DecArgs& a, int p, bool valid, float* x)
+{
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = valid ? a.feat[(size_t)c * a.P + p] : 0.f;
+}
+
+// mlp_forward with the tile's features already in registers (x, read by the
+// first part only), so that a caller can load them a tile ahead.
+__device__ bool mlp_forward_x(Front& f, const DecArgs& a, const float* x)
 {
     float v[16];
-    if (f.half == 0) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) v[c] = valid ? a.feat[(size_t)c * a.P + p] : 0.f;
-        sbuf_store8(f.X1, f.tid, 0, v);
-    }
+    if (f.half == 0) sbuf_store8(f.X1, f.tid, 0, x);
     if (f.half == f.nhalf - 1) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) v[c] = c == 0 ? 1.f : 0.f;
@@ -164,12 +178,24 @@ __device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
     }
     wg_publish(f);
     if (f.tid == 0 && f.half == 0) {
+        if (f.w3pending) {
+            if (!mbar_wait(f.w3bar, f.w3phase)) atomicExch(&g_tc_error, 1);
+            f.w3phase ^= 1u;
+            f.w3pending = false;
+        }
 #pragma unroll
         for (int s = 0; s < kH2 / 16; ++s)
             mma(f.tw, kdesc(f.H2, 0, 16 * s), kdesc(f.W3s, 0, 16 * s), idesc_bf16(a.ncb, false, false), s > 0);
         commit(f.mbar);
     }
     return wg_wait(f);
+}
+
+__device__ bool mlp_forward(Front& f, const DecArgs& a, int p, bool valid)
+{
+    float x[8];
+    if (f.half == 0) load_feat(a, p, valid, x);
+    return mlp_forward_x(f, a, x);
 }
 
 // Online max / argmax / log-sum-exp over the ncb logits in TMEM (+ b3); with
@@ -897,10 +923,16 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
     bool ok = true;
     if (tid == 0 && blockIdx.x < ntiles)
         for (int s = 0; s < 2 && s < nch; ++s) load_chunk(s, s);
+    float xf[8];                                // this tile's R_s, loaded a tile ahead (part 0)
+    if (f.half == 0) load_feat(a, blockIdx.x * 128 + row, blockIdx.x * 128 + row < a.P, xf);
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int px = tile * 128 + row;
         const bool valid = px < a.P;
-        if (!mlp_forward(f, a, px, valid)) break;
+        if (!mlp_forward_x(f, a, xf)) break;
+        if (f.half == 0) {
+            const int nx = px + 128 * (int)gridDim.x;
+            load_feat(a, nx, tile + (int)gridDim.x < ntiles && nx < a.P, xf);
+        }
         // e = exp(z - max z) in BF16.  The relevancy phi.q / |phi| with
         // phi = sum_c p_c s_c does not depend on the scale of p, so the
         // softmax normaliser 1 / sum e is never needed.
@@ -1011,20 +1043,38 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
 // The codebook streams through shared memory in 64-dim chunks ([n_cb x 64]
 // canonical images, two slots, 1-D bulk copies); per chunk one MMA (M = 128
 // pixels, N = 64 dims, K = n_cb) reads the chunk MN-major into one of two
-// 64-column TMEM accumulators, and each warpgroup writes 16 of its columns.
+// 64-column TMEM accumulators.  Each warpgroup converts 16 columns of each
+// into a 128-byte-swizzled staging area, from which two TMA tensor stores per
+// round (128 pixels x 64 dims each) write the output in whole lines; a warp
+// storing its rows directly would scatter 16-byte pieces over 32 rows.
 constexpr uint32_t kTF = 256;      // TMEM columns of the two chunk accumulators
 
-__host__ constexpr size_t export_smem(int ncb)
+// Shared memory of the export kernel without the output staging, the staging
+// (one round's two 128 x 64 BF16 boxes, 128-byte swizzled for the TMA store),
+// and whether the staging must borrow W3's shared memory (then W3 is reloaded
+// from its global image after every tile; it is idle during the codebook loop).
+// The layout starts at a 1024-byte boundary (the swizzled staging and W3s, at
+// offset 18 KB, need it), hence the first 1024.
+__host__ constexpr size_t export_smem_core(int ncb)
 {
-    return weights_bytes(ncb) + (sbuf_bytes(128, ncb) > kFwdWgBytes ? sbuf_bytes(128, ncb) : kFwdWgBytes) +
+    return 1024 + weights_bytes(ncb) + (sbuf_bytes(128, ncb) > kFwdWgBytes ? sbuf_bytes(128, ncb) : kFwdWgBytes) +
            2 * sbuf_bytes(ncb, 64) + kQueryParts * 128 * 4 + 128;
 }
+constexpr uint32_t kExportBox = sbuf_bytes(128, 64);
+constexpr size_t kMaxDynSmem = 227 * 1024;
+__host__ constexpr bool export_stage_in_w3(int ncb) { return export_smem_core(ncb) + 1024 + 2 * kExportBox > kMaxDynSmem; }
+__host__ constexpr size_t export_smem(int ncb)
+{
+    return export_smem_core(ncb) + (export_stage_in_w3(ncb) ? 0 : 1024 + 2 * kExportBox);
+}
 
-__global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecArgs a)
+__global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(const __grid_constant__ CUtensorMap tmap_out,
+                                                                          DecArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     Front f;
-    unsigned char* p = load_weights(sm, a, f);
+    unsigned char* p = load_weights(
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm) + 1023) & ~uintptr_t(1023)), a, f);
     f.X1 = SBuf{p, 16};
     f.H1 = SBuf{p + sbuf_bytes(128, 16), 64};
     f.H2 = SBuf{p + sbuf_bytes(128, 16) + sbuf_bytes(128, 64), 128};
@@ -1036,8 +1086,12 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecA
     p += 2 * chunk_bytes;
     float* sums = reinterpret_cast<float*>(p);          // [parts][128] partial sums of e
     p += kQueryParts * 128 * 4;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);     // [0] MMA, [1], [2] codebook slots
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);     // [0] MMA, [1], [2] codebook slots, [4] W3 reload
     uint32_t* slot = reinterpret_cast<uint32_t*>(p + 24);
+    p += 128;
+    unsigned char* stg = a.w3_reload ? f.W3s.p
+                                     : reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 1023) &
+                                                                        ~uintptr_t(1023));
     const int tid = threadIdx.x;
     f.mbar = mbar;
     f.phase = 0;
@@ -1046,8 +1100,11 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecA
     f.nthreads = blockDim.x;
     f.half = tid >> 7;
     f.nhalf = kQueryParts;
-    if (tid == 0)
+    f.w3bar = mbar + 4;
+    if (tid == 0) {
         for (int i = 0; i < 3; ++i) mbar_init(mbar + i, 1);
+        mbar_init(mbar + 4, 1);
+    }
     if (tid < 32) tmem_alloc(slot, 512);
     fence_proxy_async();
     fence_before();
@@ -1071,10 +1128,16 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecA
     bool ok = true;
     if (tid == 0 && blockIdx.x < ntiles)
         for (int s = 0; s < 2 && s < nch; ++s) load_chunk(s, s);
+    float xf[8];                                // this tile's R_s, loaded a tile ahead (part 0)
+    if (f.half == 0) load_feat(a, blockIdx.x * 128 + row, blockIdx.x * 128 + row < a.P, xf);
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int px = tile * 128 + row;
         const bool valid = px < a.P;
-        if (!mlp_forward(f, a, px, valid)) break;
+        if (!mlp_forward_x(f, a, xf)) break;
+        if (f.half == 0) {
+            const int nx = px + 128 * (int)gridDim.x;
+            load_feat(a, nx, tile + (int)gridDim.x < ntiles && nx < a.P, xf);
+        }
         float v[16], mh = -INFINITY;
         for (int c = c0; c < c1; c += 16) {
             tmem_ld16(f.tw + f.lane + c, v);
@@ -1104,7 +1167,7 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecA
         float tot = 0.f;
 #pragma unroll
         for (int h = 0; h < kQueryParts; ++h) tot += sums[h * 128 + row];
-        const float inv = 1.0f / tot;
+        const float inv = valid ? 1.0f / tot : 0.f;
         bool tmo = false;
         for (int kc0 = 0; kc0 < nch; kc0 += 2) {
             if (tid == 0) {
@@ -1118,6 +1181,8 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecA
                             k > 0);
                 }
                 commit(f.mbar);
+                // the staging area is rewritten below: the previous round's stores must have read it
+                bulk_wait_read_all();
             }
             if (!wg_wait(f) || bar_any(0, blockDim.x, tmo)) {
                 if (tid == 0) atomicExch(&g_tc_error, 1);
@@ -1133,31 +1198,59 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(DecA
                     if ((more && kc < nch) || (!more && next_tile && kc < nch)) load_chunk(kc, s);
                 }
             }
-            // this warpgroup's 16 columns of each chunk, scaled by 1 / sum e, as BF16
+            // this warpgroup's 16 columns of each chunk, scaled by 1 / sum e, as BF16 into the
+            // staging boxes (row-major 128-byte rows, 16-byte unit u of row r at u ^ (r & 7))
             for (int s = 0; s < 2 && kc0 + s < nch; ++s) {
                 tmem_ld16(tbase + kTF + 64 * s + 16 * f.half + f.lane, v);
-                if (valid) {
-                    __nv_bfloat162 h[8];
+                __nv_bfloat162 h[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j] * inv, v[2 * j + 1] * inv);
-                    uint4* dst = reinterpret_cast<uint4*>(a.fmap + (size_t)px * a.dd + 64 * (kc0 + s) + 16 * f.half);
-                    dst[0] = *reinterpret_cast<uint4*>(h);
-                    dst[1] = *reinterpret_cast<uint4*>(h + 4);
-                }
+                for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j] * inv, v[2 * j + 1] * inv);
+                unsigned char* dst = stg + s * kExportBox + row * 128;
+                const int u = 2 * f.half;
+                *reinterpret_cast<uint4*>(dst + ((u ^ (row & 7)) << 4)) = *reinterpret_cast<uint4*>(h);
+                *reinterpret_cast<uint4*>(dst + (((u + 1) ^ (row & 7)) << 4)) = *reinterpret_cast<uint4*>(h + 4);
             }
+            fence_proxy_async();
             fence_before();
             __syncthreads();
             fence_after();
+            if (tid == 0) {
+                for (int s = 0; s < 2 && kc0 + s < nch; ++s)
+                    tma_store_2d(&tmap_out, 64 * (kc0 + s), tile * 128, stg + s * kExportBox);
+                bulk_commit();
+                // after the tile's last round, W3 goes back into the staging area for the next tile
+                if (a.w3_reload && kc0 + 2 >= nch && tile + (int)gridDim.x < ntiles) {
+                    bulk_wait_read_all();
+                    mbar_expect_tx(f.w3bar, sbuf_bytes(a.ncb, 128));
+                    bulk_g2s(f.W3s.p, a.W3_img, sbuf_bytes(a.ncb, 128), f.w3bar);
+                    f.w3pending = true;
+                }
+            }
         }
     }
-    // drain copies still in flight (only after an early exit) before the shared memory goes away
-    if (tid == 0)
+    // drain copies still in flight before the shared memory goes away
+    if (tid == 0) {
         for (int s = 0; s < 2; ++s)
             if (pending[s]) mbar_wait(mbar + 1 + s, gphase[s]);
+        if (f.w3pending) mbar_wait(f.w3bar, f.w3phase);
+        bulk_wait_all();
+    }
     fence_before();
     __syncthreads();
     fence_after();
     if (tid < 32) tmem_dealloc(tbase, 512);
+}
+
+// W3 [ncb x 128] (fp32) -> its BF16 shared-memory image (the layout load_weights writes).
+__global__ void w3_image_kernel(const float* __restrict__ W3, int ncb, unsigned char* __restrict__ img)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncb * (kH2 / 8); i += gridDim.x * blockDim.x) {
+        const int r = i / (kH2 / 8), c0 = (i % (kH2 / 8)) * 8;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = W3[(size_t)r * kH2 + c0 + j];
+        sbuf_store8(SBuf{img, kH2}, r, c0, v);
+    }
 }
 
 // Codebook S [ncb x dd] (fp32) -> chunked canonical bf16 image: chunk kc holds
@@ -1362,6 +1455,21 @@ le_status export_fused(int32_t P, const float* feat, const le_decoder* d, const 
     if (st != LE_OK) return st;
     const int ncb = d->n_cb;
     unsigned char* img = static_cast<unsigned char*>(ws);
+    unsigned char* w3img = img + (size_t)ncb * dd * 2;
+    // output tensor map: [P rows, dd columns] BF16, boxes of 128 rows x 64 columns, 128-byte swizzle
+    EncodeTiled enc;
+    if ((st = tensor_map_encoder(&enc)) != LE_OK) return st;
+    CUtensorMap tmap;
+    const cuuint64_t dims[2] = {(cuuint64_t)dd, (cuuint64_t)P};
+    const cuuint64_t strides[1] = {(cuuint64_t)dd * 2};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed for the feature map");
+        return LE_ERR_CUDA;
+    }
     codebook_chunks_kernel<<<64, 256, 0, s>>>(codebook, ncb, dd, img);
     LE_LAUNCHED();
     DecArgs a{};
@@ -1372,11 +1480,21 @@ le_status export_fused(int32_t P, const float* feat, const le_decoder* d, const 
     a.G_img = img;
     a.dd = dd;
     a.fmap = out;
+    a.w3_reload = export_stage_in_w3(ncb) ? 1 : 0;
+    if (a.w3_reload && sbuf_bytes(ncb, 128) < 2 * kExportBox) {
+        set_error("feature map export: no shared memory for the output staging with n_cb = %d", ncb);
+        return LE_ERR_UNSUPPORTED;
+    }
+    if (a.w3_reload) {
+        w3_image_kernel<<<16, 256, 0, s>>>(d->W3, ncb, w3img);
+        LE_LAUNCHED();
+        a.W3_img = w3img;
+    }
     const size_t smem = export_smem(ncb);
     if ((st = set_smem(export_fused_kernel, smem)) != LE_OK) return st;
     const int ntiles = (P + 127) / 128;
     const int grid = ntiles < sm_count() ? ntiles : sm_count();
-    export_fused_kernel<<<grid, 128 * kQueryParts, smem, s>>>(a);
+    export_fused_kernel<<<grid, 128 * kQueryParts, smem, s>>>(tmap, a);
     LE_LAUNCHED();
     return LE_OK;
 }
@@ -1388,7 +1506,7 @@ extern "C" le_status le_feature_map_workspace(int32_t n_cb, int32_t d, size_t* b
     LE_TRACE("le_feature_map_workspace");
     LE_CHECK_ARG(bytes != nullptr, "bytes is null");
     LE_CHECK_ARG(n_cb > 0 && d > 0, "bad sizes");
-    *bytes = (size_t)n_cb * d * 2;
+    *bytes = (size_t)n_cb * d * 2 + (size_t)n_cb * 128 * 2;   // codebook image + W3 image
     return LE_OK;
 }
 
@@ -1404,7 +1522,7 @@ extern "C" le_status le_feature_map(int32_t P, const float* feat, const le_decod
         leg::set_error("feature map export needs d to be a positive multiple of 64 (got %d)", d);
         return LE_ERR_UNSUPPORTED;
     }
-    LE_CHECK_ARG(workspace_bytes >= (size_t)dec->n_cb * d * 2, "workspace too small");
+    LE_CHECK_ARG(workspace_bytes >= (size_t)dec->n_cb * d * 2 + (size_t)dec->n_cb * 128 * 2, "workspace too small");
     if (P == 0) return LE_OK;
     return leg::export_fused(P, feat, dec, codebook, d, reinterpret_cast<__nv_bfloat16*>(out), workspace,
                              leg::as_stream(stream));

@@ -776,32 +776,12 @@ __global__ void quant_finalize_kernel(const float* __restrict__ psum, const unsi
         return status;                \
     } while (0)
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-le_status encoder(EncodeTiled* fn)
-{
-    static EncodeTiled cached = nullptr;
-    if (!cached) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult qr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) !=
-                cudaSuccess ||
-            qr != cudaDriverEntryPointSuccess || !p)
-            LE_FAIL(LE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-        cached = reinterpret_cast<EncodeTiled>(p);
-    }
-    *fn = cached;
-    return LE_OK;
-}
-
 // 2-D BF16 tensor [rows, cols] row-major (row stride `stride` elements, default
 // cols; cols = 0 means cols = stride), box [box_rows, 64], 128-byte swizzle.
 le_status make_map(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows, long long stride = 0)
 {
     EncodeTiled fn;
-    le_status st = encoder(&fn);
+    le_status st = tensor_map_encoder(&fn);
     if (st != LE_OK) return st;
     if (stride == 0) stride = cols;
     if (cols == 0) cols = (int)stride;

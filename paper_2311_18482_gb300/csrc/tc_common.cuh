@@ -9,6 +9,7 @@
 // SBO = 128.  In both cases LBO is the stride between core matrices adjacent
 // in K and SBO the one between core matrices adjacent in M/N.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -71,6 +72,24 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(m))
                  : "memory");
 }
+
+// 2-D tensor store shared -> global through the tensor map (TMA), counted in
+// this thread's bulk async-group; elements outside the tensor are not written.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Until this thread's committed bulk stores have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Until this thread's committed bulk stores have completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Warp-wide TMEM allocation; the base address is written to *slot.
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
@@ -270,6 +289,29 @@ __device__ __forceinline__ void sbuf_fill(const SBuf& b, int R, const float* src
         for (int j = 0; j < 8; ++j) v[j] = (r < rs && c0 + j < cs) ? src[(size_t)r * ld + c0 + j] : 0.f;
         sbuf_store8(b, r, c0, v);
     }
+}
+
+// cuTensorMapEncodeTiled from the driver (once per process).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline le_status tensor_map_encoder(EncodeTiled* fn)
+{
+    static EncodeTiled cached = nullptr;
+    if (!cached) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) !=
+                cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess || !p) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return LE_ERR_CUDA;
+        }
+        cached = reinterpret_cast<EncodeTiled>(p);
+    }
+    *fn = cached;
+    return LE_OK;
 }
 
 }  // namespace tc

@@ -150,12 +150,12 @@ def test_fused_train_matches_unfused(leg):
         assert fro(to_np(ga), to_np(gb)) <= {"W3": 2e-2, "b3": 2e-2, "W2": 8e-2, "b2": 8e-2}.get(k, 1e-1), k
 
 
-@pytest.mark.parametrize("P", [5000, 70001])
-def test_fused_query(leg, orc, P):
+@pytest.mark.parametrize("P,ncb", [(5000, 256), (70001, 256), (3001, 64), (2000, 192)])
+def test_fused_query(leg, orc, P, ncb):
     import paper_2311_18482_gb300 as L
-    dec = synth.decoder_init(27, 256)
-    qin = synth.query_inputs(28, 256)
-    feat, _, _ = _inputs(P, 256, 29)
+    dec = synth.decoder_init(27, ncb)
+    qin = synth.query_inputs(28, ncb)
+    feat, _, _ = _inputs(P, ncb, 29)
     rel = L.le_query(L.FUSED_BF16, P, _t(qin.codebook), qin.d_clip, _t(qin.text), _t(qin.negs), feat=_t(feat),
                      dec_t=_dec_t(dec))
     L.le_device_status()
@@ -163,7 +163,7 @@ def test_fused_query(leg, orc, P):
     prob, _ = orc.softmax_argmax(z)
     ref = orc.query(prob, qin)
     err = float(np.max(np.abs(to_np(rel) - ref)))
-    print(f"fused query P={P}: max|drel| {err:.2e}")
+    print(f"fused query P={P} ncb={ncb}: max|drel| {err:.2e}")
     assert err <= 1e-2
 
 
