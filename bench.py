@@ -41,10 +41,11 @@ def parse():
     ap.add_argument("--decoder", default="auto", choices=["auto", "fused", "unfused"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussian count (default: the workload's 1M)")
     ap.add_argument("--no-extras", action="store_true", help="skip the query / unfused comparison legs")
-    ap.add_argument("--only", choices=["quantize", "smooth"], default=None,
+    ap.add_argument("--only", choices=["quantize", "smooth", "query"], default=None,
                     help="run one leg alone (quantize: the quantisation stage on --features rows; smooth: "
-                         "the adaptive smoothing on --n Gaussians)")
-    ap.add_argument("--features", type=int, default=W * H, help="feature rows for --only quantize")
+                         "the adaptive smoothing on --n Gaussians; query: the fused relevancy query and the "
+                         "feature-map export on --features random rendered features, without rendering)")
+    ap.add_argument("--features", type=int, default=W * H, help="feature rows / pixels for --only quantize|query")
     return ap.parse_args()
 
 
@@ -747,6 +748,44 @@ def run_reference(args, rank, world):
                                                   "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def decode_query_leg(leg, synth, args, hbm, kind):
+    """The query's decode + relevancy kernel and the feature-map export alone, on
+    --features pixels of N(0, 1) rendered features (256 codes, 896 dims)."""
+    import torch
+    P = args.features
+    dec = synth.decoder_init(103, 256)
+    qin = synth.query_inputs(303, 256)
+    t = lambda a: torch.from_numpy(a).cuda().contiguous()
+    dec_t = tuple(t(getattr(dec, k)) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    cb, text, negs = t(qin.codebook), t(qin.text), t(qin.negs)
+    feat = torch.randn((8, P), generator=torch.Generator(device="cuda").manual_seed(1), device="cuda")
+    ws = torch.empty(max(leg.le_query_workspace(leg.FUSED_BF16, P, 256, qin.d_clip), 1), dtype=torch.uint8,
+                     device="cuda")
+    rel = torch.empty((4, P), dtype=torch.float32, device="cuda")
+    Fm = torch.empty((P, qin.codebook.shape[1]), dtype=torch.bfloat16, device="cuda")
+    calls = {"query": lambda: leg.le_query(leg.FUSED_BF16, P, cb, qin.d_clip, text, negs, feat=feat, dec_t=dec_t,
+                                           workspace=ws, out=rel),
+             "feature_map": lambda: leg.le_feature_map(feat, dec_t, cb, out=Fm)}
+    res = {"pixels": P}
+    for name, f in calls.items():
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = max(5, args.steps)
+        t0.record()
+        for _ in range(n):
+            f()
+        t1.record()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = round(t0.elapsed_time(t1) / n, 4)
+    leg.le_device_status()
+    byts = P * qin.codebook.shape[1] * 2 + P * 8 * 4
+    res["feature_map_hbm_frac"] = round(byts / res["feature_map_ms"] / 1e6 / hbm, 4)
+    res["peak_kind"] = kind
+    return res
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -762,6 +801,8 @@ def main():
         hbm, bf16, kind = measured_peaks()
         if args.only == "quantize":
             res = quant_leg(leg, synth, args, hbm, bf16, kind)
+        elif args.only == "query":
+            res = decode_query_leg(leg, synth, args, hbm, kind)
         else:
             from paper_2311_18482_gb300.training import TrainState
             c = synth.config("c5", n=args.n)
