@@ -167,6 +167,26 @@ def test_fused_query(leg, orc, P, ncb):
     assert err <= 1e-2
 
 
+def test_fused_query_full_view_sampled(leg, orc):
+    """The query at the full 1296 x 840 view (every CTA runs ~57 tiles, each tile's R_s loaded a tile
+    ahead): 2,048 sampled pixels and the last one against the FP64 oracle."""
+    import paper_2311_18482_gb300 as L
+    P = 1296 * 840
+    dec = synth.decoder_init(41, 256)
+    qin = synth.query_inputs(42, 256)
+    feat, _, _ = _inputs(P, 256, 43)
+    rel = L.le_query(L.FUSED_BF16, P, _t(qin.codebook), qin.d_clip, _t(qin.text), _t(qin.negs), feat=_t(feat),
+                     dec_t=_dec_t(dec))
+    L.le_device_status()
+    idx = np.sort(np.concatenate([np.random.default_rng(44).choice(P - 1, 2048, replace=False), [P - 1]]))
+    got = to_np(rel)[:, idx]
+    prob, _ = orc.softmax_argmax(orc.decoder_fwd(np.ascontiguousarray(feat[:, idx]), dec))
+    ref = orc.query(prob, qin)
+    err = float(np.max(np.abs(got - ref)))
+    print(f"fused query full view, {len(idx)} sampled pixels: max|drel| {err:.2e}")
+    assert err <= 1e-2
+
+
 def test_trained_decoder_argmax_and_gain(leg, orc):
     """Train D_MLP with the fused training kernel + le_adam (lr 1e-3, betas (0.9,
     0.999), Sec. 4) on features drawn around one random 8-dim prototype per

@@ -21,7 +21,11 @@ from test_decoder_tc_gpu import _dec_t, _inputs, _t, bf16, emulate_logits, fro
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("P,ncb,d", [(5000, 256, 896), (131, 128, 896), (1, 64, 128), (3000, 16, 192)])
+# 25,000 pixels are 196 tiles on at most 152 CTAs, so some CTAs run two tiles: with 256 and 240 codes the
+# output staging borrows W3's shared memory and W3 is reloaded between a CTA's tiles; with 192 codes the
+# staging has its own region.
+@pytest.mark.parametrize("P,ncb,d", [(5000, 256, 896), (131, 128, 896), (1, 64, 128), (3000, 16, 192),
+                                     (25000, 256, 896), (25000, 240, 896), (25000, 192, 896)])
 def test_feature_map(leg, orc, P, ncb, d):
     import paper_2311_18482_gb300 as L
     dec = synth.decoder_init(31, ncb)
@@ -55,3 +59,30 @@ def test_feature_map_one_hot(leg, orc):
     torch.cuda.synchronize()
     got = F.to(torch.float32).cpu().numpy()
     assert np.array_equal(got, np.broadcast_to(bf16(S[17]).astype(np.float32), got.shape))
+
+
+def test_feature_map_full_view_sampled(leg, orc):
+    """The full 1296 x 840 view with 256 codes x 896 dims (every CTA runs ~57 tiles, W3 reloaded between
+    them): 1,024 sampled pixels (and the last one) against the emulation and the FP64 oracle, row by row."""
+    import paper_2311_18482_gb300 as L
+    ncb, d, P = 256, 896, 1296 * 840
+    dec = synth.decoder_init(37, ncb)
+    feat, _, _ = _inputs(P, ncb, 38)
+    S = np.random.default_rng(39).standard_normal((ncb, d)).astype(np.float32)
+    F = L.le_feature_map(_t(feat), _dec_t(dec), _t(S))
+    L.le_device_status()
+    idx = np.sort(np.concatenate([np.random.default_rng(40).choice(P - 1, 1024, replace=False), [P - 1]]))
+    got = F[torch.from_numpy(idx).cuda()].to(torch.float32).cpu().numpy().astype(np.float64)
+    del F
+    fs = np.ascontiguousarray(feat[:, idx])
+    z = emulate_logits(fs, dec)
+    e = np.exp(z - z.max(0))
+    emu = bf16(((bf16(e).T @ bf16(S)) / e.sum(0)[:, None]))
+    prob, _ = orc.softmax_argmax(orc.decoder_fwd(fs, dec))
+    ref = orc.feature_map(prob, S)
+    e1, e2 = fro(got, emu), fro(got, ref)
+    rows = np.linalg.norm(got - emu, axis=1) / np.linalg.norm(emu, axis=1)
+    print(f"feature map full view, {len(idx)} sampled pixels: vs emulation {e1:.2e} (worst row {rows.max():.2e}), "
+          f"vs FP64 {e2:.2e}")
+    assert e1 <= 3e-3 and rows.max() <= 1e-2
+    assert e2 <= 2e-2
