@@ -138,36 +138,36 @@ __device__ __forceinline__ void grad_epilogue(const Ctx& c, uint32_t hoff, const
 }
 
 // K-major descriptor of a C-column buffer at shared offset off (rows from 0).
-__device__ __forceinline__ uint64_t kd(const Ctx& c, uint32_t off, int C) { return kdesc_at(c.s0 + off, C, 0, 0); }
+__device__ __forceinline__ uint64_t kd(uint32_t s0, uint32_t off, int C) { return kdesc_at(s0 + off, C, 0, 0); }
 // MN-major descriptor (rows = K) of a C-column buffer.
-__device__ __forceinline__ uint64_t md(const Ctx& c, uint32_t off, int C) { return mndesc_at(c.s0 + off, C, 0, 0); }
+__device__ __forceinline__ uint64_t md(uint32_t s0, uint32_t off, int C) { return mndesc_at(s0 + off, C, 0, 0); }
 
 // One MMA round, issued by thread 0.  K steps of 16 move the start address by
-// 16 units (K-major) or 2C units (MN-major over a C-column buffer).
-__device__ __noinline__ void issue(const Ctx& c, int round, bool first_tile)
+// 16 units (K-major) or 2C units (MN-major over a C-column buffer).  The
+// arguments come by value, so the caller's context stays in registers.
+__device__ __noinline__ void issue(uint32_t s0, uint32_t t, uint64_t* bar, int round, bool first_tile)
 {
     const uint32_t keep = first_tile ? 0u : 1u;
-    const uint32_t t = c.tmem;
     switch (round) {
         case 0:   // H1 pre-activation = X W1^T
-            mma(t + kAcc, kd(c, kOX, 16), kd(c, kOW1, 16), idesc_bf16(kH, false, false), 0u);
+            mma(t + kAcc, kd(s0, kOX, 16), kd(s0, kOW1, 16), idesc_bf16(kH, false, false), 0u);
             break;
         case 1:   // H2 = H1 W2^T
         case 2: { // H3 = H2 W3^T
-            const uint64_t a = kd(c, round == 1 ? kOH1 : kOH2, kH), b = kd(c, round == 1 ? kOW2 : kOW3, kH);
+            const uint64_t a = kd(s0, round == 1 ? kOH1 : kOH2, kH), b = kd(s0, round == 1 ? kOW2 : kOW3, kH);
 #pragma unroll
             for (int k = 0; k < 8; ++k) mma(t + kAcc, a + 16 * k, b + 16 * k, idesc_bf16(kH, false, false), k > 0);
             break;
         }
         case 3: { // Z = H3 W4^T (N = 16, 8 used)
-            const uint64_t a = kd(c, kOH3, kH), b = kd(c, kOW4, kH);
+            const uint64_t a = kd(s0, kOH3, kH), b = kd(s0, kOW4, kH);
 #pragma unroll
             for (int k = 0; k < 8; ++k) mma(t + kAcc, a + 16 * k, b + 16 * k, idesc_bf16(16, false, false), k > 0);
             break;
         }
         case 4: { // dH3 (pre-mask) = dZ W4; dW4^T += H3^T dZ
-            mma(t + kAcc, kd(c, kODZ, 16), md(c, kOW4, kH), idesc_bf16(kH, false, true), 0u);
-            const uint64_t a = md(c, kOH3, kH), b = md(c, kODZ, 16);
+            mma(t + kAcc, kd(s0, kODZ, 16), md(s0, kOW4, kH), idesc_bf16(kH, false, true), 0u);
+            const uint64_t a = md(s0, kOH3, kH), b = md(s0, kODZ, 16);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 mma(t + kDW4, a + 256 * k, b + 32 * k, idesc_bf16(16, true, true), k > 0 ? 1u : keep);
@@ -177,10 +177,10 @@ __device__ __noinline__ void issue(const Ctx& c, int round, bool first_tile)
         case 6: { // dH1 = dH2 W2; dW2 += dH2^T H1; db2 += dH2^T 1
             const uint32_t dh = round == 5 ? kOH3 : kOH2, w = round == 5 ? kOW3 : kOW2, hp = round == 5 ? kOH2 : kOH1;
             const uint32_t dw = round == 5 ? kDW3 : kDW2, db = round == 5 ? kDB3 : kDB2;
-            const uint64_t ak = kd(c, dh, kH), wm = md(c, w, kH);
+            const uint64_t ak = kd(s0, dh, kH), wm = md(s0, w, kH);
 #pragma unroll
             for (int k = 0; k < 8; ++k) mma(t + kAcc, ak + 16 * k, wm + 256 * k, idesc_bf16(kH, false, true), k > 0);
-            const uint64_t am = md(c, dh, kH), hm = md(c, hp, kH), em = md(c, kOE, 16);
+            const uint64_t am = md(s0, dh, kH), hm = md(s0, hp, kH), em = md(s0, kOE, 16);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 mma(t + dw, am + 256 * k, hm + 256 * k, idesc_bf16(kH, true, true), k > 0 ? 1u : keep);
@@ -190,14 +190,14 @@ __device__ __noinline__ void issue(const Ctx& c, int round, bool first_tile)
             break;
         }
         default: { // dW1 (+ db1 in column 3) += dH1^T X
-            const uint64_t am = md(c, kOH1, kH), xm = md(c, kOX, 16);
+            const uint64_t am = md(s0, kOH1, kH), xm = md(s0, kOX, 16);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 mma(t + kDW1, am + 256 * k, xm + 32 * k, idesc_bf16(16, true, true), k > 0 ? 1u : keep);
             break;
         }
     }
-    commit(c.bar);
+    commit(bar);
 }
 
 // Sum over the warp's 32 rows of 16 values (recursive halving); lanes 2j, 2j+1 hold column j.
@@ -295,19 +295,19 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
         uint32_t* m2 = m1 + 4 * 128;
         uint32_t* m3 = m2 + 4 * 128;
         publish();
-        if (threadIdx.x == 0) issue(c, 0, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 0, first);
         if (!(ok = round_wait(c))) break;
         hidden_epilogue(c, b1, kOH1, m1);
         publish();
-        if (threadIdx.x == 0) issue(c, 1, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 1, first);
         if (!(ok = round_wait(c))) break;
         hidden_epilogue(c, b2, kOH2, m2);
         publish();
-        if (threadIdx.x == 0) issue(c, 2, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 2, first);
         if (!(ok = round_wait(c))) break;
         hidden_epilogue(c, b3, kOH3, m3);
         publish();
-        if (threadIdx.x == 0) issue(c, 3, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 3, first);
         if (!(ok = round_wait(c))) break;
         {   // loss and the output gradient
             float z[16];
@@ -335,19 +335,19 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
             db4acc += colsum16(dz, lane);       // lanes 2k, 2k+1: column k (k < 8)
         }
         publish();
-        if (threadIdx.x == 0) issue(c, 4, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 4, first);
         if (!(ok = round_wait(c))) break;
         grad_epilogue(c, kOH3, m3);              // dH3 over H3 (read by dW4, complete)
         publish();
-        if (threadIdx.x == 0) issue(c, 5, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 5, first);
         if (!(ok = round_wait(c))) break;
         grad_epilogue(c, kOH2, m2);              // dH2 over H2
         publish();
-        if (threadIdx.x == 0) issue(c, 6, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 6, first);
         if (!(ok = round_wait(c))) break;
         grad_epilogue(c, kOH1, m1);              // dH1 over H1
         publish();
-        if (threadIdx.x == 0) issue(c, 7, first);
+        if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 7, first);
         if (!(ok = round_wait(c))) break;
     }
     if (!ok) {

@@ -199,6 +199,39 @@ def test_full_size_crop_parity(leg, orc, name):
     assert rel_err(to_np(grads.unc), g2["unc"]) < 1e-4
 
 
+def test_c4_query_render_crop(leg, orc):
+    """The query-render workload (3M Gaussians, 1920x1080, 256 codes x 896 dims): render, then the fused BF16
+    decode and relevancy on the whole view; the FP64 oracle renders the 128x128 centre crop from brute-force
+    tile lists, decodes it and forms the relevancy.  Pixels on an alpha threshold are excluded."""
+    import paper_2311_18482_gb300 as L
+    c = synth.config("c4")
+    sc, cam, dec, qin = c["scene"], c["camera"], c["decoder"], c["query"]
+    g, proj, ids, ranges, K, keys, img = _run(leg, sc, cam)
+    P = cam.W * cam.H
+    dec_t = tuple(_t(getattr(dec, k)) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    rel = L.le_query(L.FUSED_BF16, P, _t(qin.codebook), qin.d_clip, _t(qin.text), _t(qin.negs), feat=img.feat,
+                     dec_t=dec_t)
+    L.le_device_status()
+    kp = orc.keypath(sc, cam)
+    assert K == orc.bin_count(kp)
+    pr = orc.project(sc, cam, kp["tiles"])
+    x0, y0 = (cam.W // 2 - 64) // 16 * 16, (cam.H // 2 - 64) // 16 * 16
+    win = (x0, y0, x0 + 128, y0 + 128)
+    tl = [(tx, ty) for ty in range(y0 // 16, y0 // 16 + 8) for tx in range(x0 // 16, x0 // 16 + 8)]
+    vals, rr = orc.lists_for_tiles(cam, kp, tl)
+    ref = orc.render(cam, sc, pr, vals, rr, win)
+    ok = (ref["flip"] == 0).ravel()
+    assert ok.mean() > 0.95            # 98.7 % here: ~35k Gaussians per crop tile, K = 192.6M copies
+    sub = lambda a: a[..., y0:y0 + 128, x0:x0 + 128].reshape(a.shape[0], -1)
+    assert rel_err(sub(to_np(img.feat))[:, ok], ref["feat"].reshape(8, -1)[:, ok]) < 1e-4
+    prob, _ = orc.softmax_argmax(orc.decoder_fwd(ref["feat"].reshape(8, -1)[:, ok], dec))
+    want = orc.query(prob, qin)
+    got = sub(to_np(rel).reshape(-1, cam.H, cam.W))[:, ok]
+    err = float(np.max(np.abs(got - want)))
+    print(f"c4 query render, {int(ok.sum())} crop pixels: max|drel| {err:.2e}, K = {K}")
+    assert err <= 1e-2
+
+
 def test_l1_and_adam(leg, orc):
     rng = np.random.default_rng(13)
     n = 1003
