@@ -884,10 +884,19 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
     const SBuf Ps{p, a.ncb};
     f.xch = reinterpret_cast<float4*>(p);
     p += sbuf_bytes(128, a.ncb) > kFwdWgBytes ? sbuf_bytes(128, a.ncb) : kFwdWgBytes;
+    // G in 64-column chunks: chunks 0 and 1 stay in their own slots for the whole
+    // kernel; chunks 2 and 3 (n_cb > 128) go into W3's shared memory, which
+    // holds exactly two chunks and is idle from the end of the third layer's
+    // MMAs to the next tile's: they are copied in while the softmax runs, and
+    // W3 is copied back (from its global image) while the relevancy and the
+    // next tile's first two layers run, so no copy is on the tile's path.
     const uint32_t chunk_bytes = sbuf_bytes(a.ncb, 64);
-    const SBuf Gs[2] = {SBuf{p, 64}, SBuf{p + chunk_bytes, 64}};
+    unsigned char* const g_own = p;
+    auto g_chunk = [&](int kc) {
+        return SBuf{kc < 2 ? g_own + kc * chunk_bytes : f.W3s.p + (kc - 2) * chunk_bytes, 64};
+    };
     p += 2 * chunk_bytes;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);     // [0] MMA, [1], [2] G slots
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);     // [0] MMA, [1] chunks 0-1, [2] chunks 2-3, [4] W3
     uint32_t* slot = reinterpret_cast<uint32_t*>(p + 24);
     const int tid = threadIdx.x;
     sbuf_fill(Aqs, 16, a.Aq, a.ncb, 16, a.ncb);
@@ -898,8 +907,11 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
     f.nthreads = blockDim.x;
     f.half = tid >> 7;
     f.nhalf = kQueryParts;
-    if (tid == 0)
+    f.w3bar = mbar + 4;
+    if (tid == 0) {
         for (int i = 0; i < 3; ++i) mbar_init(mbar + i, 1);
+        mbar_init(mbar + 4, 1);
+    }
     if (tid < 32) tmem_alloc(slot, 512);
     fence_proxy_async();
     fence_before();
@@ -912,23 +924,29 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
     int c0, c1;
     my_cols(f, a.ncb, c0, c1);                  // this part's class columns
     const int nch = a.ncb / 64;                 // G chunks (64 K-columns each)
-    uint32_t gphase[2] = {0u, 0u};
-    bool pending[2] = {false, false};          // a load into the slot is in flight (thread 0 only)
-    auto load_chunk = [&](int kc, int s) {
-        mbar_expect_tx(mbar + 1 + s, chunk_bytes);
-        bulk_g2s(Gs[s].p, a.G_img + (size_t)kc * chunk_bytes, chunk_bytes, mbar + 1 + s);
-        pending[s] = true;
-    };
+    const int nlow = nch < 2 ? nch : 2, nup = nch - nlow;
+    // loads in flight (thread 0 only): chunks 0-1 (once), chunks 2-3 (per tile)
+    bool low_pending = false, up_pending = false;
+    uint32_t up_phase = 0u;
     const int ntiles = (a.P + 127) / 128;
     bool ok = true;
-    if (tid == 0 && blockIdx.x < ntiles)
-        for (int s = 0; s < 2 && s < nch; ++s) load_chunk(s, s);
+    if (tid == 0 && blockIdx.x < ntiles) {
+        mbar_expect_tx(mbar + 1, nlow * chunk_bytes);
+        bulk_g2s(g_own, a.G_img, nlow * chunk_bytes, mbar + 1);
+        low_pending = true;
+    }
     float xf[8];                                // this tile's R_s, loaded a tile ahead (part 0)
     if (f.half == 0) load_feat(a, blockIdx.x * 128 + row, blockIdx.x * 128 + row < a.P, xf);
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int px = tile * 128 + row;
         const bool valid = px < a.P;
         if (!mlp_forward_x(f, a, xf)) break;
+        // the third layer's MMAs have read W3: chunks 2-3 of G take its place
+        if (tid == 0 && nup > 0) {
+            mbar_expect_tx(mbar + 2, nup * chunk_bytes);
+            bulk_g2s(f.W3s.p, a.G_img + 2 * (size_t)chunk_bytes, nup * chunk_bytes, mbar + 2);
+            up_pending = true;
+        }
         if (f.half == 0) {
             const int nx = px + 128 * (int)gridDim.x;
             load_feat(a, nx, tile + (int)gridDim.x < ntiles && nx < a.P, xf);
@@ -957,39 +975,37 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
             sbuf_store8(Ps, row, c + 8, v + 8);
         }
         wg_publish(f);
-        // p . (S_c [q; n]) into [0, 16), p^T G into [256, 256 + ncb), G chunk by chunk
+        // p . (S_c [q; n]) into [0, 16), p^T G into [256, 256 + ncb), all chunks in one round
         bool tmo = false;
-        for (int kc0 = 0; kc0 < nch; kc0 += 2) {
-            if (tid == 0) {
-                if (kc0 == 0)
-                    for (int s = 0; s < a.ncb / 16; ++s)
-                        mma(tbase, kdesc(Ps, 0, 16 * s), kdesc(Aqs, 0, 16 * s), idesc_bf16(16, false, false), s > 0);
-                for (int s = 0; s < 2 && kc0 + s < nch; ++s) {
-                    if (!mbar_wait(mbar + 1 + s, gphase[s])) tmo = true;
-                    gphase[s] ^= 1u;
-                    pending[s] = false;
-                    for (int k = 0; k < 4; ++k)
-                        mma(tbase + kTG, kdesc(Ps, 0, 64 * (kc0 + s) + 16 * k), kdesc(Gs[s], 0, 16 * k),
-                            idesc_bf16(a.ncb, false, false), (kc0 + s) > 0 || k > 0);
+        if (tid == 0) {
+            for (int s = 0; s < a.ncb / 16; ++s)
+                mma(tbase, kdesc(Ps, 0, 16 * s), kdesc(Aqs, 0, 16 * s), idesc_bf16(16, false, false), s > 0);
+            if (low_pending) {
+                if (!mbar_wait(mbar + 1, 0u)) tmo = true;
+                low_pending = false;
+            }
+            for (int kc = 0; kc < nch; ++kc) {
+                if (kc == 2) {
+                    if (!mbar_wait(mbar + 2, up_phase)) tmo = true;
+                    up_phase ^= 1u;
+                    up_pending = false;
                 }
-                commit(f.mbar);
+                for (int k = 0; k < 4; ++k)
+                    mma(tbase + kTG, kdesc(Ps, 0, 64 * kc + 16 * k), kdesc(g_chunk(kc), 0, 16 * k),
+                        idesc_bf16(a.ncb, false, false), kc > 0 || k > 0);
             }
-            if (!wg_wait(f) || bar_any(0, blockDim.x, tmo)) {
-                if (tid == 0) atomicExch(&g_tc_error, 1);
-                ok = false;
-                break;
-            }
-            // refill the slots: the next chunk pair of this tile, or the first pair of the next tile
-            if (tid == 0) {
-                const bool more = kc0 + 2 < nch;
-                const bool next_tile = tile + (int)gridDim.x < ntiles;
-                for (int s = 0; s < 2; ++s) {
-                    const int kc = more ? kc0 + 2 + s : s;
-                    if ((more && kc < nch) || (!more && next_tile && kc < nch)) load_chunk(kc, s);
-                }
-            }
+            commit(f.mbar);
         }
-        if (!ok) break;
+        if (!wg_wait(f) || bar_any(0, blockDim.x, tmo)) {
+            if (tid == 0) atomicExch(&g_tc_error, 1);
+            break;
+        }
+        // the G MMAs are done with W3's shared memory: W3 goes back for the next tile
+        if (tid == 0 && nup > 0 && tile + (int)gridDim.x < ntiles) {
+            mbar_expect_tx(f.w3bar, sbuf_bytes(a.ncb, 128));
+            bulk_g2s(f.W3s.p, a.W3_img, sbuf_bytes(a.ncb, 128), f.w3bar);
+            f.w3pending = true;
+        }
         // relevancy: each part sums e^T G e over its columns into TMEM column 16 + part
         float ptgp = 0.f, pp[16];
         for (int c = c0; c < c1; c += 16) {
@@ -1026,9 +1042,11 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
         __syncthreads();
     }
     // drain copies still in flight (only after an early exit) before the shared memory goes away
-    if (tid == 0)
-        for (int s = 0; s < 2; ++s)
-            if (pending[s]) mbar_wait(mbar + 1 + s, gphase[s]);
+    if (tid == 0) {
+        if (low_pending) mbar_wait(mbar + 1, 0u);
+        if (up_pending) mbar_wait(mbar + 2, up_phase);
+        if (f.w3pending) mbar_wait(f.w3bar, f.w3phase);
+    }
     fence_before();
     __syncthreads();
     fence_after();
@@ -1404,6 +1422,7 @@ le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_
     return LE_OK;
 }
 
+// [n_cb x n_cb] FP32 (its first n_cb x 256 bytes hold W3's image), Aq, G's BF16 image.
 size_t query_fused_workspace(int32_t, int32_t n_cb, int32_t)
 {
     return align_up(sizeof(float) * n_cb * n_cb, 256) + align_up(sizeof(float) * 16 * n_cb, 256) +
@@ -1429,12 +1448,19 @@ le_status query_fused(int32_t P, const float* feat, const le_decoder* d, const f
     query_prep_kernel<<<dim3(ncb / 16, ncb / 16 + 1), 256, 0, s>>>(codebook, ncb, dd, d_clip, text, Q, negs, n_neg,
                                                                    img, Aq);
     LE_LAUNCHED();
+    // W3's shared-memory image, reloaded after each tile when G's chunks 2-3 borrow its place (n_cb > 128)
+    unsigned char* w3img = reinterpret_cast<unsigned char*>(w);
+    if (ncb > 128) {
+        w3_image_kernel<<<16, 256, 0, s>>>(d->W3, ncb, w3img);
+        LE_LAUNCHED();
+    }
     DecArgs a{};
     a.P = P;
     a.ncb = ncb;
     a.feat = feat;
     a.W1 = d->W1; a.b1 = d->b1; a.W2 = d->W2; a.b2 = d->b2; a.W3 = d->W3; a.b3 = d->b3;
     a.G_img = img;
+    a.W3_img = w3img;
     a.Aq = Aq;
     a.Q = Q;
     a.n_neg = n_neg;

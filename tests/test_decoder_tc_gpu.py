@@ -150,7 +150,7 @@ def test_fused_train_matches_unfused(leg):
         assert fro(to_np(ga), to_np(gb)) <= {"W3": 2e-2, "b3": 2e-2, "W2": 8e-2, "b2": 8e-2}.get(k, 1e-1), k
 
 
-@pytest.mark.parametrize("P,ncb", [(5000, 256), (70001, 256), (3001, 64), (2000, 192)])
+@pytest.mark.parametrize("P,ncb", [(5000, 256), (70001, 256), (3001, 64), (2000, 192), (30000, 192), (30000, 128)])
 def test_fused_query(leg, orc, P, ncb):
     import paper_2311_18482_gb300 as L
     dec = synth.decoder_init(27, ncb)
