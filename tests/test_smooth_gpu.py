@@ -104,21 +104,25 @@ def test_smooth_vs_bf16_emulation_and_oracle(leg, orc, n):
         assert _rel(got["d" + k], ref["d" + k]) <= bars[k], k
 
 
-def test_smooth_accumulates_into_strided_records(leg, orc):
-    """d_feat is added into the feature slots of 20-float records (grad2d + 10, stride 20)."""
+# (offset, stride) in floats: grad2d's feature slots (8-byte aligned rows), an odd offset (4-byte
+# aligned rows), a 16-byte aligned strided layout
+@pytest.mark.parametrize("off,stride", [(10, 20), (9, 20), (12, 24)])
+def test_smooth_accumulates_into_strided_records(leg, orc, off, stride):
+    """d_feat is added into the feature slots of strided records (grad2d + 10, stride 20, in training)."""
     n = 3000
     mlp, means, feat, unc = _inputs(n, 90)
     c = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     params = {k: c(getattr(mlp, k)) for k in KEYS}
-    rec = torch.randn((n, 20), device="cuda")
+    rec = torch.randn((n, stride), device="cuda")
     before = rec.clone()
-    loss, _, grads, _ = leg.le_smooth(c(means), c(feat), c(unc), params, d_feat=rec[:, 10:], d_feat_stride=20)
+    loss, _, grads, _ = leg.le_smooth(c(means), c(feat), c(unc), params, d_feat=rec[:, off:],
+                                      d_feat_stride=stride)
     dense = _run(leg, mlp, means, feat, unc)
     torch.cuda.synchronize()
-    assert torch.equal(rec[:, :10], before[:, :10]) and torch.equal(rec[:, 18:], before[:, 18:])
+    assert torch.equal(rec[:, :off], before[:, :off]) and torch.equal(rec[:, off + 8:], before[:, off + 8:])
     # rec = before + d_feat element by element (one FP32 rounding of the sum, at most a
     # couple of ulps of `before` away from adding the dense result afterwards)
-    expect = before[:, 10:18].cpu().numpy().astype(np.float64) + dense["d_feat"]
-    got = rec[:, 10:18].cpu().numpy().astype(np.float64)
+    expect = before[:, off:off + 8].cpu().numpy().astype(np.float64) + dense["d_feat"]
+    got = rec[:, off:off + 8].cpu().numpy().astype(np.float64)
     assert np.abs(got - expect).max() <= 2.5e-7 * np.abs(expect).max()
     assert np.abs(dense["d_feat"]).max() > 1e-5
