@@ -31,7 +31,6 @@
 // Every mbarrier wait is bounded (about a second); on timeout the kernel
 // records it in g_tc_error, stops issuing work, frees its TMEM and returns.
 #include "tc_common.cuh"
-#include "gemm_fp32.cuh"
 
 namespace leg {
 
@@ -1422,11 +1421,10 @@ le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_
     return LE_OK;
 }
 
-// [n_cb x n_cb] FP32 (its first n_cb x 256 bytes hold W3's image), Aq, G's BF16 image.
+// W3's BF16 shared-memory image [n_cb x 128], Aq [16 x n_cb] FP32, G's BF16 image [n_cb x n_cb].
 size_t query_fused_workspace(int32_t, int32_t n_cb, int32_t)
 {
-    return align_up(sizeof(float) * n_cb * n_cb, 256) + align_up(sizeof(float) * 16 * n_cb, 256) +
-           align_up(2ull * n_cb * n_cb, 256);
+    return align_up(256ull * n_cb, 256) + align_up(sizeof(float) * 16 * n_cb, 256) + align_up(2ull * n_cb * n_cb, 256);
 }
 
 le_status query_fused(int32_t P, const float* feat, const le_decoder* d, const float* codebook, int32_t dd,
@@ -1441,15 +1439,15 @@ le_status query_fused(int32_t P, const float* feat, const le_decoder* d, const f
         return LE_ERR_UNSUPPORTED;
     }
     char* w = static_cast<char*>(ws);
-    float* Aq = reinterpret_cast<float*>(w + align_up(sizeof(float) * ncb * ncb, 256));
-    unsigned char* img = reinterpret_cast<unsigned char*>(w + align_up(sizeof(float) * ncb * ncb, 256) +
+    unsigned char* w3img = reinterpret_cast<unsigned char*>(w);
+    float* Aq = reinterpret_cast<float*>(w + align_up(256ull * ncb, 256));
+    unsigned char* img = reinterpret_cast<unsigned char*>(w + align_up(256ull * ncb, 256) +
                                                           align_up(sizeof(float) * 16 * ncb, 256));
     // G = S_c S_c^T (as the BF16 image) and Aq = [text; negs] S_c^T, FP32 on CUDA cores, one launch
     query_prep_kernel<<<dim3(ncb / 16, ncb / 16 + 1), 256, 0, s>>>(codebook, ncb, dd, d_clip, text, Q, negs, n_neg,
                                                                    img, Aq);
     LE_LAUNCHED();
     // W3's shared-memory image, reloaded after each tile when G's chunks 2-3 borrow its place (n_cb > 128)
-    unsigned char* w3img = reinterpret_cast<unsigned char*>(w);
     if (ncb > 128) {
         w3_image_kernel<<<16, 256, 0, s>>>(d->W3, ncb, w3img);
         LE_LAUNCHED();
