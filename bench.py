@@ -279,6 +279,7 @@ def run_ours(args, rank, world):
     clocks.start()
     leg.reset_launch_count()
     st.events = []
+    torch.cuda.reset_peak_memory_stats()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     Ks = []
     t0.record()
@@ -290,6 +291,7 @@ def run_ours(args, rank, world):
     barrier()
     launches = leg.launch_count()
     clk = clocks.stop()
+    peak_alloc, peak_reserved = torch.cuda.max_memory_allocated(), torch.cuda.max_memory_reserved()
     ms = t0.elapsed_time(t1)
     stage_ms = {}
     evs = st.events
@@ -332,7 +334,11 @@ def run_ours(args, rank, world):
                       "l2": "inputs larger than L2 (272 MB of parameters + 2.2 GB of state per step)"},
            "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12},
            "gpu_launches": launches, "clocks": clk, "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-           "instances_K": K_mean}
+           "instances_K": K_mean,
+           "peak_hbm": {"allocated_gb": round(peak_alloc / 1e9, 3), "reserved_gb": round(peak_reserved / 1e9, 3),
+                        "note": "device memory in use over the timed steps (torch's caching allocator): the "
+                                "Gaussians and their Adam moments, the 16 views' targets and every step buffer; "
+                                "the library allocates none itself"}}
     # (instances_read is added with the roofline below)
 
     # --- roofline of the dominant kernel (render_bwd_kernel, FP32-ALU bound):
@@ -408,11 +414,13 @@ def compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, arg
     res = {}
     for name, mode in (("fused", leg.FUSED_BF16), ("unfused", leg.UNFUSED_FP32)):
         try:
+            before = torch.cuda.memory_allocated()
             s2 = st if name == mode_name else make_state(mode)
             s2.events = []
             for i in range(3):
                 s2.step(cams[i], rgb_dev[i], idx_dev[i])
             torch.cuda.synchronize()
+            torch.cuda.reset_peak_memory_stats()
             s2.events = []
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0.record()
@@ -426,6 +434,9 @@ def compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, arg
             s2.events = None
             res[name] = {"step_ms": round(t0.elapsed_time(t1) / n, 4),
                          "decoder_ms": round(sum(dec_ms) / len(dec_ms), 4)}
+            if s2 is not st:
+                # device memory this path needs on top of what was already in use
+                res[name]["extra_peak_hbm_gb"] = round((torch.cuda.max_memory_allocated() - before) / 1e9, 3)
         except leg.LegError as e:
             res[name] = {"unavailable": str(e)[:200]}
     return res
