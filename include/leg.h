@@ -175,8 +175,11 @@ le_status le_bin_sort(const le_camera* cam, int32_t n, const float* depth, const
  *   tile copies (k_cap is clamped to it).  Larger n -> LE_ERR_INVALID_ARG;
  *   more copies -> LE_ERR_CAPACITY with *k_out = K and a message naming the
  *   limit.  Inputs and outputs are those of le_bin_sort.
- *   The first call on a device looks up the array's device address with that
- *   device current; make that first call before any stream capture.
+ *   Every call looks up the array's device address in the calling thread's
+ *   current context (the first call on a device also loads this library's
+ *   module there), so a call made after cudaDeviceReset, or with another
+ *   context current, uses that context's array.  Like le_bin_sort, it
+ *   synchronizes `stream` once to read K.
  *   All calls share the one array, which keeps the last call's contents (every
  *   scratch word is rewritten before it is read, so nothing needs clearing):
  *   calls whose GPU work overlaps -- on different streams or host threads --

@@ -404,10 +404,12 @@ def densify_thresholds(grad_thresh, percent_dense, extent, min_opacity):
     return (np.float32(grad_thresh), np.float32(math.log(pd * ex)), np.float32(math.log(mo / (1.0 - mo))))
 
 
-def densify_stats(grad2d, radius, acc, cnt):
-    """In place: acc [n] float32, cnt [n] int32 (adaptive density control statistics)."""
-    g = _f32(grad2d)
+def densify_stats(grad_mean2d, radius, acc, cnt):
+    """In place: acc [n] float32 += |dL/dmean2d|, cnt [n] int32 += 1 for every Gaussian
+    with radius > 0 (adaptive density control statistics).  grad_mean2d: [n, 2]."""
+    g = _f32(grad_mean2d)
     r = np.ascontiguousarray(radius, np.int32)
+    assert g.shape == (len(r), 2), g.shape
     assert acc.dtype == np.float32 and cnt.dtype == np.int32
     lib().orc_densify_stats(C.c_int(len(r)), _p(g), _p(r), _p(acc), _p(cnt))
 

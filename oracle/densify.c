@@ -59,12 +59,15 @@ int64_t orc_densify_plan(int n, const float* log_scales, const float* opacity_ra
 }
 
 /* Per-step statistics: acc_i += |(g_x, g_y)| = sqrt(g_x g_x + g_y g_y) (FP32,
- * in this order), cnt_i += 1, for every Gaussian with radius_i > 0. */
-void orc_densify_stats(int n, const float* grad2d, const int32_t* radius, float* acc, int32_t* cnt)
+ * in this order), cnt_i += 1, for every Gaussian with radius_i > 0 (a Gaussian
+ * outside the view has radius 0 and no screen-space gradient to count).
+ * grad_mean2d: [n][2], the gradient of the loss with respect to each
+ * Gaussian's projected mean in pixels. */
+void orc_densify_stats(int n, const float* grad_mean2d, const int32_t* radius, float* acc, int32_t* cnt)
 {
     for (int i = 0; i < n; ++i) {
         if (radius[i] <= 0) continue;
-        const float gx = grad2d[20 * (size_t)i], gy = grad2d[20 * (size_t)i + 1];
+        const float gx = grad_mean2d[2 * (size_t)i], gy = grad_mean2d[2 * (size_t)i + 1];
         acc[i] += sqrtf(gx * gx + gy * gy);
         cnt[i] += 1;
     }

@@ -333,12 +333,17 @@ def le_bin_sort(cam, proj: Projected, buffers: BinSortBuffers | None = None, k_c
 
 def le_bin_sort_static(cam, proj: Projected, sorted_ids, tile_ranges, sorted_keys=None):
     """le_bin_sort with the library's static scratch (no workspace; see leg.h).
-    The caller provides the outputs; returns K."""
+    The caller provides the outputs; returns K.  On LE_ERR_CAPACITY the raised
+    LegError carries the instance count the call reported as `.k`."""
     K = C.c_int64()
-    _check(load().le_bin_sort_static(C.byref(camera_struct(cam)), proj.depth.shape[0], _ptr(proj.depth),
-                                     _ptr(proj.rect), _ptr(proj.tile_ellipse), _ptr(proj.tiles_touched),
-                                     sorted_ids.numel(),
-                                     _ptr(sorted_ids), _ptr(sorted_keys), _ptr(tile_ranges), C.byref(K), _stream()))
+    st = load().le_bin_sort_static(C.byref(camera_struct(cam)), proj.depth.shape[0], _ptr(proj.depth),
+                                   _ptr(proj.rect), _ptr(proj.tile_ellipse), _ptr(proj.tiles_touched),
+                                   sorted_ids.numel(),
+                                   _ptr(sorted_ids), _ptr(sorted_keys), _ptr(tile_ranges), C.byref(K), _stream())
+    if st != LE_OK:
+        err = LegError(st, load().le_last_error().decode())
+        err.k = K.value
+        raise err
     return K.value
 
 

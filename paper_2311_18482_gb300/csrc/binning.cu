@@ -23,8 +23,6 @@
 //      row, one lane per 32nd tile of the row).
 // Only the depth sort's look-back waits on other blocks (bounded, see
 // onesweep_kernel).
-#include <mutex>
-
 #include "common.cuh"
 
 namespace leg {
@@ -921,27 +919,21 @@ constexpr int64_t kStaticMaxK = LE_STATIC_MAX_INSTANCES;
 
 __device__ __align__(256) unsigned char g_static_scratch[sort_ws_bytes(kStaticMaxN)];
 
-// Device address of g_static_scratch per device, looked up on the first call
-// made with that device current.
-std::mutex g_static_mu;
-void* g_static_ptr[256] = {};
-
+// Device address of g_static_scratch in the calling thread's current context.
+// It is looked up on every call rather than cached: a cache keyed by device
+// would outlive the context (cudaDeviceReset, or another context made current
+// on that device) and hand a later call a dangling address.  After the first
+// call on a device has loaded this library's module the lookup is a host-side
+// table query, small next to the stream synchronisation every call makes.
 le_status static_scratch(void** out)
 {
-    int dev = 0;
-    LE_CUDA(cudaGetDevice(&dev));
-    LE_CHECK_ARG(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (g_static_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            set_error("cudaGetSymbolAddress(static scratch) failed: %s", cudaGetErrorString(e));
-            return LE_ERR_CUDA;
-        }
-        g_static_ptr[dev] = p;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        set_error("cudaGetSymbolAddress(static scratch) failed: %s", cudaGetErrorString(e));
+        return LE_ERR_CUDA;
     }
-    *out = g_static_ptr[dev];
+    *out = p;
     return LE_OK;
 }
 

@@ -1342,15 +1342,15 @@ __global__ void selftest_wait_kernel()
     if (threadIdx.x == 0 && !mbar_wait(&bar, 0u)) atomicExch(&g_tc_error, 1);
 }
 
+// SM count of the calling thread's current device, read on every launch (a
+// cheap attribute query), so a process driving parts of different sizes gets
+// each one's own persistent grid.
 int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        n = 1;
     return n;
 }
 

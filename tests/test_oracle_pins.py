@@ -853,6 +853,42 @@ def test_ssim_gradient_fd(orc):
 # ---------------------------------------------------------------------------
 # Adaptive density control (3DGS's clone / split / prune, kept by Sec. 4)
 
+def test_densify_stats_hand_case(orc):
+    """Two steps of the statistics on three Gaussians, worked by hand: 3-4-5 and
+    6-8-10 triangles give exact FP32 norms; a Gaussian with radius 0 (outside
+    the view) is neither accumulated nor counted.  Accumulating |g|^2, only one
+    component, or counting radius-0 Gaussians each changes an entry."""
+    acc = np.zeros(3, np.float32)
+    cnt = np.zeros(3, np.int32)
+    orc.densify_stats(np.array([[3, 4], [0.5, -1.25], [6, 8]], np.float32), np.array([2, 0, 1]), acc, cnt)
+    assert acc.tolist() == [5.0, 0.0, 10.0] and cnt.tolist() == [1, 0, 1]
+    orc.densify_stats(np.array([[-6, -8], [1, 1], [5, 12]], np.float32), np.array([1, 5, 0]), acc, cnt)
+    assert acc.tolist() == [15.0, float(np.float32(np.sqrt(np.float32(2)))), 10.0]
+    assert cnt.tolist() == [2, 1, 1]
+
+
+def test_densify_stats_vs_hypot(orc):
+    """Three steps on random gradients against numpy's hypot summed in FP64: the
+    oracle's FP32 norm and sum stay within a few FP32 roundings of it."""
+    rng = np.random.default_rng(83)
+    n = 20000
+    acc = np.zeros(n, np.float32)
+    cnt = np.zeros(n, np.int32)
+    ref = np.zeros(n)
+    ref_cnt = np.zeros(n, np.int64)
+    for _ in range(3):
+        g = (rng.standard_normal((n, 2)) * 10.0 ** rng.uniform(-6, 0, (n, 1))).astype(np.float32)
+        rad = rng.integers(0, 3, n).astype(np.int32)
+        orc.densify_stats(g, rad, acc, cnt)
+        vis = rad > 0
+        ref[vis] += np.hypot(g[vis, 0].astype(np.float64), g[vis, 1].astype(np.float64))
+        ref_cnt[vis] += 1
+    assert np.array_equal(cnt, ref_cnt)
+    err = np.abs(acc.astype(np.float64) - ref)
+    assert np.all(err <= 4 * 2.0 ** -24 * ref + 1e-30), err.max()
+    assert np.all((ref == 0) == (acc == 0))
+
+
 def _densify_inputs(n, seed):
     rng = np.random.default_rng(seed)
     P = {"means": rng.uniform(-1, 1, (n, 3)).astype(np.float32),

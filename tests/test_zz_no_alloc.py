@@ -1,11 +1,16 @@
 """le_bin_sort_static: the binning entry point for callers that cannot
-allocate device memory (its scratch is a static array inside the library).
+allocate device memory -- code that runs inside a host application or plugin
+whose device memory belongs to someone else, or a per-frame path that cannot
+take cudaMalloc's implicit synchronisation.  Its scratch is a static array
+inside the library.
 
 Two calls in a row, through the C ABI, on different scenes: each must give
 exactly the sorted ids, 64-bit keys, tile ranges and K of le_bin_sort with a
 caller workspace (binning is integer work, so the bar is bit-exactness).  The
 second call also shows that what the first left in the shared array does not
-leak into it.  This file is named to be collected last.
+leak into it.  A repeated call is checked to take no device memory: neither
+PyTorch's allocator nor the driver's free-memory count moves across it.  This
+file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -24,7 +29,6 @@ def _project(leg, name, **kw):
 
 
 def test_static_scratch_matches_workspace_path(leg):
-    import paper_2311_18482_gb300.binding as B
     for name, kw in (("c2", dict(n=20000, W=320, H=240)), ("c1", {})):
         cam, proj = _project(leg, name, **kw)
         ids_ws, ranges_ws, K_ws, keys_ws = leg.le_bin_sort(cam, proj, want_keys=True)
@@ -42,6 +46,24 @@ def test_static_scratch_matches_workspace_path(leg):
         assert torch.equal(ranges, ranges_ws)
 
 
+def test_static_scratch_allocates_nothing(leg):
+    cam, proj = _project(leg, "c2", n=20000, W=320, H=240)
+    _, _, K_ws, _ = leg.le_bin_sort(cam, proj)
+    ids = torch.empty(K_ws, dtype=torch.int32, device="cuda")
+    ranges = torch.empty((cam.tiles_x * cam.tiles_y, 2), dtype=torch.int32, device="cuda")
+    assert leg.le_bin_sort_static(cam, proj, ids, ranges) == K_ws   # warm-up: module and kernels loaded
+    torch.cuda.synchronize()
+    first = ids.clone()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    K = leg.le_bin_sort_static(cam, proj, ids, ranges)
+    torch.cuda.synchronize()
+    alloc1, free1 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    assert K == K_ws and torch.equal(ids, first)
+    assert alloc1 == alloc0
+    assert free1 == free0, (free0, free1)
+    del first
+
+
 def test_static_scratch_limits(leg):
     import paper_2311_18482_gb300.binding as B
     # more Gaussians than the static limit: rejected before any work
@@ -51,12 +73,14 @@ def test_static_scratch_limits(leg):
     with pytest.raises(B.LegError) as e:
         leg.le_bin_sort_static(cam, proj, ids, ranges)
     assert e.value.status == B.LE_ERR_INVALID_ARG
-    # a capacity smaller than K: LE_ERR_CAPACITY, K still reported
+    # a capacity smaller than K: LE_ERR_CAPACITY, and K is still reported
     cam, proj = _project(leg, "c1")
+    _, _, K_ws, _ = leg.le_bin_sort(cam, proj)
     ranges = torch.empty((cam.tiles_x * cam.tiles_y, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(B.LegError) as e:
         leg.le_bin_sort_static(cam, proj, ids, ranges)
     assert e.value.status == B.LE_ERR_CAPACITY
+    assert e.value.k == K_ws > ids.numel()
 
 
 def B_MAX_N():
