@@ -405,6 +405,7 @@ def run_ours(args, rank, world):
     if not args.no_extras and rank == 0:
         out["fused_vs_plain"] = compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, args)
         out["query"] = query_leg(leg, synth, scene, cams, args)
+        out["query_c4"] = query_c4_leg(leg, synth, args)
         out["quantize"] = quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind)
         out["smooth"] = smooth_leg(leg, synth, st, args, bf16_peak)
         out["rgb_dssim"] = rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak)
@@ -448,12 +449,12 @@ def compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, arg
     return res
 
 
-def query_leg(leg, synth, scene, cams, args):
-    """Query render at the same 1M Gaussians / 1296x840: preprocess, bin, render,
-    decode to the 256-entry codebook, relevancy (fused if available)."""
+def query_leg(leg, synth, scene, cams, args, Wq=W, Hq=H, dec=None, qin=None):
+    """Query render: preprocess, bin, render, decode to the 256-entry codebook of
+    896-dim entries, relevancy for 4 prompts / 4 negatives (fused and unfused)."""
     import torch
-    qin = synth.query_inputs(303, 256)
-    dec = synth.decoder_init(103, 256)
+    qin = qin or synth.query_inputs(303, 256)
+    dec = dec or synth.decoder_init(103, 256)
     dev = "cuda"
     t = lambda a: torch.from_numpy(a).to(dev).contiguous()
     dec_t = tuple(t(getattr(dec, k)) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
@@ -461,8 +462,8 @@ def query_leg(leg, synth, scene, cams, args):
     g = leg.Gaussians.from_scene(scene)
     proj = leg.Projected.empty(scene.N)
     bins = leg.BinSortBuffers()
-    img = leg.Image.empty(H, W)
-    P = W * H
+    img = leg.Image.empty(Hq, Wq)
+    P = Wq * Hq
     res = {}
     for name, mode in (("fused", leg.FUSED_BF16), ("unfused", leg.UNFUSED_FP32)):
         try:
@@ -486,18 +487,21 @@ def query_leg(leg, synth, scene, cams, args):
                     leg.le_query(mode, P, cb, qin.d_clip, text, negs, feat=img.feat, dec_t=dec_t, workspace=ws_q,
                                  out=rel)
             for i in range(3):
-                once(i)
+                once(i % len(cams))
             torch.cuda.synchronize()
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             n = max(5, args.steps // 2)
             t0.record()
             for i in range(n):
-                once(i % N_VIEWS)
+                once(i % len(cams))
             t1.record()
             torch.cuda.synchronize()
             res[name] = {"ms_per_query_render": round(t0.elapsed_time(t1) / n, 4)}
+            del prob, ws_q, ws_d
         except leg.LegError as e:
             res[name] = {"unavailable": str(e)[:200]}
+    if Wq != W or Hq != H:
+        return res
     # the materialised language feature map F = M_infer S (BF16, [P, 896]) of the last render
     try:
         Fm = torch.empty((P, qin.codebook.shape[1]), dtype=torch.bfloat16, device=dev)
@@ -518,6 +522,19 @@ def query_leg(leg, synth, scene, cams, args):
                               "peak_kind": kind, "note": "le_feature_map: decode + softmax + F = p S, BF16 out"}
     except leg.LegError as e:
         res["feature_map"] = {"unavailable": str(e)[:200]}
+    return res
+
+
+def query_c4_leg(leg, synth, args):
+    """The query-render workload at its own size: 3M Gaussians (50 clusters) at
+    1920x1080, pose 0, decode to 256 codes of 896 dims, relevancy for 4 prompts /
+    4 negatives; the same view every iteration."""
+    import torch
+    c = synth.config("c4")
+    res = query_leg(leg, synth, c["scene"], [c["camera"]], args, Wq=c["camera"].W, Hq=c["camera"].H,
+                    dec=c["decoder"], qin=c["query"])
+    res["workload"] = "c4: 3M Gaussians, 1920x1080, 256 codes x 896 dims, 4 prompts + 4 negatives"
+    torch.cuda.empty_cache()
     return res
 
 
@@ -581,17 +598,20 @@ def rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak):
 def densify_leg(leg, st, args, hbm_peak):
     """Adaptive density control over the training state's 1M Gaussians: statistics from the last
     step's screen-space gradients (a synthetic accumulated state: every visible Gaussian seen on
-    10 steps), then one clone/split/prune call into new buffers."""
+    10 steps), then one clone/split/prune call into new buffers with 3DGS's size pruning on
+    (largest screen radius > 20 px, largest scale > 0.1 x extent), and one opacity reset."""
     import torch
     g = st.g
     n = g.n
     acc = torch.zeros(n, device="cuda")
     cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    mr = torch.zeros(n, dtype=torch.int32, device="cuda")
     for _ in range(10):
-        leg.le_densify_stats(st.grad2d, st.proj.radius, acc, cnt)
+        leg.le_densify_stats(st.grad2d, st.proj.radius, acc, cnt, mr)
     noise = torch.randn((n, 2, 3), generator=torch.Generator(device="cuda").manual_seed(5), device="cuda")
     thresh = float(torch.quantile((acc / cnt.clamp_min(1))[cnt > 0][:1_000_000], 0.9))   # densify ~10 %
-    kw = dict(grad_thresh=thresh, percent_dense=0.01, scene_extent=4.0, min_opacity=0.005, n_cap=2 * n)
+    kw = dict(grad_thresh=thresh, percent_dense=0.01, scene_extent=4.0, min_opacity=0.005, n_cap=2 * n,
+              max_radius=mr, max_screen_size=20.0, world_frac=0.1)
     for _ in range(2):
         out = leg.le_densify(g, st.gm, st.gvv, acc, cnt, noise, **kw)
     torch.cuda.synchronize()
@@ -604,10 +624,18 @@ def densify_leg(leg, st, args, hbm_peak):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / reps
     n2 = out[0].n
+    op, om, ov = (x.opacity_raw.clone() for x in out)
+    t0.record()
+    for _ in range(reps):
+        leg.le_opacity_reset(op, om, ov, 0.01)
+    t1.record()
+    torch.cuda.synchronize()
+    ms_reset = t0.elapsed_time(t1) / reps
     par = 4 * (3 + 3 + 4 + 1 + 48 + 8 + 1)
-    byts = 3 * par * n + 3 * par * n2 + 12 * n     # read params, m, v; write them for n2; statistics
+    byts = 3 * par * n + 3 * par * n2 + 16 * n     # read params, m, v; write them for n2; statistics
     return {"ms": round(ms, 4), "gaussians_in": n, "gaussians_out": n2, "hbm_frac": round(byts / ms / 1e6 / hbm_peak, 4),
-            "note": "one le_densify call (classify, scan, host read of the totals, scatter)"}
+            "opacity_reset_ms": round(ms_reset, 4),
+            "note": "one le_densify call (classify with size pruning, scan, host read of the totals, scatter)"}
 
 
 def quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind):

@@ -452,13 +452,27 @@ le_status le_smooth(int32_t n, const float* means, const float* feat, const floa
  * reconstruction"; reading: 3DGS's clone / split / prune rule).
  * le_densify_stats -- every step after le_render_bwd_screen: for every
  *   Gaussian with radius > 0, acc[i] += sqrt(gx^2 + gy^2) (gx, gy = grad2d
- *   [i][0..1], dL/dmean2d in pixels), cnt[i] += 1.
+ *   [i][0..1], dL/dmean2d in pixels), cnt[i] += 1, and, when max_radius is
+ *   not null, max_radius[i] = max(max_radius[i], radius[i]) (the largest
+ *   screen radius since the caller last zeroed the statistics).
+ * le_opacity_reset -- 3DGS's periodic opacity reset: opacity_raw[i] =
+ *   min(opacity_raw[i], fl(logit(max_opacity))) (opacity = min(opacity,
+ *   max_opacity); 3DGS: 0.01) and the opacity's Adam moments m, v zeroed.
+ *   n floats each, device pointers.  LE_ERR_INVALID_ARG for max_opacity
+ *   outside (0, 1).
  * le_densify -- with g_i = acc_i / cnt_i: pruned if sigmoid(opacity_raw) <
- *   min_opacity; else split if g_i >= grad_thresh and its largest scale >
+ *   min_opacity, or (size pruning, 3DGS's removal of Gaussians too large in
+ *   view and world space) if max_screen_size > 0 and max_radius_i >
+ *   max_screen_size, or if world_frac > 0 and its largest scale > world_frac *
+ *   scene_extent; a pruned Gaussian is neither cloned nor split (max_radius
+ *   may be null when max_screen_size == 0); else split if g_i >= grad_thresh
+ *   and its largest scale >
  *   percent_dense * scene_extent; else cloned if g_i >= grad_thresh; else kept.
  *   The decisions are FP32 comparisons against thresholds computed in double
  *   (opacity_raw < logit(min_opacity), max log-scale > ln(percent_dense *
- *   extent), cnt > 0 and acc >= fl(grad_thresh * cnt)), reproducible bit for bit.
+ *   extent), max log-scale > ln(world_frac * extent), (float)max_radius >
+ *   max_screen_size, cnt > 0 and acc >= fl(grad_thresh * cnt)), reproducible
+ *   bit for bit.
  *   Output (g_out, m_out, v_out, capacity n_cap Gaussians each): the kept and
  *   cloned Gaussians in index order, then the clones, then two children per
  *   split Gaussian; a child k copies its parent except mean = mu + R(q)
@@ -473,13 +487,18 @@ typedef struct le_densify_config {
     float percent_dense;     /* 3DGS: 0.01 */
     float scene_extent;
     float min_opacity;       /* 3DGS: 0.005 */
+    float max_screen_size;   /* pixels; 0 = off (3DGS: 20 once opacity resets have begun) */
+    float world_frac;        /* fraction of scene_extent; 0 = off (3DGS: 0.1, with the screen test) */
 } le_densify_config;
 
 le_status le_densify_stats(int32_t n, const float* grad2d, const int32_t* radius, float* acc, int32_t* cnt,
+                           int32_t* max_radius, void* stream);
+le_status le_opacity_reset(int32_t n, float* opacity_raw, float* m_opacity, float* v_opacity, float max_opacity,
                            void* stream);
 le_status le_densify_workspace(int32_t n, size_t* bytes);
 le_status le_densify(const le_densify_config* cfg, const le_gaussians* g, const le_gaussian_grads* m,
-                     const le_gaussian_grads* v, const float* acc, const int32_t* cnt, const float* noise,
+                     const le_gaussian_grads* v, const float* acc, const int32_t* cnt, const int32_t* max_radius,
+                     const float* noise,
                      int64_t n_cap, const le_gaussian_grads* g_out, const le_gaussian_grads* m_out,
                      const le_gaussian_grads* v_out, int64_t* n_out, void* workspace, size_t workspace_bytes,
                      void* stream);

@@ -397,35 +397,59 @@ def smooth(means, feat, unc, mlp, w_s=0.1, lam=1.0) -> dict:
     return out
 
 
-def densify_thresholds(grad_thresh, percent_dense, extent, min_opacity):
-    """(grad_thresh, log_big, logit_min) as FP32 values, derived in double (see densify.c)."""
+def densify_thresholds(grad_thresh, percent_dense, extent, min_opacity, world_frac=0.0):
+    """(grad_thresh, log_big, logit_min, log_world) as FP32 values, derived in double (see
+    densify.c); log_world is +inf when world-size pruning is off (world_frac <= 0)."""
     import math
-    pd, ex, mo = (float(np.float32(x)) for x in (percent_dense, extent, min_opacity))   # the FP32 config values
-    return (np.float32(grad_thresh), np.float32(math.log(pd * ex)), np.float32(math.log(mo / (1.0 - mo))))
+    pd, ex, mo, wf = (float(np.float32(x)) for x in (percent_dense, extent, min_opacity, world_frac))
+    lw = np.float32(math.log(wf * ex)) if wf > 0 else np.float32(np.inf)
+    return (np.float32(grad_thresh), np.float32(math.log(pd * ex)), np.float32(math.log(mo / (1.0 - mo))), lw)
 
 
-def densify_stats(grad_mean2d, radius, acc, cnt):
-    """In place: acc [n] float32 += |dL/dmean2d|, cnt [n] int32 += 1 for every Gaussian
-    with radius > 0 (adaptive density control statistics).  grad_mean2d: [n, 2]."""
+def opacity_logit(max_opacity):
+    """fl(ln(m / (1 - m))) of the FP32 value m, derived in double."""
+    import math
+    mo = float(np.float32(max_opacity))
+    return np.float32(math.log(mo / (1.0 - mo)))
+
+
+def densify_stats(grad_mean2d, radius, acc, cnt, max_radius=None):
+    """In place: acc [n] float32 += |dL/dmean2d|, cnt [n] int32 += 1 and max_radius [n] int32
+    = max(max_radius, radius) for every Gaussian with radius > 0 (adaptive density control
+    statistics).  grad_mean2d: [n, 2]."""
     g = _f32(grad_mean2d)
     r = np.ascontiguousarray(radius, np.int32)
     assert g.shape == (len(r), 2), g.shape
     assert acc.dtype == np.float32 and cnt.dtype == np.int32
-    lib().orc_densify_stats(C.c_int(len(r)), _p(g), _p(r), _p(acc), _p(cnt))
+    assert max_radius is None or max_radius.dtype == np.int32
+    lib().orc_densify_stats(C.c_int(len(r)), _p(g), _p(r), _p(acc), _p(cnt),
+                            None if max_radius is None else _p(max_radius))
+
+
+def opacity_reset(opacity_raw, m, v, max_opacity=0.01):
+    """In place (float32 arrays): opacity_raw = min(opacity_raw, logit(max_opacity)); m = v = 0."""
+    assert opacity_raw.dtype == m.dtype == v.dtype == np.float32
+    lib().orc_opacity_reset(C.c_int(len(opacity_raw)), _p(opacity_raw), _p(m), _p(v),
+                            C.c_float(opacity_logit(max_opacity)))
 
 
 def densify(params: dict, m: dict, v: dict, acc, cnt, noise, grad_thresh=0.0002, percent_dense=0.01, extent=1.0,
-            min_opacity=0.005) -> dict:
+            min_opacity=0.005, max_radius=None, max_screen_size=0.0, world_frac=0.0) -> dict:
     """Adaptive density control (3DGS's, kept by Sec. 4): returns the new parameter and moment
-    dicts (same field names: means, log_scales, quats, opacity_raw, sh, feat, unc) and the plan."""
+    dicts (same field names: means, log_scales, quats, opacity_raw, sh, feat, unc) and the plan.
+    max_screen_size > 0 (pixels; needs max_radius) and world_frac > 0 (fraction of extent)
+    also prune Gaussians too large on screen or in the world."""
     ls = _f32(params["log_scales"])
     op = _f32(params["opacity_raw"])
     n = len(op)
     acc, cnt = _f32(acc), np.ascontiguousarray(cnt, np.int32)
-    gt, lb, lm = densify_thresholds(grad_thresh, percent_dense, extent, min_opacity)
+    mr = None if max_radius is None else np.ascontiguousarray(max_radius, np.int32)
+    assert max_screen_size <= 0 or mr is not None
+    gt, lb, lm, lw = densify_thresholds(grad_thresh, percent_dense, extent, min_opacity, world_frac)
     kind = np.zeros(n, np.int32)
-    total = lib().orc_densify_plan(C.c_int(n), _p(ls), _p(op), _p(acc), _p(cnt), C.c_float(gt), C.c_float(lb),
-                                   C.c_float(lm), _p(kind))
+    total = lib().orc_densify_plan(C.c_int(n), _p(ls), _p(op), _p(acc), _p(cnt), None if mr is None else _p(mr),
+                                   C.c_float(gt), C.c_float(lb), C.c_float(lm), C.c_float(max_screen_size),
+                                   C.c_float(lw), _p(kind))
     keep = np.nonzero((kind == 1) | (kind == 2))[0]
     clone = np.nonzero(kind == 2)[0]
     split = np.nonzero(kind == 3)[0]

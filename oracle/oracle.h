@@ -120,8 +120,11 @@ void orc_rgb_loss(int W, int H, const double* img, const double* target, double 
 
 /* densify.c */
 int64_t orc_densify_plan(int n, const float* log_scales, const float* opacity_raw, const float* acc,
-                         const int32_t* cnt, float grad_thresh, float log_big, float logit_min, int32_t* kind);
-void orc_densify_stats(int n, const float* grad_mean2d, const int32_t* radius, float* acc, int32_t* cnt);
+                         const int32_t* cnt, const int32_t* max_radius, float grad_thresh, float log_big,
+                         float logit_min, float max_screen, float log_world, int32_t* kind);
+void orc_densify_stats(int n, const float* grad_mean2d, const int32_t* radius, float* acc, int32_t* cnt,
+                       int32_t* max_radius);
+void orc_opacity_reset(int n, float* opacity_raw, float* m, float* v, float logit_max);
 void orc_split_mean(const float* mu, const float* log_s, const float* q, const float* nz, double* out);
 
 /* quant.c */

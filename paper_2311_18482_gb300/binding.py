@@ -50,7 +50,7 @@ class LeAdamConfig(C.Structure):
 
 class LeDensifyConfig(C.Structure):
     _fields_ = [("grad_thresh", C.c_float), ("percent_dense", C.c_float), ("scene_extent", C.c_float),
-                ("min_opacity", C.c_float)]
+                ("min_opacity", C.c_float), ("max_screen_size", C.c_float), ("world_frac", C.c_float)]
 
 
 _PROJ_FIELDS = ("splat", "depth", "radius", "rect", "tiles_touched", "clamp_mask", "tile_ellipse")
@@ -117,10 +117,11 @@ _SIG = {
     "le_feature_map": [C.c_int32, _P, C.POINTER(LeDecoder), _P, C.c_int32, _P, _P, C.c_size_t, _P],
     "le_rgb_loss_workspace": [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "le_rgb_loss": [C.c_int32, C.c_int32, _P, _P, C.c_float, _P, _P, _P, C.c_size_t, _P],
-    "le_densify_stats": [C.c_int32, _P, _P, _P, _P, _P],
+    "le_densify_stats": [C.c_int32, _P, _P, _P, _P, _P, _P],
+    "le_opacity_reset": [C.c_int32, _P, _P, _P, C.c_float, _P],
     "le_densify_workspace": [C.c_int32, C.POINTER(C.c_size_t)],
     "le_densify": [C.POINTER(LeDensifyConfig), C.POINTER(LeGaussians), C.POINTER(LeGaussianGrads),
-                   C.POINTER(LeGaussianGrads), _P, _P, _P, C.c_int64, C.POINTER(LeGaussianGrads),
+                   C.POINTER(LeGaussianGrads), _P, _P, _P, _P, C.c_int64, C.POINTER(LeGaussianGrads),
                    C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads), C.POINTER(C.c_int64), _P, C.c_size_t, _P],
     "le_rgb_l1": [C.c_int64, _P, _P, _P, _P, _P],
     "le_device_status": [_P],
@@ -649,20 +650,30 @@ def le_rgb_loss(img, target, lambda_ssim=0.2, loss=None, grad=None, workspace=No
     return loss, grad
 
 
-def le_densify_stats(grad2d, radius, acc, cnt):
-    """acc [n] float32 += |dL/dmean2d| and cnt [n] int32 += 1 for every visible Gaussian (in place)."""
-    _check(load().le_densify_stats(acc.shape[0], _ptr(grad2d), _ptr(radius), _ptr(acc), _ptr(cnt), _stream()))
+def le_densify_stats(grad2d, radius, acc, cnt, max_radius=None):
+    """acc [n] float32 += |dL/dmean2d|, cnt [n] int32 += 1 and max_radius [n] int32 (optional)
+    = max(max_radius, radius) for every visible Gaussian (in place)."""
+    _check(load().le_densify_stats(acc.shape[0], _ptr(grad2d), _ptr(radius), _ptr(acc), _ptr(cnt),
+                                   _ptr(max_radius), _stream()))
+
+
+def le_opacity_reset(opacity_raw, m_opacity, v_opacity, max_opacity=0.01):
+    """In place: opacity = min(opacity, max_opacity) and the opacity's Adam moments zeroed."""
+    _check(load().le_opacity_reset(opacity_raw.numel(), _ptr(opacity_raw), _ptr(m_opacity), _ptr(v_opacity),
+                                   max_opacity, _stream()))
 
 
 def le_densify(g: Gaussians, m: Gaussians, v: Gaussians, acc, cnt, noise, grad_thresh=0.0002, percent_dense=0.01,
-               scene_extent=1.0, min_opacity=0.005, n_cap=None):
-    """Adaptive density control: returns (g', m', v') as Gaussians of the new size."""
+               scene_extent=1.0, min_opacity=0.005, n_cap=None, max_radius=None, max_screen_size=0.0,
+               world_frac=0.0):
+    """Adaptive density control: returns (g', m', v') as Gaussians of the new size.  max_screen_size
+    (pixels, needs max_radius) and world_frac (of scene_extent) > 0 turn on the size pruning."""
     n = g.n
     n_cap = n_cap if n_cap is not None else 2 * n
     grow = lambda t: torch.empty((n_cap,) + tuple(t.shape[1:]), dtype=t.dtype, device=t.device)
     outs = [Gaussians(*(grow(getattr(x, k)) for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat",
                                                        "unc")), g.sh_degree) for x in (g, g, g)]
-    cfg = LeDensifyConfig(grad_thresh, percent_dense, scene_extent, min_opacity)
+    cfg = LeDensifyConfig(grad_thresh, percent_dense, scene_extent, min_opacity, max_screen_size, world_frac)
     ws_n = C.c_size_t()
     _check(load().le_densify_workspace(n, C.byref(ws_n)))
     ws = torch.empty(max(ws_n.value, 1), dtype=torch.uint8, device=g.means.device)
@@ -670,7 +681,7 @@ def le_densify(g: Gaussians, m: Gaussians, v: Gaussians, acc, cnt, noise, grad_t
     gs, ms, vs = g.struct(), grads_struct(m), grads_struct(v)
     os_ = [grads_struct(o) for o in outs]
     _check(load().le_densify(C.byref(cfg), C.byref(gs), C.byref(ms), C.byref(vs), _ptr(acc), _ptr(cnt),
-                             _ptr(noise.contiguous()), n_cap, C.byref(os_[0]), C.byref(os_[1]), C.byref(os_[2]),
+                             _ptr(max_radius), _ptr(noise.contiguous()), n_cap, C.byref(os_[0]), C.byref(os_[1]), C.byref(os_[2]),
                              C.byref(n_out), _ptr(ws), ws.numel(), _stream()))
     k = n_out.value
     cut = lambda o: Gaussians(*(getattr(o, f)[:k] for f in ("means", "log_scales", "quats", "opacity_raw", "sh",

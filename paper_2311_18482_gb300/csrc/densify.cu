@@ -1,7 +1,10 @@
 // Adaptive density control of 3D Gaussian Splatting, which Sec. 4 keeps
-// (clone / split / prune), as three steps the training loop calls:
+// (clone / split / prune, opacity reset), as the steps the training loop calls:
 //   le_densify_stats  every step: acc_i += |dL/dmean2d_i| (pixels), cnt_i += 1
-//                     for every Gaussian with a nonzero screen radius;
+//                     and max_radius_i = max(max_radius_i, radius_i) for every
+//                     Gaussian with a nonzero screen radius;
+//   le_opacity_reset  every few thousand steps: opacity = min(opacity, 0.01),
+//                     the opacity's Adam moments zeroed;
 //   le_densify        every few hundred steps: classify each Gaussian (pruned,
 //                     kept, kept + clone, split), count the three output
 //                     segments per block, scan the block counts, then scatter
@@ -11,7 +14,9 @@
 // The decisions use FP32 comparisons against thresholds derived once in double
 // (no transcendental function on the device), so they are reproducible bit for
 // bit: opacity_raw < logit(min_opacity); max log-scale > ln(percent_dense *
-// extent); cnt > 0 and acc >= fl(grad_thresh * cnt).  A split child k copies
+// extent); cnt > 0 and acc >= fl(grad_thresh * cnt); and, when enabled, the
+// size tests that prune Gaussians too large on screen (max_radius >
+// max_screen_size) or in the world (max log-scale > ln(world_frac * extent)).  A split child k copies
 // its parent except mean = mu + R(q) diag(exp(log-scale)) n_k (the caller's
 // standard normal samples) and log-scale - ln(1.6); clones and children start
 // with zero Adam moments.
@@ -23,7 +28,7 @@ namespace {
 constexpr int kDB = 1024;                  // Gaussians per classification block
 
 struct DensifyThresholds {
-    float grad_thresh, log_big, logit_min, ln16;
+    float grad_thresh, log_big, logit_min, ln16, max_screen, log_world;
 };
 
 struct Fields {
@@ -36,22 +41,37 @@ __host__ __device__ constexpr int field_w(int f, int nc)
 }
 
 __global__ void densify_stats_kernel(int n, const float4* __restrict__ grad2d, const int* __restrict__ radius,
-                                     float* __restrict__ acc, int* __restrict__ cnt)
+                                     float* __restrict__ acc, int* __restrict__ cnt, int* __restrict__ max_radius)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || radius[i] <= 0) return;
+    if (i >= n) return;
+    const int r = radius[i];
+    if (r <= 0) return;
     const float4 g = grad2d[5 * (size_t)i];
     acc[i] = __fadd_rn(acc[i], __fsqrt_rn(__fadd_rn(__fmul_rn(g.x, g.x), __fmul_rn(g.y, g.y))));
     cnt[i] += 1;
+    if (max_radius && r > max_radius[i]) max_radius[i] = r;
+}
+
+// opacity_raw = min(opacity_raw, logit_max); the opacity's Adam moments zeroed.
+__global__ void opacity_reset_kernel(int n, float* __restrict__ op, float* __restrict__ m, float* __restrict__ v,
+                                     float logit_max)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    op[i] = fminf(op[i], logit_max);
+    m[i] = 0.f;
+    v[i] = 0.f;
 }
 
 __device__ __forceinline__ int classify(int i, const float* ls, const float* op, const float* acc, const int* cnt,
-                                        const DensifyThresholds& t)
+                                        const int* max_radius, const DensifyThresholds& t)
 {
     const float smax = fmaxf(fmaxf(ls[3 * i], ls[3 * i + 1]), ls[3 * i + 2]);
     const int c = cnt[i];
     const bool cand = c > 0 && acc[i] >= __fmul_rn(t.grad_thresh, (float)c);
-    if (op[i] < t.logit_min) return 0;
+    const bool big_screen = t.max_screen > 0.f && (float)max_radius[i] > t.max_screen;
+    if (op[i] < t.logit_min || big_screen || smax > t.log_world) return 0;
     if (cand) return smax > t.log_big ? 3 : 2;
     return 1;
 }
@@ -59,7 +79,8 @@ __device__ __forceinline__ int classify(int i, const float* ls, const float* op,
 // kind[i] and per-block counts of the three output segments: [3][nblocks].
 __global__ void __launch_bounds__(256) densify_count_kernel(int n, const float* __restrict__ ls,
                                                             const float* __restrict__ op, const float* __restrict__ acc,
-                                                            const int* __restrict__ cnt, DensifyThresholds t,
+                                                            const int* __restrict__ cnt,
+                                                            const int* __restrict__ max_radius, DensifyThresholds t,
                                                             uint8_t* __restrict__ kind, unsigned* __restrict__ bcount)
 {
     __shared__ unsigned c3[3];
@@ -69,7 +90,7 @@ __global__ void __launch_bounds__(256) densify_count_kernel(int n, const float* 
     for (int r = 0; r < kDB / 256; ++r) {
         const int i = blockIdx.x * kDB + r * 256 + threadIdx.x;
         if (i < n) {
-            const int k = classify(i, ls, op, acc, cnt, t);
+            const int k = classify(i, ls, op, acc, cnt, max_radius, t);
             kind[i] = (uint8_t)k;
             k1 += k == 1 || k == 2;
             k2 += k == 2;
@@ -270,7 +291,7 @@ bool fields_ok(const le_gaussian_grads* g)
 using namespace leg;
 
 extern "C" le_status le_densify_stats(int32_t n, const float* grad2d, const int32_t* radius, float* acc, int32_t* cnt,
-                                      void* stream)
+                                      int32_t* max_radius, void* stream)
 {
     LE_TRACE("le_densify_stats");
     LE_CHECK_ARG(n >= 0, "n = %d < 0", n);
@@ -278,7 +299,22 @@ extern "C" le_status le_densify_stats(int32_t n, const float* grad2d, const int3
     LE_CHECK_ARG(grad2d && radius && acc && cnt, "null pointer");
     LE_CHECK_ARG(aligned16(grad2d), "grad2d must be 16-byte aligned");
     densify_stats_kernel<<<(n + 255) / 256, 256, 0, as_stream(stream)>>>(n, reinterpret_cast<const float4*>(grad2d),
-                                                                         radius, acc, cnt);
+                                                                         radius, acc, cnt, max_radius);
+    LE_LAUNCHED();
+    return LE_OK;
+}
+
+extern "C" le_status le_opacity_reset(int32_t n, float* opacity_raw, float* m_opacity, float* v_opacity,
+                                      float max_opacity, void* stream)
+{
+    LE_TRACE("le_opacity_reset");
+    LE_CHECK_ARG(n >= 0, "n = %d < 0", n);
+    LE_CHECK_ARG(max_opacity > 0.f && max_opacity < 1.f, "max_opacity = %g outside (0, 1)", (double)max_opacity);
+    if (n == 0) return LE_OK;
+    LE_CHECK_ARG(opacity_raw && m_opacity && v_opacity, "null pointer");
+    const float logit_max = (float)log((double)max_opacity / (1.0 - (double)max_opacity));
+    opacity_reset_kernel<<<(n + 255) / 256, 256, 0, as_stream(stream)>>>(n, opacity_raw, m_opacity, v_opacity,
+                                                                         logit_max);
     LE_LAUNCHED();
     return LE_OK;
 }
@@ -293,7 +329,8 @@ extern "C" le_status le_densify_workspace(int32_t n, size_t* bytes)
 }
 
 extern "C" le_status le_densify(const le_densify_config* cfg, const le_gaussians* g, const le_gaussian_grads* m,
-                                const le_gaussian_grads* v, const float* acc, const int32_t* cnt, const float* noise,
+                                const le_gaussian_grads* v, const float* acc, const int32_t* cnt,
+                                const int32_t* max_radius, const float* noise,
                                 int64_t n_cap, const le_gaussian_grads* g_out, const le_gaussian_grads* m_out,
                                 const le_gaussian_grads* v_out, int64_t* n_out, void* workspace,
                                 size_t workspace_bytes, void* stream)
@@ -302,7 +339,8 @@ extern "C" le_status le_densify(const le_densify_config* cfg, const le_gaussians
     LE_CHECK_ARG(cfg && g && n_out, "null config / gaussians / n_out");
     LE_CHECK_ARG(g->n >= 0 && g->sh_degree >= 0 && g->sh_degree <= 3, "bad gaussians");
     LE_CHECK_ARG(cfg->min_opacity > 0.f && cfg->min_opacity < 1.f && cfg->percent_dense > 0.f &&
-                     cfg->scene_extent > 0.f && cfg->grad_thresh >= 0.f,
+                     cfg->scene_extent > 0.f && cfg->grad_thresh >= 0.f && cfg->max_screen_size >= 0.f &&
+                     cfg->world_frac >= 0.f,
                  "bad densify config");
     const int n = g->n;
     if (n == 0) {
@@ -314,6 +352,7 @@ extern "C" le_status le_densify(const le_densify_config* cfg, const le_gaussians
     LE_CHECK_ARG(fields_ok(m) && fields_ok(v) && fields_ok(g_out) && fields_ok(m_out) && fields_ok(v_out),
                  "null moment / output pointer");
     LE_CHECK_ARG(acc && cnt && noise && workspace, "null statistics / noise / workspace");
+    LE_CHECK_ARG(cfg->max_screen_size == 0.f || max_radius, "max_screen_size > 0 needs max_radius");
     size_t need = 0;
     le_densify_workspace(n, &need);
     LE_CHECK_ARG(workspace_bytes >= need, "workspace has %zu bytes, needs %zu", workspace_bytes, need);
@@ -328,8 +367,11 @@ extern "C" le_status le_densify(const le_densify_config* cfg, const le_gaussians
     t.log_big = (float)log((double)cfg->percent_dense * (double)cfg->scene_extent);
     t.logit_min = (float)log((double)cfg->min_opacity / (1.0 - (double)cfg->min_opacity));
     t.ln16 = (float)log(1.6);
+    t.max_screen = cfg->max_screen_size;
+    t.log_world = cfg->world_frac > 0.f ? (float)log((double)cfg->world_frac * (double)cfg->scene_extent) : INFINITY;
     cudaStream_t s = as_stream(stream);
-    densify_count_kernel<<<nb, 256, 0, s>>>(n, g->log_scales, g->opacity_raw, acc, cnt, t, kind, bcount);
+    densify_count_kernel<<<nb, 256, 0, s>>>(n, g->log_scales, g->opacity_raw, acc, cnt, max_radius, t, kind,
+                                            bcount);
     LE_LAUNCHED();
     densify_scan_kernel<<<1, 1024, 0, s>>>(bcount, nb, totals);
     LE_LAUNCHED();

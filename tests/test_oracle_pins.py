@@ -920,6 +920,65 @@ def test_densify_plan_matches_definitions(orc):
     assert o["n_out"] == int(np.sum(want == 1) + 2 * np.sum(want >= 2))
 
 
+def test_densify_size_pruning_matches_definitions(orc):
+    """With 3DGS's size pruning on (largest screen radius > 20 px, largest scale > 0.1 x extent),
+    the decisions equal the definitions evaluated in FP64 away from the thresholds; a Gaussian
+    too large is pruned even when its gradient asks for a clone or split, and turning either
+    test off brings back the plain decisions."""
+    n = 4000
+    P, acc, cnt = _densify_inputs(n, 72)
+    rng = np.random.default_rng(73)
+    P["log_scales"] = rng.normal(-1.5, 1.0, (n, 3)).astype(np.float32)
+    mr = rng.integers(0, 40, n).astype(np.int32)
+    noise = np.zeros((n, 2, 3), np.float32)
+    kw = dict(grad_thresh=0.0002, percent_dense=0.01, extent=4.0, min_opacity=0.005)
+    o = orc.densify(P, P, P, acc, cnt, noise, max_radius=mr, max_screen_size=20.0, world_frac=0.1, **kw)
+    op = 1 / (1 + np.exp(-P["opacity_raw"].astype(np.float64)))
+    g = np.where(cnt > 0, acc / np.maximum(cnt, 1), 0.0)
+    smax = np.exp(P["log_scales"].astype(np.float64).max(1))
+    pruned = (op < 0.005) | (mr > 20) | (smax > 0.1 * 4.0)
+    want = np.where(pruned, 0, np.where((cnt > 0) & (g >= 0.0002), np.where(smax > 0.01 * 4.0, 3, 2), 1))
+    far = (np.abs(op - 0.005) > 1e-6) & (np.abs(g - 0.0002) > 1e-9) & (np.abs(smax - 0.04) > 1e-7) & \
+          (np.abs(smax - 0.4) > 1e-6)
+    assert np.array_equal(o["kind"][far], want[far])
+    for why in ((mr > 20), (smax > 0.4)):                   # each size test prunes Gaussians on its own
+        assert np.any(why & (op >= 0.005) & far)
+    o_off = orc.densify(P, P, P, acc, cnt, noise, **kw)
+    plain = np.where(op < 0.005, 0, np.where((cnt > 0) & (g >= 0.0002), np.where(smax > 0.04, 3, 2), 1))
+    assert np.array_equal(o_off["kind"][far], plain[far])
+    assert np.any(o["kind"] != o_off["kind"])
+
+
+def test_densify_max_radius_statistic(orc):
+    """The largest screen radius since the statistics were reset, over three steps by hand;
+    a Gaussian outside the view (radius 0) keeps its value."""
+    acc = np.zeros(3, np.float32)
+    cnt = np.zeros(3, np.int32)
+    mr = np.zeros(3, np.int32)
+    g = np.ones((3, 2), np.float32)
+    for r in ([3, 0, 25], [7, 0, 4], [5, 2, 0]):
+        orc.densify_stats(g, np.array(r, np.int32), acc, cnt, mr)
+    assert mr.tolist() == [7, 2, 25] and cnt.tolist() == [3, 1, 2]
+
+
+def test_opacity_reset(orc):
+    """3DGS's opacity reset: sigmoid(opacity_raw') = min(sigmoid(opacity_raw), 0.01) in FP64 up to the
+    FP32 rounding of the threshold; values already below are left bit for bit; the opacity's Adam
+    moments restart at zero."""
+    rng = np.random.default_rng(74)
+    raw = np.concatenate([rng.normal(0, 4, 5000), [-4.59512, -4.59511, -20.0, 30.0]]).astype(np.float32)
+    m = rng.standard_normal(len(raw)).astype(np.float32)
+    v = rng.uniform(0, 1, len(raw)).astype(np.float32)
+    r2 = raw.copy()
+    orc.opacity_reset(r2, m, v, 0.01)
+    sig = lambda x: 1 / (1 + np.exp(-x.astype(np.float64)))
+    assert np.all(np.abs(sig(r2) - np.minimum(sig(raw), 0.01)) <= 0.01 * 1e-6)
+    low = sig(raw) < 0.01 * (1 - 1e-6)
+    assert np.array_equal(r2[low].view(np.uint32), raw[low].view(np.uint32))
+    assert np.all(r2[~low] == orc.opacity_logit(0.01))
+    assert np.all(m == 0) and np.all(v == 0)
+
+
 def test_densify_layout_and_children(orc):
     """Output order (kept, clones, split children), moments carried or zeroed, child means
     mu + R diag(s) n: with n = +-e_k the child sits at distance s_k along R's k-th column."""
