@@ -12,7 +12,7 @@
 // K copies at all:
 //   1. e[i] = bits(depth_i) << 32 | i          (culled: 0xFFFFFFFF, sorted last)
 //   2. stable LSD radix sort of e on bits 32..63 (4 passes over the N Gaussians,
-//      one kernel each, see depth_sort)
+//      each count / scan / scatter, see depth_sort)
 //   3. split the depth-sorted Gaussians into chunks; per chunk, the number of
 //      copies in every tile from per-row difference arrays of the row spans
 //   4. one exclusive scan of those counts in tile-major order: entry (t, c) is
@@ -21,8 +21,7 @@
 //   5. blocks of (8 tile rows x a super-chunk of Gaussians) write the copies in
 //      depth order through per-tile cursors held in registers (one warp per
 //      row, one lane per 32nd tile of the row).
-// Only the depth sort's look-back waits on other blocks (bounded, see
-// onesweep_kernel).
+// No kernel waits on another block.
 #include "common.cuh"
 
 namespace leg {
@@ -41,6 +40,7 @@ struct DirectIn {
     __device__ uint32_t operator()(int i) const { return p[i]; }
 };
 
+template <int NW = kWarps>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -53,17 +53,17 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     if (lane == 31) warp_sums[w] = x;
     __syncthreads();
     if (w == 0) {
-        uint32_t s = lane < kWarps ? warp_sums[lane] : 0u;
+        uint32_t s = lane < NW ? warp_sums[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
-        if (lane < kWarps) warp_sums[lane] = s;
+        if (lane < NW) warp_sums[lane] = s;
     }
     __syncthreads();
     const uint32_t before = (w > 0 ? warp_sums[w - 1] : 0u) + x - v;
-    if (total) *total = warp_sums[kWarps - 1];
+    if (total) *total = warp_sums[NW - 1];
     return before;
 }
 
@@ -179,173 +179,186 @@ le_status exclusive_scan(In in, int n, uint32_t* out, uint32_t* partials, uint32
 
 // ----------------------------------------------------------------------------
 // Depth sort: stable LSD radix sort of e = bits(depth) << 32 | index on bits
-// 32-63 in four 8-bit passes, one kernel per pass.  The digit histograms of
-// all four passes are counted once, while the keys are built (they do not
-// depend on the order); each pass's blocks then find their offsets by
-// decoupled look-back: a block takes a virtual index in launch order,
-// publishes its per-digit counts, and adds up its predecessors' counts until
-// it meets one that has published its inclusive prefix.  A block only waits
-// for blocks that started before it, which publish their counts without
-// waiting; every wait is still bounded (about a second) and reports a timeout.
-constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kCountMask = (1u << 30) - 1u;
+// 32-63 in four 8-bit passes.  Each pass is count / scan / scatter over tiles
+// of kSortTile consecutive elements, and no block waits on another:
+//   count    per-tile digit counts, counts[d][b] (digit-major, rows padded to
+//            a multiple of 4), and the digits' totals (pass 0's are counted
+//            while the keys are built);
+//   rowscan  one warp per digit: the exclusive prefix of its row plus the
+//            digit's base (the totals of all smaller digits), so counts[d][b]
+//            becomes the first output position of tile b's digit-d elements;
+//   scatter  each tile ranks its elements stably (warp-private digit counters,
+//            warps in element order) and writes them to their positions.
+// The last scatter also gathers each Gaussian's rectangle and tile ellipse
+// into depth order (zero for culled Gaussians) for the kernels that follow.
 constexpr int kSortPasses = 4;
+constexpr int kSortThreads = 512;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 elements per tile
+constexpr int kSortWarps = kSortThreads / 32;
 
 __device__ __forceinline__ uint32_t digit_of(uint64_t e, int shift) { return (uint32_t)(e >> shift) & 255u; }
 
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v)
+__host__ __device__ constexpr int sort_tiles(int n) { return (n + kSortTile - 1) / kSortTile; }
+__host__ __device__ constexpr int sort_row(int n) { return (sort_tiles(n) + 3) / 4 * 4; }
+
+// Tile b's digit counts from shared memory to counts[d][b] and the totals.
+__device__ __forceinline__ void publish_counts(const uint32_t* h, uint32_t* counts, int row, uint32_t* totals)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    if (threadIdx.x < 256) {
+        const uint32_t c = h[threadIdx.x];
+        counts[(size_t)threadIdx.x * row + blockIdx.x] = c;
+        if (c) atomicAdd(totals + threadIdx.x, c);
+    }
 }
 
-// Look-back words hold flag and count in one 32-bit word and guard no other
-// data, so relaxed (but coherent) loads suffice, and a window of them can be
-// in flight at once.
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p)
+// e[i] (culled: 0xFFFFFFFF in the high word, sorted last) and pass 0's counts.
+__global__ void __launch_bounds__(kSortThreads) depth_elems_kernel(int n, const float* __restrict__ depth,
+                                                                   const int* __restrict__ tiles,
+                                                                   uint64_t* __restrict__ e, uint32_t* counts,
+                                                                   int row, uint32_t* totals)
 {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-constexpr int kLookWindow = 16;
-
-// e[i] (culled: 0xFFFFFFFF in the high word, sorted last) and the histograms of
-// the four digits of the high word, hist[pass][digit].
-__global__ void __launch_bounds__(256) depth_elems_kernel(int n, const float* __restrict__ depth,
-                                                          const int* __restrict__ tiles, uint64_t* __restrict__ e,
-                                                          uint32_t* __restrict__ hist)
-{
-    __shared__ uint32_t h[kSortPasses * 256];
-    for (int k = threadIdx.x; k < kSortPasses * 256; k += blockDim.x) h[k] = 0;
+    __shared__ uint32_t h[256];
+    if (threadIdx.x < 256) h[threadIdx.x] = 0;
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = blockIdx.x * 1024 + r * 256 + threadIdx.x;
+    for (int k = 0; k < kSortItems; ++k) {
+        const int i = blockIdx.x * kSortTile + k * kSortThreads + threadIdx.x;
         if (i < n) {
             const uint32_t hi = tiles[i] > 0 ? __float_as_uint(depth[i]) : 0xFFFFFFFFu;
             e[i] = ((uint64_t)hi << 32) | (uint32_t)i;
-#pragma unroll
-            for (int q = 0; q < kSortPasses; ++q) atomicAdd(&h[q * 256 + ((hi >> (8 * q)) & 255u)], 1u);
+            atomicAdd(&h[hi & 255u], 1u);
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kSortPasses * 256; k += blockDim.x)
-        if (h[k]) atomicAdd(hist + k, h[k]);
+    publish_counts(h, counts, row, totals);
 }
 
-// Exclusive scan of each pass's 256 digit counts, in place.
-__global__ void __launch_bounds__(kSortPasses * 256) digit_base_kernel(uint32_t* hist)
+// Per-tile counts of the digit (e >> shift) & 255.
+__global__ void __launch_bounds__(kSortThreads) sort_count_kernel(const uint64_t* __restrict__ in, int n, int shift,
+                                                                  uint32_t* counts, int row, uint32_t* totals)
 {
-    __shared__ uint32_t sm[kSortPasses * 256];
-    const int t = threadIdx.x, d = t & 255;
-    const uint32_t v = hist[t];
-    sm[t] = v;
+    __shared__ uint32_t h[256];
+    if (threadIdx.x < 256) h[threadIdx.x] = 0;
     __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {
-        const uint32_t add = d >= o ? sm[t - o] : 0u;
-        __syncthreads();
-        sm[t] += add;
-        __syncthreads();
-    }
-    hist[t] = sm[t] - v;
-}
-
-// One pass on digit (e >> shift) & 255 from in to out.  dbase: the pass's
-// exclusive digit offsets; status: [blocks][256] look-back words (zeroed);
-// vctr: the pass's virtual-block counter (zeroed); err: set on a timed-out wait.
-__global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t* __restrict__ in,
-                                                            uint64_t* __restrict__ out, int n, int shift,
-                                                            const uint32_t* __restrict__ dbase, uint32_t* status,
-                                                            uint32_t* vctr, uint32_t* err)
-{
-    __shared__ uint64_t stage[kTile];
-    __shared__ uint32_t warp_cnt[kWarps][256];
-    __shared__ uint32_t gbase[256], lbase[256];
-    __shared__ uint32_t ws[kWarps];
-    __shared__ int s_vb;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_vb = (int)atomicAdd(vctr, 1u);
-    for (int j = threadIdx.x; j < kWarps * 256; j += kThreads) (&warp_cnt[0][0])[j] = 0;
-    __syncthreads();
-    const int vb = s_vb;
-    const int base = vb * kTile;
-    const int cnt = min(kTile, n - base);
-
-    // each warp owns the contiguous sub-range [w*512, (w+1)*512) of the block
-    const uint32_t lt = (1u << lane) - 1u;
-    uint64_t e[kItems];
-    uint32_t dg[kItems];
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const int j = w * (kTile / kWarps) + k * 32 + lane;
+    for (int k = 0; k < kSortItems; ++k) {
+        const int i = blockIdx.x * kSortTile + k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[digit_of(in[i], shift)], 1u);
+    }
+    __syncthreads();
+    publish_counts(h, counts, row, totals);
+}
+
+// counts[d][0..nt) -> base(d) + exclusive prefix along the row, one warp per
+// digit d; base(d) = the totals of digits 0..d-1.  Lanes own 8 consecutive
+// entries (two 16-byte accesses) per round of 256.
+__global__ void __launch_bounds__(256) sort_rowscan_kernel(uint32_t* counts, int nt, int row,
+                                                           const uint32_t* __restrict__ totals)
+{
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+    uint32_t base = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int dd = lane * 8 + k;
+        base += dd < d ? totals[dd] : 0u;
+    }
+    base = __reduce_add_sync(0xffffffffu, base);
+    uint32_t* r = counts + (size_t)d * row;
+    for (int b0 = 0; b0 < nt; b0 += 256) {
+        const int b = b0 + lane * 8;
+        uint4 v0 = make_uint4(0, 0, 0, 0), v1 = make_uint4(0, 0, 0, 0);
+        if (b < row) v0 = *reinterpret_cast<const uint4*>(r + b);
+        if (b + 4 < row) v1 = *reinterpret_cast<const uint4*>(r + b + 4);
+        uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t c = b + k < nt ? x[k] : 0u;
+            x[k] = sum;
+            sum += c;
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t off = base + incl - sum;
+        if (b < row) *reinterpret_cast<uint4*>(r + b) = make_uint4(off + x[0], off + x[1], off + x[2], off + x[3]);
+        if (b + 4 < row)
+            *reinterpret_cast<uint4*>(r + b + 4) = make_uint4(off + x[4], off + x[5], off + x[6], off + x[7]);
+        base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+// Rectangles and tile ellipses of the depth-sorted Gaussians (the last pass).
+struct SortGather {
+    const int* tiles;
+    const ushort4* rect;
+    const float4* ell;
+    ushort4* drect;
+    float4* dell;
+};
+
+// One pass on digit (e >> shift) & 255 from in to out; offsets: counts after
+// sort_rowscan_kernel.  gather.drect non-null: also gather into depth order.
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const uint64_t* __restrict__ in,
+                                                                    uint64_t* __restrict__ out, int n, int shift,
+                                                                    const uint32_t* __restrict__ offsets, int row,
+                                                                    SortGather gather)
+{
+    __shared__ uint64_t stage[kSortTile];
+    __shared__ uint32_t warp_cnt[kSortWarps][256];
+    __shared__ uint32_t gbase[256], lbase[256];
+    __shared__ uint32_t ws[kSortWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < kSortWarps * 256; j += kSortThreads) (&warp_cnt[0][0])[j] = 0;
+    if (threadIdx.x < 256) gbase[threadIdx.x] = offsets[(size_t)threadIdx.x * row + blockIdx.x];
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile;
+    const int cnt = min(kSortTile, n - base);
+
+    // each warp owns the contiguous sub-range [w * 256, (w + 1) * 256) of the tile
+    const uint32_t lt = (1u << lane) - 1u;
+    uint64_t e[kSortItems];
+    uint32_t dg[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const int j = w * (kSortTile / kSortWarps) + k * 32 + lane;
         const bool valid = j < cnt;
         e[k] = valid ? in[base + j] : 0ull;
         dg[k] = valid ? digit_of(e[k], shift) : 0xFFFFFFFFu;
-        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
+    }
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const uint32_t vm = __ballot_sync(0xffffffffu, dg[k] != 0xFFFFFFFFu);
+        if (dg[k] != 0xFFFFFFFFu) {
             const uint32_t peers = __match_any_sync(vm, dg[k]);
             if (lane == __ffs(peers) - 1) warp_cnt[w][dg[k]] += __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
-    // per digit (thread d): exclusive prefix over warps and the block's count;
-    // publish the count, look back for the offset, publish the inclusive prefix
+    // per digit (thread d): exclusive prefix over warps, the tile's count, and the
+    // tile-local start of the digit's run
     uint32_t tot = 0;
     if (threadIdx.x < 256) {
         const int d = threadIdx.x;
-        for (int ww = 0; ww < kWarps; ++ww) {
+        for (int ww = 0; ww < kSortWarps; ++ww) {
             const uint32_t v = warp_cnt[ww][d];
             warp_cnt[ww][d] = tot;
             tot += v;
         }
-        uint32_t* mine = status + (size_t)vb * 256 + d;
-        uint32_t excl = 0;
-        if (vb == 0) {
-            st_release(mine, kFlagPre | tot);
-        } else {
-            st_release(mine, kFlagAgg | tot);
-            const long long t0 = clock64();
-            // predecessors b, b-1, ... read kLookWindow at a time; stop at the first
-            // inclusive prefix, re-read from the first one not yet published
-            for (int b = vb - 1; b >= 0;) {
-                uint32_t sv[kLookWindow];
-#pragma unroll
-                for (int k = 0; k < kLookWindow; ++k)
-                    sv[k] = b - k >= 0 ? ld_relaxed(status + (size_t)(b - k) * 256 + d) : kFlagPre;
-                int used = kLookWindow;
-                bool found = false, waiting = false;
-#pragma unroll
-                for (int k = 0; k < kLookWindow; ++k) {
-                    if (found || waiting) continue;
-                    const uint32_t flag = sv[k] & ~kCountMask;
-                    if (flag == 0u) {
-                        waiting = true;
-                        used = k;
-                    } else {
-                        excl += sv[k] & kCountMask;
-                        if (flag == kFlagPre) found = true;
-                    }
-                }
-                if (found) break;
-                b -= used;
-                if (waiting && clock64() - t0 > (1ll << 31)) {
-                    atomicExch(err, 1u);
-                    break;
-                }
-            }
-            st_release(mine, kFlagPre | (excl + tot));
-        }
-        gbase[d] = dbase[d] + excl;
     }
-    const uint32_t lb = block_exclusive_scan(tot, ws, nullptr);
+    const uint32_t lb = block_exclusive_scan<kSortWarps>(tot, ws, nullptr);
     if (threadIdx.x < 256) lbase[threadIdx.x] = lb;
     __syncthreads();
-    // stage the block's elements in digit order (stable), then write them out
+    // stage the tile's elements in digit order (stable), then write them out
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const int j = w * (kTile / kWarps) + k * 32 + lane;
-        const bool valid = j < cnt;
+    for (int k = 0; k < kSortItems; ++k) {
+        const bool valid = dg[k] != 0xFFFFFFFFu;
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
         uint32_t peers = 0, pos = 0;
         if (valid) {
@@ -360,10 +373,24 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t* __re
         __syncwarp();
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += kThreads) {
+    for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
         const uint64_t v = stage[j];
         const uint32_t d = digit_of(v, shift);
-        out[gbase[d] + (j - lbase[d])] = v;
+        const uint32_t p = gbase[d] + (j - lbase[d]);
+        out[p] = v;
+        if (gather.drect) {
+            const uint32_t gid = (uint32_t)v;
+            uint2 r = make_uint2(0u, 0u);
+            float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0;
+            if (gather.tiles[gid] > 0) {
+                r = reinterpret_cast<const uint2*>(gather.rect)[gid];
+                e0 = gather.ell[2 * (size_t)gid];
+                e1 = gather.ell[2 * (size_t)gid + 1];
+            }
+            reinterpret_cast<uint2*>(gather.drect)[p] = r;
+            gather.dell[2 * (size_t)p] = e0;
+            gather.dell[2 * (size_t)p + 1] = e1;
+        }
     }
 }
 
@@ -393,22 +420,6 @@ __device__ __forceinline__ void row_span(const float4 e0, const float4 e1, const
     xl = (int)fminf(fmaxf(fl, x0), x1);
     xr = (int)fminf(fmaxf(fr, x0), x1);
     if (xr < xl) xr = xl;
-}
-
-// Rectangles and tile ellipses in depth order (zero for culled Gaussians), so
-// the kernels below read them with coalesced loads.
-__global__ void gather_rect_kernel(int n, const uint64_t* __restrict__ dsorted, const int* __restrict__ tiles,
-                                   const ushort4* __restrict__ rect, const float4* __restrict__ ell,
-                                   ushort4* __restrict__ drect, float4* __restrict__ dell)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const uint32_t gid = (uint32_t)dsorted[j];
-    const bool vis = tiles[gid] > 0;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    drect[j] = vis ? rect[gid] : make_ushort4(0, 0, 0, 0);
-    dell[2 * j] = vis ? ell[2 * (size_t)gid] : z;
-    dell[2 * j + 1] = vis ? ell[2 * (size_t)gid + 1] : z;
 }
 
 // Copies of chunk c (depth-sorted Gaussians [c*chunk, (c+1)*chunk)) per tile,
@@ -606,14 +617,13 @@ struct SortWs {
     uint64_t *eA, *eB;
     ushort4* drect;
     float4* dell;
-    uint32_t *counts, *base, *partials, *misc;
-    uint32_t* sort_state;   // [passes][256] digit counts / offsets, then [passes][blocks][256] look-back words
+    uint32_t *counts, *base, *partials;   // counts: the depth sort's per-tile digit counts / offsets
+    uint32_t* sort_state;   // the depth sort's digit totals, [passes][256]
     uint8_t* flags;         // lazy placement: two tile-activity arrays and two row-group arrays, [kMaxTiles] each
     int nchunks, chunk;
     size_t bytes;
 };
 
-inline int nblocks(int64_t n) { return (int)((n + kTile - 1) / kTile); }
 
 __host__ __device__ constexpr int chunks_for(int n)
 {
@@ -622,23 +632,19 @@ __host__ __device__ constexpr int chunks_for(int n)
 
 __host__ __device__ constexpr size_t seg(size_t bytes) { return (bytes + 255) / 256 * 256; }
 
-__host__ __device__ constexpr size_t sort_state_words(int n)
-{
-    return (size_t)kSortPasses * 256 * (1 + (size_t)((n + kTile - 1) / kTile));
-}
+// The depth sort's digit totals, [passes][256].
+__host__ __device__ constexpr size_t sort_state_words(int) { return (size_t)kSortPasses * 256; }
+
+// The depth sort's per-tile counts / offsets, [256][sort_row(n)].
+__host__ __device__ constexpr size_t sort_count_words(int n) { return 256ull * sort_row(n); }
 
 // Scratch layout of le_bin_sort for n Gaussians (independent of the copy count).
-// misc: [0, 4) the passes' virtual-block counters, [4] the sort's timeout flag.
 __host__ __device__ constexpr size_t sort_ws_bytes(int n)
 {
-    return seg(8ull * n) * 3 + seg(32ull * n) + seg(4ull * (256ull * ((n + kTile - 1) / kTile) + 1)) +
+    return seg(8ull * n) * 3 + seg(32ull * n) + seg(4ull * sort_count_words(n)) +
            seg(4ull * ((size_t)kMaxTiles * chunks_for(n) + 1)) +
-           seg(4ull * (((size_t)kMaxTiles * chunks_for(n) + 1 > 256ull * ((n + kTile - 1) / kTile) + 1
-                            ? (size_t)kMaxTiles * chunks_for(n) + 1
-                            : 256ull * ((n + kTile - 1) / kTile) + 1) /
-                           kTile +
-                       2)) +
-           seg(4ull * 64) + seg(4ull * sort_state_words(n)) + seg(4ull * kMaxTiles);
+           seg(4ull * (((size_t)kMaxTiles * chunks_for(n) + 1) / kTile + 2)) + seg(4ull * sort_state_words(n)) +
+           seg(4ull * kMaxTiles);
 }
 
 SortWs sort_ws_layout(char* base, int32_t n)
@@ -652,34 +658,39 @@ SortWs sort_ws_layout(char* base, int32_t n)
     };
     w.nchunks = chunks_for(n);
     w.chunk = n > 0 ? (n + w.nchunks - 1) / w.nchunks : 1;
-    const size_t radix_len = 256ull * nblocks(n) + 1;
     const size_t count_len = (size_t)kMaxTiles * w.nchunks + 1;
-    const size_t scan_max = count_len > radix_len ? count_len : radix_len;
     w.eA = (uint64_t*)take(8ull * n);
     w.eB = (uint64_t*)take(8ull * n);
     w.drect = (ushort4*)take(8ull * n);
     w.dell = (float4*)take(32ull * n);
-    w.counts = (uint32_t*)take(4ull * radix_len);
+    w.counts = (uint32_t*)take(4ull * sort_count_words(n));
     w.base = (uint32_t*)take(4ull * count_len);
-    w.partials = (uint32_t*)take(4ull * (scan_max / kTile + 2));
-    w.misc = (uint32_t*)take(4ull * 64);
+    w.partials = (uint32_t*)take(4ull * (count_len / kTile + 2));
     w.sort_state = (uint32_t*)take(4ull * sort_state_words(n));
     w.flags = (uint8_t*)take(4ull * kMaxTiles);
     w.bytes = off;
     return w;
 }
 
-// The four passes (the histograms are in w.sort_state, counted by
-// depth_elems_kernel).  Result in *cur.
-le_status depth_sort(uint64_t*& cur, uint64_t*& alt, int n, const SortWs& w, cudaStream_t s)
+// The four passes (pass 0's counts are in w.counts and w.sort_state, counted
+// by depth_elems_kernel).  Result in *cur; the rectangles and tile ellipses in
+// depth order in w.drect and w.dell.
+le_status depth_sort(uint64_t*& cur, uint64_t*& alt, int n, const SortWs& w, const int* tiles, const ushort4* rect,
+                     const float4* ell, cudaStream_t s)
 {
-    const int nb = nblocks(n);
-    digit_base_kernel<<<1, kSortPasses * 256, 0, s>>>(w.sort_state);
-    LE_LAUNCHED();
+    const int nt = sort_tiles(n), row = sort_row(n);
     for (int q = 0; q < kSortPasses; ++q) {
-        uint32_t* status = w.sort_state + kSortPasses * 256 + (size_t)q * nb * 256;
-        onesweep_kernel<<<nb, kThreads, 0, s>>>(cur, alt, n, 32 + 8 * q, w.sort_state + q * 256, status,
-                                                w.misc + q, w.misc + 4);
+        const int shift = 32 + 8 * q;
+        uint32_t* totals = w.sort_state + 256 * q;
+        if (q > 0) {
+            sort_count_kernel<<<nt, kSortThreads, 0, s>>>(cur, n, shift, w.counts, row, totals);
+            LE_LAUNCHED();
+        }
+        sort_rowscan_kernel<<<256 / 8, 256, 0, s>>>(w.counts, nt, row, totals);
+        LE_LAUNCHED();
+        SortGather g{};
+        if (q == kSortPasses - 1) g = SortGather{tiles, rect, ell, w.drect, w.dell};
+        sort_scatter_kernel<<<nt, kSortThreads, 0, s>>>(cur, alt, n, shift, w.counts, row, g);
         LE_LAUNCHED();
         uint64_t* t = cur;
         cur = alt;
@@ -736,18 +747,17 @@ le_status bin_prepare(const le_camera* cam, int32_t n, const float* depth, const
     if (n == 0) return LE_OK;
 
     // 1-2: sort the Gaussians by depth (stable: equal depths keep index order; culled last)
-    LE_CUDA(cudaMemsetAsync(w.misc, 0, 4 * 64, s));
     LE_CUDA(cudaMemsetAsync(w.sort_state, 0, 4 * sort_state_words(n), s));
-    depth_elems_kernel<<<(n + 1023) / 1024, 256, 0, s>>>(n, depth, tiles_touched, w.eA, w.sort_state);
+    depth_elems_kernel<<<sort_tiles(n), kSortThreads, 0, s>>>(n, depth, tiles_touched, w.eA, w.counts, sort_row(n),
+                                                              w.sort_state);
     LE_LAUNCHED();
     cur = w.eA;
     uint64_t* alt = w.eB;
-    if ((st = depth_sort(cur, alt, n, w, s)) != LE_OK) return st;
-    // 3: rectangles and ellipses in depth order; copies per (tile, chunk of depth-sorted Gaussians)
-    gather_rect_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, cur, tiles_touched, reinterpret_cast<const ushort4*>(rect),
-                                                       reinterpret_cast<const float4*>(tile_ellipse), w.drect,
-                                                       w.dell);
-    LE_LAUNCHED();
+    // 3: (with the last pass) rectangles and ellipses in depth order
+    if ((st = depth_sort(cur, alt, n, w, tiles_touched, reinterpret_cast<const ushort4*>(rect),
+                         reinterpret_cast<const float4*>(tile_ellipse), s)) != LE_OK)
+        return st;
+    // copies per (tile, chunk of depth-sorted Gaussians)
     const size_t diff_smem = sizeof(int) * (TX + 1) * TY;
     if (diff_smem > 48 * 1024)
         LE_CUDA(cudaFuncSetAttribute(chunk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diff_smem));
@@ -756,14 +766,9 @@ le_status bin_prepare(const le_camera* cam, int32_t n, const float* depth, const
     // 4: one exclusive scan in tile-major order gives every (tile, chunk) base and K
     const int len = ntiles * w.nchunks;
     if ((st = exclusive_scan(DirectIn{w.base}, len, w.base, w.partials, w.base + len, s)) != LE_OK) return st;
-    uint32_t K32 = 0, sort_err = 0;
+    uint32_t K32 = 0;
     LE_CUDA(cudaMemcpyAsync(&K32, w.base + len, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    LE_CUDA(cudaMemcpyAsync(&sort_err, w.misc + 4, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     LE_CUDA(cudaStreamSynchronize(s));
-    if (sort_err) {
-        set_error("the depth sort gave up on a bounded wait");
-        return LE_ERR_TIMEOUT;
-    }
     *k_out = K32;
     if ((int64_t)K32 > k_cap) {
         set_error("instance count K = %u exceeds k_cap = %lld", K32, (long long)k_cap);
