@@ -472,129 +472,105 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
         counts[(size_t)t * nchunks + blockIdx.x] = (uint32_t)diff[(t / TX) * W1 + (t % TX)];
 }
 
-// Placement.  Block (g, C): tile rows [R g, R g + R) (R = kPlaceRows), one per warp, and the
-// Gaussians of super-chunk C (count chunks [C*cs, (C+1)*cs)).  The cursor of
+// Placement.  Block (g, C): tile rows [R g, R g + R) (R = kPlaceRows) and the
+// Gaussians of super-chunk C (count chunks [C*cs, (C+1)*cs)).  Each warp owns one
+// row and one segment of 32 tile columns (NS segments per row); the cursor of
 // tile (row, tx) starts at base[t * nchunks + C*cs] -- the exclusive scan of the
 // counts in tile-major order -- and lives in a register of lane tx % 32 of the
-// row's warp, so no two threads share a cursor and no barrier is needed between
-// Gaussians.  The block first compacts, 4 per thread at a time and in depth order, the
-// super-chunk's Gaussians whose rectangle meets its rows; a warp then takes
-// those 32 at a time: each lane computes the row span of its Gaussian (when its
-// rectangle covers the row), a ballot keeps the non-empty ones and, for each in
-// depth order, every lane whose tiles fall in the span writes them.  Only one cursor per
-// (tile, block) advances at a time, so the partly written output sectors stay
-// few enough to remain in L2.
-constexpr int kPlaceRows = LE_PLACE_ROWS;          // tile rows per block, one warp each
-constexpr int kPlaceThreads = 32 * kPlaceRows;
+// row's warp for that segment, so no two threads share a cursor and no barrier
+// is needed between Gaussians.  Per round the block compacts, in depth order,
+// the super-chunk's Gaussians whose rectangle meets its rows, computes each
+// (row, Gaussian) tile span once into shared memory, and every warp then walks
+// the spans of its row that meet its segment, in depth order, each lane writing
+// the copies of its tile.  Only one cursor per (tile, block) advances at a time,
+// so the partly written output sectors stay few enough to remain in L2.
+constexpr int kPlaceRows = LE_PLACE_ROWS;   // tile rows per block
 
-// Exclusive scan of one value per thread over a block of kPlaceThreads threads.
-__device__ __forceinline__ uint32_t place_block_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[w] = x;
-    __syncthreads();
-    uint32_t before = 0, all = 0;
-#pragma unroll
-    for (int k = 0; k < kPlaceRows; ++k) {
-        const uint32_t t = warp_sums[k];
-        if (k < w) before += t;
-        all += t;
-    }
-    *total = all;
-    return before + x - v;
-}
-
-constexpr int kPlaceBatch = 4 * kPlaceThreads;   // Gaussians examined per compaction round
+template <int NS>
+struct PlaceShape {
+    static constexpr int kThreads = 32 * kPlaceRows * NS;
+    static constexpr int kItems = NS <= 2 ? 4 : (NS <= 4 ? 2 : 1);   // Gaussians per thread per round
+    static constexpr int kBatch = kItems * kThreads;                 // <= 1024
+};
 
 // tile_act / rows_act (nullable): only tiles with a non-zero flag get copies,
 // blocks of row groups without one return at once; super-chunk blockIdx.y is
 // super_base + blockIdx.y.
-template <int NK>
-__global__ void __launch_bounds__(kPlaceThreads) place_kernel(int n, const uint64_t* __restrict__ dsorted,
-                                                              const ushort4* __restrict__ drect,
-                                                              const float4* __restrict__ dell,
-                                                              const float* __restrict__ depth, int TX, int TY,
-                                                              int super_chunk, int cstride, int nchunks,
-                                                              const uint32_t* __restrict__ base,
-                                                              uint32_t* __restrict__ ids, uint64_t* __restrict__ keys,
-                                                              const uint8_t* __restrict__ tile_act,
-                                                              const uint8_t* __restrict__ rows_act, int super_base)
+template <int NS>
+__global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
+    int n, const uint64_t* __restrict__ dsorted, const ushort4* __restrict__ drect, const float4* __restrict__ dell,
+    const float* __restrict__ depth, int TX, int TY, int super_chunk, int cstride, int nchunks,
+    const uint32_t* __restrict__ base, uint32_t* __restrict__ ids, uint64_t* __restrict__ keys,
+    const uint8_t* __restrict__ tile_act, const uint8_t* __restrict__ rows_act, int super_base)
 {
+    using S = PlaceShape<NS>;
     if (rows_act && !rows_act[blockIdx.x]) return;
-    __shared__ uint32_t sg[kPlaceBatch], sj[kPlaceBatch];
-    __shared__ ushort4 sr[kPlaceBatch];
-    __shared__ uint32_t ws[kPlaceRows];
-    const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kPlaceRows + (threadIdx.x >> 5);
-    const bool row_ok = row < TY;
+    __shared__ uint32_t sg[S::kBatch], sj[S::kBatch];
+    __shared__ ushort4 sr[S::kBatch];
+    __shared__ uint32_t span[kPlaceRows][S::kBatch];   // xl | xr << 16 of the row's tiles, 0 = none
+    __shared__ uint32_t ws[S::kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rloc = warp / NS, seg = warp % NS;
     const int rb = blockIdx.x * kPlaceRows, re = min(TY, rb + kPlaceRows);
+    const int row = rb + rloc;
+    const bool row_ok = row < TY;
     const int C = super_base + blockIdx.y;
-    uint32_t ctr[NK];
-    uint32_t act = 0;   // bit k: this lane's tile lane + 32 k takes copies
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        const int tx = lane + 32 * k;
-        const bool ok = row_ok && tx < TX;
-        ctr[k] = ok ? base[(size_t)(row * TX + tx) * nchunks + (size_t)C * cstride] : 0u;
-        if (ok && (!tile_act || tile_act[row * TX + tx])) act |= 1u << k;
-    }
+    const int tx = 32 * seg + lane, slo = 32 * seg, shi = min(TX, 32 * seg + 32);
+    const bool mine = row_ok && tx < TX && (!tile_act || tile_act[row * TX + tx]);
+    uint32_t ctr = mine ? base[(size_t)(row * TX + tx) * nchunks + (size_t)C * cstride] : 0u;
     const int j0 = C * super_chunk, j1 = min(n, j0 + super_chunk);
-    for (int jb = j0; jb < j1; jb += kPlaceBatch) {
-        // compaction: the batch's Gaussians whose rectangle meets this block's
-        // rows, in depth order (thread t examines 4 consecutive ones)
+    for (int jb = j0; jb < j1; jb += S::kBatch) {
+        // compaction: the round's Gaussians whose rectangle meets this block's
+        // rows, in depth order (thread t examines kItems consecutive ones)
         __syncthreads();
-        ushort4 rr[4];
+        ushort4 rr[S::kItems];
         uint32_t flags = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int j = jb + 4 * threadIdx.x + k;
+        for (int k = 0; k < S::kItems; ++k) {
+            const int j = jb + S::kItems * threadIdx.x + k;
             rr[k] = j < j1 ? drect[j] : make_ushort4(0, 0, 0, 0);
             if (rr[k].z > rr[k].x && rr[k].y < re && rr[k].w > rb) flags |= 1u << k;
         }
         uint32_t m = 0;
-        uint32_t pos = place_block_scan((uint32_t)__popc(flags), ws, &m);
+        uint32_t pos = block_exclusive_scan<S::kThreads / 32>((uint32_t)__popc(flags), ws, &m);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < S::kItems; ++k)
             if (flags & (1u << k)) {
-                const int j = jb + 4 * threadIdx.x + k;
+                const int j = jb + S::kItems * threadIdx.x + k;
                 sr[pos] = rr[k];
                 sg[pos] = (uint32_t)dsorted[j];
                 sj[pos] = (uint32_t)j;
                 ++pos;
             }
         __syncthreads();
+        // the tile spans of every (row of the block, compacted Gaussian)
+        for (int q = threadIdx.x; q < (int)m; q += S::kThreads) {
+            const ushort4 r = sr[q];
+            const size_t jj = sj[q];
+            const float4 e0 = __ldg(dell + 2 * jj), e1 = __ldg(dell + 2 * jj + 1);
+#pragma unroll
+            for (int k = 0; k < kPlaceRows; ++k) {
+                const int ty = rb + k;
+                int xl = 0, xr = 0;
+                if (ty < re && r.y <= ty && ty < r.w) row_span(e0, e1, r, ty, xl, xr);
+                span[k][q] = xr > xl ? (uint32_t)xl | ((uint32_t)xr << 16) : 0u;
+            }
+        }
+        __syncthreads();
         if (!row_ok) continue;
         for (int q0 = 0; q0 < (int)m; q0 += 32) {
-            int xl = 0, xr = 0;
-            if (q0 + lane < (int)m) {
-                const ushort4 r = sr[q0 + lane];
-                if (r.y <= row && row < r.w) {
-                    const size_t jj = sj[q0 + lane];
-                    row_span(__ldg(dell + 2 * jj), __ldg(dell + 2 * jj + 1), r, row, xl, xr);
-                }
-            }
-            uint32_t mask = __ballot_sync(0xffffffffu, xr > xl);
+            const uint32_t sp = q0 + lane < (int)m ? span[rloc][q0 + lane] : 0u;
+            const int xl = (int)(sp & 0xFFFFu), xr = (int)(sp >> 16);
+            uint32_t mask = __ballot_sync(0xffffffffu, xr > xl && xl < shi && xr > slo);
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const int bl = __shfl_sync(0xffffffffu, xl, b), br = __shfl_sync(0xffffffffu, xr, b);
-                const uint32_t gid = sg[q0 + b];
-                const uint32_t dbits = keys ? __float_as_uint(depth[gid]) : 0u;
-#pragma unroll
-                for (int k = 0; k < NK; ++k) {
-                    const int tx = lane + 32 * k;
-                    if (tx >= bl && tx < br && ((act >> k) & 1u)) {
-                        const uint32_t p = ctr[k];
-                        ids[p] = gid;
-                        if (keys) keys[p] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | dbits;
-                        ctr[k] = p + 1;
-                    }
+                const uint32_t spb = span[rloc][q0 + b];
+                if (mine && tx >= (int)(spb & 0xFFFFu) && tx < (int)(spb >> 16)) {
+                    const uint32_t gid = sg[q0 + b];
+                    ids[ctr] = gid;
+                    if (keys) keys[ctr] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | __float_as_uint(depth[gid]);
+                    ++ctr;
                 }
             }
         }
@@ -807,10 +783,10 @@ le_status place(const le_camera* cam, int32_t n, const float* depth, const SortW
     if (s1 <= s0) return LE_OK;
     const dim3 grid(g.ngroups, s1 - s0);
     const int TX = tiles_x(cam), TY = tiles_y(cam);
-#define LE_PLACE(NK)                                                                                             \
-    place_kernel<NK><<<grid, kPlaceThreads, 0, s>>>(n, cur, w.drect, w.dell, depth, TX, TY, w.chunk * g.cs, g.cs, \
-                                                    w.nchunks, w.base, sorted_ids, sorted_keys, tile_act,      \
-                                                    rows_act, s0)
+#define LE_PLACE(NS)                                                                                         \
+    place_kernel<NS><<<grid, PlaceShape<NS>::kThreads, 0, s>>>(n, cur, w.drect, w.dell, depth, TX, TY,          \
+                                                              w.chunk * g.cs, g.cs, w.nchunks, w.base,         \
+                                                              sorted_ids, sorted_keys, tile_act, rows_act, s0)
     switch (g.nk) {
         case 1: LE_PLACE(1); break;
         case 2: LE_PLACE(2); break;

@@ -47,79 +47,127 @@ __device__ __forceinline__ float splat_alpha0(float opacity, float q)
     return __fmul_rn(opacity, ex2_approx(-q));
 }
 
-__global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
-                                                            const uint32_t* __restrict__ ids,
-                                                            const uint2* __restrict__ ranges,
-                                                            float* __restrict__ out_rgb, float* __restrict__ out_feat,
-                                                            float* __restrict__ out_unc, float* __restrict__ T_final,
-                                                            int* __restrict__ n_contrib)
+// Paired FP32 arithmetic: one instruction performs the IEEE round-to-nearest
+// operation on both components, each exactly as the scalar operation would.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sel2(bool x, bool y, float2 v) { return make_float2(x ? v.x : 0.f, y ? v.y : 0.f); }
+
+// Forward compositing state of one thread's two pixels (rows y and y + 8 of a
+// column): transmittance, the 12 colour sums (rgb, u, s_G), the list position
+// after the last blended Gaussian, and whether each pixel has stopped.
+struct PixelPair {
+    float2 T;
+    float2 acc[12];
+    int last[2];
+    bool done[2];
+};
+
+// Blends staged records [0, cnt) (list positions pos0 + j) front to back into
+// both pixels.  Per pixel: skip a Gaussian with q < 0 or alpha < 1/255, stop
+// before the one that would make T (1 - alpha) < 1e-4.
+__device__ __forceinline__ void blend_batch(const float4 (*rec)[kBlock], int cnt, int pos0, float fpx, float2 npy,
+                                            PixelPair& s)
+{
+    for (int j = 0; j < cnt && !(s.done[0] && s.done[1]); ++j) {
+        const float4 g0 = rec[0][j], g1 = rec[1][j];
+        const float dx = __fsub_rn(g0.x, fpx);
+        const float ax = splat_ax(g0.z, dx), bx = splat_bx(g0.w, dx);
+        const float2 dy = __fadd2_rn(f2(g0.y), npy);
+        const float2 q = __ffma2_rn(f2(g1.x), __fmul2_rn(dy, dy), __ffma2_rn(f2(bx), dy, f2(ax)));
+        const float2 a0 = __fmul2_rn(f2(g1.y), make_float2(ex2_approx(-q.x), ex2_approx(-q.y)));
+        const float2 alpha = make_float2(fminf(0.99f, a0.x), fminf(0.99f, a0.y));
+        const float2 test = __fmul2_rn(s.T, __fadd2_rn(f2(1.f), make_float2(-alpha.x, -alpha.y)));
+        const bool okx = !s.done[0] && q.x >= 0.f && alpha.x >= (1.f / 255.f);
+        const bool oky = !s.done[1] && q.y >= 0.f && alpha.y >= (1.f / 255.f);
+        const bool stopx = okx && test.x < 1e-4f, stopy = oky && test.y < 1e-4f;
+        s.done[0] = s.done[0] || stopx;
+        s.done[1] = s.done[1] || stopy;
+        const bool bx_ = okx && !stopx, by_ = oky && !stopy;
+        if (!(bx_ || by_)) continue;
+        const float2 w = __fmul2_rn(sel2(bx_, by_, alpha), s.T);
+        const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
+        const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
+#pragma unroll
+        for (int c = 0; c < 12; ++c) s.acc[c] = __ffma2_rn(f2(f[c]), w, s.acc[c]);   // rgb, u, s_G 0..7
+        if (bx_) {
+            s.T.x = test.x;
+            s.last[0] = pos0 + j + 1;
+        }
+        if (by_) {
+            s.T.y = test.y;
+            s.last[1] = pos0 + j + 1;
+        }
+    }
+}
+
+// Stages list entries [s0 + b0, s0 + b0 + 256) of a tile: 128 threads, two records each.
+__device__ __forceinline__ void stage_batch(float4 (*rec)[kBlock], const float4* __restrict__ splat,
+                                            const uint32_t* __restrict__ ids, uint32_t s0, int b0, int n)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = threadIdx.x + h * (kBlock / 2);
+        const int k = b0 + i;
+        if (k < n) {
+            const float4* r = splat + (size_t)ids[s0 + k] * 5;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) rec[c][i] = __ldg(r + c);
+        }
+    }
+}
+
+// Walks list entries [s0, s0 + n) of the tile (list positions off + k) for both pixels.
+__device__ __forceinline__ void composite_range(float4 (*rec)[kBlock], const float4* __restrict__ splat,
+                                                const uint32_t* __restrict__ ids, uint32_t s0, int n, int off,
+                                                float fpx, float2 npy, PixelPair& s)
+{
+    for (int b0 = 0; b0 < n; b0 += kBlock) {
+        if (__syncthreads_count(s.done[0] && s.done[1]) == kBlock / 2) break;
+        stage_batch(rec, splat, ids, s0, b0, n);
+        __syncthreads();
+        blend_batch(rec, min(kBlock, n - b0), off + b0, fpx, npy, s);
+    }
+}
+
+// One CTA of 128 threads per 16x16 tile; thread t owns column t % 16 of rows t / 16 and t / 16 + 8.
+__global__ void __launch_bounds__(kBlock / 2) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
+                                                                const uint32_t* __restrict__ ids,
+                                                                const uint2* __restrict__ ranges,
+                                                                float* __restrict__ out_rgb, float* __restrict__ out_feat,
+                                                                float* __restrict__ out_unc, float* __restrict__ T_final,
+                                                                int* __restrict__ n_contrib)
 {
     __shared__ float4 rec[5][kBlock];
     const int tile = blockIdx.x;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
-    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
-    const bool inside = px < cam.W && py < cam.H;
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py0 = ty * LE_TILE + (threadIdx.x >> 4);
+    const bool in0 = px < cam.W && py0 < cam.H, in1 = px < cam.W && py0 + 8 < cam.H;
     const uint2 rg = ranges[tile];
-    const int n = (int)(rg.y - rg.x);
-    const float fpx = (float)px, fpy = (float)py;
-
-    bool done = !inside;
-    float T = 1.f;
-    float acc[12];
+    PixelPair s;
+    s.T = f2(1.f);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
-    int last = 0;
-
-    for (int b0 = 0; b0 < n; b0 += kBlock) {
-        if (__syncthreads_count(done) == kBlock) break;
-        const int k = b0 + threadIdx.x;
-        if (k < n) {
-            const float4* r = splat + (size_t)ids[rg.x + k] * 5;
+    for (int c = 0; c < 12; ++c) s.acc[c] = f2(0.f);
+    s.last[0] = s.last[1] = 0;
+    s.done[0] = !in0;
+    s.done[1] = !in1;
+    composite_range(rec, splat, ids, rg.x, (int)(rg.y - rg.x), 0, (float)px,
+                    make_float2(-(float)py0, -(float)(py0 + 8)), s);
+    const size_t P = (size_t)cam.W * cam.H;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
-        }
-        __syncthreads();
-        const int cnt = min(kBlock, n - b0);
-        for (int j = 0; !done && j < cnt; ++j) {
-            const float4 g0 = rec[0][j], g1 = rec[1][j];
-            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
-            const float q = splat_q(splat_ax(g0.z, dx), splat_bx(g0.w, dx), g1.x, dy);
-            if (q < 0.f) continue;
-            const float alpha = fminf(0.99f, splat_alpha0(g1.y, q));
-            if (alpha < (1.f / 255.f)) continue;
-            const float test = T * (1.f - alpha);
-            if (test < 1e-4f) {
-                done = true;
-                break;
-            }
-            const float w = alpha * T;
-            const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
-            acc[0] = fmaf(g1.z, w, acc[0]);
-            acc[1] = fmaf(g1.w, w, acc[1]);
-            acc[2] = fmaf(g2.x, w, acc[2]);
-            acc[3] = fmaf(g2.y, w, acc[3]);     // uncertainty
-            acc[4] = fmaf(g2.z, w, acc[4]);     // feature 0..7
-            acc[5] = fmaf(g2.w, w, acc[5]);
-            acc[6] = fmaf(g3.x, w, acc[6]);
-            acc[7] = fmaf(g3.y, w, acc[7]);
-            acc[8] = fmaf(g3.z, w, acc[8]);
-            acc[9] = fmaf(g3.w, w, acc[9]);
-            acc[10] = fmaf(g4.x, w, acc[10]);
-            acc[11] = fmaf(g4.y, w, acc[11]);
-            T = test;
-            last = b0 + j + 1;
-        }
+    for (int h = 0; h < 2; ++h) {
+        if (!(h ? in1 : in0)) continue;
+        const size_t o = (size_t)(py0 + 8 * h) * cam.W + px;
+        const float T = h ? s.T.y : s.T.x;
+        const auto comp = [&](int c) { return h ? s.acc[c].y : s.acc[c].x; };
+        out_rgb[o] = __fmaf_rn(T, cam.bg[0], comp(0));
+        out_rgb[P + o] = __fmaf_rn(T, cam.bg[1], comp(1));
+        out_rgb[2 * P + o] = __fmaf_rn(T, cam.bg[2], comp(2));
+        out_unc[o] = comp(3);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) out_feat[c * P + o] = comp(4 + c);
+        T_final[o] = T;
+        n_contrib[o] = s.last[h];
     }
-    if (!inside) return;
-    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
-    out_rgb[o] = __fmaf_rn(T, cam.bg[0], acc[0]);
-    out_rgb[P + o] = __fmaf_rn(T, cam.bg[1], acc[1]);
-    out_rgb[2 * P + o] = __fmaf_rn(T, cam.bg[2], acc[2]);
-    out_unc[o] = acc[3];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[4 + c];
-    T_final[o] = T;
-    n_contrib[o] = last;
 }
 
 // One phase of the lazily placed forward render (le_bin_render_fwd): tile t
@@ -135,7 +183,7 @@ __global__ void __launch_bounds__(kBlock) render_fwd_kernel(CamParams cam, const
 // the tiles active in this phase.
 constexpr int kStopped = 1 << 30;
 
-__global__ void __launch_bounds__(kBlock) render_fwd_phase_kernel(
+__global__ void __launch_bounds__(kBlock / 2) render_fwd_phase_kernel(
     CamParams cam, const float4* __restrict__ splat, const uint32_t* __restrict__ ids,
     const uint32_t* __restrict__ base, int nchunks, int c_lo, int c_hi, const uint8_t* __restrict__ act,
     uint8_t* __restrict__ next_act, uint8_t* __restrict__ next_rows, float* __restrict__ out_rgb,
@@ -145,89 +193,67 @@ __global__ void __launch_bounds__(kBlock) render_fwd_phase_kernel(
     const int tile = blockIdx.x;
     if (act && !act[tile]) return;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
-    const int px = tx * LE_TILE + (threadIdx.x & 15), py = ty * LE_TILE + (threadIdx.x >> 4);
-    const bool inside = px < cam.W && py < cam.H;
-    const size_t P = (size_t)cam.W * cam.H, o = (size_t)py * cam.W + px;
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py0 = ty * LE_TILE + (threadIdx.x >> 4);
+    const bool in[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 8 < cam.H};
+    const size_t P = (size_t)cam.W * cam.H;
+    const size_t o[2] = {(size_t)py0 * cam.W + px, (size_t)(py0 + 8) * cam.W + px};
     const uint32_t tstart = base[(size_t)tile * nchunks], tend = base[(size_t)(tile + 1) * nchunks];
     const uint32_t s0 = c_lo == 0 ? tstart : base[(size_t)tile * nchunks + c_lo];
     const uint32_t s1 = c_hi >= nchunks ? tend : base[(size_t)tile * nchunks + c_hi];
     const int n = (int)(s1 - s0), off = (int)(s0 - tstart);
-    const float fpx = (float)px, fpy = (float)py;
 
-    bool done = !inside;
-    float T = 1.f;
-    float acc[12];
+    PixelPair s;
+    s.T = f2(1.f);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = 0.f;
-    int last = 0;
-    if (c_lo > 0 && inside) {
-        T = T_final[o];
-        acc[0] = out_rgb[o];
-        acc[1] = out_rgb[P + o];
-        acc[2] = out_rgb[2 * P + o];
-        acc[3] = out_unc[o];
+    for (int c = 0; c < 12; ++c) s.acc[c] = f2(0.f);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[4 + c] = out_feat[c * P + o];
-        const int nc = n_contrib[o];
-        last = nc & (kStopped - 1);
-        done = (nc & kStopped) != 0;
-    }
-
-    for (int b0 = 0; b0 < n; b0 += kBlock) {
-        if (__syncthreads_count(done) == kBlock) break;
-        const int k = b0 + threadIdx.x;
-        if (k < n) {
-            const float4* r = splat + (size_t)ids[s0 + k] * 5;
+    for (int h = 0; h < 2; ++h) {
+        s.last[h] = 0;
+        s.done[h] = !in[h];
+        if (c_lo > 0 && in[h]) {
+            float v[12];
+            v[0] = out_rgb[o[h]];
+            v[1] = out_rgb[P + o[h]];
+            v[2] = out_rgb[2 * P + o[h]];
+            v[3] = out_unc[o[h]];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) rec[q][threadIdx.x] = __ldg(r + q);
-        }
-        __syncthreads();
-        const int cnt = min(kBlock, n - b0);
-        for (int j = 0; !done && j < cnt; ++j) {
-            const float4 g0 = rec[0][j], g1 = rec[1][j];
-            const float dx = __fsub_rn(g0.x, fpx), dy = __fsub_rn(g0.y, fpy);
-            const float q = splat_q(splat_ax(g0.z, dx), splat_bx(g0.w, dx), g1.x, dy);
-            if (q < 0.f) continue;
-            const float alpha = fminf(0.99f, splat_alpha0(g1.y, q));
-            if (alpha < (1.f / 255.f)) continue;
-            const float test = T * (1.f - alpha);
-            if (test < 1e-4f) {
-                done = true;
-                break;
+            for (int c = 0; c < 8; ++c) v[4 + c] = out_feat[c * P + o[h]];
+            const float T = T_final[o[h]];
+            const int nc = n_contrib[o[h]];
+            if (h) {
+                s.T.y = T;
+#pragma unroll
+                for (int c = 0; c < 12; ++c) s.acc[c].y = v[c];
+            } else {
+                s.T.x = T;
+#pragma unroll
+                for (int c = 0; c < 12; ++c) s.acc[c].x = v[c];
             }
-            const float w = alpha * T;
-            const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
-            acc[0] = fmaf(g1.z, w, acc[0]);
-            acc[1] = fmaf(g1.w, w, acc[1]);
-            acc[2] = fmaf(g2.x, w, acc[2]);
-            acc[3] = fmaf(g2.y, w, acc[3]);
-            acc[4] = fmaf(g2.z, w, acc[4]);
-            acc[5] = fmaf(g2.w, w, acc[5]);
-            acc[6] = fmaf(g3.x, w, acc[6]);
-            acc[7] = fmaf(g3.y, w, acc[7]);
-            acc[8] = fmaf(g3.z, w, acc[8]);
-            acc[9] = fmaf(g3.w, w, acc[9]);
-            acc[10] = fmaf(g4.x, w, acc[10]);
-            acc[11] = fmaf(g4.y, w, acc[11]);
-            T = test;
-            last = off + b0 + j + 1;
+            s.last[h] = nc & (kStopped - 1);
+            s.done[h] = (nc & kStopped) != 0;
         }
     }
-    const bool complete = __syncthreads_count(done) == kBlock || s1 == tend;
+    composite_range(rec, splat, ids, s0, n, off, (float)px, make_float2(-(float)py0, -(float)(py0 + 8)), s);
+    const bool complete = __syncthreads_count(s.done[0] && s.done[1]) == kBlock / 2 || s1 == tend;
     if (!complete && threadIdx.x == 0) {
         next_act[tile] = 1;
         next_rows[ty / LE_PLACE_ROWS] = 1;
     }
-    if (!inside) return;
-    // the background only once the pixel is final (the same FMA as render_fwd_kernel)
-    out_rgb[o] = complete ? __fmaf_rn(T, cam.bg[0], acc[0]) : acc[0];
-    out_rgb[P + o] = complete ? __fmaf_rn(T, cam.bg[1], acc[1]) : acc[1];
-    out_rgb[2 * P + o] = complete ? __fmaf_rn(T, cam.bg[2], acc[2]) : acc[2];
-    out_unc[o] = acc[3];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) out_feat[c * P + o] = acc[4 + c];
-    T_final[o] = T;
-    n_contrib[o] = complete ? last : (last | (done ? kStopped : 0));
+    for (int h = 0; h < 2; ++h) {
+        if (!in[h]) continue;
+        const float T = h ? s.T.y : s.T.x;
+        const auto comp = [&](int c) { return h ? s.acc[c].y : s.acc[c].x; };
+        // the background only once the pixel is final (the same FMA as render_fwd_kernel)
+        out_rgb[o[h]] = complete ? __fmaf_rn(T, cam.bg[0], comp(0)) : comp(0);
+        out_rgb[P + o[h]] = complete ? __fmaf_rn(T, cam.bg[1], comp(1)) : comp(1);
+        out_rgb[2 * P + o[h]] = complete ? __fmaf_rn(T, cam.bg[2], comp(2)) : comp(2);
+        out_unc[o[h]] = comp(3);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) out_feat[c * P + o[h]] = comp(4 + c);
+        T_final[o[h]] = T;
+        n_contrib[o[h]] = complete ? s.last[h] : (s.last[h] | (s.done[h] ? kStopped : 0));
+    }
 }
 
 // One stage of a recursive-halving ("transpose") reduction of N values held by
@@ -273,12 +299,21 @@ __device__ __forceinline__ int field_of_lane(int lane)
     return valid >= 1 ? base : -1;
 }
 
+// Four pixels per thread -- rows y, y + 4, y + 8, y + 12 of one column -- in
+// two pairs (y, y + 4) and (y + 8, y + 12) whose arithmetic runs on paired
+// FP32 instructions.  Per Gaussian and thread the 12 channel gradients
+// w dL/dC_c and the dot products f . dL/dC are paired FMAs into (even pixel,
+// odd pixel) partial sums; the conic and mean gradients, which all share the
+// column's dx, come from three sums over the thread's pixels -- D = sum dP,
+// E = sum dP dy, F = sum dP dy^2 with dP = dL/dpower -- formed once per record:
+// dconic = (-dx^2 D / 2, -dx E, -F / 2), dmean = (-A dx D - B E, -C E - B dx D).
 template <int PPT>
 __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
     CamParams cam, const float4* __restrict__ splat, const uint32_t* __restrict__ ids, const uint2* __restrict__ ranges,
     const float* __restrict__ T_final, const int* __restrict__ n_contrib, const float* __restrict__ dL_drgb,
     const float* __restrict__ dL_dfeat, const float* __restrict__ dL_dunc, float4* __restrict__ grad2d)
 {
+    static_assert(PPT == 4, "two pixel pairs per thread");
     constexpr int NT = kBlock / PPT;
     __shared__ float4 rec[5][kBlock];
     __shared__ uint32_t sid[kBlock];
@@ -290,28 +325,44 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
     const float fpx = (float)px;
     const size_t P = (size_t)cam.W * cam.H;
 
-    float py[PPT], dC[PPT][12], T[PPT], Tf[PPT], S[PPT], bgdot[PPT];
+    // pair p holds pixels q = 2p (x) and 2p + 1 (y)
+    float2 npy[2], dC[2][12], T[2], Tf[2], S[2], nbg[2];
     int last[PPT];
     int lmax = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
         const int y = ty * LE_TILE + (threadIdx.x >> 4) + q * (LE_TILE / PPT);
-        py[q] = (float)y;
         const bool inside = px < cam.W && y < cam.H;
         const size_t o = (size_t)y * cam.W + px;
-        T[q] = inside ? T_final[o] : 0.f;
-        last[q] = inside ? n_contrib[o] : 0;
-        dC[q][0] = inside ? dL_drgb[o] : 0.f;
-        dC[q][1] = inside ? dL_drgb[P + o] : 0.f;
-        dC[q][2] = inside ? dL_drgb[2 * P + o] : 0.f;
-        dC[q][3] = inside ? dL_dunc[o] : 0.f;
+        float d[12];
+        d[0] = inside ? dL_drgb[o] : 0.f;
+        d[1] = inside ? dL_drgb[P + o] : 0.f;
+        d[2] = inside ? dL_drgb[2 * P + o] : 0.f;
+        d[3] = inside ? dL_dunc[o] : 0.f;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) dC[q][4 + c] = inside ? dL_dfeat[c * P + o] : 0.f;
-        Tf[q] = T[q];
-        // S = sum_c acc_c dL/dC_c, the "colour behind" seen through this pixel's
-        // upstream gradient; it obeys the blending recurrence of acc itself.
-        S[q] = 0.f;
-        bgdot[q] = cam.bg[0] * dC[q][0] + cam.bg[1] * dC[q][1] + cam.bg[2] * dC[q][2];
+        for (int c = 0; c < 8; ++c) d[4 + c] = inside ? dL_dfeat[c * P + o] : 0.f;
+        const float t = inside ? T_final[o] : 0.f;
+        last[q] = inside ? n_contrib[o] : 0;
+        // -bg . dL/dC (the background term of dL/dalpha); S = sum_c acc_c dL/dC_c, the
+        // "colour behind" seen through this pixel's upstream gradient, obeys the
+        // blending recurrence of acc itself
+        const float nb = -(cam.bg[0] * d[0] + cam.bg[1] * d[1] + cam.bg[2] * d[2]);
+        float2* pr[5] = {&npy[q >> 1], &T[q >> 1], &Tf[q >> 1], &S[q >> 1], &nbg[q >> 1]};
+        const float v[5] = {-(float)y, t, t, 0.f, nb};
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if (q & 1)
+                pr[k]->y = v[k];
+            else
+                pr[k]->x = v[k];
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            if (q & 1)
+                dC[q >> 1][c].y = d[c];
+            else
+                dC[q >> 1][c].x = d[c];
+        }
         lmax = max(lmax, last[q]);
     }
 
@@ -345,51 +396,69 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
             const float4 g0 = rec[0][j], g1 = rec[1][j];
             const float dx = __fsub_rn(g0.x, fpx);
             const float ax = splat_ax(g0.z, dx), bx = splat_bx(g0.w, dx);
-            float dy[PPT], G[PPT], a0[PPT], alpha[PPT];
-            bool contrib[PPT], any_mine = false;
+            // the forward kernel's skip decisions, per pixel, with identical roundings
+            float2 dy[2], G[2], al[2], a0[2];
+            bool cb[PPT], any_mine = false;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                dy[q] = __fsub_rn(g0.y, py[q]);
-                const float qq = splat_q(ax, bx, g1.x, dy[q]);
-                G[q] = ex2_approx(-qq);
-                a0[q] = __fmul_rn(g1.y, G[q]);
-                alpha[q] = fminf(0.99f, a0[q]);
-                contrib[q] = pos < last[q] && qq >= 0.f && alpha[q] >= (1.f / 255.f);
-                any_mine = any_mine || contrib[q];
+            for (int p = 0; p < 2; ++p) {
+                dy[p] = __fadd2_rn(f2(g0.y), npy[p]);
+                const float2 qq = __ffma2_rn(f2(g1.x), __fmul2_rn(dy[p], dy[p]), __ffma2_rn(f2(bx), dy[p], f2(ax)));
+                G[p] = make_float2(ex2_approx(-qq.x), ex2_approx(-qq.y));
+                a0[p] = __fmul2_rn(f2(g1.y), G[p]);
+                al[p] = make_float2(fminf(0.99f, a0[p].x), fminf(0.99f, a0[p].y));
+                cb[2 * p] = pos < last[2 * p] && qq.x >= 0.f && al[p].x >= (1.f / 255.f);
+                cb[2 * p + 1] = pos < last[2 * p + 1] && qq.y >= 0.f && al[p].y >= (1.f / 255.f);
+                any_mine = any_mine || cb[2 * p] || cb[2 * p + 1];
             }
             if (!__any_sync(0xffffffffu, any_mine)) continue;
             float gr[18];
+            {
+                float2 acc[12], sD = f2(0.f), sE = f2(0.f), sF = f2(0.f), sO = f2(0.f);
 #pragma unroll
-            for (int c = 0; c < 18; ++c) gr[c] = 0.f;
-            if (any_mine) {
-                const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
-                // the conic itself, for the mean gradient (dL/dpower is per unit of the natural exponent)
-                const float cA = g0.z * kConicUnscaleAC, cB = g0.w * kConicUnscaleB, cC = g1.x * kConicUnscaleAC;
-                const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
+                for (int c = 0; c < 12; ++c) acc[c] = f2(0.f);
+                if (any_mine) {
+                    const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
+                    const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    if (!contrib[q]) continue;
-                    const float inv1ma = __fdividef(1.f, 1.f - alpha[q]);
-                    T[q] *= inv1ma;
-                    const float w = alpha[q] * T[q];
-                    float fdc = 0.f;
+                    for (int p = 0; p < 2; ++p) {
+                        const bool cx = cb[2 * p], cy = cb[2 * p + 1];
+                        if (!(cx || cy)) continue;
+                        const float2 inv = make_float2(cx ? __fdividef(1.f, 1.f - al[p].x) : 1.f,
+                                                       cy ? __fdividef(1.f, 1.f - al[p].y) : 1.f);
+                        T[p] = __fmul2_rn(T[p], inv);
+                        const float2 am = sel2(cx, cy, al[p]);
+                        const float2 w = __fmul2_rn(am, T[p]);
+                        float2 fdc = __fmul2_rn(f2(f[0]), dC[p][0]);
 #pragma unroll
-                    for (int c = 0; c < 12; ++c) {
-                        gr[6 + c] = fmaf(w, dC[q][c], gr[6 + c]);      // rgb (6..8), unc (9), feat (10..17)
-                        fdc = fmaf(f[c], dC[q][c], fdc);
-                    }
-                    const float dalpha = T[q] * (fdc - S[q]) - Tf[q] * inv1ma * bgdot[q];
-                    S[q] = fmaf(alpha[q], fdc - S[q], S[q]);
-                    if (a0[q] < 0.99f) {
-                        const float dpow = dalpha * alpha[q];
-                        gr[5] = fmaf(dalpha, G[q], gr[5]);
-                        gr[2] = fmaf(-0.5f * dpow * dx, dx, gr[2]);
-                        gr[3] = fmaf(-dpow * dx, dy[q], gr[3]);
-                        gr[4] = fmaf(-0.5f * dpow * dy[q], dy[q], gr[4]);
-                        gr[0] = fmaf(dpow, -cA * dx - cB * dy[q], gr[0]);
-                        gr[1] = fmaf(dpow, -cC * dy[q] - cB * dx, gr[1]);
+                        for (int c = 0; c < 12; ++c) {
+                            acc[c] = __ffma2_rn(w, dC[p][c], acc[c]);      // rgb (0..2), unc (3), feat (4..11)
+                            if (c > 0) fdc = __ffma2_rn(f2(f[c]), dC[p][c], fdc);
+                        }
+                        const float2 diff = __fadd2_rn(fdc, make_float2(-S[p].x, -S[p].y));
+                        const float2 dal = __ffma2_rn(T[p], diff, __fmul2_rn(__fmul2_rn(Tf[p], inv), nbg[p]));
+                        S[p] = __ffma2_rn(am, diff, S[p]);
+                        // alpha below the 0.99 clamp: dalpha/dpower = alpha, dalpha/do = G
+                        const bool mx = cx && a0[p].x < 0.99f, my = cy && a0[p].y < 0.99f;
+                        const float2 dP = __fmul2_rn(dal, sel2(mx, my, al[p]));
+                        sO = __ffma2_rn(dal, sel2(mx, my, G[p]), sO);
+                        sD = __fadd2_rn(sD, dP);
+                        const float2 t = __fmul2_rn(dP, dy[p]);
+                        sE = __fadd2_rn(sE, t);
+                        sF = __ffma2_rn(t, dy[p], sF);
                     }
                 }
+                // the conic itself, for the mean gradient (dL/dpower is per unit of the natural exponent)
+                const float cA = g0.z * kConicUnscaleAC, cB = g0.w * kConicUnscaleB, cC = g1.x * kConicUnscaleAC;
+                const float D = sD.x + sD.y, E = sE.x + sE.y, F = sF.x + sF.y;
+                const float dxD = dx * D;
+                gr[0] = -(cA * dxD + cB * E);
+                gr[1] = -(cC * E + cB * dxD);
+                gr[2] = -0.5f * dx * dxD;
+                gr[3] = -dx * E;
+                gr[4] = -0.5f * F;
+                gr[5] = sO.x + sO.y;
+#pragma unroll
+                for (int c = 0; c < 12; ++c) gr[6 + c] = acc[c].x + acc[c].y;
             }
             warp_sum18(gr, lane);
             if (my_field >= 0) atomicAdd(reinterpret_cast<float*>(grad2d + (size_t)sid[j] * 5) + my_field, gr[0]);
@@ -409,7 +478,7 @@ le_status render_fwd_phase(const le_camera* cam, const float* splat, const uint3
                            int32_t* n_contrib, cudaStream_t s)
 {
     const CamParams cp = cam_params(cam);
-    render_fwd_phase_kernel<<<cp.TX * cp.TY, kBlock, 0, s>>>(cp, reinterpret_cast<const float4*>(splat), ids, base,
+    render_fwd_phase_kernel<<<cp.TX * cp.TY, kBlock / 2, 0, s>>>(cp, reinterpret_cast<const float4*>(splat), ids, base,
                                                             nchunks, c_lo, c_hi, act, next_act, next_rows, out_rgb,
                                                             out_feat, out_unc, T_final, n_contrib);
     LE_LAUNCHED();
@@ -429,7 +498,7 @@ extern "C" le_status le_render_fwd(const le_camera* cam, int32_t n, const float*
     LE_CHECK_ARG(n == 0 || (splat && aligned16(splat)), "splat must be non-null and 16-byte aligned");
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(tile_ranges) & 7u) == 0, "tile_ranges must be 8-byte aligned");
     const CamParams cp = cam_params(cam);
-    render_fwd_kernel<<<cp.TX * cp.TY, kBlock, 0, as_stream(stream)>>>(
+    render_fwd_kernel<<<cp.TX * cp.TY, kBlock / 2, 0, as_stream(stream)>>>(
         cp, reinterpret_cast<const float4*>(splat), sorted_ids, reinterpret_cast<const uint2*>(tile_ranges), out_rgb,
         out_feat, out_unc, T_final, n_contrib);
     LE_LAUNCHED();
