@@ -4,12 +4,13 @@
 //
 // One CTA per 16x16 tile.  The tile's depth-ordered range is streamed through
 // shared memory in batches of 256 splat records (80 B each, 16-byte loads);
-// every thread then reads the batch by broadcast.  The forward runs one pixel
-// per thread (pixels stop at different depths; pairing them costs more than it
-// saves), the backward four (rows y, y + 4, y + 8, y + 12; 64 threads per
-// tile), so each staged record read, each loop step and each warp reduction
-// serves four pixels.  The CTA stops fetching once every pixel's
-// transmittance has dropped below 1e-4 (__syncthreads_count ballot).
+// every thread then reads the batch by broadcast.  The forward runs two pixels
+// per thread (128 threads per tile), the backward four (64 threads per tile),
+// each warp on a compact block of rows, and both do the two-pixel arithmetic
+// with paired FP32 instructions; so each staged record read, loop step and
+// (backward) warp reduction serves several pixels.  The CTA stops fetching
+// once every pixel's transmittance has dropped below 1e-4
+// (__syncthreads_count ballot).
 //
 // The backward walks the same range back to front from each pixel's last
 // contributor, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
@@ -52,7 +53,7 @@ __device__ __forceinline__ float splat_alpha0(float opacity, float q)
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 sel2(bool x, bool y, float2 v) { return make_float2(x ? v.x : 0.f, y ? v.y : 0.f); }
 
-// Forward compositing state of one thread's two pixels (rows y and y + 8 of a
+// Forward compositing state of one thread's two pixels (rows y and y + 2 of a
 // column): transmittance, the 12 colour sums (rgb, u, s_G), the list position
 // after the last blended Gaussian, and whether each pixel has stopped.
 struct PixelPair {
@@ -129,7 +130,12 @@ __device__ __forceinline__ void composite_range(float4 (*rec)[kBlock], const flo
     }
 }
 
-// One CTA of 128 threads per 16x16 tile; thread t owns column t % 16 of rows t / 16 and t / 16 + 8.
+// Forward pixel layout: one CTA of 128 threads per 16x16 tile, warp w covering
+// the compact 16 x 4 block of rows [4w, 4w + 4) (its pixels tend to stop at
+// similar depths, so fewer lanes idle while the warp walks on); thread t owns
+// column t % 16 of rows fwd_row(t) and fwd_row(t) + 2.
+__device__ __forceinline__ int fwd_row(int t) { return 4 * (t >> 5) + ((t >> 4) & 1); }
+
 __global__ void __launch_bounds__(kBlock / 2) render_fwd_kernel(CamParams cam, const float4* __restrict__ splat,
                                                                 const uint32_t* __restrict__ ids,
                                                                 const uint2* __restrict__ ranges,
@@ -140,8 +146,8 @@ __global__ void __launch_bounds__(kBlock / 2) render_fwd_kernel(CamParams cam, c
     __shared__ float4 rec[5][kBlock];
     const int tile = blockIdx.x;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
-    const int px = tx * LE_TILE + (threadIdx.x & 15), py0 = ty * LE_TILE + (threadIdx.x >> 4);
-    const bool in0 = px < cam.W && py0 < cam.H, in1 = px < cam.W && py0 + 8 < cam.H;
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py0 = ty * LE_TILE + fwd_row(threadIdx.x);
+    const bool in0 = px < cam.W && py0 < cam.H, in1 = px < cam.W && py0 + 2 < cam.H;
     const uint2 rg = ranges[tile];
     PixelPair s;
     s.T = f2(1.f);
@@ -151,12 +157,12 @@ __global__ void __launch_bounds__(kBlock / 2) render_fwd_kernel(CamParams cam, c
     s.done[0] = !in0;
     s.done[1] = !in1;
     composite_range(rec, splat, ids, rg.x, (int)(rg.y - rg.x), 0, (float)px,
-                    make_float2(-(float)py0, -(float)(py0 + 8)), s);
+                    make_float2(-(float)py0, -(float)(py0 + 2)), s);
     const size_t P = (size_t)cam.W * cam.H;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         if (!(h ? in1 : in0)) continue;
-        const size_t o = (size_t)(py0 + 8 * h) * cam.W + px;
+        const size_t o = (size_t)(py0 + 2 * h) * cam.W + px;
         const float T = h ? s.T.y : s.T.x;
         const auto comp = [&](int c) { return h ? s.acc[c].y : s.acc[c].x; };
         out_rgb[o] = __fmaf_rn(T, cam.bg[0], comp(0));
@@ -193,10 +199,10 @@ __global__ void __launch_bounds__(kBlock / 2) render_fwd_phase_kernel(
     const int tile = blockIdx.x;
     if (act && !act[tile]) return;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
-    const int px = tx * LE_TILE + (threadIdx.x & 15), py0 = ty * LE_TILE + (threadIdx.x >> 4);
-    const bool in[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 8 < cam.H};
+    const int px = tx * LE_TILE + (threadIdx.x & 15), py0 = ty * LE_TILE + fwd_row(threadIdx.x);
+    const bool in[2] = {px < cam.W && py0 < cam.H, px < cam.W && py0 + 2 < cam.H};
     const size_t P = (size_t)cam.W * cam.H;
-    const size_t o[2] = {(size_t)py0 * cam.W + px, (size_t)(py0 + 8) * cam.W + px};
+    const size_t o[2] = {(size_t)py0 * cam.W + px, (size_t)(py0 + 2) * cam.W + px};
     const uint32_t tstart = base[(size_t)tile * nchunks], tend = base[(size_t)(tile + 1) * nchunks];
     const uint32_t s0 = c_lo == 0 ? tstart : base[(size_t)tile * nchunks + c_lo];
     const uint32_t s1 = c_hi >= nchunks ? tend : base[(size_t)tile * nchunks + c_hi];
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(kBlock / 2) render_fwd_phase_kernel(
             s.done[h] = (nc & kStopped) != 0;
         }
     }
-    composite_range(rec, splat, ids, s0, n, off, (float)px, make_float2(-(float)py0, -(float)(py0 + 8)), s);
+    composite_range(rec, splat, ids, s0, n, off, (float)px, make_float2(-(float)py0, -(float)(py0 + 2)), s);
     const bool complete = __syncthreads_count(s.done[0] && s.done[1]) == kBlock / 2 || s1 == tend;
     if (!complete && threadIdx.x == 0) {
         next_act[tile] = 1;
@@ -299,9 +305,10 @@ __device__ __forceinline__ int field_of_lane(int lane)
     return valid >= 1 ? base : -1;
 }
 
-// Four pixels per thread -- rows y, y + 4, y + 8, y + 12 of one column -- in
-// two pairs (y, y + 4) and (y + 8, y + 12) whose arithmetic runs on paired
-// FP32 instructions.  Per Gaussian and thread the 12 channel gradients
+// Four pixels per thread -- rows y, y + 2, y + 4, y + 6 of one column, warp w
+// covering the compact 16 x 8 block of rows [8w, 8w + 8) -- in two pairs
+// (y, y + 2) and (y + 4, y + 6) whose arithmetic runs on paired FP32
+// instructions.  Per Gaussian and thread the 12 channel gradients
 // w dL/dC_c and the dot products f . dL/dC are paired FMAs into (even pixel,
 // odd pixel) partial sums; the conic and mean gradients, which all share the
 // column's dx, come from three sums over the thread's pixels -- D = sum dP,
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
     int lmax = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        const int y = ty * LE_TILE + (threadIdx.x >> 4) + q * (LE_TILE / PPT);
+        const int y = ty * LE_TILE + 8 * (threadIdx.x >> 5) + ((threadIdx.x >> 4) & 1) + 2 * q;
         const bool inside = px < cam.W && y < cam.H;
         const size_t o = (size_t)y * cam.W + px;
         float d[12];

@@ -27,19 +27,19 @@ GPU at 1M Gaussians.
 4. Central differences on the GPU at 1M Gaussians (1296x840): 64 randomly chosen
    Gaussians that reach at least one pixel (3,693 of the 1M do on this view), one
    random direction in each parameter group (mean in the image plane, log-scales,
-   quaternion, opacity, SH, feature, uncertainty); the loss is a smooth random
-   linear functional of the rendered channels.  The loss is linear in SH (away
-   from the colour clamp), feature and uncertainty, so there the differences must
-   match the gradient closely: relative L2 error over the 64 samples <= 1e-3 and
-   every sample within 1e-3 of the group's largest gradient.  Geometric
-   parameters move the alpha = 1/255 contours, and every pixel a contour crosses
-   adds a jump of about T c / 255 that the derivative of the smooth pieces leaves
-   out; the number of crossed pixels grows with h just as the signal does, so the
-   jumps stay a fixed fraction of the difference (1-5 % per Gaussian measured for
-   h from 3e-5 to 1e-3).  Bars there: relative L2 error <= 0.1 and cosine >= 0.99
-   over the 64 samples (a dropped term or a sign error in a mean, conic or opacity
-   gradient moves these by far more), every sample within 0.1 of the group's
-   largest gradient.
+   quaternion, opacity, SH, feature, uncertainty).  The loss is a smooth random
+   linear functional of the rendered channels, times, per Gaussian i, a fixed
+   mask that is 0 where i's alpha (at the unperturbed parameters) is below 2/255
+   and 1 above 4/255.  Without the mask a geometric perturbation moves i's
+   alpha = 1/255 contour, every pixel it crosses adds a jump of about T c / 255
+   that the derivative of the smooth pieces leaves out, and those jumps grow with
+   h as the signal does (1-10 % of the difference, measured); with the mask the
+   crossed pixels carry no weight, and the analytic gradient is taken for the
+   same masked functional.  Bars: relative L2 error over the 64 samples <= 2e-2
+   (geometric groups; the remaining jumps are transmittance-cutoff crossings of
+   about 1e-4 c each) and <= 1e-3 (SH, feature, uncertainty, in which the loss is
+   linear away from the colour clamp), every sample within the same fraction of
+   the group's largest gradient, cosine >= 0.999.
 """
 import math
 
@@ -236,26 +236,41 @@ def test_c3_finite_differences_on_gpu(leg):
     ids, ranges, K, img = leg.le_bin_render_fwd(cam, proj)
     grads, _ = leg.le_render_bwd(cam, g, proj, ids, ranges, img, wr.float(), wf.float(), wu.float())
     torch.cuda.synchronize()
+    reach = np.nonzero(to_np(grads.opacity_raw) != 0)[0]      # Gaussians that reach at least one pixel
+    pick = rng.choice(reach, 64, replace=False)
+    rec = proj.splat.clone()
+    ys, xs = torch.meshgrid(torch.arange(H, device="cuda", dtype=torch.float32),
+                            torch.arange(W, device="cuda", dtype=torch.float32), indexing="ij")
+
+    def mask(i):
+        """0 where Gaussian i's alpha < 2/255, 1 above 4/255 (the record's base-2 conic)."""
+        r = rec[i]
+        dx, dy = r[0] - xs, r[1] - ys
+        q = r[2] * dx * dx + r[3] * dx * dy + r[4] * dy * dy
+        alpha = torch.clamp(r[5] * torch.exp2(-q), max=0.99)
+        return torch.clamp((255.0 * alpha.double() - 2.0) / 2.0, 0.0, 1.0)
+
     proj2 = leg.Projected.empty(N)
     bins = leg.BinSortBuffers()
     img2 = leg.Image.empty(H, W)
 
-    def loss():
+    def loss(mr, mf, mu):
         leg.le_preprocess(g, cam, proj2)
         leg.le_bin_render_fwd(cam, proj2, bins, img2)
-        return float((img2.rgb.double() * wr).sum() + (img2.feat.double() * wf).sum() +
-                     (img2.unc.double() * wu).sum())
+        return float((img2.rgb.double() * mr).sum() + (img2.feat.double() * mf).sum() +
+                     (img2.unc.double() * mu).sum())
 
-    reach = np.nonzero(to_np(grads.opacity_raw) != 0)[0]      # Gaussians that reach at least one pixel
-    pick = rng.choice(reach, 64, replace=False)
     R = np.asarray(cam.view, np.float64).reshape(3, 4)[:, :3]
     groups = {"means": 1e-4, "log_scales": 1e-4, "quats": 1e-4, "opacity_raw": 3e-4, "sh": 1e-2, "feat": 1e-2,
               "unc": 1e-2}
     res = {k: [] for k in groups}
     for i in pick:
+        m = mask(i)
+        mr, mf, mu = wr * m, wf * m, wu * m
+        gi, _ = leg.le_render_bwd(cam, g, proj, ids, ranges, img, mr.float(), mf.float(), mu.float())
         for k, h in groups.items():
             p = getattr(g, k)
-            a = getattr(grads, k)[i].double().cpu().numpy().reshape(-1)
+            a = getattr(gi, k)[i].double().cpu().numpy().reshape(-1)
             if k == "means":       # in the image plane: the depth order of the lists stays the same
                 ab = rng.standard_normal(2)
                 v = (ab[0] * R[0] + ab[1] * R[1]) / np.linalg.norm(ab)
@@ -266,9 +281,9 @@ def test_c3_finite_differences_on_gpu(leg):
             vt = torch.from_numpy(v.reshape(orig.shape).astype(np.float32)).cuda()
             pp, pm = orig + h * vt, orig - h * vt
             p[i] = pp
-            lp = loss()
+            lp = loss(mr, mf, mu)
             p[i] = pm
-            lm = loss()
+            lm = loss(mr, mf, mu)
             p[i] = orig
             delta = (pp.double() - pm.double()).cpu().numpy().reshape(-1)   # the FP32 step actually taken
             res[k].append((float(a @ delta), lp - lm))
@@ -282,8 +297,7 @@ def test_c3_finite_differences_on_gpu(leg):
         cos = float(an @ fd / (np.linalg.norm(an) * np.linalg.norm(fd)))
         worst = float(np.abs(fd - an).max() / scale)
         print(f"  {k:12s} relative L2 {l2:.2e} cosine {cos:.6f} worst |fd - an| / max|an| {worst:.2e}")
-        linear = k in ("sh", "feat", "unc")
-        if not (scale > 0 and l2 <= (1e-3 if linear else 0.1) and worst <= (1e-3 if linear else 0.1) and
-                (linear or cos >= 0.99)):
+        bar = 1e-3 if k in ("sh", "feat", "unc") else 2e-2
+        if not (scale > 0 and l2 <= bar and worst <= bar and cos >= 0.999):
             bad.append(k)
     assert not bad, bad
