@@ -406,6 +406,7 @@ def run_ours(args, rank, world):
         out["fused_vs_plain"] = compare_decoders(leg, st, mode_name, make_state, cams, rgb_dev, idx_dev, args)
         out["query"] = query_leg(leg, synth, scene, cams, args)
         out["query_c4"] = query_c4_leg(leg, synth, args)
+        out["decoder_paper_widths"] = decoder_wide_leg(leg, synth, args, bf16_peak)
         out["quantize"] = quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind)
         out["smooth"] = smooth_leg(leg, synth, st, args, bf16_peak)
         out["rgb_dssim"] = rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak)
@@ -522,6 +523,47 @@ def query_leg(leg, synth, scene, cams, args, Wq=W, Hq=H, dec=None, qin=None):
                               "peak_kind": kind, "note": "le_feature_map: decode + softmax + F = p S, BF16 out"}
     except leg.LegError as e:
         res["feature_map"] = {"unavailable": str(e)[:200]}
+    return res
+
+
+def decoder_wide_leg(leg, synth, args, bf16_peak):
+    """The decoder at the widths of supp. Tab. dmlp (8 -> 128 -> 256 -> 128 codes): one training
+    call (forward, uncertainty-weighted CE, every gradient) on a 1296x840 view's rendered features
+    (N(0,1) stand-ins) on the tensor cores against the unfused FP32 path."""
+    import numpy as np
+    import torch
+    P = W * H
+    dec = synth.decoder_init(105, 128, h1=128, h2=256)
+    dec_t = tuple(torch.from_numpy(getattr(dec, k)).cuda() for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    g = torch.Generator(device="cuda").manual_seed(6)
+    feat = torch.randn((8, P), generator=g, device="cuda")
+    unc = torch.rand(P, generator=g, device="cuda")
+    tgt = torch.randint(0, 128, (P,), generator=g, device="cuda", dtype=torch.int32)
+    res = {"pixels": P, "widths": "8-128-256-128"}
+    for name, mode in (("fused", leg.FUSED_BF16), ("unfused", leg.UNFUSED_FP32)):
+        try:
+            out = leg.le_decode(mode, feat, dec_t, unc=unc, target=tgt)
+            ws = out["workspace"]
+            for _ in range(2):
+                leg.le_decode(mode, feat, dec_t, unc=unc, target=tgt, workspace=ws)
+            torch.cuda.synchronize()
+            n = max(5, args.steps // 4)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(n):
+                leg.le_decode(mode, feat, dec_t, unc=unc, target=tgt, workspace=ws)
+            t1.record()
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / n
+            res[name] = {"ms": round(ms, 4)}
+            del ws, out
+        except leg.LegError as e:
+            res[name] = {"unavailable": str(e)[:200]}
+    flop = 3 * 2 * (8 * 128 + 128 * 256 + 256 * 128) * P
+    if "ms" in res.get("fused", {}):
+        res["fused"]["tensor_frac"] = round(flop / res["fused"]["ms"] / 1e9 / bf16_peak, 4)
+    res["algorithmic_flop"] = flop
+    torch.cuda.empty_cache()
     return res
 
 

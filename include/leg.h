@@ -318,9 +318,16 @@ typedef struct le_decoder_grads {
  *     L_CE = sum CE_px (1 - u_px)/P, L_u = sum u_px / P (overwritten);
  *     d_feat [8,P], d_unc [P], dgrads = gradient of
  *     L_s = lambda_ce L_CE + lambda_u L_u (u is differentiated too).
- *   workspace: le_decode_workspace bytes.
- * Fused path supports d_in = 8, h1 = 64, h2 = 128, n_cb in {16..256, multiple
- * of 16} (training: n_cb <= 128); otherwise LE_ERR_UNSUPPORTED. */
+ *   workspace: le_decode_workspace bytes (256-byte aligned), queried with
+ *     mode | LE_DECODE_TRAIN for a training call.
+ * Fused path: d_in = 8 with h1 = 64, h2 = 128 (the two-hidden-layer network
+ * at half the widths of supp. Tab. dmlp) or h1 = 128, h2 = 256 (the widths of
+ * supp. Tab. dmlp itself), n_cb in {16..256, multiple of 16}, training n_cb <=
+ * 128; otherwise LE_ERR_UNSUPPORTED.  At 8-128-256-N a training call needs a
+ * workspace of about 1.8 KB per pixel (each 128-pixel tile's BF16 activations
+ * and their gradients, written by a first pass and contracted into the weight
+ * gradients by a second); inference needs only the weights' images. */
+#define LE_DECODE_TRAIN 4           /* le_decode_workspace only: size for a training call */
 le_status le_decode_workspace(int32_t mode, int32_t P, const le_decoder* dec, size_t* bytes);
 le_status le_decode(int32_t mode, int32_t P, const float* feat, const float* unc, const le_decoder* dec,
                     const int32_t* target, float lambda_ce, float lambda_u, float* loss, float* d_feat,

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libleg.so")
 
 LE_OK, LE_ERR_INVALID_ARG, LE_ERR_CAPACITY, LE_ERR_CUDA, LE_ERR_TIMEOUT, LE_ERR_UNSUPPORTED = range(6)
 UNFUSED_FP32, FUSED_BF16 = 0, 1
+DECODE_TRAIN = 4          # le_decode_workspace: the workspace of a training call
 SPLAT_STRIDE = 20
 TILE = 16
 
@@ -492,7 +493,7 @@ def le_decode(mode: int, feat, dec_t, unc=None, target=None, lambda_ce=1.0, lamb
     dev = feat.device
     dec = decoder_struct(*dec_t)
     ncb = dec.n_cb
-    nb = le_decode_workspace(mode, P, dec)
+    nb = le_decode_workspace(mode | (DECODE_TRAIN if target is not None else 0), P, dec)
     if workspace is None or workspace.numel() < nb:
         workspace = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
     out = {}

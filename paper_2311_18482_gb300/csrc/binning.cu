@@ -483,14 +483,18 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
 // (row, Gaussian) tile span once into shared memory, and every warp then walks
 // the spans of its row that meet its segment, in depth order, each lane writing
 // the copies of its tile.  Only one cursor per (tile, block) advances at a time,
-// so the partly written output sectors stay few enough to remain in L2.
+// so the partly written output sectors stay few enough to remain in L2.  Two
+// rows per block give the first lazy phase (the nearest few chunks, every tile
+// row) enough blocks to fill the GPU.
 constexpr int kPlaceRows = LE_PLACE_ROWS;   // tile rows per block
 
 template <int NS>
 struct PlaceShape {
     static constexpr int kThreads = 32 * kPlaceRows * NS;
-    static constexpr int kItems = NS <= 2 ? 4 : (NS <= 4 ? 2 : 1);   // Gaussians per thread per round
-    static constexpr int kBatch = kItems * kThreads;                 // <= 1024
+    // Gaussians per thread per compaction round: the largest power of two <= 8
+    // that keeps a round within 1024 Gaussians
+    static constexpr int kItems = 1024 / kThreads >= 8 ? 8 : (1024 / kThreads >= 4 ? 4 : (1024 / kThreads >= 2 ? 2 : 1));
+    static constexpr int kBatch = kItems * kThreads;
 };
 
 // tile_act / rows_act (nullable): only tiles with a non-zero flag get copies,
@@ -558,18 +562,31 @@ __global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
         }
         __syncthreads();
         if (!row_ok) continue;
+        const uint32_t key_hi = (uint32_t)(row * TX + tx);
         for (int q0 = 0; q0 < (int)m; q0 += 32) {
             const uint32_t sp = q0 + lane < (int)m ? span[rloc][q0 + lane] : 0u;
+            const uint32_t gl = q0 + lane < (int)m ? sg[q0 + lane] : 0u;
             const int xl = (int)(sp & 0xFFFFu), xr = (int)(sp >> 16);
             uint32_t mask = __ballot_sync(0xffffffffu, xr > xl && xl < shi && xr > slo);
+            if (__popc(mask) > 8 && !keys) {
+                // dense: all 32 steps, the spans and ids broadcast from registers (no
+                // step waits on the previous one's load)
+#pragma unroll
+                for (int b = 0; b < 32; ++b) {
+                    const uint32_t spb = __shfl_sync(0xffffffffu, sp, b);
+                    const uint32_t gid = __shfl_sync(0xffffffffu, gl, b);
+                    if (mine && tx >= (int)(spb & 0xFFFFu) && tx < (int)(spb >> 16)) ids[ctr++] = gid;
+                }
+                continue;
+            }
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const uint32_t spb = span[rloc][q0 + b];
+                const uint32_t spb = __shfl_sync(0xffffffffu, sp, b);
+                const uint32_t gid = __shfl_sync(0xffffffffu, gl, b);
                 if (mine && tx >= (int)(spb & 0xFFFFu) && tx < (int)(spb >> 16)) {
-                    const uint32_t gid = sg[q0 + b];
                     ids[ctr] = gid;
-                    if (keys) keys[ctr] = ((uint64_t)(uint32_t)(row * TX + tx) << 32) | __float_as_uint(depth[gid]);
+                    if (keys) keys[ctr] = ((uint64_t)key_hi << 32) | __float_as_uint(depth[gid]);
                     ++ctr;
                 }
             }
@@ -757,19 +774,20 @@ le_status bin_prepare(const le_camera* cam, int32_t n, const float* depth, const
 }
 
 // Placement geometry: super-chunks of `cs` count chunks, small enough for about
-// eight waves of blocks (row groups differ a lot in work; many short blocks
-// balance them).
+// eight waves of blocks when every chunk is placed (row groups differ a lot in
+// work; many short blocks balance them); one chunk each for the lazy phases,
+// whose first phase covers only the nearest few chunks.
 struct PlaceGrid {
     int ngroups, cs, nsuper, nk;
 };
 
-PlaceGrid place_grid(const le_camera* cam, const SortWs& w)
+PlaceGrid place_grid(const le_camera* cam, const SortWs& w, bool lazy)
 {
     PlaceGrid g;
     const int TY = tiles_y(cam);
     g.ngroups = (TY + kPlaceRows - 1) / kPlaceRows;
     const int want = (8 * 1216 + g.ngroups - 1) / g.ngroups;
-    g.cs = w.nchunks / want > 1 ? w.nchunks / want : 1;
+    g.cs = !lazy && w.nchunks / want > 1 ? w.nchunks / want : 1;
     g.nsuper = (w.nchunks + g.cs - 1) / g.cs;
     g.nk = (tiles_x(cam) + 31) / 32;
     return g;
@@ -823,7 +841,7 @@ extern "C" le_status le_bin_sort(const le_camera* cam, int32_t n, const float* d
     le_status st = bin_prepare(cam, n, depth, rect, tile_ellipse, tiles_touched, workspace, workspace_bytes, k_cap,
                                sorted_ids != nullptr, tile_ranges, k_out, s, w, cur);
     if (st != LE_OK || n == 0 || *k_out == 0) return st;
-    const PlaceGrid g = place_grid(cam, w);
+    const PlaceGrid g = place_grid(cam, w, false);
     return place(cam, n, depth, w, cur, g, 0, g.nsuper, nullptr, nullptr, sorted_ids, sorted_keys, s);
 }
 
@@ -860,7 +878,7 @@ extern "C" le_status le_bin_render_fwd(const le_camera* cam, int32_t n, const fl
     // the tiles with a pixel still blending; a tile's later chunks are never
     // written.  The result equals placing everything and rendering once, bit
     // for bit (the same entries are blended in the same order).
-    const PlaceGrid g = place_grid(cam, w);
+    const PlaceGrid g = place_grid(cam, w, true);
     const int bounds[5] = {0, 16, 64, 256, 1 << 30};
     uint8_t* act[2] = {w.flags, w.flags + kMaxTiles};
     uint8_t* rows[2] = {w.flags + 2 * kMaxTiles, w.flags + 3 * kMaxTiles};

@@ -63,7 +63,7 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Tile rows per placement block (binning) -- also the granularity of the lazy
 // placement's row-group flags written by the compositing phases.
-#define LE_PLACE_ROWS 4
+#define LE_PLACE_ROWS 2
 
 // 2^x on the special-function unit (approximate, flush-to-zero).
 __device__ __forceinline__ float ex2_approx(float x)

@@ -15,6 +15,13 @@ le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_
                        cudaStream_t s);
 size_t decode_fused_workspace(int32_t P, const le_decoder* dec);
 le_status check_fused_decoder(const le_decoder* dec, bool train);
+bool wide_decoder(const le_decoder* d);
+le_status check_wide_decoder(const le_decoder* d, bool train);
+size_t wide_workspace(int32_t P, const le_decoder* d, bool train);
+le_status wide_decode(int32_t P, const float* feat, const float* unc, const le_decoder* d, const int32_t* target,
+                      float lambda_ce, float lambda_u, float* loss, float* d_feat, float* d_unc,
+                      const le_decoder_grads* dg, int32_t* argmax, float* prob, void* ws, size_t ws_bytes,
+                      cudaStream_t s);
 
 namespace {
 
@@ -217,8 +224,10 @@ extern "C" le_status le_decode_workspace(int32_t mode, int32_t P, const le_decod
 {
     LE_TRACE("le_decode_workspace");
     LE_CHECK_ARG(bytes && dec && P >= 0, "bad arguments");
+    const bool train = (mode & LE_DECODE_TRAIN) != 0;
+    mode &= ~LE_DECODE_TRAIN;
     if (mode == LE_DECODE_FUSED_BF16) {
-        *bytes = decode_fused_workspace(P, dec);
+        *bytes = wide_decoder(dec) ? wide_workspace(P, dec, train) : decode_fused_workspace(P, dec);
         return LE_OK;
     }
     LE_CHECK_ARG(mode == LE_DECODE_UNFUSED_FP32, "unknown decode mode %d", mode);
@@ -247,6 +256,9 @@ extern "C" le_status le_decode(int32_t mode, int32_t P, const float* feat, const
     cudaStream_t s = as_stream(stream);
     if (mode == LE_DECODE_FUSED_BF16) {
         LE_CHECK_ARG(logits == nullptr, "the fused path never materialises logits");
+        if (wide_decoder(dec))
+            return wide_decode(P, feat, unc, dec, target, lambda_ce, lambda_u, loss, d_feat, d_unc, dgrads, argmax,
+                               prob, workspace, workspace_bytes, s);
         if ((st = check_fused_decoder(dec, train)) != LE_OK) return st;
         LE_CHECK_ARG(workspace_bytes >= decode_fused_workspace(P, dec), "workspace too small");
         return decode_fused(P, feat, unc, dec, target, lambda_ce, lambda_u, loss, d_feat, d_unc, dgrads, argmax,

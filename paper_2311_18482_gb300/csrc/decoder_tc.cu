@@ -1563,6 +1563,7 @@ extern "C" le_status le_selftest_bounded_wait(void* stream)
 namespace leg {
 le_status quant_take_timeout(bool* timed_out);
 le_status smooth_take_timeout(bool* timed_out);
+le_status wide_take_timeout(bool* timed_out);
 }
 
 extern "C" le_status le_device_status(void* stream)
@@ -1577,9 +1578,13 @@ extern "C" le_status le_device_status(void* stream)
     bool smooth_flag = false;
     const le_status ss = leg::smooth_take_timeout(&smooth_flag);
     if (ss != LE_OK) return ss;
-    if ((quant_flag || smooth_flag) && !flag) {
-        leg::set_error(quant_flag ? "the quantisation kernel gave up on a bounded wait"
-                                  : "the smoothing kernel gave up on a bounded wait");
+    bool wide_flag = false;
+    const le_status ws = leg::wide_take_timeout(&wide_flag);
+    if (ws != LE_OK) return ws;
+    if ((quant_flag || smooth_flag || wide_flag) && !flag) {
+        leg::set_error(quant_flag    ? "the quantisation kernel gave up on a bounded wait"
+                       : smooth_flag ? "the smoothing kernel gave up on a bounded wait"
+                                     : "a decoder kernel at the widths 8-128-256-N gave up on a bounded wait");
         return LE_ERR_TIMEOUT;
     }
     if (flag) {

@@ -14,9 +14,10 @@
 //
 // The backward walks the same range back to front from each pixel's last
 // contributor, recovering T_i = T_{i+1} / (1 - alpha_i) from the stored final
-// transmittance, sums each Gaussian's 18 gradient terms over the warp with a
-// recursive-halving shuffle reduction (20 shuffles instead of 18 x 5) after
-// which 18 lanes each issue one scalar atomic add into the gradient record.
+// transmittance, and sums each Gaussian's 18 gradient terms over the warp by a
+// transpose through shared memory (every lane stores its 18 partial sums, lane
+// f < 18 adds up field f with 16-byte reads), after which those 18 lanes each
+// issue one scalar atomic add into the gradient record.
 #include "common.cuh"
 
 namespace leg {
@@ -262,49 +263,6 @@ __global__ void __launch_bounds__(kBlock / 2) render_fwd_phase_kernel(
     }
 }
 
-// One stage of a recursive-halving ("transpose") reduction of N values held by
-// every lane: lanes with bit O set keep the upper half of the values, the
-// others the lower half, each adding its partner's copy of the half it keeps.
-template <int N, int O>
-__device__ __forceinline__ void halve(float* v, bool upper)
-{
-    constexpr int H = (N + 1) / 2;
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        const float lo = v[i];
-        const float hi = (i + H < N) ? v[i + H] : 0.f;
-        const float recv = __shfl_xor_sync(0xffffffffu, upper ? lo : hi, O);
-        v[i] = (upper ? hi : lo) + recv;
-    }
-}
-
-// Warp-wide sums of 18 values in 9+5+3+2+1 = 20 shuffles; afterwards v[0] of
-// lane l is the sum of value field_of_lane(l) (or nothing, when that is -1).
-__device__ __forceinline__ void warp_sum18(float* v, int lane)
-{
-    halve<18, 16>(v, lane & 16);
-    halve<9, 8>(v, lane & 8);
-    halve<5, 4>(v, lane & 4);
-    halve<3, 2>(v, lane & 2);
-    halve<2, 1>(v, lane & 1);
-}
-
-__device__ __forceinline__ int field_of_lane(int lane)
-{
-    int valid = 18, base = 0;
-    const int H[5] = {9, 5, 3, 2, 1}, O[5] = {16, 8, 4, 2, 1};
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        if (lane & O[s]) {
-            base += H[s];
-            valid = valid > H[s] ? valid - H[s] : 0;
-        } else {
-            valid = valid < H[s] ? valid : H[s];
-        }
-    }
-    return valid >= 1 ? base : -1;
-}
-
 // Four pixels per thread -- rows y, y + 2, y + 4, y + 6 of one column, warp w
 // covering the compact 16 x 8 block of rows [8w, 8w + 8) -- in two pairs
 // (y, y + 2) and (y + 4, y + 6) whose arithmetic runs on paired FP32
@@ -325,12 +283,16 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
     __shared__ float4 rec[5][kBlock];
     __shared__ uint32_t sid[kBlock];
     __shared__ int s_max;
+    // per warp, the lanes' 18 gradient partial sums, field-major; the row stride
+    // of 36 floats staggers the rows over the banks for the 16-byte reads
+    __shared__ __align__(16) float red[NT / 32][18][36];
     const int tile = blockIdx.x;
     const int tx = tile % cam.TX, ty = tile / cam.TX;
     const int px = tx * LE_TILE + (threadIdx.x & 15);
     const uint2 rg = ranges[tile];
     const float fpx = (float)px;
     const size_t P = (size_t)cam.W * cam.H;
+    float(*wred)[36] = red[threadIdx.x >> 5];
 
     // pair p holds pixels q = 2p (x) and 2p + 1 (y)
     float2 npy[2], dC[2][12], T[2], Tf[2], S[2], nbg[2];
@@ -380,7 +342,6 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
     __syncthreads();
     const int nproc = s_max;
     const int lane = threadIdx.x & 31;
-    const int my_field = field_of_lane(lane);
 
     for (int b_end = nproc; b_end > 0; b_end -= kBlock) {
         const int b_start = max(0, b_end - kBlock);
@@ -430,10 +391,10 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
                     for (int p = 0; p < 2; ++p) {
                         const bool cx = cb[2 * p], cy = cb[2 * p + 1];
                         if (!(cx || cy)) continue;
-                        const float2 inv = make_float2(cx ? __fdividef(1.f, 1.f - al[p].x) : 1.f,
-                                                       cy ? __fdividef(1.f, 1.f - al[p].y) : 1.f);
-                        T[p] = __fmul2_rn(T[p], inv);
+                        // alpha of the blended pixels, 0 for the others (1 / (1 - 0) = 1 leaves T)
                         const float2 am = sel2(cx, cy, al[p]);
+                        const float2 inv = make_float2(__fdividef(1.f, 1.f - am.x), __fdividef(1.f, 1.f - am.y));
+                        T[p] = __fmul2_rn(T[p], inv);
                         const float2 w = __fmul2_rn(am, T[p]);
                         float2 fdc = __fmul2_rn(f2(f[0]), dC[p][0]);
 #pragma unroll
@@ -467,8 +428,23 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
 #pragma unroll
                 for (int c = 0; c < 12; ++c) gr[6 + c] = acc[c].x + acc[c].y;
             }
-            warp_sum18(gr, lane);
-            if (my_field >= 0) atomicAdd(reinterpret_cast<float*>(grad2d + (size_t)sid[j] * 5) + my_field, gr[0]);
+            // warp sums of the 18 fields: a transpose through shared memory, lane f < 18 adding field f
+#pragma unroll
+            for (int c = 0; c < 18; ++c) wred[c][lane] = gr[c];
+            __syncwarp();
+            if (lane < 18) {
+                const float4* row = reinterpret_cast<const float4*>(wred[lane]);
+                float2 a = f2(0.f), b = f2(0.f);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float4 v = row[k];
+                    a = __fadd2_rn(a, make_float2(v.x, v.y));
+                    b = __fadd2_rn(b, make_float2(v.z, v.w));
+                }
+                const float2 t = __fadd2_rn(a, b);
+                atomicAdd(reinterpret_cast<float*>(grad2d + (size_t)sid[j] * 5) + lane, t.x + t.y);
+            }
+            __syncwarp();
         }
     }
 }

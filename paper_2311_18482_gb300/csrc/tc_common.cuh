@@ -83,6 +83,15 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int 
                  : "memory");
 }
 
+// 1-D bulk copy this CTA's shared memory -> global, counted in this thread's
+// bulk async-group (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 // Until this thread's committed bulk stores have read their shared-memory source.

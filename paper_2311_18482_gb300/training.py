@@ -93,8 +93,8 @@ class TrainState:
         self.d_unc = torch.empty((H, W), dtype=torch.float32, device=device)
         self.grad2d = torch.empty((N, B.SPLAT_STRIDE), dtype=torch.float32, device=device)
         self.mode = decoder_mode
-        self.dec_ws = torch.empty(max(B.le_decode_workspace(decoder_mode, P, self.dec), 1), dtype=torch.uint8,
-                                  device=device)
+        self.dec_ws = torch.empty(max(B.le_decode_workspace(decoder_mode | B.DECODE_TRAIN, P, self.dec), 1),
+                                  dtype=torch.uint8, device=device)
         self.step_count = 0
         self.lr = lr
         # RGB loss: "l1" (the training-loop configuration) or "l1_dssim", 3DGS's (1 - lambda) L1 +
