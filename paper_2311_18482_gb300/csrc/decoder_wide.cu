@@ -17,7 +17,8 @@
 //   activations  one 64 KB region holds the operand of the next MMA stage --
 //                H1, H2 and, training, dZ, dH2, dH1 -- each written by the
 //                epilogue once the MMAs reading its predecessor have completed;
-//                the ReLU masks of h1 and h2 stay in registers (4 + 8 words).
+//                the ReLU masks of h1 and h2 are kept as bits (4 + 8 words per
+//                row, in shared memory so that the epilogue loops stay rolled).
 //   TMEM         512 columns: [0, 256) hidden-layer accumulators (h1, h2, dh2,
 //                dh1), [256, 256 + N) the logits, later [256, 272) dx.
 // Training (N <= 128) takes two passes:
@@ -54,8 +55,8 @@ constexpr uint32_t kW1Bytes = sbuf_bytes(kW1, 16), kW2Bytes = sbuf_bytes(kW2, kW
 
 // Shared memory of wide_kernel (offsets from a 1024-byte aligned base).
 constexpr uint32_t kSW1 = 0, kSW2 = kSW1 + kW1Bytes, kSW3 = kSW2 + kW2Bytes, kSX = kSW3 + kW3Half,
-                   kSA = kSX + kXBytes, kSBias = kSA + kABytes, kSBar = kSBias + (kW1 + kW2 + 256) * 4,
-                   kSSlot = kSBar + 4 * 8, kSmem = kSSlot + 16;
+                   kSA = kSX + kXBytes, kSBias = kSA + kABytes, kSMask = kSBias + (kW1 + kW2 + 256) * 4,
+                   kSBar = kSMask + kRows * 12 * 4, kSSlot = kSBar + 4 * 8, kSmem = kSSlot + 16;
 
 // One tile's operand images in the training workspace (pass 1 writes, pass 2 reads).
 constexpr uint32_t kBX = 0, kBH1 = kBX + kXBytes, kBH2 = kBH1 + sbuf_bytes(kRows, kW1),
@@ -98,15 +99,16 @@ __device__ __forceinline__ bool wide_wait(uint64_t* bar, uint32_t& phase)
     return !bad;
 }
 
-// Accumulator columns [col, col + 16 * n16) of this thread's row + bias, ReLU,
-// stored as BF16 into the canonical buffer (C columns); bit j of mask[j / 32]
-// is set where the result is positive.
+// Accumulator columns [0, C) of this thread's row + bias, ReLU, stored as BF16
+// into the canonical buffer (C columns); bit j of the 16-bit mask half
+// mask[j / 16] is set where the result is positive (mask: this row's words in
+// shared memory, read back as 32-bit words by mask_epilogue).
 template <int C>
 __device__ __forceinline__ void relu_epilogue(uint32_t tl, const float* bias, unsigned char* dst, int row,
-                                              uint32_t* mask)
+                                              uint16_t* mask)
 {
     float v[16];
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < C; c += 16) {
         tmem_ld16(tl + c, v);
         uint32_t bits = 0;
@@ -115,26 +117,26 @@ __device__ __forceinline__ void relu_epilogue(uint32_t tl, const float* bias, un
             v[j] = fmaxf(v[j] + bias[c + j], 0.f);
             bits |= (v[j] > 0.f ? 1u : 0u) << j;
         }
-        mask[c / 32] = (c & 16) ? (mask[c / 32] | (bits << 16)) : bits;
-        sbuf_store8(SBuf{dst, C}, row, c, v);
-        sbuf_store8(SBuf{dst, C}, row, c + 8, v + 8);
+        mask[c / 16] = (uint16_t)bits;
+        sts_bf16x8(smem_u32(dst) + sbuf_off(row, c, C), v);
+        sts_bf16x8(smem_u32(dst) + sbuf_off(row, c + 8, C), v + 8);
     }
 }
 
 // Accumulator columns times the ReLU mask, stored as BF16 (the backward through
 // a ReLU layer).
 template <int C>
-__device__ __forceinline__ void mask_epilogue(uint32_t tl, const uint32_t* mask, unsigned char* dst, int row)
+__device__ __forceinline__ void mask_epilogue(uint32_t tl, const uint16_t* mask, unsigned char* dst, int row)
 {
     float v[16];
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < C; c += 16) {
         tmem_ld16(tl + c, v);
-        const uint32_t bits = mask[c / 32] >> (c & 16);
+        const uint32_t bits = mask[c / 16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = ((bits >> j) & 1u) ? v[j] : 0.f;
-        sbuf_store8(SBuf{dst, C}, row, c, v);
-        sbuf_store8(SBuf{dst, C}, row, c + 8, v + 8);
+        sts_bf16x8(smem_u32(dst) + sbuf_off(row, c, C), v);
+        sts_bf16x8(smem_u32(dst) + sbuf_off(row, c + 8, C), v + 8);
     }
 }
 
@@ -176,6 +178,8 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
     float* const bias = reinterpret_cast<float*>(sm + kSBias);
     const float *b1s = bias, *b2s = bias + kW1, *b3s = bias + kW1 + kW2;
     uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + kSBar);   // 0 MMA done, 1 weights, 2 W3 half
+    uint16_t* const m1 = reinterpret_cast<uint16_t*>(sm + kSMask) + threadIdx.x * 24;   // h1: 8 halves
+    uint16_t* const m2 = m1 + 8;                                                       // h2: 16 halves
     uint32_t* const slot = reinterpret_cast<uint32_t*>(sm + kSSlot);
     const int tid = threadIdx.x;
     const int ncb = a.ncb;
@@ -234,7 +238,6 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
         }
         if (!(ok = wide_wait(bars, ph))) break;
         // E1: H1 = relu(h1 + b1)
-        uint32_t m1[kW1 / 32], m2[kW2 / 32];
         relu_epilogue<kW1>(tl + kTH, b1s, sA, tid, m1);
         cta_publish();
         if (tid == 0) {
@@ -324,8 +327,8 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         v[j] = c + j < ncb ? g * (__expf(v[j] + b3s[c + j] - lse) - (c + j == t ? 1.f : 0.f)) : 0.f;
-                    sbuf_store8(SBuf{sA, 128}, tid, c, v);
-                    sbuf_store8(SBuf{sA, 128}, tid, c + 8, v + 8);
+                    sts_bf16x8(smem_u32(sA) + sbuf_off(tid, c, 128), v);
+                    sts_bf16x8(smem_u32(sA) + sbuf_off(tid, c + 8, 128), v + 8);
                 }
             }
         }
