@@ -41,10 +41,11 @@ def parse():
     ap.add_argument("--decoder", default="auto", choices=["auto", "fused", "unfused"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussian count (default: the workload's 1M)")
     ap.add_argument("--no-extras", action="store_true", help="skip the query / unfused comparison legs")
-    ap.add_argument("--only", choices=["quantize", "smooth", "query"], default=None,
+    ap.add_argument("--only", choices=["quantize", "smooth", "query", "decoder_wide"], default=None,
                     help="run one leg alone (quantize: the quantisation stage on --features rows; smooth: "
                          "the adaptive smoothing on --n Gaussians; query: the fused relevancy query and the "
-                         "feature-map export on --features random rendered features, without rendering)")
+                         "feature-map export on --features random rendered features, without rendering; "
+                         "decoder_wide: one training call of the 8-128-256-128 decoder on --features pixels)")
     ap.add_argument("--features", type=int, default=W * H, help="feature rows / pixels for --only quantize|query")
     return ap.parse_args()
 
@@ -314,23 +315,45 @@ def run_ours(args, rank, world):
     K_mean = float(np.mean(Ks))
 
     # --- end to end through the public API: per step H2D of the view's targets
-    # from pinned host memory, the step, D2H of the loss vector
-    loss_host = torch.empty(3, dtype=torch.float32).pin_memory()
-    rgb_stage = torch.empty_like(rgb_dev[0])
-    idx_stage = torch.empty_like(idx_dev[0])
+    # from pinned host memory, the step, D2H of the loss vector.  The targets of
+    # step i + 1 are copied on a second stream into the other of two staging
+    # buffers while step i computes (events order each copy after the step that
+    # last read its buffer, and the step after its copy); every copy and every
+    # loss read-back lies inside the timed region.
+    loss_host = torch.empty((args.steps, 3), dtype=torch.float32).pin_memory()
+    rgb_stage = [torch.empty_like(rgb_dev[0]) for _ in range(2)]
+    idx_stage = [torch.empty_like(idx_dev[0]) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    main_stream = torch.cuda.current_stream()
+
+    def stage(i):
+        b, k = i & 1, i % N_VIEWS
+        with torch.cuda.stream(copy_stream):
+            if i >= 2:
+                copy_stream.wait_event(consumed[b])
+            rgb_stage[b].copy_(rgb_host[k], non_blocking=True)
+            idx_stage[b].copy_(idx_host[k], non_blocking=True)
+            copied[b].record(copy_stream)
+
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
+    copy_stream.wait_event(e0)
+    stage(0)
     for i in range(args.steps):
-        k = i % N_VIEWS
-        rgb_stage.copy_(rgb_host[k], non_blocking=True)
-        idx_stage.copy_(idx_host[k], non_blocking=True)
-        loss = st.step(cams[k], rgb_stage, idx_stage)
-        loss_host.copy_(loss, non_blocking=True)
+        b, k = i & 1, i % N_VIEWS
+        if i + 1 < args.steps:
+            stage(i + 1)
+        main_stream.wait_event(copied[b])
+        loss = st.step(cams[k], rgb_stage[b], idx_stage[b])
+        consumed[b].record(main_stream)
+        loss_host[i].copy_(loss, non_blocking=True)
     e1.record()
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    h2d = rgb_stage.numel() * 4 + idx_stage.numel() * 4
+    h2d = rgb_stage[0].numel() * 4 + idx_stage[0].numel() * 4
 
     out = {"metric": METRIC, "value": round(ms_step, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": False,
@@ -526,13 +549,11 @@ def query_leg(leg, synth, scene, cams, args, Wq=W, Hq=H, dec=None, qin=None):
     return res
 
 
-def decoder_wide_leg(leg, synth, args, bf16_peak):
+def decoder_wide_leg(leg, synth, args, bf16_peak, P=W * H):
     """The decoder at the widths of supp. Tab. dmlp (8 -> 128 -> 256 -> 128 codes): one training
     call (forward, uncertainty-weighted CE, every gradient) on a 1296x840 view's rendered features
     (N(0,1) stand-ins) on the tensor cores against the unfused FP32 path."""
-    import numpy as np
     import torch
-    P = W * H
     dec = synth.decoder_init(105, 128, h1=128, h2=256)
     dec_t = tuple(torch.from_numpy(getattr(dec, k)).cuda() for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
     g = torch.Generator(device="cuda").manual_seed(6)
@@ -918,6 +939,8 @@ def main():
             res = quant_leg(leg, synth, args, hbm, bf16, kind)
         elif args.only == "query":
             res = decode_query_leg(leg, synth, args, hbm, kind)
+        elif args.only == "decoder_wide":
+            res = decoder_wide_leg(leg, synth, args, bf16, P=args.features)
         else:
             from paper_2311_18482_gb300.training import TrainState
             c = synth.config("c5", n=args.n)
