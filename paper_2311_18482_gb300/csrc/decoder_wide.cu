@@ -5,9 +5,9 @@
 //
 // At these widths the weights alone take 132 KB of BF16 (196 KB for 256
 // codes), so the two-tiles-in-flight plan of decoder_tc.cu does not fit.  One
-// persistent CTA per SM, 128 threads (thread t serves row t of the 128-pixel
-// tile, i.e. TMEM lane t; thread 0 also issues the MMAs and bulk copies), one
-// tile in flight:
+// persistent CTA per SM, one tile in flight, four warpgroups: thread t serves
+// row t % 128 of the 128-pixel tile (TMEM lane) and the columns of part t / 128
+// in every epilogue; thread 0 also issues the MMAs and bulk copies:
 //   weights      BF16 canonical images of W1 [128 x 16] (input padded to 16),
 //                W2 [256 x 128] and W3 [N x 256], prepared once per call in the
 //                caller's workspace and copied into shared memory once per CTA;
@@ -56,7 +56,8 @@ constexpr uint32_t kW1Bytes = sbuf_bytes(kW1, 16), kW2Bytes = sbuf_bytes(kW2, kW
 // Shared memory of wide_kernel (offsets from a 1024-byte aligned base).
 constexpr uint32_t kSW1 = 0, kSW2 = kSW1 + kW1Bytes, kSW3 = kSW2 + kW2Bytes, kSX = kSW3 + kW3Half,
                    kSA = kSX + kXBytes, kSBias = kSA + kABytes, kSMask = kSBias + (kW1 + kW2 + 256) * 4,
-                   kSBar = kSMask + kRows * 12 * 4, kSSlot = kSBar + 4 * 8, kSmem = kSSlot + 16;
+                   kSXch = kSMask + kRows * 12 * 4, kSBar = kSXch + 4 * kRows * 16, kSSlot = kSBar + 4 * 8,
+                   kSmem = kSSlot + 16;
 
 // One tile's operand images in the training workspace (pass 1 writes, pass 2 reads).
 constexpr uint32_t kBX = 0, kBH1 = kBX + kXBytes, kBH2 = kBH1 + sbuf_bytes(kRows, kW1),
@@ -88,28 +89,32 @@ __device__ __forceinline__ void cta_publish()
     fence_after();
 }
 
+// Four warpgroups serve the tile: thread t handles row t % 128 (TMEM lane) and
+// the columns of part t / 128 in every epilogue.
+constexpr int kParts = 4, kThreads = kParts * kRows;
+
 // Wait for the MMA barrier (every thread); false for every thread if any timed out.
 __device__ __forceinline__ bool wide_wait(uint64_t* bar, uint32_t& phase)
 {
     const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
-    const bool bad = bar_any(0, kRows, !ok);
+    const bool bad = bar_any(0, kThreads, !ok);
     if (bad && threadIdx.x == 0) atomicExch(&g_wide_error, 1);
     fence_after();
     return !bad;
 }
 
-// Accumulator columns [0, C) of this thread's row + bias, ReLU, stored as BF16
-// into the canonical buffer (C columns); bit j of the 16-bit mask half
-// mask[j / 16] is set where the result is positive (mask: this row's words in
-// shared memory, read back as 32-bit words by mask_epilogue).
+// Accumulator columns [c0, c1) of this thread's row + bias, ReLU, stored as
+// BF16 into the canonical buffer (C columns); bit j of the 16-bit mask half
+// mask[c / 16] is set where column c + j is positive (mask: the row's halves
+// in shared memory).
 template <int C>
-__device__ __forceinline__ void relu_epilogue(uint32_t tl, const float* bias, unsigned char* dst, int row,
-                                              uint16_t* mask)
+__device__ __forceinline__ void relu_epilogue(uint32_t tl, const float* bias, unsigned char* dst, int row, int c0,
+                                              int c1, uint16_t* mask)
 {
     float v[16];
 #pragma unroll 1
-    for (int c = 0; c < C; c += 16) {
+    for (int c = c0; c < c1; c += 16) {
         tmem_ld16(tl + c, v);
         uint32_t bits = 0;
 #pragma unroll
@@ -123,14 +128,15 @@ __device__ __forceinline__ void relu_epilogue(uint32_t tl, const float* bias, un
     }
 }
 
-// Accumulator columns times the ReLU mask, stored as BF16 (the backward through
-// a ReLU layer).
+// Accumulator columns [c0, c1) times the ReLU mask, stored as BF16 (the
+// backward through a ReLU layer).
 template <int C>
-__device__ __forceinline__ void mask_epilogue(uint32_t tl, const uint16_t* mask, unsigned char* dst, int row)
+__device__ __forceinline__ void mask_epilogue(uint32_t tl, const uint16_t* mask, unsigned char* dst, int row, int c0,
+                                              int c1)
 {
     float v[16];
 #pragma unroll 1
-    for (int c = 0; c < C; c += 16) {
+    for (int c = c0; c < c1; c += 16) {
         tmem_ld16(tl + c, v);
         const uint32_t bits = mask[c / 16];
 #pragma unroll
@@ -140,15 +146,14 @@ __device__ __forceinline__ void mask_epilogue(uint32_t tl, const uint16_t* mask,
     }
 }
 
-// Row-wise maximum, argmax (ties to the lowest index), log-sum-exp and the
-// target's logit over the ncb logits (+ b3) at TMEM columns [tz, tz + ncb).
-__device__ __forceinline__ void row_lse(uint32_t tz, const float* b3, int ncb, int t, float& lse, int& am, float& zt)
+// Running maximum (first index on ties), sum of exp(z - max) and the target's
+// logit over the logits (+ b3) of columns [c0, min(c1, ncb)).
+__device__ __forceinline__ float4 part_lse(uint32_t tz, const float* b3, int c0, int c1, int ncb, int t)
 {
-    float m = -INFINITY, s = 0.f, v[16];
-    am = 0;
-    zt = 0.f;
+    float m = -INFINITY, s = 0.f, zt = 0.f, v[16];
+    int am = 0;
 #pragma unroll 1
-    for (int c = 0; c < ncb; c += 16) {
+    for (int c = c0; c < c1 && c < ncb; c += 16) {
         tmem_ld16(tz + c, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -163,11 +168,11 @@ __device__ __forceinline__ void row_lse(uint32_t tz, const float* b3, int ncb, i
             }
         }
     }
-    lse = m + __logf(s);
+    return make_float4(m, s, __int_as_float(am), zt);
 }
 
 template <bool TRAIN>
-__global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
+__global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* const sW1 = sm + kSW1;
@@ -177,17 +182,22 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
     unsigned char* const sA = sm + kSA;
     float* const bias = reinterpret_cast<float*>(sm + kSBias);
     const float *b1s = bias, *b2s = bias + kW1, *b3s = bias + kW1 + kW2;
+    float4* const xch = reinterpret_cast<float4*>(sm + kSXch);          // [kParts][kRows]
     uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + kSBar);   // 0 MMA done, 1 weights, 2 W3 half
-    uint16_t* const m1 = reinterpret_cast<uint16_t*>(sm + kSMask) + threadIdx.x * 24;   // h1: 8 halves
-    uint16_t* const m2 = m1 + 8;                                                       // h2: 16 halves
     uint32_t* const slot = reinterpret_cast<uint32_t*>(sm + kSSlot);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, row = tid & (kRows - 1), part = tid / kRows;
+    uint16_t* const m1 = reinterpret_cast<uint16_t*>(sm + kSMask) + row * 24;   // h1: 8 halves
+    uint16_t* const m2 = m1 + 8;                                                // h2: 16 halves
     const int ncb = a.ncb;
     const bool halves = ncb > 128;
     const uint32_t w3bytes = halves ? kW3Half : (uint32_t)ncb * kW2 * 2;
     const unsigned char* w3img = a.img + kW1Bytes + kW2Bytes;
+    // this part's columns: 32 of h1, 64 of h2, a quarter of the logits (32 up to 128 codes, 64 beyond)
+    const int h1c0 = part * (kW1 / kParts), h1c1 = h1c0 + kW1 / kParts;
+    const int h2c0 = part * (kW2 / kParts), h2c1 = h2c0 + kW2 / kParts;
+    const int zw = halves ? 64 : 32, zc0 = part * zw, zc1 = zc0 + zw;
 
-    for (int i = tid; i < kW1 + kW2 + ncb; i += kRows)
+    for (int i = tid; i < kW1 + kW2 + ncb; i += kThreads)
         bias[i] = i < kW1 ? a.b1[i] : (i < kW1 + kW2 ? a.b2[i - kW1] : a.b3[i - kW1 - kW2]);
     if (tid == 0) {
         for (int k = 0; k < 3; ++k) mbar_init(bars + k, 1);
@@ -202,29 +212,29 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
     __syncthreads();
     fence_after();
     const uint32_t tbase = *reinterpret_cast<volatile uint32_t*>(slot);
-    const uint32_t tl = tbase + ((uint32_t)(32 * (tid >> 5)) << 16);   // this warp's TMEM lanes
+    const uint32_t tl = tbase + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16);   // this warp's TMEM lanes
     uint32_t ph = 0, ph3 = 0;
-    int resident = 0;                     // the W3 half in the slot (halves only)
+    int resident = 0;                     // the W3 half in the slot (halves only; thread 0)
     bool ok = mbar_wait(bars + 1, 0);
-    if (bar_any(0, kRows, !ok)) {
+    if (bar_any(0, kThreads, !ok)) {
         if (tid == 0) atomicExch(&g_wide_error, 1);
         ok = false;
     }
     float lce = 0.f, lu = 0.f;
     const int ntiles = (a.P + kRows - 1) / kRows;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-        const int p = tile * kRows + tid;
+        const int p = tile * kRows + row;
         const bool valid = p < a.P;
         unsigned char* blob = TRAIN ? a.blobs + (size_t)tile * kBlob : nullptr;
         // E0: X = [x | 1 | 0] (column 8 is the bias input of dW1's contraction)
-        {
+        if (part == 0) {
             float x[16];
 #pragma unroll
             for (int c = 0; c < 8; ++c) x[c] = valid ? a.feat[(size_t)c * a.P + p] : 0.f;
 #pragma unroll
             for (int c = 8; c < 16; ++c) x[c] = c == 8 ? 1.f : 0.f;
-            sbuf_store8(SBuf{sX, 16}, tid, 0, x);
-            sbuf_store8(SBuf{sX, 16}, tid, 8, x + 8);
+            sbuf_store8(SBuf{sX, 16}, row, 0, x);
+            sbuf_store8(SBuf{sX, 16}, row, 8, x + 8);
         }
         cta_publish();
         if (tid == 0) {
@@ -238,7 +248,7 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
         }
         if (!(ok = wide_wait(bars, ph))) break;
         // E1: H1 = relu(h1 + b1)
-        relu_epilogue<kW1>(tl + kTH, b1s, sA, tid, m1);
+        relu_epilogue<kW1>(tl + kTH, b1s, sA, row, h1c0, h1c1, m1);
         cta_publish();
         if (tid == 0) {
             const uint32_t a0 = smem_u32(sA), w2 = smem_u32(sW2);
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
         }
         if (!(ok = wide_wait(bars, ph))) break;
         // E2: H2 = relu(h2 + b2), over H1 (whose MMAs have completed)
-        relu_epilogue<kW2>(tl + kTH, b2s, sA, tid, m2);
+        relu_epilogue<kW2>(tl + kTH, b2s, sA, row, h2c0, h2c1, m2);
         cta_publish();
         if (tid == 0) {
             const uint32_t a0 = smem_u32(sA), w3 = smem_u32(sW3);
@@ -294,18 +304,31 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
             }
         }
         if (!(ok = wide_wait(bars, ph))) break;
-        // E3: logits -> argmax / probabilities (inference) or the cross-entropy and dz (training)
+        // E3: logits -> argmax / probabilities (inference) or the cross-entropy and dz (training);
+        // the parts' statistics combine in column order
         {
             const int t = TRAIN && valid ? a.target[p] : -1;
-            float lse, zt;
-            int am;
-            row_lse(tl + kTZ, b3s, ncb, t, lse, am, zt);
+            xch[part * kRows + row] = part_lse(tl + kTZ, b3s, zc0, zc1, ncb, t);
+            __syncthreads();
+            float m = -INFINITY, ssum = 0.f, zt = 0.f;
+            int am = 0;
+#pragma unroll
+            for (int q = 0; q < kParts; ++q) {
+                const float4 o = xch[q * kRows + row];
+                if (o.x == -INFINITY) continue;               // a part without columns
+                const float mn = fmaxf(m, o.x);
+                ssum = (m == -INFINITY ? 0.f : ssum * __expf(m - mn)) + o.y * __expf(o.x - mn);
+                if (o.x > m) am = __float_as_int(o.z);
+                m = mn;
+                zt += o.w;                                    // only the part holding the target has it
+            }
+            const float lse = m + __logf(ssum);
             if (!TRAIN) {
-                if (valid && a.argmax) a.argmax[p] = am;
+                if (part == 0 && valid && a.argmax) a.argmax[p] = am;
                 if (a.prob) {
                     float v[16];
 #pragma unroll 1
-                    for (int c = 0; c < ncb; c += 16) {
+                    for (int c = zc0; c < zc1 && c < ncb; c += 16) {
                         tmem_ld16(tl + kTZ + c, v);      // every lane: the load is warp-collective
                         if (valid)
 #pragma unroll
@@ -317,24 +340,26 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
                 const float u = valid ? a.unc[p] : 0.f;
                 const float ce = valid ? lse - zt : 0.f;
                 const float g = valid ? a.lambda_ce * (1.f - u) : 0.f;
-                if (valid) a.d_unc[p] = (a.lambda_u - a.lambda_ce * ce) * a.invP;
-                lce += ce * (1.f - u) * a.invP;
-                lu += u * a.invP;
+                if (part == 0) {
+                    if (valid) a.d_unc[p] = (a.lambda_u - a.lambda_ce * ce) * a.invP;
+                    lce += ce * (1.f - u) * a.invP;
+                    lu += u * a.invP;
+                }
                 float v[16];
 #pragma unroll 1
-                for (int c = 0; c < 128; c += 16) {
+                for (int c = zc0; c < zc1; c += 16) {
                     if (c < ncb) tmem_ld16(tl + kTZ + c, v);
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         v[j] = c + j < ncb ? g * (__expf(v[j] + b3s[c + j] - lse) - (c + j == t ? 1.f : 0.f)) : 0.f;
-                    sts_bf16x8(smem_u32(sA) + sbuf_off(tid, c, 128), v);
-                    sts_bf16x8(smem_u32(sA) + sbuf_off(tid, c + 8, 128), v + 8);
+                    sts_bf16x8(smem_u32(sA) + sbuf_off(row, c, 128), v);
+                    sts_bf16x8(smem_u32(sA) + sbuf_off(row, c + 8, 128), v + 8);
                 }
             }
         }
         if (!TRAIN) {
             fence_before();
-            __syncthreads();     // every TMEM read of this tile before the next tile's MMAs
+            __syncthreads();     // every TMEM read and exchange of this tile before the next tile's MMAs
             fence_after();
             continue;
         }
@@ -352,7 +377,7 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
         }
         if (!(ok = wide_wait(bars, ph))) break;
         // E4: dH2 = dh2 * [h2 > 0]
-        mask_epilogue<kW2>(tl + kTH, m2, sA, tid);
+        mask_epilogue<kW2>(tl + kTH, m2, sA, row, h2c0, h2c1);
         cta_publish();
         if (tid == 0) {
             // S5: dh1 = dH2 W2 (K = 256; W2 read MN-major)
@@ -368,7 +393,7 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
         }
         if (!(ok = wide_wait(bars, ph))) break;
         // E5: dH1 = dh1 * [h1 > 0]
-        mask_epilogue<kW1>(tl + kTH, m1, sA, tid);
+        mask_epilogue<kW1>(tl + kTH, m1, sA, row, h1c0, h1c1);
         cta_publish();
         if (tid == 0) {
             // S6: dx = dH1 W1 (K = 128; W1 read MN-major), into the logits' columns
@@ -384,7 +409,7 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
         }
         if (!(ok = wide_wait(bars, ph))) break;
         // E6: dL/dR_s
-        {
+        if (part == 0) {
             float v[16];
             tmem_ld16(tl + kTZ, v);
             if (valid)
@@ -401,7 +426,7 @@ __global__ void __launch_bounds__(kRows, 1) wide_kernel(WideArgs a)
             lce += __shfl_xor_sync(0xffffffffu, lce, o);
             lu += __shfl_xor_sync(0xffffffffu, lu, o);
         }
-        if ((tid & 31) == 0) {
+        if (part == 0 && (tid & 31) == 0) {
             atomicAdd(a.loss, lce);
             atomicAdd(a.loss + 1, lu);
         }
@@ -659,7 +684,7 @@ le_status wide_decode(int32_t P, const float* feat, const float* unc, const le_d
     const int grid = ntiles < sms ? ntiles : sms;
     if (!train) {
         LE_CUDA(cudaFuncSetAttribute(wide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-        wide_kernel<false><<<grid, kRows, kSmem, s>>>(a);
+        wide_kernel<false><<<grid, kThreads, kSmem, s>>>(a);
         LE_LAUNCHED();
         return LE_OK;
     }
@@ -671,7 +696,7 @@ le_status wide_decode(int32_t P, const float* feat, const float* unc, const le_d
     LE_CUDA(cudaMemsetAsync(dg->W3, 0, sizeof(float) * ncb * kW2, s));
     LE_CUDA(cudaMemsetAsync(dg->b3, 0, sizeof(float) * ncb, s));
     LE_CUDA(cudaFuncSetAttribute(wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-    wide_kernel<true><<<grid, kRows, kSmem, s>>>(a);
+    wide_kernel<true><<<grid, kThreads, kSmem, s>>>(a);
     LE_LAUNCHED();
     WgradArgs g{};
     g.ntiles = ntiles;
