@@ -41,11 +41,12 @@ def parse():
     ap.add_argument("--decoder", default="auto", choices=["auto", "fused", "unfused"])
     ap.add_argument("--n", type=int, default=N_GAUSS, help="Gaussian count (default: the workload's 1M)")
     ap.add_argument("--no-extras", action="store_true", help="skip the query / unfused comparison legs")
-    ap.add_argument("--only", choices=["quantize", "smooth", "query", "decoder_wide"], default=None,
+    ap.add_argument("--only", choices=["quantize", "smooth", "query", "decoder_wide", "configs"], default=None,
                     help="run one leg alone (quantize: the quantisation stage on --features rows; smooth: "
                          "the adaptive smoothing on --n Gaussians; query: the fused relevancy query and the "
                          "feature-map export on --features random rendered features, without rendering; "
-                         "decoder_wide: one training call of the 8-128-256-128 decoder on --features pixels)")
+                         "decoder_wide: one training call of the 8-128-256-128 decoder on --features pixels; configs: "
+                         "the c1 / c3 autograd steps and the c2 training step at their stated sizes)")
     ap.add_argument("--features", type=int, default=W * H, help="feature rows / pixels for --only quantize|query")
     return ap.parse_args()
 
@@ -339,6 +340,7 @@ def run_ours(args, rank, world):
 
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.perf_counter()
     e0.record()
     copy_stream.wait_event(e0)
     stage(0)
@@ -352,6 +354,7 @@ def run_ours(args, rank, world):
         loss_host[i].copy_(loss, non_blocking=True)
     e1.record()
     barrier()
+    e2e_wall_ms = (time.perf_counter() - h0) * 1e3 / args.steps
     e2e_ms = e0.elapsed_time(e1) / args.steps
     h2d = rgb_stage[0].numel() * 4 + idx_stage[0].numel() * 4
 
@@ -360,7 +363,12 @@ def run_ours(args, rank, world):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mode_name == "unfused" else "f32+bf16",
            "data": "synthetic (seeded 50-cluster scene, Voronoi index maps, smooth RGB targets)",
            "config": workload_config(args.n, world), "decoder_path": mode_name,
-           "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12},
+           "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12,
+                   "host_wall_ms": round(e2e_wall_ms, 4),
+                   "note": "each step's targets are copied from pinned host memory on a second stream while "
+                           "the previous step computes, and each step's loss is read back to pinned memory; "
+                           "value = events around the whole loop on the compute stream, host_wall_ms = host "
+                           "clock around the same loop (synchronised at both ends)"},
            "gpu_launches": launches, "clocks": clk, "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
            "instances_K": K_mean,
            "peak_hbm": {"allocated_gb": round(peak_alloc / 1e9, 3), "reserved_gb": round(peak_reserved / 1e9, 3),
@@ -430,6 +438,7 @@ def run_ours(args, rank, world):
         out["query"] = query_leg(leg, synth, scene, cams, args)
         out["query_c4"] = query_c4_leg(leg, synth, args)
         out["decoder_paper_widths"] = decoder_wide_leg(leg, synth, args, bf16_peak)
+        out["configs"] = configs_leg(leg, synth, args)
         out["quantize"] = quant_leg(leg, synth, args, hbm_peak, bf16_peak, peak_kind)
         out["smooth"] = smooth_leg(leg, synth, st, args, bf16_peak)
         out["rgb_dssim"] = rgb_dssim_leg(leg, st, rgb_dev, args, hbm_peak)
@@ -585,6 +594,66 @@ def decoder_wide_leg(leg, synth, args, bf16_peak, P=W * H):
         res["fused"]["tensor_frac"] = round(flop / res["fused"]["ms"] / 1e9 / bf16_peak, 4)
     res["algorithmic_flop"] = flop
     torch.cuda.empty_cache()
+    return res
+
+
+def configs_leg(leg, synth, args):
+    """The smaller workloads at their stated sizes, each timed with CUDA events after warm-up:
+    c1 (2,000 Gaussians, 128x128, SH degree 0) and c3 (1M Gaussians, 1296x840, SH degree 3) as
+    the autograd step -- rasterize forward, a fixed random upstream gradient on RGB, feature and
+    uncertainty, backward to every per-Gaussian parameter -- and c2 (100k Gaussians, 640x480, SH
+    degree 3) as the training step with decoder training (fused BF16 and unfused FP32 decoder)."""
+    import torch
+    from paper_2311_18482_gb300.training import TrainState
+
+    def timed(f, n, warm=3):
+        for _ in range(warm):
+            f()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(n):
+            f()
+        t1.record()
+        torch.cuda.synchronize()
+        return round(t0.elapsed_time(t1) / n, 4)
+
+    def autograd_step(name, n_iter):
+        c = synth.config(name)
+        sc, cam = c["scene"], c["camera"]
+        params = [torch.from_numpy(getattr(sc, k)).cuda().requires_grad_(True)
+                  for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat", "unc")]
+        g = torch.Generator(device="cuda").manual_seed(7)
+        dr = torch.randn((3, cam.H, cam.W), generator=g, device="cuda")
+        df = torch.randn((8, cam.H, cam.W), generator=g, device="cuda")
+        du = torch.randn((cam.H, cam.W), generator=g, device="cuda")
+        buffers = leg.BinSortBuffers()
+
+        def step():
+            for p in params:
+                p.grad = None
+            rgb, feat, unc, _ = leg.rasterize(*params, cam, sc.sh_degree, buffers)
+            ((rgb * dr).sum() + (feat * df).sum() + (unc * du).sum()).backward()
+        ms = timed(step, n_iter)
+        del params, buffers
+        torch.cuda.empty_cache()
+        return {"gaussians": sc.N, "width": cam.W, "height": cam.H, "sh_degree": sc.sh_degree,
+                "ms_fwd_bwd": ms, "path": "torch.autograd.Function (le_preprocess, le_bin_sort, le_render_fwd, "
+                                          "le_render_bwd); includes the host read of K"}
+
+    res = {"c1": autograd_step("c1", 50)}
+    c = synth.config("c2")
+    cam = c["camera"]
+    rgb = torch.from_numpy(c["rgb_target"]).cuda()
+    idx = torch.from_numpy(c["target_idx"]).cuda()
+    c2 = {"gaussians": c["scene"].N, "width": cam.W, "height": cam.H, "codebook": 128}
+    for name, mode in (("fused", leg.FUSED_BF16), ("unfused", leg.UNFUSED_FP32)):
+        st = TrainState(c["scene"], c["decoder"], cam.W, cam.H, "cuda", decoder_mode=mode)
+        c2[name] = {"ms_per_step": timed(lambda: st.step(cam, rgb, idx), 30)}
+        del st
+        torch.cuda.empty_cache()
+    res["c2"] = c2
+    res["c3"] = autograd_step("c3", 10)
     return res
 
 
@@ -941,6 +1010,8 @@ def main():
             res = decode_query_leg(leg, synth, args, hbm, kind)
         elif args.only == "decoder_wide":
             res = decoder_wide_leg(leg, synth, args, bf16, P=args.features)
+        elif args.only == "configs":
+            res = configs_leg(leg, synth, args)
         else:
             from paper_2311_18482_gb300.training import TrainState
             c = synth.config("c5", n=args.n)

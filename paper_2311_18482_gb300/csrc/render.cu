@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(kBlock / 2) render_fwd_kernel(CamParams cam, c
 // the tiles active in this phase.
 constexpr int kStopped = 1 << 30;
 
-__global__ void __launch_bounds__(kBlock / 2) render_fwd_phase_kernel(
+// At most 64 registers (8 blocks of 128 threads per SM): at 80 registers (6 blocks)
+// the phase kernels of one 1M-Gaussian view took 1.5 % longer.
+__global__ void __launch_bounds__(kBlock / 2, 8) render_fwd_phase_kernel(
     CamParams cam, const float4* __restrict__ splat, const uint32_t* __restrict__ ids,
     const uint32_t* __restrict__ base, int nchunks, int c_lo, int c_hi, const uint8_t* __restrict__ act,
     uint8_t* __restrict__ next_act, uint8_t* __restrict__ next_rows, float* __restrict__ out_rgb,
@@ -390,8 +392,10 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
                         const bool cx = cb[2 * p], cy = cb[2 * p + 1];
-                        if (!(cx || cy)) continue;
-                        // alpha of the blended pixels, 0 for the others (1 / (1 - 0) = 1 leaves T)
+                        // alpha of the blended pixels, 0 for the others (1 / (1 - 0) = 1 leaves T,
+                        // and w, dP and the opacity term are 0): both pairs run straight-line, which
+                        // keeps the kernel at 127 registers (8 blocks per SM; a branch per pair took
+                        // 168 registers, 6 blocks, and 11 % more time at 1M Gaussians)
                         const float2 am = sel2(cx, cy, al[p]);
                         const float2 inv = make_float2(__fdividef(1.f, 1.f - am.x), __fdividef(1.f, 1.f - am.y));
                         T[p] = __fmul2_rn(T[p], inv);
