@@ -430,9 +430,11 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
                                                           const float4* __restrict__ dell, int TX, int TY,
                                                           int chunk, int nchunks, uint32_t* __restrict__ counts)
 {
-    extern __shared__ int diff[];
+    extern __shared__ __align__(16) int diff[];
     const int W1 = TX + 1, cells = W1 * TY;
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) diff[i] = 0;
+    // zeroed with 16-byte stores (the launch rounds the array up to whole int4s)
+    for (int i = threadIdx.x; i < (cells + 3) / 4; i += blockDim.x)
+        reinterpret_cast<int4*>(diff)[i] = make_int4(0, 0, 0, 0);
     __syncthreads();
     const int j0 = blockIdx.x * chunk, j1 = min(n, j0 + chunk);
     for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
@@ -449,7 +451,8 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
         }
     }
     __syncthreads();
-    // inclusive prefix sum along each row: one warp per row, 32 cells a step
+    // inclusive prefix sum along each row (one warp per row, 32 cells a step),
+    // each cell's count written straight to its (tile, chunk) entry
     const int lane = threadIdx.x & 31;
     for (int y = threadIdx.x >> 5; y < TY; y += blockDim.x >> 5) {
         int carry = 0;
@@ -462,14 +465,10 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
                 if (lane >= o) v += t;
             }
             v += carry;
-            if (x < TX) diff[y * W1 + x] = v;
+            if (x < TX) counts[(size_t)(y * TX + x) * nchunks + blockIdx.x] = (uint32_t)v;
             carry = __shfl_sync(0xffffffffu, v, 31);
         }
     }
-    __syncthreads();
-    const int T = TX * TY;
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        counts[(size_t)t * nchunks + blockIdx.x] = (uint32_t)diff[(t / TX) * W1 + (t % TX)];
 }
 
 // Placement.  Block (g, C): tile rows [R g, R g + R) (R = kPlaceRows) and the
@@ -751,7 +750,7 @@ le_status bin_prepare(const le_camera* cam, int32_t n, const float* depth, const
                          reinterpret_cast<const float4*>(tile_ellipse), s)) != LE_OK)
         return st;
     // copies per (tile, chunk of depth-sorted Gaussians)
-    const size_t diff_smem = sizeof(int) * (TX + 1) * TY;
+    const size_t diff_smem = sizeof(int4) * (((size_t)(TX + 1) * TY + 3) / 4);
     if (diff_smem > 48 * 1024)
         LE_CUDA(cudaFuncSetAttribute(chunk_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diff_smem));
     chunk_count_kernel<<<w.nchunks, 256, diff_smem, s>>>(n, w.drect, w.dell, TX, TY, w.chunk, w.nchunks, w.base);

@@ -635,43 +635,36 @@ __device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bi
         }
         epi_signal(e);
         if (!epi_wait(e)) return false;
-        // E3: softmax over this half's logit columns [c0, c1), one pass per
-        // 16-column group g: z + b3, the group's max m_g (and the target's
-        // logit), e = exp(z - m_g) parked in the free TMEM columns and its sum
-        // s_g.  The half's max mh and sum sh = sum_g s_g exp(m_g - mh) are
-        // exchanged with the other half; then dz = e w exp(m_g - m) / sum.
+        // E3: softmax over this half's logit columns [c0, c1).  Pass 1: max (and
+        // the target's logit); pass 2: e = exp(z - max), their sum, e parked in
+        // the free TMEM columns; exchange with the other half; pass 3: dz.
         const int jt = t - c0;
         const bool own_t = jt >= 0 && t < c1;
-        float mg0 = -INFINITY, mg1 = -INFINITY, mg2 = -INFINITY, mg3 = -INFINITY, zt_h = 0.f;
-        float mh = -INFINITY, sh = 0.f;
+        float mh = -INFINITY, zt_h = 0.f;
 #pragma unroll 1
         for (int uu = 0; uu < 4; ++uu)
             if (c0 + 16 * uu < c1) {
                 tmem_ld16(tl + c0 + 16 * uu, v);
                 add_bias16(v, b3s, c0 + 16 * uu);
-                float mx = v[0];
 #pragma unroll
-                for (int j = 1; j < 16; ++j) mx = fmaxf(mx, v[j]);
+                for (int j = 0; j < 16; ++j) mh = fmaxf(mh, v[j]);
                 if (own_t && (jt >> 4) == uu) zt_h = select16(v, jt & 15);
-                const float mxl = mx * kL2E;
-                float sum = 0.f;
+            }
+        const float mhl = mh * kL2E;
+        float sh = 0.f;
+#pragma unroll 1
+        for (int uu = 0; uu < 4; ++uu)
+            if (c0 + 16 * uu < c1) {
+                tmem_ld16(tl + c0 + 16 * uu, v);
+                add_bias16(v, b3s, c0 + 16 * uu);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    v[j] = ex2_approx(fmaf(v[j], kL2E, -mxl));
-                    sum += v[j];
+                    v[j] = ex2_approx(fmaf(v[j], kL2E, -mhl));
+                    sh += v[j];
                 }
                 tmem_st16(tl + c0 + 16 * uu, v);
-                // running max and sum of the half (the sum rescaled to the new max)
-                const float mn = fmaxf(mh, mx);
-                sh = sh * ex2_approx((mh - mn) * kL2E) + sum * ex2_approx((mx - mn) * kL2E);
-                mh = mn;
-                mg0 = uu == 0 ? mx : mg0;
-                mg1 = uu == 1 ? mx : mg1;
-                mg2 = uu == 2 ? mx : mg2;
-                mg3 = uu == 3 ? mx : mg3;
             }
         tmem_wait_st();
-        const float mhl = mh * kL2E;
         // the halves exchange (max, sum, target logit) through D's columns [0, 16),
         // which pass 3 then overwrites with dz: no stale FP32 bits stay in D to
         // reach an MMA (as bf16 they can be Inf or NaN)
@@ -698,16 +691,13 @@ __device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bi
             acc_u += u;
         }
         // dz * P (1/P is applied when the gradients are written)
-        const float wsum = w / ssum;
-        const float scale = c0 < c1 ? wsum * ex2_approx((mh - m) * kL2E) : 0.f;
+        const float scale = c0 < c1 ? w * ex2_approx((mh - m) * kL2E) / ssum : 0.f;
 #pragma unroll 1
         for (int uu = 0; uu < 4; ++uu)
             if (c0 + 16 * uu < c1) {
-                const float mgu = uu == 0 ? mg0 : uu == 1 ? mg1 : uu == 2 ? mg2 : mg3;
-                const float sc = wsum * ex2_approx((mgu - m) * kL2E);
                 tmem_ld16(tl + c0 + 16 * uu, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] *= sc;
+                for (int j = 0; j < 16; ++j) v[j] *= scale;
                 store16(D, 128, row, c0 + 16 * uu, v);
             }
         if (own_t && valid) {
