@@ -63,7 +63,7 @@ struct DecArgs {
     float* rel;
     // feature-map export
     int dd;                         // feature dims d (multiple of 64)
-    int export_np;                  // pairs of codebook slots in shared memory (1 or 2)
+    int export_cpr;                 // codebook chunks per round (1 or 2)
     __nv_bfloat16* fmap;            // [P, dd] out
 };
 
@@ -1059,44 +1059,44 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
 // BF16.  Four warpgroups serve the same 128 rows as in the query kernel; e =
 // exp(z - max z) is stored in BF16 and each output row is scaled by 1/sum e.
 // The codebook streams through shared memory in 64-dim chunks ([n_cb x 64]
-// canonical images, 1-D bulk copies), two chunks per round; per chunk one MMA
-// (M = 128 pixels, N = 64 dims, K = n_cb) reads the chunk MN-major into a
-// 64-column TMEM accumulator.  Each warpgroup converts 16 columns of each
-// into a 128-byte-swizzled staging area, from which two TMA tensor stores per
-// round (128 pixels x 64 dims each) write the output in whole lines; a warp
-// storing its rows directly would scatter 16-byte pieces over 32 rows.
-// Where shared memory allows (n_cb <= 128) the codebook has two pairs of
-// slots and TMEM two 128-column accumulator buffers: round R's chunks are
-// copied while round R - 1 computes, and round R + 1's MMAs run while round
-// R's epilogue converts and stores; with one pair (n_cb > 128) a round's
-// copy waits for the previous round's MMAs.
+// canonical images, 1-D bulk copies), two chunks per round where shared
+// memory allows (n_cb <= 128), else one; per chunk one MMA (M = 128 pixels,
+// N = 64 dims, K = n_cb) reads the chunk MN-major into a 64-column TMEM
+// accumulator.  Each warpgroup converts 16 columns of each into a
+// 128-byte-swizzled staging area, from which one TMA tensor store per chunk
+// (128 pixels x 64 dims) writes the output in whole lines; a warp storing its
+// rows directly would scatter 16-byte pieces over 32 rows.  The codebook
+// slots form two groups and TMEM holds two accumulator buffers, so round R's
+// chunks are copied while round R - 1 computes, and round R + 1's MMAs run
+// while round R's epilogue converts and stores.
 constexpr uint32_t kTF = 256;      // TMEM columns of the accumulator buffers, [256, 384) and [384, 512)
 
-// Shared memory of the export kernel without the output staging, for `np`
-// pairs of codebook slots; the staging (one round's two 128 x 64 BF16 boxes,
-// 128-byte swizzled for the TMA store); and whether the staging must borrow
-// W3's shared memory (then W3 is reloaded from its global image after every
-// tile; it is idle during the codebook loop).  The layout starts at a
-// 1024-byte boundary (the swizzled staging and W3s, at offset 18 KB, need
-// it), hence the first 1024.
-__host__ constexpr size_t export_smem_core(int ncb, int np)
+// Shared memory of the export kernel without the output staging, for `cpr`
+// chunks per round (two slot groups of cpr codebook chunks); the staging (one
+// round's cpr 128 x 64 BF16 boxes, 128-byte swizzled for the TMA store); and
+// whether the staging must borrow W3's shared memory (then W3 is reloaded
+// from its global image after every tile; it is idle during the codebook
+// loop).  The layout starts at a 1024-byte boundary (the swizzled staging and
+// W3s, at offset 18 KB, need it), hence the first 1024.
+__host__ constexpr size_t export_smem_core(int ncb, int cpr)
 {
     return 1024 + weights_bytes(ncb) + (sbuf_bytes(128, ncb) > kFwdWgBytes ? sbuf_bytes(128, ncb) : kFwdWgBytes) +
-           2 * np * sbuf_bytes(ncb, 64) + kQueryParts * 128 * 4 + 128;
+           2 * cpr * sbuf_bytes(ncb, 64) + kQueryParts * 128 * 4 + 128;
 }
 constexpr uint32_t kExportBox = sbuf_bytes(128, 64);
 constexpr size_t kMaxDynSmem = 227 * 1024;
-__host__ constexpr int export_pairs(int ncb)
+__host__ constexpr int export_cpr(int ncb)
 {
     return export_smem_core(ncb, 2) + 1024 + 2 * kExportBox <= kMaxDynSmem ? 2 : 1;
 }
 __host__ constexpr bool export_stage_in_w3(int ncb)
 {
-    return export_smem_core(ncb, export_pairs(ncb)) + 1024 + 2 * kExportBox > kMaxDynSmem;
+    return export_smem_core(ncb, export_cpr(ncb)) + 1024 + export_cpr(ncb) * kExportBox > kMaxDynSmem;
 }
 __host__ constexpr size_t export_smem(int ncb)
 {
-    return export_smem_core(ncb, export_pairs(ncb)) + (export_stage_in_w3(ncb) ? 0 : 1024 + 2 * kExportBox);
+    return export_smem_core(ncb, export_cpr(ncb)) +
+           (export_stage_in_w3(ncb) ? 0 : 1024 + export_cpr(ncb) * kExportBox);
 }
 
 __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(const __grid_constant__ CUtensorMap tmap_out,
@@ -1112,10 +1112,10 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     const SBuf Ps{p, a.ncb};
     f.xch = reinterpret_cast<float4*>(p);
     p += sbuf_bytes(128, a.ncb) > kFwdWgBytes ? sbuf_bytes(128, a.ncb) : kFwdWgBytes;
-    const int NP = a.export_np;                  // pairs of codebook slots: 1 or 2
+    const int CPR = a.export_cpr;                // codebook chunks per round: 1 or 2
     const uint32_t chunk_bytes = sbuf_bytes(a.ncb, 64);
-    unsigned char* const gslots = p;             // slot i in [0, 2 NP): pair i / 2
-    p += 2 * NP * chunk_bytes;
+    unsigned char* const gslots = p;             // slot i in [0, 2 CPR): group i / CPR
+    p += 2 * CPR * chunk_bytes;
     float* sums = reinterpret_cast<float*>(p);   // [parts][128] partial sums of e
     p += kQueryParts * 128 * 4;
     // [0] MLP MMAs, [1, 5) codebook slots, [5] and [6] the chunk MMAs of TMEM
@@ -1148,29 +1148,31 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     const int row = f.tid;
     int c0, c1;
     my_cols(f, a.ncb, c0, c1);
-    const int nch = a.dd / 64, npairs = (nch + 1) / 2;
+    const int nch = a.dd / 64, nrounds = (nch + CPR - 1) / CPR;
     const int ntiles = (a.P + 127) / 128;
-    // Rounds are numbered over all tiles of this CTA: round R is chunk pair
-    // R % npairs of the CTA's tile R / npairs, in slot pair R % NP, accumulated
-    // in TMEM buffer R & 1.  Thread 0 owns the copies and the MMAs.
+    // Rounds are numbered over all tiles of this CTA: round R covers chunks
+    // [CPR q, CPR q + CPR) (q = R % nrounds) of the CTA's tile R / nrounds, in
+    // slot group R & 1, accumulated in TMEM buffer R & 1.  Thread 0 owns the
+    // copies and the MMAs.
     uint32_t gphase[4] = {0u, 0u, 0u, 0u}, cphase[2] = {0u, 0u};
     bool pending[4] = {false, false, false, false};
-    auto tile_of = [&](int R) { return blockIdx.x + (R / npairs) * (int)gridDim.x; };
+    auto tile_of = [&](int R) { return blockIdx.x + (R / nrounds) * (int)gridDim.x; };
     auto load_round = [&](int R) {
         if (tile_of(R) >= ntiles) return;
-        const int q = R % npairs, sp = R % NP;
-        for (int s = 0; s < 2 && 2 * q + s < nch; ++s) {
-            const int i = 2 * sp + s;
+        const int q = R % nrounds;
+        for (int s = 0; s < CPR && CPR * q + s < nch; ++s) {
+            const int i = CPR * (R & 1) + s;
             mbar_expect_tx(mbar + 1 + i, chunk_bytes);
-            bulk_g2s(gslots + i * chunk_bytes, a.G_img + (size_t)(2 * q + s) * chunk_bytes, chunk_bytes, mbar + 1 + i);
+            bulk_g2s(gslots + i * chunk_bytes, a.G_img + (size_t)(CPR * q + s) * chunk_bytes, chunk_bytes,
+                     mbar + 1 + i);
             pending[i] = true;
         }
     };
     auto issue_round = [&](int R) {
-        const int q = R % npairs, sp = R % NP;
+        const int q = R % nrounds;
         bool okr = true;
-        for (int s = 0; s < 2 && 2 * q + s < nch; ++s) {
-            const int i = 2 * sp + s;
+        for (int s = 0; s < CPR && CPR * q + s < nch; ++s) {
+            const int i = CPR * (R & 1) + s;
             if (!mbar_wait(mbar + 1 + i, gphase[i])) okr = false;
             gphase[i] ^= 1u;
             pending[i] = false;
@@ -1184,7 +1186,7 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     };
     bool ok = true;
     if (tid == 0)
-        for (int R = 0; R < NP; ++R) load_round(R);
+        for (int R = 0; R < 2; ++R) load_round(R);
     int R = 0, R_issue = 0;                      // the next round to complete / to issue
     float xf[8];                                 // this tile's R_s, loaded a tile ahead (part 0)
     if (f.half == 0) load_feat(a, blockIdx.x * 128 + row, blockIdx.x * 128 + row < a.P, xf);
@@ -1226,14 +1228,14 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
 #pragma unroll
         for (int h = 0; h < kQueryParts; ++h) tot += sums[h * 128 + row];
         const float inv = valid ? 1.0f / tot : 0.f;
-        const int R_end = R + npairs;            // this tile's rounds are [R, R_end)
+        const int R_end = R + nrounds;           // this tile's rounds are [R, R_end)
         for (; R < R_end; ++R) {
-            const int q = R % npairs;
+            const int q = R % nrounds;
             bool tmo = false;
             if (tid == 0) {
-                // round R's MMAs, and with two slot pairs round R + 1's as well (its
-                // chunks were copied during round R - 1), into the other TMEM buffer
-                while (R_issue < R_end && R_issue <= R + NP - 1)
+                // round R's MMAs and round R + 1's (its chunks were copied during
+                // round R - 1), into the other TMEM buffer
+                while (R_issue < R_end && R_issue <= R + 1)
                     if (!issue_round(R_issue++)) tmo = true;
                 // the staging is rewritten below: the previous round's stores must have read it
                 bulk_wait_read_all();
@@ -1247,11 +1249,11 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
                 break;
             }
             fence_after();
-            // slot pair R % NP is free: round R + NP's chunks (this tile's or the CTA's next tile's)
-            if (tid == 0) load_round(R + NP);
+            // slot group R & 1 is free: round R + 2's chunks (this tile's or the CTA's next tile's)
+            if (tid == 0) load_round(R + 2);
             // this warpgroup's 16 columns of each chunk, scaled by 1 / sum e, as BF16 into the
             // staging boxes (row-major 128-byte rows, 16-byte unit u of row r at u ^ (r & 7))
-            for (int s = 0; s < 2 && 2 * q + s < nch; ++s) {
+            for (int s = 0; s < CPR && CPR * q + s < nch; ++s) {
                 tmem_ld16(tbase + kTF + 128 * (R & 1) + 64 * s + 16 * f.half + f.lane, v);
                 __nv_bfloat162 h[8];
 #pragma unroll
@@ -1266,8 +1268,8 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
             __syncthreads();
             fence_after();
             if (tid == 0) {
-                for (int s = 0; s < 2 && 2 * q + s < nch; ++s)
-                    tma_store_2d(&tmap_out, 64 * (2 * q + s), tile * 128, stg + s * kExportBox);
+                for (int s = 0; s < CPR && CPR * q + s < nch; ++s)
+                    tma_store_2d(&tmap_out, 64 * (CPR * q + s), tile * 128, stg + s * kExportBox);
                 bulk_commit();
                 // after the tile's last round, W3 goes back into the staging area for the next tile
                 if (a.w3_reload && R + 1 == R_end && tile + (int)gridDim.x < ntiles) {
@@ -1544,8 +1546,8 @@ le_status export_fused(int32_t P, const float* feat, const le_decoder* d, const 
     a.dd = dd;
     a.fmap = out;
     a.w3_reload = export_stage_in_w3(ncb) ? 1 : 0;
-    a.export_np = export_pairs(ncb);
-    if (a.w3_reload && sbuf_bytes(ncb, 128) < 2 * kExportBox) {
+    a.export_cpr = export_cpr(ncb);
+    if (a.w3_reload && sbuf_bytes(ncb, 128) < (uint32_t)export_cpr(ncb) * kExportBox) {
         set_error("feature map export: no shared memory for the output staging with n_cb = %d", ncb);
         return LE_ERR_UNSUPPORTED;
     }

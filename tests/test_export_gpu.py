@@ -23,9 +23,12 @@ pytestmark = pytest.mark.gpu
 
 # 25,000 pixels are 196 tiles on at most 152 CTAs, so some CTAs run two tiles: with 256 and 240 codes the
 # output staging borrows W3's shared memory and W3 is reloaded between a CTA's tiles; with 192 codes the
-# staging has its own region.
+# staging has its own region (one pair of codebook slots).  With 128 codes or fewer there are two slot
+# pairs and the copies run a round ahead, across a CTA's tiles: 7 rounds per tile (896 dims), 2 rounds
+# with a one-chunk last round (192 dims), one round per tile (64 dims, copies two tiles ahead).
 @pytest.mark.parametrize("P,ncb,d", [(5000, 256, 896), (131, 128, 896), (1, 64, 128), (3000, 16, 192),
-                                     (25000, 256, 896), (25000, 240, 896), (25000, 192, 896)])
+                                     (25000, 256, 896), (25000, 240, 896), (25000, 192, 896),
+                                     (25000, 128, 896), (25000, 64, 192), (60000, 16, 64)])
 def test_feature_map(leg, orc, P, ncb, d):
     import paper_2311_18482_gb300 as L
     dec = synth.decoder_init(31, ncb)
@@ -61,11 +64,13 @@ def test_feature_map_one_hot(leg, orc):
     assert np.array_equal(got, np.broadcast_to(bf16(S[17]).astype(np.float32), got.shape))
 
 
-def test_feature_map_full_view_sampled(leg, orc):
-    """The full 1296 x 840 view with 256 codes x 896 dims (every CTA runs ~57 tiles, W3 reloaded between
-    them): 1,024 sampled pixels (and the last one) against the emulation and the FP64 oracle, row by row."""
+@pytest.mark.parametrize("ncb", [256, 128])
+def test_feature_map_full_view_sampled(leg, orc, ncb):
+    """The full 1296 x 840 view with 256 codes (every CTA runs ~57 tiles, W3 reloaded between them) and
+    with 128 codes (two codebook slot pairs, copies a round ahead) x 896 dims: 1,024 sampled pixels (and
+    the last one) against the emulation and the FP64 oracle, row by row."""
     import paper_2311_18482_gb300 as L
-    ncb, d, P = 256, 896, 1296 * 840
+    d, P = 896, 1296 * 840
     dec = synth.decoder_init(37, ncb)
     feat, _, _ = _inputs(P, ncb, 38)
     S = np.random.default_rng(39).standard_normal((ncb, d)).astype(np.float32)
