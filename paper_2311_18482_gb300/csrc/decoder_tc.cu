@@ -63,7 +63,6 @@ struct DecArgs {
     float* rel;
     // feature-map export
     int dd;                         // feature dims d (multiple of 64)
-    int export_cpr;                 // codebook chunks per round (1 or 2)
     __nv_bfloat16* fmap;            // [P, dd] out
 };
 
@@ -1059,44 +1058,34 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
 // BF16.  Four warpgroups serve the same 128 rows as in the query kernel; e =
 // exp(z - max z) is stored in BF16 and each output row is scaled by 1/sum e.
 // The codebook streams through shared memory in 64-dim chunks ([n_cb x 64]
-// canonical images, 1-D bulk copies), two chunks per round where shared
-// memory allows (n_cb <= 128), else one; per chunk one MMA (M = 128 pixels,
-// N = 64 dims, K = n_cb) reads the chunk MN-major into a 64-column TMEM
-// accumulator.  Each warpgroup converts 16 columns of each into a
-// 128-byte-swizzled staging area, from which one TMA tensor store per chunk
-// (128 pixels x 64 dims) writes the output in whole lines; a warp storing its
-// rows directly would scatter 16-byte pieces over 32 rows.  The codebook
-// slots form two groups and TMEM holds two accumulator buffers, so round R's
-// chunks are copied while round R - 1 computes, and round R + 1's MMAs run
-// while round R's epilogue converts and stores.
-constexpr uint32_t kTF = 256;      // TMEM columns of the accumulator buffers, [256, 384) and [384, 512)
+// canonical images, 1-D bulk copies) in two slots; per chunk (one round) one
+// MMA (M = 128 pixels, N = 64 dims, K = n_cb) reads the chunk MN-major into a
+// 64-column TMEM accumulator.  Each warpgroup converts 16 columns into a
+// 128-byte-swizzled staging box, from which one TMA tensor store (128 pixels x
+// 64 dims) writes the output in whole lines; a warp storing its rows directly
+// would scatter 16-byte pieces over 32 rows.  Slots, accumulators and staging
+// boxes come in twos, so round R's chunk is copied while round R - 1
+// computes, round R + 1's MMA runs while round R's epilogue converts, and
+// round R's store drains while round R + 1's epilogue fills the other box.
+constexpr uint32_t kTF = 256;      // TMEM columns of the two accumulators, [256, 320) and [384, 448)
 
-// Shared memory of the export kernel without the output staging, for `cpr`
-// chunks per round (two slot groups of cpr codebook chunks); the staging (one
-// round's cpr 128 x 64 BF16 boxes, 128-byte swizzled for the TMA store); and
-// whether the staging must borrow W3's shared memory (then W3 is reloaded
-// from its global image after every tile; it is idle during the codebook
-// loop).  The layout starts at a 1024-byte boundary (the swizzled staging and
-// W3s, at offset 18 KB, need it), hence the first 1024.
-__host__ constexpr size_t export_smem_core(int ncb, int cpr)
+// Shared memory of the export kernel without the output staging; the staging
+// (two 128 x 64 BF16 boxes, 128-byte swizzled for the TMA store); and whether
+// the staging must borrow W3's shared memory (then W3 is reloaded from its
+// global image after every tile; it is idle during the codebook loop).  The
+// layout starts at a 1024-byte boundary (the swizzled staging and W3s, at
+// offset 18 KB, need it), hence the first 1024.
+__host__ constexpr size_t export_smem_core(int ncb)
 {
     return 1024 + weights_bytes(ncb) + (sbuf_bytes(128, ncb) > kFwdWgBytes ? sbuf_bytes(128, ncb) : kFwdWgBytes) +
-           2 * cpr * sbuf_bytes(ncb, 64) + kQueryParts * 128 * 4 + 128;
+           2 * sbuf_bytes(ncb, 64) + kQueryParts * 128 * 4 + 128;
 }
 constexpr uint32_t kExportBox = sbuf_bytes(128, 64);
 constexpr size_t kMaxDynSmem = 227 * 1024;
-__host__ constexpr int export_cpr(int ncb)
-{
-    return export_smem_core(ncb, 2) + 1024 + 2 * kExportBox <= kMaxDynSmem ? 2 : 1;
-}
-__host__ constexpr bool export_stage_in_w3(int ncb)
-{
-    return export_smem_core(ncb, export_cpr(ncb)) + 1024 + export_cpr(ncb) * kExportBox > kMaxDynSmem;
-}
+__host__ constexpr bool export_stage_in_w3(int ncb) { return export_smem_core(ncb) + 1024 + 2 * kExportBox > kMaxDynSmem; }
 __host__ constexpr size_t export_smem(int ncb)
 {
-    return export_smem_core(ncb, export_cpr(ncb)) +
-           (export_stage_in_w3(ncb) ? 0 : 1024 + export_cpr(ncb) * kExportBox);
+    return export_smem_core(ncb) + (export_stage_in_w3(ncb) ? 0 : 1024 + 2 * kExportBox);
 }
 
 __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(const __grid_constant__ CUtensorMap tmap_out,
@@ -1112,14 +1101,13 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     const SBuf Ps{p, a.ncb};
     f.xch = reinterpret_cast<float4*>(p);
     p += sbuf_bytes(128, a.ncb) > kFwdWgBytes ? sbuf_bytes(128, a.ncb) : kFwdWgBytes;
-    const int CPR = a.export_cpr;                // codebook chunks per round: 1 or 2
     const uint32_t chunk_bytes = sbuf_bytes(a.ncb, 64);
-    unsigned char* const gslots = p;             // slot i in [0, 2 CPR): group i / CPR
-    p += 2 * CPR * chunk_bytes;
+    unsigned char* const gslots = p;             // codebook slots 0 and 1
+    p += 2 * chunk_bytes;
     float* sums = reinterpret_cast<float*>(p);   // [parts][128] partial sums of e
     p += kQueryParts * 128 * 4;
-    // [0] MLP MMAs, [1, 5) codebook slots, [5] and [6] the chunk MMAs of TMEM
-    // buffer 0 and 1, [7] W3 reload; the TMEM base address after them
+    // [0] MLP MMAs, [1] and [2] codebook slots, [5] and [6] the chunk MMAs of
+    // TMEM accumulators 0 and 1, [7] W3 reload; the TMEM base address after them
     uint64_t* mbar = reinterpret_cast<uint64_t*>(p);
     uint32_t* slot = reinterpret_cast<uint32_t*>(p + 64);
     p += 128;
@@ -1148,40 +1136,29 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     const int row = f.tid;
     int c0, c1;
     my_cols(f, a.ncb, c0, c1);
-    const int nch = a.dd / 64, nrounds = (nch + CPR - 1) / CPR;
+    const int nch = a.dd / 64;
     const int ntiles = (a.P + 127) / 128;
-    // Rounds are numbered over all tiles of this CTA: round R covers chunks
-    // [CPR q, CPR q + CPR) (q = R % nrounds) of the CTA's tile R / nrounds, in
-    // slot group R & 1, accumulated in TMEM buffer R & 1.  Thread 0 owns the
-    // copies and the MMAs.
-    uint32_t gphase[4] = {0u, 0u, 0u, 0u}, cphase[2] = {0u, 0u};
-    bool pending[4] = {false, false, false, false};
-    auto tile_of = [&](int R) { return blockIdx.x + (R / nrounds) * (int)gridDim.x; };
+    // Rounds are numbered over all tiles of this CTA: round R is chunk R % nch
+    // of the CTA's tile R / nch, in slot, accumulator and staging box R & 1.
+    // Thread 0 owns the copies, the MMAs and the stores.
+    uint32_t gphase[2] = {0u, 0u}, cphase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
     auto load_round = [&](int R) {
-        if (tile_of(R) >= ntiles) return;
-        const int q = R % nrounds;
-        for (int s = 0; s < CPR && CPR * q + s < nch; ++s) {
-            const int i = CPR * (R & 1) + s;
-            mbar_expect_tx(mbar + 1 + i, chunk_bytes);
-            bulk_g2s(gslots + i * chunk_bytes, a.G_img + (size_t)(CPR * q + s) * chunk_bytes, chunk_bytes,
-                     mbar + 1 + i);
-            pending[i] = true;
-        }
+        if (blockIdx.x + (R / nch) * (int)gridDim.x >= ntiles) return;
+        const int i = R & 1;
+        mbar_expect_tx(mbar + 1 + i, chunk_bytes);
+        bulk_g2s(gslots + i * chunk_bytes, a.G_img + (size_t)(R % nch) * chunk_bytes, chunk_bytes, mbar + 1 + i);
+        pending[i] = true;
     };
     auto issue_round = [&](int R) {
-        const int q = R % nrounds;
-        bool okr = true;
-        for (int s = 0; s < CPR && CPR * q + s < nch; ++s) {
-            const int i = CPR * (R & 1) + s;
-            if (!mbar_wait(mbar + 1 + i, gphase[i])) okr = false;
-            gphase[i] ^= 1u;
-            pending[i] = false;
-            const uint64_t gm = mndesc(SBuf{gslots + i * chunk_bytes, 64}, 0, 0);
-            for (int k = 0; k < a.ncb / 16; ++k)
-                mma(tbase + kTF + 128 * (R & 1) + 64 * s, kdesc(Ps, 0, 16 * k), gm + 128 * k,
-                    idesc_bf16(64, false, true), k > 0);
-        }
-        commit(mbar + 5 + (R & 1));
+        const int i = R & 1;
+        const bool okr = mbar_wait(mbar + 1 + i, gphase[i]);
+        gphase[i] ^= 1u;
+        pending[i] = false;
+        const uint64_t gm = mndesc(SBuf{gslots + i * chunk_bytes, 64}, 0, 0);
+        for (int k = 0; k < a.ncb / 16; ++k)
+            mma(tbase + kTF + 128 * i, kdesc(Ps, 0, 16 * k), gm + 128 * k, idesc_bf16(64, false, true), k > 0);
+        commit(mbar + 5 + i);
         return okr;
     };
     bool ok = true;
@@ -1228,17 +1205,17 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
 #pragma unroll
         for (int h = 0; h < kQueryParts; ++h) tot += sums[h * 128 + row];
         const float inv = valid ? 1.0f / tot : 0.f;
-        const int R_end = R + nrounds;           // this tile's rounds are [R, R_end)
+        const int R_end = R + nch;               // this tile's rounds are [R, R_end)
         for (; R < R_end; ++R) {
-            const int q = R % nrounds;
+            const int q = R % nch;
             bool tmo = false;
             if (tid == 0) {
-                // round R's MMAs and round R + 1's (its chunks were copied during
-                // round R - 1), into the other TMEM buffer
+                // round R's MMA and round R + 1's (its chunk was copied during
+                // round R - 1), into the other accumulator
                 while (R_issue < R_end && R_issue <= R + 1)
                     if (!issue_round(R_issue++)) tmo = true;
-                // the staging is rewritten below: the previous round's stores must have read it
-                bulk_wait_read_all();
+                // box R & 1 is rewritten below: round R - 2's store must have read it
+                bulk_wait_read_but1();
             }
             const bool done = mbar_wait(mbar + 5 + (R & 1), cphase[R & 1]);
             cphase[R & 1] ^= 1u;
@@ -1249,16 +1226,16 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
                 break;
             }
             fence_after();
-            // slot group R & 1 is free: round R + 2's chunks (this tile's or the CTA's next tile's)
+            // slot R & 1 is free: round R + 2's chunk (this tile's or the CTA's next tile's)
             if (tid == 0) load_round(R + 2);
-            // this warpgroup's 16 columns of each chunk, scaled by 1 / sum e, as BF16 into the
-            // staging boxes (row-major 128-byte rows, 16-byte unit u of row r at u ^ (r & 7))
-            for (int s = 0; s < CPR && CPR * q + s < nch; ++s) {
-                tmem_ld16(tbase + kTF + 128 * (R & 1) + 64 * s + 16 * f.half + f.lane, v);
+            // this warpgroup's 16 columns of the chunk, scaled by 1 / sum e, as BF16 into staging
+            // box R & 1 (row-major 128-byte rows, 16-byte unit u of row r at u ^ (r & 7))
+            {
+                tmem_ld16(tbase + kTF + 128 * (R & 1) + 16 * f.half + f.lane, v);
                 __nv_bfloat162 h[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j] * inv, v[2 * j + 1] * inv);
-                unsigned char* dst = stg + s * kExportBox + row * 128;
+                unsigned char* dst = stg + (R & 1) * kExportBox + row * 128;
                 const int u = 2 * f.half;
                 *reinterpret_cast<uint4*>(dst + ((u ^ (row & 7)) << 4)) = *reinterpret_cast<uint4*>(h);
                 *reinterpret_cast<uint4*>(dst + (((u + 1) ^ (row & 7)) << 4)) = *reinterpret_cast<uint4*>(h + 4);
@@ -1268,8 +1245,7 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
             __syncthreads();
             fence_after();
             if (tid == 0) {
-                for (int s = 0; s < CPR && CPR * q + s < nch; ++s)
-                    tma_store_2d(&tmap_out, 64 * (CPR * q + s), tile * 128, stg + s * kExportBox);
+                tma_store_2d(&tmap_out, 64 * q, tile * 128, stg + (R & 1) * kExportBox);
                 bulk_commit();
                 // after the tile's last round, W3 goes back into the staging area for the next tile
                 if (a.w3_reload && R + 1 == R_end && tile + (int)gridDim.x < ntiles) {
@@ -1288,7 +1264,7 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
             mbar_wait(mbar + 5 + (R & 1), cphase[R & 1]);
             cphase[R & 1] ^= 1u;
         }
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 2; ++i)
             if (pending[i]) mbar_wait(mbar + 1 + i, gphase[i]);
         if (f.w3pending) mbar_wait(f.w3bar, f.w3phase);
         bulk_wait_all();
@@ -1546,8 +1522,7 @@ le_status export_fused(int32_t P, const float* feat, const le_decoder* d, const 
     a.dd = dd;
     a.fmap = out;
     a.w3_reload = export_stage_in_w3(ncb) ? 1 : 0;
-    a.export_cpr = export_cpr(ncb);
-    if (a.w3_reload && sbuf_bytes(ncb, 128) < (uint32_t)export_cpr(ncb) * kExportBox) {
+    if (a.w3_reload && sbuf_bytes(ncb, 128) < 2 * kExportBox) {
         set_error("feature map export: no shared memory for the output staging with n_cb = %d", ncb);
         return LE_ERR_UNSUPPORTED;
     }
