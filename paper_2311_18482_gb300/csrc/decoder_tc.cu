@@ -1058,22 +1058,19 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) query_fused_kernel(DecAr
 // BF16.  Four warpgroups serve the same 128 rows as in the query kernel; e =
 // exp(z - max z) is stored in BF16 and each output row is scaled by 1/sum e.
 // The codebook streams through shared memory in 64-dim chunks ([n_cb x 64]
-// canonical images, 1-D bulk copies) in two slots; per chunk (one round) one
-// MMA (M = 128 pixels, N = 64 dims, K = n_cb) reads the chunk MN-major into a
-// 64-column TMEM accumulator.  Each warpgroup converts 16 columns into a
-// 128-byte-swizzled staging box, from which one TMA tensor store (128 pixels x
-// 64 dims) writes the output in whole lines; a warp storing its rows directly
-// would scatter 16-byte pieces over 32 rows.  Slots, accumulators and staging
-// boxes come in twos, so round R's chunk is copied while round R - 1
-// computes, round R + 1's MMA runs while round R's epilogue converts, and
-// round R's store drains while round R + 1's epilogue fills the other box.
-constexpr uint32_t kTF = 256;      // TMEM columns of the two accumulators, [256, 320) and [384, 448)
+// canonical images, two slots, 1-D bulk copies); per chunk one MMA (M = 128
+// pixels, N = 64 dims, K = n_cb) reads the chunk MN-major into one of two
+// 64-column TMEM accumulators.  Each warpgroup converts 16 columns of each
+// into a 128-byte-swizzled staging area, from which two TMA tensor stores per
+// round (128 pixels x 64 dims each) write the output in whole lines; a warp
+// storing its rows directly would scatter 16-byte pieces over 32 rows.
+constexpr uint32_t kTF = 256;      // TMEM columns of the two chunk accumulators
 
-// Shared memory of the export kernel without the output staging; the staging
-// (two 128 x 64 BF16 boxes, 128-byte swizzled for the TMA store); and whether
-// the staging must borrow W3's shared memory (then W3 is reloaded from its
-// global image after every tile; it is idle during the codebook loop).  The
-// layout starts at a 1024-byte boundary (the swizzled staging and W3s, at
+// Shared memory of the export kernel without the output staging, the staging
+// (one round's two 128 x 64 BF16 boxes, 128-byte swizzled for the TMA store),
+// and whether the staging must borrow W3's shared memory (then W3 is reloaded
+// from its global image after every tile; it is idle during the codebook loop).
+// The layout starts at a 1024-byte boundary (the swizzled staging and W3s, at
 // offset 18 KB, need it), hence the first 1024.
 __host__ constexpr size_t export_smem_core(int ncb)
 {
@@ -1102,14 +1099,12 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     f.xch = reinterpret_cast<float4*>(p);
     p += sbuf_bytes(128, a.ncb) > kFwdWgBytes ? sbuf_bytes(128, a.ncb) : kFwdWgBytes;
     const uint32_t chunk_bytes = sbuf_bytes(a.ncb, 64);
-    unsigned char* const gslots = p;             // codebook slots 0 and 1
+    const SBuf Gs[2] = {SBuf{p, 64}, SBuf{p + chunk_bytes, 64}};
     p += 2 * chunk_bytes;
-    float* sums = reinterpret_cast<float*>(p);   // [parts][128] partial sums of e
+    float* sums = reinterpret_cast<float*>(p);          // [parts][128] partial sums of e
     p += kQueryParts * 128 * 4;
-    // [0] MLP MMAs, [1] and [2] codebook slots, [5] and [6] the chunk MMAs of
-    // TMEM accumulators 0 and 1, [7] W3 reload; the TMEM base address after them
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);
-    uint32_t* slot = reinterpret_cast<uint32_t*>(p + 64);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(p);     // [0] MMA, [1], [2] codebook slots, [4] W3 reload
+    uint32_t* slot = reinterpret_cast<uint32_t*>(p + 24);
     p += 128;
     unsigned char* stg = a.w3_reload ? f.W3s.p
                                      : reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 1023) &
@@ -1122,9 +1117,11 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     f.nthreads = blockDim.x;
     f.half = tid >> 7;
     f.nhalf = kQueryParts;
-    f.w3bar = mbar + 7;
-    if (tid == 0)
-        for (int i = 0; i < 8; ++i) mbar_init(mbar + i, 1);
+    f.w3bar = mbar + 4;
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i) mbar_init(mbar + i, 1);
+        mbar_init(mbar + 4, 1);
+    }
     if (tid < 32) tmem_alloc(slot, 512);
     fence_proxy_async();
     fence_before();
@@ -1137,35 +1134,18 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
     int c0, c1;
     my_cols(f, a.ncb, c0, c1);
     const int nch = a.dd / 64;
-    const int ntiles = (a.P + 127) / 128;
-    // Rounds are numbered over all tiles of this CTA: round R is chunk R % nch
-    // of the CTA's tile R / nch, in slot, accumulator and staging box R & 1.
-    // Thread 0 owns the copies, the MMAs and the stores.
-    uint32_t gphase[2] = {0u, 0u}, cphase[2] = {0u, 0u};
+    uint32_t gphase[2] = {0u, 0u};
     bool pending[2] = {false, false};
-    auto load_round = [&](int R) {
-        if (blockIdx.x + (R / nch) * (int)gridDim.x >= ntiles) return;
-        const int i = R & 1;
-        mbar_expect_tx(mbar + 1 + i, chunk_bytes);
-        bulk_g2s(gslots + i * chunk_bytes, a.G_img + (size_t)(R % nch) * chunk_bytes, chunk_bytes, mbar + 1 + i);
-        pending[i] = true;
+    auto load_chunk = [&](int kc, int s) {
+        mbar_expect_tx(mbar + 1 + s, chunk_bytes);
+        bulk_g2s(Gs[s].p, a.G_img + (size_t)kc * chunk_bytes, chunk_bytes, mbar + 1 + s);
+        pending[s] = true;
     };
-    auto issue_round = [&](int R) {
-        const int i = R & 1;
-        const bool okr = mbar_wait(mbar + 1 + i, gphase[i]);
-        gphase[i] ^= 1u;
-        pending[i] = false;
-        const uint64_t gm = mndesc(SBuf{gslots + i * chunk_bytes, 64}, 0, 0);
-        for (int k = 0; k < a.ncb / 16; ++k)
-            mma(tbase + kTF + 128 * i, kdesc(Ps, 0, 16 * k), gm + 128 * k, idesc_bf16(64, false, true), k > 0);
-        commit(mbar + 5 + i);
-        return okr;
-    };
+    const int ntiles = (a.P + 127) / 128;
     bool ok = true;
-    if (tid == 0)
-        for (int R = 0; R < 2; ++R) load_round(R);
-    int R = 0, R_issue = 0;                      // the next round to complete / to issue
-    float xf[8];                                 // this tile's R_s, loaded a tile ahead (part 0)
+    if (tid == 0 && blockIdx.x < ntiles)
+        for (int s = 0; s < 2 && s < nch; ++s) load_chunk(s, s);
+    float xf[8];                                // this tile's R_s, loaded a tile ahead (part 0)
     if (f.half == 0) load_feat(a, blockIdx.x * 128 + row, blockIdx.x * 128 + row < a.P, xf);
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int px = tile * 128 + row;
@@ -1205,37 +1185,44 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
 #pragma unroll
         for (int h = 0; h < kQueryParts; ++h) tot += sums[h * 128 + row];
         const float inv = valid ? 1.0f / tot : 0.f;
-        const int R_end = R + nch;               // this tile's rounds are [R, R_end)
-        for (; R < R_end; ++R) {
-            const int q = R % nch;
-            bool tmo = false;
+        bool tmo = false;
+        for (int kc0 = 0; kc0 < nch; kc0 += 2) {
             if (tid == 0) {
-                // round R's MMA and round R + 1's (its chunk was copied during
-                // round R - 1), into the other accumulator
-                while (R_issue < R_end && R_issue <= R + 1)
-                    if (!issue_round(R_issue++)) tmo = true;
-                // box R & 1 is rewritten below: round R - 2's store must have read it
-                bulk_wait_read_but1();
+                for (int s = 0; s < 2 && kc0 + s < nch; ++s) {
+                    if (!mbar_wait(mbar + 1 + s, gphase[s])) tmo = true;
+                    gphase[s] ^= 1u;
+                    pending[s] = false;
+                    const uint64_t gm = mndesc(Gs[s], 0, 0);
+                    for (int k = 0; k < a.ncb / 16; ++k)
+                        mma(tbase + kTF + 64 * s, kdesc(Ps, 0, 16 * k), gm + 128 * k, idesc_bf16(64, false, true),
+                            k > 0);
+                }
+                commit(f.mbar);
+                // the staging area is rewritten below: the previous round's stores must have read it
+                bulk_wait_read_all();
             }
-            const bool done = mbar_wait(mbar + 5 + (R & 1), cphase[R & 1]);
-            cphase[R & 1] ^= 1u;
-            if (bar_any(0, blockDim.x, tmo || !done)) {
+            if (!wg_wait(f) || bar_any(0, blockDim.x, tmo)) {
                 if (tid == 0) atomicExch(&g_tc_error, 1);
                 ok = false;
-                ++R;                             // its wait is spent; the drain waits for the later ones
                 break;
             }
-            fence_after();
-            // slot R & 1 is free: round R + 2's chunk (this tile's or the CTA's next tile's)
-            if (tid == 0) load_round(R + 2);
-            // this warpgroup's 16 columns of the chunk, scaled by 1 / sum e, as BF16 into staging
-            // box R & 1 (row-major 128-byte rows, 16-byte unit u of row r at u ^ (r & 7))
-            {
-                tmem_ld16(tbase + kTF + 128 * (R & 1) + 16 * f.half + f.lane, v);
+            // refill the slots: the next chunk pair of this tile, or the first pair of the next tile
+            if (tid == 0) {
+                const bool more = kc0 + 2 < nch;
+                const bool next_tile = tile + (int)gridDim.x < ntiles;
+                for (int s = 0; s < 2; ++s) {
+                    const int kc = more ? kc0 + 2 + s : s;
+                    if ((more && kc < nch) || (!more && next_tile && kc < nch)) load_chunk(kc, s);
+                }
+            }
+            // this warpgroup's 16 columns of each chunk, scaled by 1 / sum e, as BF16 into the
+            // staging boxes (row-major 128-byte rows, 16-byte unit u of row r at u ^ (r & 7))
+            for (int s = 0; s < 2 && kc0 + s < nch; ++s) {
+                tmem_ld16(tbase + kTF + 64 * s + 16 * f.half + f.lane, v);
                 __nv_bfloat162 h[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j] * inv, v[2 * j + 1] * inv);
-                unsigned char* dst = stg + (R & 1) * kExportBox + row * 128;
+                unsigned char* dst = stg + s * kExportBox + row * 128;
                 const int u = 2 * f.half;
                 *reinterpret_cast<uint4*>(dst + ((u ^ (row & 7)) << 4)) = *reinterpret_cast<uint4*>(h);
                 *reinterpret_cast<uint4*>(dst + (((u + 1) ^ (row & 7)) << 4)) = *reinterpret_cast<uint4*>(h + 4);
@@ -1245,10 +1232,11 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
             __syncthreads();
             fence_after();
             if (tid == 0) {
-                tma_store_2d(&tmap_out, 64 * q, tile * 128, stg + (R & 1) * kExportBox);
+                for (int s = 0; s < 2 && kc0 + s < nch; ++s)
+                    tma_store_2d(&tmap_out, 64 * (kc0 + s), tile * 128, stg + s * kExportBox);
                 bulk_commit();
                 // after the tile's last round, W3 goes back into the staging area for the next tile
-                if (a.w3_reload && R + 1 == R_end && tile + (int)gridDim.x < ntiles) {
+                if (a.w3_reload && kc0 + 2 >= nch && tile + (int)gridDim.x < ntiles) {
                     bulk_wait_read_all();
                     mbar_expect_tx(f.w3bar, sbuf_bytes(a.ncb, 128));
                     bulk_g2s(f.W3s.p, a.W3_img, sbuf_bytes(a.ncb, 128), f.w3bar);
@@ -1257,15 +1245,10 @@ __global__ void __launch_bounds__(128 * kQueryParts, 1) export_fused_kernel(cons
             }
         }
     }
-    // drain what is still in flight before the shared memory and TMEM go away:
-    // MMAs issued but not waited for (only after an error), copies, stores
+    // drain copies still in flight before the shared memory goes away
     if (tid == 0) {
-        for (; R < R_issue; ++R) {
-            mbar_wait(mbar + 5 + (R & 1), cphase[R & 1]);
-            cphase[R & 1] ^= 1u;
-        }
-        for (int i = 0; i < 2; ++i)
-            if (pending[i]) mbar_wait(mbar + 1 + i, gphase[i]);
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) mbar_wait(mbar + 1 + s, gphase[s]);
         if (f.w3pending) mbar_wait(f.w3bar, f.w3phase);
         bulk_wait_all();
     }
