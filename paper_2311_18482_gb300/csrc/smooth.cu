@@ -5,10 +5,12 @@
 // its mean over the Gaussians times lambda_smo, the gradient of every MLP
 // parameter (through the first term) and of s_G (through the second).
 //
-// smooth_kernel: persistent, one CTA (4 warps, one Gaussian per thread and
-// TMEM lane) per SM, tiles of 128 Gaussians one after another.  Thread 0
-// issues each tcgen05.mma round; after it completes, all threads run its
-// epilogue (bias, ReLU and its mask, BF16 into shared memory):
+// smooth_kernel: persistent, one CTA per SM, tiles of 128 Gaussians one after
+// another.  Four warpgroups serve the tile's 128 rows (TMEM lanes), each
+// taking 32 of every 128-column epilogue's columns; the loss epilogue is
+// warpgroup 0's.  Thread 0 issues each tcgen05.mma round; after it completes,
+// all threads run its epilogue (bias, ReLU and its mask, BF16 into shared
+// memory):
 //   forward  H1 = relu(X W1^T + b1), H2, H3, Z = H3 W4^T + b4 (FP32 accumulation)
 //   loss     per row: diff = Z - s_G, n = |diff|; dZ = lambda/n_total diff/n;
 //            d_feat -= lambda/n_total max(u, w_s) diff/n (added to the caller's array)
@@ -32,7 +34,8 @@ namespace {
 using namespace tc;
 
 constexpr int kH = 128, kS = 8;
-constexpr int kThreadsS = 128;
+constexpr int kParts = 4;                    // warpgroups per CTA
+constexpr int kThreadsS = 128 * kParts;
 // TMEM columns
 constexpr uint32_t kAcc = 0, kDW2 = 128, kDW3 = 256, kDW1 = 384, kDW4 = 400, kDB2 = 416, kDB3 = 432;
 
@@ -72,6 +75,7 @@ struct Ctx {
     uint32_t phase;
     uint32_t tmem, lanef;
     int row;
+    int part;                      // warpgroup: columns [32 part, 32 part + 32) of each hidden epilogue
 };
 
 // Wait for the MMA round just committed; every thread agrees on the outcome.
@@ -93,13 +97,13 @@ __device__ __forceinline__ void publish()
     fence_after();
 }
 
-// Epilogue of a 128-column hidden layer: v = acc + b; relu; BF16 into H; the
-// ReLU mask (16 bits per 16 columns) into mask[word * 128 + row].
+// This warpgroup's 32 columns of the epilogue of a 128-column hidden layer:
+// v = acc + b; relu; BF16 into H; the ReLU mask bits into mask[part * 128 + row].
 __device__ __forceinline__ void hidden_epilogue(const Ctx& c, const float* b, uint32_t hoff, uint32_t* mask)
 {
     const SBuf Hs{c.sm + hoff, kH};
-#pragma unroll 2
-    for (int q = 0; q < 8; q += 2) {
+    {
+        const int q = 2 * c.part;
         uint32_t mw = 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -118,12 +122,12 @@ __device__ __forceinline__ void hidden_epilogue(const Ctx& c, const float* b, ui
     }
 }
 
-// Backward epilogue: dH = acc o mask, BF16 into H's buffer.
+// This warpgroup's 32 columns of a backward epilogue: dH = acc o mask, BF16 into H's buffer.
 __device__ __forceinline__ void grad_epilogue(const Ctx& c, uint32_t hoff, const uint32_t* mask)
 {
     const SBuf Hs{c.sm + hoff, kH};
-#pragma unroll 2
-    for (int q = 0; q < 8; q += 2) {
+    {
+        const int q = 2 * c.part;
         const uint32_t mw = mask[(q >> 1) * 128 + c.row];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -231,9 +235,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
     c.bar = reinterpret_cast<uint64_t*>(c.sm + kOBar);
     c.tslot = reinterpret_cast<uint32_t*>(c.sm + kOBar + 16);
     c.phase = 0;
-    c.row = threadIdx.x;
+    c.row = threadIdx.x & 127;
+    c.part = threadIdx.x >> 7;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    c.lanef = (uint32_t)(32 * warp) << 16;
+    c.lanef = (uint32_t)(32 * (warp & 3)) << 16;
     // weights (BF16, [out][in]), biases (FP32), the ones operand
     sbuf_fill(SBuf{c.sm + kOW1, 16}, 128, a.W1, 3, kH, 3);
     sbuf_fill(SBuf{c.sm + kOW2, kH}, 128, a.W2, kH, kH, kH);
@@ -243,7 +248,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
     for (int i = threadIdx.x; i < 3 * kH + 16; i += blockDim.x)
         bs[i] = i < kH ? a.b1[i] : i < 2 * kH ? a.b2[i - kH] : i < 3 * kH ? a.b3[i - 2 * kH]
               : (i - 3 * kH < kS ? a.b4[i - 3 * kH] : 0.f);
-    {
+    if (c.part == 0) {
         float v[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         sbuf_store8(SBuf{c.sm + kOE, 16}, c.row, 0, v);
         sbuf_store8(SBuf{c.sm + kOE, 16}, c.row, 8, z);
@@ -267,9 +272,10 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
         any = true;
         const int g = t * 128 + c.row;
         const bool valid = g < a.n;
+        const bool p0 = c.part == 0;             // warpgroup 0: the row's inputs, X and the loss
         // this row's s_G, u and current d_feat, loaded now so that the forward rounds hide their latency
         float fg[kS], df[kS], ug = 0.f;
-        if (valid) {
+        if (valid && p0) {
             const float4 f0 = reinterpret_cast<const float4*>(a.feat)[2 * (size_t)g];
             const float4 f1 = reinterpret_cast<const float4*>(a.feat)[2 * (size_t)g + 1];
             fg[0] = f0.x; fg[1] = f0.y; fg[2] = f0.z; fg[3] = f0.w;
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
 #pragma unroll
             for (int k = 0; k < kS; ++k) fg[k] = df[k] = 0.f;
         }
-        {   // X = [p, 1, 0...]
+        if (p0) {   // X = [p, 1, 0...]
             float v[8] = {0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f}, z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (valid) {
                 v[0] = a.means[3 * (size_t)g];
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
         publish();
         if (threadIdx.x == 0) issue(c.s0, c.tmem, c.bar, 3, first);
         if (!(ok = round_wait(c))) break;
-        {   // loss and the output gradient
+        if (p0) {   // loss and the output gradient
             float z[16];
             tmem_ld16(c.tmem + c.lanef + kAcc, z);
             float diff[kS], nn = 0.f;
@@ -359,10 +365,12 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
         }
     } else if (any) {
         // flush: TMEM lane = this thread's row of each accumulator
+        // flush: TMEM lane = this thread's row of each accumulator; warpgroup p takes
+        // columns [32 p, 32 p + 32) of dW2 and dW3 and one of the small blocks
         float v[16];
         const int r = c.row;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 2 * c.part; q < 2 * c.part + 2; ++q) {
             tmem_ld16(c.tmem + c.lanef + kDW2 + 16 * q, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) atomicAdd(a.dW2 + (size_t)r * kH + 16 * q + j, v[j]);
@@ -370,21 +378,28 @@ __global__ void __launch_bounds__(kThreadsS, 1) smooth_kernel(SmoothArgs a)
 #pragma unroll
             for (int j = 0; j < 16; ++j) atomicAdd(a.dW3 + (size_t)r * kH + 16 * q + j, v[j]);
         }
-        tmem_ld16(c.tmem + c.lanef + kDW1, v);
+        if (c.part == 0) {
+            tmem_ld16(c.tmem + c.lanef + kDW1, v);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) atomicAdd(a.dW1 + (size_t)r * 3 + j, v[j]);
-        atomicAdd(a.db1 + r, v[3]);
-        tmem_ld16(c.tmem + c.lanef + kDW4, v);    // row r = h3 dim, column k = output k
+            for (int j = 0; j < 3; ++j) atomicAdd(a.dW1 + (size_t)r * 3 + j, v[j]);
+            atomicAdd(a.db1 + r, v[3]);
+        } else if (c.part == 1) {
+            tmem_ld16(c.tmem + c.lanef + kDW4, v);    // row r = h3 dim, column k = output k
 #pragma unroll
-        for (int k = 0; k < kS; ++k) atomicAdd(a.dW4 + (size_t)k * kH + r, v[k]);
-        tmem_ld16(c.tmem + c.lanef + kDB2, v);
-        atomicAdd(a.db2 + r, v[0]);
-        tmem_ld16(c.tmem + c.lanef + kDB3, v);
-        atomicAdd(a.db3 + r, v[0]);
+            for (int k = 0; k < kS; ++k) atomicAdd(a.dW4 + (size_t)k * kH + r, v[k]);
+        } else if (c.part == 2) {
+            tmem_ld16(c.tmem + c.lanef + kDB2, v);
+            atomicAdd(a.db2 + r, v[0]);
+        } else {
+            tmem_ld16(c.tmem + c.lanef + kDB3, v);
+            atomicAdd(a.db3 + r, v[0]);
+        }
+        if (c.part == 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        if (lane == 0) atomicAdd(a.loss, lsum * a.scale);
-        if ((lane & 1) == 0 && (lane >> 1) < kS) atomicAdd(a.db4 + (lane >> 1), db4acc);
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if (lane == 0) atomicAdd(a.loss, lsum * a.scale);
+            if ((lane & 1) == 0 && (lane >> 1) < kS) atomicAdd(a.db4 + (lane >> 1), db4acc);
+        }
     }
     fence_before();
     __syncthreads();
