@@ -314,3 +314,25 @@ def test_lazy_bin_render_equals_full(leg, case):
     assert rel_err(to_np(g2l), to_np(g2f)) < 1e-4
     for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat", "unc"):
         assert rel_err(to_np(getattr(gl, k)), to_np(getattr(gf, k))) < 1e-4, k
+
+
+def test_lazy_capacity_retry(leg):
+    """le_bin_render_fwd with room for only half of the K copies: the first call stops with
+    LE_ERR_CAPACITY (K is reported, nothing is placed), and the binding's retry with room for K gives
+    the lists and images of a call that had room from the start, bit for bit."""
+    c = synth.config("c2", n=20000, W=320, H=240)
+    sc, cam = c["scene"], c["camera"]
+    g = leg.Gaussians.from_scene(sc)
+    proj = leg.le_preprocess(g, cam)
+    ids0, r0, K0, img0 = leg.le_bin_render_fwd(cam, proj)
+    torch.cuda.synchronize()
+    ref = {k: getattr(img0, k).clone() for k in ("rgb", "feat", "unc", "T", "n_contrib")}
+    r0 = r0.clone()
+    assert K0 > 2
+    small = leg.BinSortBuffers()
+    ids1, r1, K1, img1 = leg.le_bin_render_fwd(cam, proj, buffers=small, k_cap=K0 // 2)
+    torch.cuda.synchronize()
+    leg.le_device_status()
+    assert K1 == K0 and small.k_cap >= K0 and torch.equal(r1, r0)
+    for k, v in ref.items():
+        assert torch.equal(getattr(img1, k), v), k
