@@ -23,6 +23,10 @@
  *     [channel][H][W]; pixel (i, j) is sampled at integer coordinates.
  *   - 16-byte alignment is required for `splat`, `grad2d`, `sh` and the
  *     decoder weights (torch allocations satisfy it).
+ *   - An empty input (n = 0 Gaussians, P = 0 pixels) is valid: the call reads
+ *     and writes no per-element array (those pointers may be null), and
+ *     fixed-size outputs (losses, gradients of network weights, images) are
+ *     written as for no contribution.
  */
 #ifndef LEG_H
 #define LEG_H

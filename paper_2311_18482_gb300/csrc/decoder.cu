@@ -245,7 +245,20 @@ extern "C" le_status le_decode(int32_t mode, int32_t P, const float* feat, const
     if (st != LE_OK) return st;
     LE_CHECK_ARG(P >= 0, "P < 0");
     LE_CHECK_ARG(mode == LE_DECODE_UNFUSED_FP32 || mode == LE_DECODE_FUSED_BF16, "unknown decode mode %d", mode);
-    if (P == 0) return LE_OK;
+    if (P == 0) {
+        // no pixels: a training call's loss and weight gradients are zero
+        if (target != nullptr || loss != nullptr) {
+            LE_CHECK_ARG(loss && dgrads && dgrads->W1 && dgrads->b1 && dgrads->W2 && dgrads->b2 && dgrads->W3 &&
+                             dgrads->b3,
+                         "training needs loss and dgrads");
+            cudaStream_t s = as_stream(stream);
+            float* const z[7] = {loss, dgrads->W1, dgrads->b1, dgrads->W2, dgrads->b2, dgrads->W3, dgrads->b3};
+            const size_t n[7] = {2, (size_t)dec->h1 * dec->d_in, (size_t)dec->h1, (size_t)dec->h2 * dec->h1,
+                                 (size_t)dec->h2, (size_t)dec->n_cb * dec->h2, (size_t)dec->n_cb};
+            for (int i = 0; i < 7; ++i) LE_CUDA(cudaMemsetAsync(z[i], 0, n[i] * sizeof(float), s));
+        }
+        return LE_OK;
+    }
     LE_CHECK_ARG(feat != nullptr, "feat is null");
     const bool train = target != nullptr;
     if (train) {

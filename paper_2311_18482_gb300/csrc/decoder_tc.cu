@@ -1539,7 +1539,7 @@ extern "C" le_status le_feature_map(int32_t P, const float* feat, const le_decod
 {
     LE_TRACE("le_feature_map");
     LE_CHECK_ARG(P >= 0, "P = %d < 0", P);
-    LE_CHECK_ARG(dec != nullptr && codebook && out && workspace, "null pointer");
+    LE_CHECK_ARG(dec != nullptr && codebook && workspace && (P == 0 || out), "null pointer");
     LE_CHECK_ARG(P == 0 || feat != nullptr, "null feat");
     LE_CHECK_ARG(leg::aligned16(out) && leg::aligned16(workspace), "out and workspace must be 16-byte aligned");
     if (d <= 0 || d % 64 != 0) {

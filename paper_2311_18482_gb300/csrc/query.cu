@@ -83,7 +83,7 @@ extern "C" le_status le_query(int32_t mode, int32_t P, const float* feat, const 
     LE_TRACE("le_query");
     LE_CHECK_ARG(P >= 0 && d > 0 && d_clip > 0 && d_clip <= d, "bad sizes");
     LE_CHECK_ARG(Q >= 1 && n_neg >= 1 && Q + n_neg <= kMaxEmb, "need 1 <= Q, n_neg and Q + n_neg <= %d", kMaxEmb);
-    LE_CHECK_ARG(codebook && text && negs && relevancy, "null pointer");
+    LE_CHECK_ARG(codebook && text && negs && (P == 0 || relevancy), "null pointer");
     if (P == 0) return LE_OK;
     cudaStream_t s = as_stream(stream);
     size_t need = 0;
