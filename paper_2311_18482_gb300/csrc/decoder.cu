@@ -2,7 +2,7 @@
 // uncertainty-weighted cross-entropy (Eqs. 9-12) and its backward pass --
 // the unfused FP32 path: every layer is a CUDA-core GEMM over all pixels whose
 // activations and logits go through HBM (workspace).  It is the fallback of
-// the fused tcgen05 path (decoder_tc.cu) and the reference its error is judged
+// the fused tcgen05 path (decoder_tc.cu) and the reference its error is measured
 // against.  le_decode dispatches between the two.
 #include "common.cuh"
 #include "gemm_fp32.cuh"
