@@ -701,19 +701,30 @@ def le_adam(param, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, 
 
 
 # ---------------------------------------------------------------------------
+_K_HINT = {}   # device -> the last rasterize call's instance count K
+
+
 class _Rasterize(torch.autograd.Function):
     """Differentiable rasterization (Eq. 1 plus R_s and R_u): returns
     (rgb [3,H,W], feat [8,H,W], unc [H,W]); backward returns gradients for
-    means, log_scales, quats, opacity_raw, sh, feat, unc."""
+    means, log_scales, quats, opacity_raw, sh, feat, unc.  The forward bins and
+    renders with lazily placed lists (le_bin_render_fwd: the entries any pixel
+    reads, which is all the backward reads)."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_raw, sh, feat, unc, cam, sh_degree, buffers):
         g = Gaussians(means.contiguous(), log_scales.contiguous(), quats.contiguous(), opacity_raw.contiguous(),
                       sh.contiguous(), feat.contiguous(), unc.contiguous(), sh_degree)
         proj = le_preprocess(g, cam)
-        ids, ranges, K, _ = le_bin_sort(cam, proj, buffers)
-        img = le_render_fwd(cam, proj, ids, ranges)
-        ctx.cam, ctx.g, ctx.proj, ctx.ids, ctx.ranges, ctx.img = cam, g, proj, ids.clone(), ranges.clone(), img
+        own = buffers is None
+        # fresh lists sized from the previous call's K on this device (one binning, no capacity retry)
+        hint = _K_HINT.get(means.device)
+        k_cap = max(16 * g.n, int(1.25 * hint) + 1024) if own and hint is not None else None
+        ids, ranges, K, img = le_bin_render_fwd(cam, proj, BinSortBuffers() if own else buffers, k_cap=k_cap)
+        _K_HINT[means.device] = K
+        # buffers the caller reuses may be overwritten by a later forward before this backward
+        ctx.cam, ctx.g, ctx.proj, ctx.img = cam, g, proj, img
+        ctx.ids, ctx.ranges = (ids, ranges) if own else (ids.clone(), ranges.clone())
         ctx.mark_non_differentiable(img.T)
         return img.rgb, img.feat, img.unc, img.T
 
@@ -731,6 +742,6 @@ class _Rasterize(torch.autograd.Function):
 
 
 def rasterize(means, log_scales, quats, opacity_raw, sh, feat, unc, cam, sh_degree, buffers=None):
-    """Autograd entry: (rgb, feat, unc, T_final) images of the Gaussians seen from `cam`."""
-    return _Rasterize.apply(means, log_scales, quats, opacity_raw, sh, feat, unc, cam, sh_degree,
-                            buffers or BinSortBuffers())
+    """Autograd entry: (rgb, feat, unc, T_final) images of the Gaussians seen from `cam`.  buffers
+    (optional): BinSortBuffers reused across calls (the lists are then copied for the backward)."""
+    return _Rasterize.apply(means, log_scales, quats, opacity_raw, sh, feat, unc, cam, sh_degree, buffers)
