@@ -33,21 +33,12 @@ namespace {
 constexpr int kBlock = LE_TILE * LE_TILE;
 
 // q = A' dx^2 + B' dx dy + C' dy^2 in base-2 exponent units (the record's scaled
-// conic; alpha = o 2^-q), with a fixed operation order: the forward and the
-// backward kernel take identical skip decisions.  ax = A' dx^2 and bx = B' dx
-// depend on the column only, so the backward computes them once for its two
-// pixels of a column.
+// conic; alpha = o 2^-q), with a fixed operation order -- q = fma(C', dy * dy,
+// fma(bx, dy, ax)), alpha0 = o * 2^-q -- so that the forward and the backward
+// kernel take identical skip decisions.  ax = A' dx^2 and bx = B' dx depend on
+// the column only, so each thread computes them once for its pixels of a column.
 __device__ __forceinline__ float splat_ax(float Ap, float dx) { return __fmul_rn(Ap, __fmul_rn(dx, dx)); }
 __device__ __forceinline__ float splat_bx(float Bp, float dx) { return __fmul_rn(Bp, dx); }
-__device__ __forceinline__ float splat_q(float ax, float bx, float Cp, float dy)
-{
-    return __fmaf_rn(Cp, __fmul_rn(dy, dy), __fmaf_rn(bx, dy, ax));
-}
-
-__device__ __forceinline__ float splat_alpha0(float opacity, float q)
-{
-    return __fmul_rn(opacity, ex2_approx(-q));
-}
 
 // Paired FP32 arithmetic: one instruction performs the IEEE round-to-nearest
 // operation on both components, each exactly as the scalar operation would.
