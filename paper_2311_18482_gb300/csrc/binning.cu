@@ -520,7 +520,12 @@ __global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
     const int C = super_base + blockIdx.y;
     const int tx = 32 * seg + lane, slo = 32 * seg, shi = min(TX, 32 * seg + 32);
     const bool mine = row_ok && tx < TX && (!tile_act || tile_act[row * TX + tx]);
-    uint32_t ctr = mine ? base[(size_t)(row * TX + tx) * nchunks + (size_t)C * cstride] : 0u;
+    const size_t tb = (size_t)(row * TX + tx) * nchunks;
+    uint32_t ctr = mine ? base[tb + (size_t)C * cstride] : 0u;
+    // a block none of whose tiles has a copy in this super-chunk has nothing to place
+    // (the scan holds K at the end, so the last tile's end offset is there too)
+    const uint32_t cend = mine ? base[tb + (size_t)min((C + 1) * cstride, nchunks)] : 0u;
+    if (!__syncthreads_or(cend > ctr)) return;
     const int j0 = C * super_chunk, j1 = min(n, j0 + super_chunk);
     for (int jb = j0; jb < j1; jb += S::kBatch) {
         // compaction: the round's Gaussians whose rectangle meets this block's
