@@ -129,3 +129,33 @@ def test_backward_halves_match_single_calls(leg, n):
             assert float((a - b).abs().max()) <= 1e-5 * max(float(b.abs().max()), 1e-6), k
     assert float(ga.unc.min()) >= 0.0 and float(ga.unc.max()) <= 1.0
     assert not torch.equal(ga.means, g.means)
+
+
+def test_training_step_ragged_view(leg):
+    """The whole training step on a view whose size is no multiple of anything the kernels tile by:
+    333 x 217 pixels (partial 16 x 16 tiles on both edges; 72,261 pixels, so the decoder's last
+    128-pixel tile holds 69), 6,000 Gaussians of SH degree 1.  The fused BF16 and the unfused FP32
+    decoder paths render identically, agree on the first step's losses (L1 to the order of its block
+    sums, CE and L_u within the fused decoder's BF16 bounds) and stay within 1e-3 over two more steps; u stays in [0, 1]."""
+    from paper_2311_18482_gb300.training import TrainState
+    W, H = 333, 217
+    sc = synth.cluster_scene(11, 6000, 12, sh_degree=1)
+    dec = synth.decoder_init(12, 128)
+    rgb = torch.from_numpy(synth.smooth_rgb_target(13, W, H)).cuda()
+    idx = torch.from_numpy(synth.voronoi_index_map(14, W, H, 128)).cuda()
+    a = TrainState(sc, dec, W, H, decoder_mode=leg.FUSED_BF16)
+    b = TrainState(sc, dec, W, H, decoder_mode=leg.UNFUSED_FP32)
+    for k in range(3):
+        cam = synth.circle_pose(k, 4, W, H)
+        la, lb = a.step(cam, rgb, idx).clone(), b.step(cam, rgb, idx).clone()
+        torch.cuda.synchronize()
+        if k == 0:
+            assert torch.equal(a.img.rgb, b.img.rgb) and torch.equal(a.img.feat, b.img.feat)
+            assert abs(float(la[0]) - float(lb[0])) <= 1e-6 * abs(float(lb[0]))   # block sums land in any order
+            assert torch.allclose(la[1:], lb[1:], rtol=2e-4, atol=1e-7), (la, lb)
+        else:
+            assert torch.allclose(la, lb, rtol=1e-3, atol=1e-6), (k, la, lb)
+    leg.le_device_status()
+    for st in (a, b):
+        u = st.layout.views(st.params)["unc"]
+        assert float(u.min()) >= 0.0 and float(u.max()) <= 1.0
