@@ -657,10 +657,11 @@ def configs_leg(leg, synth, args):
         sc, cam = c["scene"], c["camera"]
         params = [torch.from_numpy(getattr(sc, k)).cuda().requires_grad_(True)
                   for k in ("means", "log_scales", "quats", "opacity_raw", "sh", "feat", "unc")]
-        g = torch.Generator(device="cuda").manual_seed(7)
-        dr = torch.randn((3, cam.H, cam.W), generator=g, device="cuda")
-        df = torch.randn((8, cam.H, cam.W), generator=g, device="cuda")
-        du = torch.randn((cam.H, cam.W), generator=g, device="cuda")
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        dr = torch.randn((3, cam.H, cam.W), generator=gen, device="cuda")
+        df = torch.randn((8, cam.H, cam.W), generator=gen, device="cuda")
+        du = torch.randn((cam.H, cam.W), generator=gen, device="cuda")
+
         def step():
             for p in params:
                 p.grad = None
