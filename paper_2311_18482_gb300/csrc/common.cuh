@@ -80,21 +80,66 @@ constexpr float kConicScaleAC = 0.72134752044448170f, kConicScaleB = 1.442695040
 constexpr float kConicUnscaleAC = 1.3862943611198906f, kConicUnscaleB = 0.69314718055994531f;
 
 // Adam (Kingma & Ba; Sec. 4 trains with it) with both bias corrections folded
-// in: step_size = lr / (1 - b1^t), inv_sqrt_c2 = 1 / sqrt(1 - b2^t).
+// in: step_size = lr / (1 - b1^t), inv_sqrt_c2 = 1 / sqrt(1 - b2^t); c1 = 1 - b1,
+// c2 = 1 - b2 (FP32).
 struct AdamParams {
-    float b1, b2, step_size, inv_sqrt_c2, eps;
+    float b1, b2, c1, c2, step_size, inv_sqrt_c2, eps;
 };
+
+// sqrt(x) and 1/x on the special-function unit (approximate: a relative error
+// of a few 2^-23, far inside the step's own FP32 noise; x >= 0, resp. x >= eps).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // One element: m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
 // p <- clamp(p - step_size m / (sqrt(v) inv_sqrt_c2 + eps), lo, hi).  A fixed
-// sequence of IEEE operations, so every kernel that applies it agrees bit for bit.
+// sequence of operations (the moments in IEEE FP32, the denominator's square
+// root and reciprocal on the SFU), so every kernel that applies it -- scalar
+// or four elements at a time (adam_step4) -- agrees bit for bit.
 __device__ __forceinline__ float adam_step(float p, float g, float& m, float& v, const AdamParams& h, float lo,
                                            float hi)
 {
-    m = __fmaf_rn(h.b1, m, __fmul_rn(1.f - h.b1, g));
-    v = __fmaf_rn(h.b2, v, __fmul_rn(__fmul_rn(1.f - h.b2, g), g));
-    const float den = __fmaf_rn(__fsqrt_rn(v), h.inv_sqrt_c2, h.eps);
-    return fminf(fmaxf(__fsub_rn(p, __fdiv_rn(__fmul_rn(h.step_size, m), den)), lo), hi);
+    m = __fmaf_rn(h.b1, m, __fmul_rn(h.c1, g));
+    v = __fmaf_rn(h.b2, v, __fmul_rn(__fmul_rn(h.c2, g), g));
+    const float den = __fmaf_rn(sqrt_approx(v), h.inv_sqrt_c2, h.eps);
+    return fminf(fmaxf(__fmaf_rn(-__fmul_rn(h.step_size, m), rcp_approx(den), p), lo), hi);
+}
+
+// adam_step on (x, y) with paired FP32 instructions: per component the same
+// IEEE operations as the scalar form.
+__device__ __forceinline__ float2 adam_step2(float2 p, float2 g, float2& m, float2& v, const AdamParams& h, float lo,
+                                             float hi)
+{
+    m = __ffma2_rn(make_float2(h.b1, h.b1), m, __fmul2_rn(make_float2(h.c1, h.c1), g));
+    v = __ffma2_rn(make_float2(h.b2, h.b2), v, __fmul2_rn(__fmul2_rn(make_float2(h.c2, h.c2), g), g));
+    const float2 den = __ffma2_rn(make_float2(sqrt_approx(v.x), sqrt_approx(v.y)),
+                                  make_float2(h.inv_sqrt_c2, h.inv_sqrt_c2), make_float2(h.eps, h.eps));
+    const float2 sm = __fmul2_rn(make_float2(h.step_size, h.step_size), m);
+    const float2 r = __ffma2_rn(make_float2(-sm.x, -sm.y), make_float2(rcp_approx(den.x), rcp_approx(den.y)), p);
+    return make_float2(fminf(fmaxf(r.x, lo), hi), fminf(fmaxf(r.y, lo), hi));
+}
+
+// Four consecutive elements (two pairs).
+__device__ __forceinline__ void adam_step4(float4& p, float4 g, float4& m, float4& v, const AdamParams& h, float lo,
+                                           float hi)
+{
+    float2 ma = make_float2(m.x, m.y), mb = make_float2(m.z, m.w);
+    float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
+    const float2 pa = adam_step2(make_float2(p.x, p.y), make_float2(g.x, g.y), ma, va, h, lo, hi);
+    const float2 pb = adam_step2(make_float2(p.z, p.w), make_float2(g.z, g.w), mb, vb, h, lo, hi);
+    p = make_float4(pa.x, pa.y, pb.x, pb.y);
+    m = make_float4(ma.x, ma.y, mb.x, mb.y);
+    v = make_float4(va.x, va.y, vb.x, vb.y);
 }
 
 AdamParams adam_params(int32_t step, float lr, float beta1, float beta2, float eps);

@@ -430,10 +430,7 @@ struct AdamSink {
     {
         float4 pp = reinterpret_cast<float4*>(p[f])[i4], mm = reinterpret_cast<float4*>(m[f])[i4];
         float4 vv = reinterpret_cast<float4*>(v[f])[i4];
-        pp.x = adam_step(pp.x, g.x, mm.x, vv.x, h, lo, hi);
-        pp.y = adam_step(pp.y, g.y, mm.y, vv.y, h, lo, hi);
-        pp.z = adam_step(pp.z, g.z, mm.z, vv.z, h, lo, hi);
-        pp.w = adam_step(pp.w, g.w, mm.w, vv.w, h, lo, hi);
+        adam_step4(pp, g, mm, vv, h, lo, hi);
         reinterpret_cast<float4*>(p[f])[i4] = pp;
         reinterpret_cast<float4*>(m[f])[i4] = mm;
         reinterpret_cast<float4*>(v[f])[i4] = vv;
@@ -448,14 +445,8 @@ struct AdamSink {
         float4* __restrict__ V = reinterpret_cast<float4*>(v[f]);
         float4 pa = P[i4], ma = M[i4], va = V[i4];
         float4 pb = P[i4 + step4], mb = M[i4 + step4], vb = V[i4 + step4];
-        pa.x = adam_step(pa.x, ga.x, ma.x, va.x, h, lo, hi);
-        pa.y = adam_step(pa.y, ga.y, ma.y, va.y, h, lo, hi);
-        pa.z = adam_step(pa.z, ga.z, ma.z, va.z, h, lo, hi);
-        pa.w = adam_step(pa.w, ga.w, ma.w, va.w, h, lo, hi);
-        pb.x = adam_step(pb.x, gb.x, mb.x, vb.x, h, lo, hi);
-        pb.y = adam_step(pb.y, gb.y, mb.y, vb.y, h, lo, hi);
-        pb.z = adam_step(pb.z, gb.z, mb.z, vb.z, h, lo, hi);
-        pb.w = adam_step(pb.w, gb.w, mb.w, vb.w, h, lo, hi);
+        adam_step4(pa, ga, ma, va, h, lo, hi);
+        adam_step4(pb, gb, mb, vb, h, lo, hi);
         P[i4] = pa;
         M[i4] = ma;
         V[i4] = va;

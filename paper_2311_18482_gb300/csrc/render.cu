@@ -261,9 +261,12 @@ __global__ void __launch_bounds__(kBlock / 2, 8) render_fwd_phase_kernel(
 // Four pixels per thread -- rows y, y + 2, y + 4, y + 6 of one column, warp w
 // covering the compact 16 x 8 block of rows [8w, 8w + 8) -- in two pairs
 // (y, y + 2) and (y + 4, y + 6) whose arithmetic runs on paired FP32
-// instructions.  Per Gaussian and thread the 12 channel gradients
-// w dL/dC_c and the dot products f . dL/dC are paired FMAs into (even pixel,
-// odd pixel) partial sums; the conic and mean gradients, which all share the
+// instructions.  The channel contractions pair channels instead: per Gaussian
+// and thread the 12 channel gradients sum_q w_q dL/dC_q,c and each pixel's
+// f . dL/dC are paired FMAs over channel pairs (2k, 2k + 1), whose record
+// values sit in the pairs of its 16-byte words, so only w is broadcast (pixel
+// pairs broadcast every f_c: 0.380 against 0.374 ms at 1M Gaussians); the conic
+// and mean gradients, which all share the
 // column's dx, come from three sums over the thread's pixels -- D = sum dP,
 // E = sum dP dy, F = sum dP dy^2 with dP = dL/dpower -- formed once per record:
 // dconic = (-dx^2 D / 2, -dx E, -F / 2), dmean = (-A dx D - B E, -C E - B dx D).
@@ -289,8 +292,9 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
     const size_t P = (size_t)cam.W * cam.H;
     float(*wred)[36] = red[threadIdx.x >> 5];
 
-    // pair p holds pixels q = 2p (x) and 2p + 1 (y)
-    float2 npy[2], dC[2][12], T[2], Tf[2], S[2], nbg[2];
+    // pair p holds pixels q = 2p (x) and 2p + 1 (y); dC[q][k] = pixel q's upstream
+    // gradient of channels (2k, 2k + 1)
+    float2 npy[2], dC[PPT][6], T[2], Tf[2], S[2], nbg[2];
     int last[PPT];
     int lmax = 0;
 #pragma unroll
@@ -321,12 +325,7 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
                 pr[k]->x = v[k];
         }
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            if (q & 1)
-                dC[q >> 1][c].y = d[c];
-            else
-                dC[q >> 1][c].x = d[c];
-        }
+        for (int k = 0; k < 6; ++k) dC[q][k] = make_float2(d[2 * k], d[2 * k + 1]);
         lmax = max(lmax, last[q]);
     }
 
@@ -376,12 +375,16 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
             if (!__any_sync(0xffffffffu, any_mine)) continue;
             float gr[18];
             {
-                float2 acc[12], sD = f2(0.f), sE = f2(0.f), sF = f2(0.f), sO = f2(0.f);
+                // acc[k]: channels (2k, 2k + 1) of sum_q w_q dL/dC_q over the thread's pixels
+                float2 acc[6], sD = f2(0.f), sE = f2(0.f), sF = f2(0.f), sO = f2(0.f);
 #pragma unroll
-                for (int c = 0; c < 12; ++c) acc[c] = f2(0.f);
+                for (int k = 0; k < 6; ++k) acc[k] = f2(0.f);
                 if (any_mine) {
                     const float4 g2 = rec[2][j], g3 = rec[3][j], g4 = rec[4][j];
-                    const float f[12] = {g1.z, g1.w, g2.x, g2.y, g2.z, g2.w, g3.x, g3.y, g3.z, g3.w, g4.x, g4.y};
+                    // the record's channels in the pairs its 16-byte words already hold
+                    const float2 fp[6] = {make_float2(g1.z, g1.w), make_float2(g2.x, g2.y),
+                                          make_float2(g2.z, g2.w), make_float2(g3.x, g3.y),
+                                          make_float2(g3.z, g3.w), make_float2(g4.x, g4.y)};
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
                         const bool cx = cb[2 * p], cy = cb[2 * p + 1];
@@ -393,12 +396,20 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
                         const float2 inv = make_float2(__fdividef(1.f, 1.f - am.x), __fdividef(1.f, 1.f - am.y));
                         T[p] = __fmul2_rn(T[p], inv);
                         const float2 w = __fmul2_rn(am, T[p]);
-                        float2 fdc = __fmul2_rn(f2(f[0]), dC[p][0]);
+                        // f . dL/dC per pixel, the even and odd channels in the two halves
+                        float2 ea = __fmul2_rn(fp[0], dC[2 * p][0]), eb = __fmul2_rn(fp[0], dC[2 * p + 1][0]);
+                        const float2 wa = f2(w.x), wb = f2(w.y);
 #pragma unroll
-                        for (int c = 0; c < 12; ++c) {
-                            acc[c] = __ffma2_rn(w, dC[p][c], acc[c]);      // rgb (0..2), unc (3), feat (4..11)
-                            if (c > 0) fdc = __ffma2_rn(f2(f[c]), dC[p][c], fdc);
+                        for (int k = 0; k < 6; ++k) {
+                            if (k > 0) {
+                                ea = __ffma2_rn(fp[k], dC[2 * p][k], ea);
+                                eb = __ffma2_rn(fp[k], dC[2 * p + 1][k], eb);
+                            }
+                            // rgb (0..2), unc (3), feat (4..11)
+                            acc[k] = __ffma2_rn(wa, dC[2 * p][k], acc[k]);
+                            acc[k] = __ffma2_rn(wb, dC[2 * p + 1][k], acc[k]);
                         }
+                        const float2 fdc = make_float2(__fadd_rn(ea.x, ea.y), __fadd_rn(eb.x, eb.y));
                         const float2 diff = __fadd2_rn(fdc, make_float2(-S[p].x, -S[p].y));
                         const float2 dal = __ffma2_rn(T[p], diff, __fmul2_rn(__fmul2_rn(Tf[p], inv), nbg[p]));
                         S[p] = __ffma2_rn(am, diff, S[p]);
@@ -423,7 +434,10 @@ __global__ void __launch_bounds__(kBlock / PPT) render_bwd_kernel(
                 gr[4] = -0.5f * F;
                 gr[5] = sO.x + sO.y;
 #pragma unroll
-                for (int c = 0; c < 12; ++c) gr[6 + c] = acc[c].x + acc[c].y;
+                for (int k = 0; k < 6; ++k) {
+                    gr[6 + 2 * k] = acc[k].x;
+                    gr[7 + 2 * k] = acc[k].y;
+                }
             }
             // warp sums of the 18 fields: a transpose through shared memory, lane f < 18 adding field f
 #pragma unroll

@@ -38,10 +38,7 @@ __global__ void __launch_bounds__(256) adam_kernel(int64_t n, float* __restrict_
         float4 pp = reinterpret_cast<float4*>(p)[i], mm = reinterpret_cast<float4*>(m)[i];
         float4 vv = reinterpret_cast<float4*>(v)[i];
         const float4 gg = reinterpret_cast<const float4*>(g)[i];
-        pp.x = adam_step(pp.x, gg.x, mm.x, vv.x, h, lo, hi);
-        pp.y = adam_step(pp.y, gg.y, mm.y, vv.y, h, lo, hi);
-        pp.z = adam_step(pp.z, gg.z, mm.z, vv.z, h, lo, hi);
-        pp.w = adam_step(pp.w, gg.w, mm.w, vv.w, h, lo, hi);
+        adam_step4(pp, gg, mm, vv, h, lo, hi);
         reinterpret_cast<float4*>(p)[i] = pp;
         reinterpret_cast<float4*>(m)[i] = mm;
         reinterpret_cast<float4*>(v)[i] = vv;
@@ -55,7 +52,7 @@ __global__ void __launch_bounds__(256) adam_kernel(int64_t n, float* __restrict_
 AdamParams adam_params(int32_t step, float lr, float beta1, float beta2, float eps)
 {
     const double c1 = 1.0 - pow((double)beta1, step), c2 = 1.0 - pow((double)beta2, step);
-    return AdamParams{beta1, beta2, (float)(lr / c1), (float)(1.0 / sqrt(c2)), eps};
+    return AdamParams{beta1, beta2, 1.0f - beta1, 1.0f - beta2, (float)(lr / c1), (float)(1.0 / sqrt(c2)), eps};
 }
 
 }  // namespace leg
