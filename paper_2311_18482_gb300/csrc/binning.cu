@@ -484,7 +484,12 @@ __global__ void __launch_bounds__(256) chunk_count_kernel(int n, const ushort4* 
 // the copies of its tile.  Only one cursor per (tile, block) advances at a time,
 // so the partly written output sectors stay few enough to remain in L2.  Two
 // rows per block give the first lazy phase (the nearest few chunks, every tile
-// row) enough blocks to fill the GPU.
+// row) enough blocks to fill the GPU.  Only the tiles that receive copies in
+// the block's super-chunk (an active tile with a non-empty count) do work: the
+// compaction keeps the Gaussians whose rectangle reaches the column range of
+// such tiles in one of the block's rows, spans are computed for those rows
+// only, and a warp without such a tile skips the walk (bin + render at 1M
+// Gaussians 0.602 -> 0.577 ms; the placed lists are unchanged).
 constexpr int kPlaceRows = LE_PLACE_ROWS;   // tile rows per block
 
 template <int NS>
@@ -525,7 +530,29 @@ __global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
     // a block none of whose tiles has a copy in this super-chunk has nothing to place
     // (the scan holds K at the end, so the last tile's end offset is there too)
     const uint32_t cend = mine ? base[tb + (size_t)min((C + 1) * cstride, nchunks)] : 0u;
-    if (!__syncthreads_or(cend > ctr)) return;
+    // the tiles that receive copies here, and per row of the block the column
+    // range they span: only Gaussians reaching such a range are compacted, only
+    // those rows' spans computed, only warps with such a tile walk them
+    const bool work = cend > ctr;
+    __shared__ int s_xlo[kPlaceRows], s_xhi[kPlaceRows];
+    if (threadIdx.x < kPlaceRows) {
+        s_xlo[threadIdx.x] = 1 << 30;
+        s_xhi[threadIdx.x] = -1;
+    }
+    __syncthreads();
+    const int wlo = __reduce_min_sync(0xffffffffu, work ? tx : 1 << 30);
+    const int whi = __reduce_max_sync(0xffffffffu, work ? tx + 1 : -1);
+    if (lane == 0 && whi > 0) {
+        atomicMin(&s_xlo[rloc], wlo);
+        atomicMax(&s_xhi[rloc], whi);
+    }
+    if (!__syncthreads_or(work)) return;
+    int xlo[kPlaceRows], xhi[kPlaceRows];
+#pragma unroll
+    for (int k = 0; k < kPlaceRows; ++k) {
+        xlo[k] = s_xlo[k];
+        xhi[k] = s_xhi[k];
+    }
     const int j0 = C * super_chunk, j1 = min(n, j0 + super_chunk);
     for (int jb = j0; jb < j1; jb += S::kBatch) {
         // compaction: the round's Gaussians whose rectangle meets this block's
@@ -537,7 +564,13 @@ __global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
         for (int k = 0; k < S::kItems; ++k) {
             const int j = jb + S::kItems * threadIdx.x + k;
             rr[k] = j < j1 ? drect[j] : make_ushort4(0, 0, 0, 0);
-            if (rr[k].z > rr[k].x && rr[k].y < re && rr[k].w > rb) flags |= 1u << k;
+            bool hit = false;
+#pragma unroll
+            for (int r = 0; r < kPlaceRows; ++r) {
+                const int ty = rb + r;
+                hit = hit || (rr[k].y <= ty && ty < rr[k].w && rr[k].x < xhi[r] && rr[k].z > xlo[r]);
+            }
+            if (rr[k].z > rr[k].x && hit) flags |= 1u << k;
         }
         uint32_t m = 0;
         uint32_t pos = block_exclusive_scan<S::kThreads / 32>((uint32_t)__popc(flags), ws, &m);
@@ -560,18 +593,18 @@ __global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
             for (int k = 0; k < kPlaceRows; ++k) {
                 const int ty = rb + k;
                 int xl = 0, xr = 0;
-                if (ty < re && r.y <= ty && ty < r.w) row_span(e0, e1, r, ty, xl, xr);
+                if (ty < re && r.y <= ty && ty < r.w && r.x < xhi[k] && r.z > xlo[k]) row_span(e0, e1, r, ty, xl, xr);
                 span[k][q] = xr > xl ? (uint32_t)xl | ((uint32_t)xr << 16) : 0u;
             }
         }
         __syncthreads();
-        if (!row_ok) continue;
+        if (!row_ok || whi < 0) continue;
         const uint32_t key_hi = (uint32_t)(row * TX + tx);
         for (int q0 = 0; q0 < (int)m; q0 += 32) {
             const uint32_t sp = q0 + lane < (int)m ? span[rloc][q0 + lane] : 0u;
             const uint32_t gl = q0 + lane < (int)m ? sg[q0 + lane] : 0u;
             const int xl = (int)(sp & 0xFFFFu), xr = (int)(sp >> 16);
-            uint32_t mask = __ballot_sync(0xffffffffu, xr > xl && xl < shi && xr > slo);
+            uint32_t mask = __ballot_sync(0xffffffffu, xr > xl && xl < whi && xr > wlo);
             if (__popc(mask) > 8 && !keys) {
                 // dense: all 32 steps, the spans and ids broadcast from registers (no
                 // step waits on the previous one's load)
