@@ -444,8 +444,10 @@ __global__ void __launch_bounds__(kThreads, 1) wide_kernel(WideArgs a)
 // and db3 (A = dZ^T, B = H2 | ones), 1 -> dW2 [256 x 128] and db2 (A = dH2^T
 // in two 128-row halves, B = H1 | ones), 2 -> dW1 [128 x 8] and db1 (A =
 // dH1^T, B = X, whose column 8 is one).  Every operand is read MN-major:
-// the images are pixel-major, and the pixels are the contraction.  Two stages
-// of bulk copies feed the MMAs.
+// the images are pixel-major, and the pixels are the contraction.  Four stages
+// of bulk copies, each half a tile (64 pixel rows: the first or second half of
+// every image's bytes in the canonical layout), feed the MMAs, so three are in
+// flight while one is contracted.
 struct WgradArgs {
     int ntiles, ncb;
     float invP;
@@ -453,9 +455,10 @@ struct WgradArgs {
     float *dW1, *db1, *dW2, *db2, *dW3, *db3;
 };
 
-constexpr uint32_t kStage = sbuf_bytes(kRows, 128) + sbuf_bytes(kRows, kW2);   // 96 KB
-constexpr uint32_t kGOnes = 2 * kStage, kGBar = kGOnes + sbuf_bytes(kRows, 16), kGSlot = kGBar + 4 * 8,
-                   kGSmem = kGSlot + 16;
+constexpr int kWStages = 4;
+constexpr uint32_t kStage = (sbuf_bytes(kRows, 128) + sbuf_bytes(kRows, kW2)) / 2;   // 48 KB: half a tile
+constexpr uint32_t kGOnes = kWStages * kStage, kGBar = kGOnes + sbuf_bytes(kRows, 16),
+                   kGSlot = kGBar + 2 * kWStages * 8, kGSmem = kGSlot + 16;
 
 __device__ __forceinline__ void role_parts(int role, uint32_t& off0, uint32_t& n0, uint32_t& off1, uint32_t& n1)
 {
@@ -472,8 +475,8 @@ __global__ void __launch_bounds__(kRows, 1) wide_wgrad_kernel(WgradArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* const ones = sm + kGOnes;
-    uint64_t* const full = reinterpret_cast<uint64_t*>(sm + kGBar);     // [2]
-    uint64_t* const empty = full + 2;                                   // [2]
+    uint64_t* const full = reinterpret_cast<uint64_t*>(sm + kGBar);     // [kWStages]
+    uint64_t* const empty = full + kWStages;                            // [kWStages]
     uint32_t* const slot = reinterpret_cast<uint32_t*>(sm + kGSlot);
     const int tid = threadIdx.x, role = blockIdx.y;
     uint32_t off0, n0, off1, n1;
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(kRows, 1) wide_wgrad_kernel(WgradArgs a)
         sbuf_store8(SBuf{ones, 16}, tid, 8, v + 8);
     }
     if (tid == 0)
-        for (int k = 0; k < 4; ++k) mbar_init(full + k, 1);
+        for (int k = 0; k < 2 * kWStages; ++k) mbar_init(full + k, 1);
     if (tid < 32) tmem_alloc(slot, 512);
     fence_proxy_async();
     fence_before();
@@ -497,25 +500,29 @@ __global__ void __launch_bounds__(kRows, 1) wide_wgrad_kernel(WgradArgs a)
     const int n = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     bool ok = true;
     if (tid == 0) {
-        auto load = [&](int i, int s) {
-            const unsigned char* b = a.blobs + (size_t)((int)blockIdx.x + i * (int)gridDim.x) * kBlob;
-            mbar_expect_tx(full + s, n0 + n1);
-            bulk_g2s(sm + s * kStage, b + off0, n0, full + s);
-            bulk_g2s(sm + s * kStage + n0, b + off1, n1, full + s);
+        // half-tile q = 2 i + hf of this CTA's i-th tile goes through stage q % kWStages
+        const uint32_t h0 = n0 / 2, h1 = n1 / 2;
+        auto load = [&](int q) {
+            const int st = q % kWStages, hf = q & 1;
+            const unsigned char* b = a.blobs + (size_t)((int)blockIdx.x + (q >> 1) * (int)gridDim.x) * kBlob;
+            mbar_expect_tx(full + st, h0 + h1);
+            bulk_g2s(sm + st * kStage, b + off0 + hf * h0, h0, full + st);
+            bulk_g2s(sm + st * kStage + h0, b + off1 + hf * h1, h1, full + st);
         };
-        for (int i = 0; i < 2 && i < n; ++i) load(i, i);
+        const int nq = 2 * n;
+        for (int q = 0; q < kWStages && q < nq; ++q) load(q);
         const uint32_t on = smem_u32(ones);
-        for (int i = 0; i < n && ok; ++i) {
-            const int s = i & 1;
-            if (!mbar_wait(full + s, (uint32_t)(i >> 1) & 1u)) {
+        for (int q = 0; q < nq && ok; ++q) {
+            const int st = q % kWStages;
+            if (!mbar_wait(full + st, (uint32_t)(q / kWStages) & 1u)) {
                 ok = false;
                 break;
             }
             fence_after();
-            const uint32_t p0 = smem_u32(sm + s * kStage), p1 = p0 + n0;
+            const uint32_t p0 = smem_u32(sm + st * kStage), p1 = p0 + h0;
 #pragma unroll 1
-            for (int k = 0; k < kRows / 16; ++k) {
-                const uint32_t acc = i > 0 || k > 0;
+            for (int k = 0; k < kRows / 32; ++k) {
+                const uint32_t acc = q > 0 || k > 0;
                 if (role == 0) {
                     const uint64_t A = mndesc_at(p0, 128, 16 * k, 0);
                     mma(tbase, A, mndesc_at(p1, kW2, 16 * k, 0), idesc_bf16(kW2, true, true), acc);
@@ -533,18 +540,20 @@ __global__ void __launch_bounds__(kRows, 1) wide_wgrad_kernel(WgradArgs a)
                         idesc_bf16(16, true, true), acc);
                 }
             }
-            commit(empty + s);
-            // refill the other stage (tile i - 1's) with tile i + 1
-            if (i >= 1 && i + 1 < n) {
-                if (!mbar_wait(empty + (s ^ 1), (uint32_t)((i - 1) >> 1) & 1u)) {
+            commit(empty + st);
+            // refill the stage of half-tile q - 1 with half-tile q - 1 + kWStages
+            if (q >= 1 && q - 1 + kWStages < nq) {
+                const int sp = (q - 1) % kWStages;
+                if (!mbar_wait(empty + sp, (uint32_t)((q - 1) / kWStages) & 1u)) {
                     ok = false;
                     break;
                 }
-                load(i + 1, s ^ 1);
+                load(q - 1 + kWStages);
             }
         }
-        // the last tile's MMAs
-        if (ok && n > 0 && !mbar_wait(empty + ((n - 1) & 1), (uint32_t)((n - 1) >> 1) & 1u)) ok = false;
+        // the last half-tile's MMAs
+        if (ok && nq > 0 && !mbar_wait(empty + (nq - 1) % kWStages, (uint32_t)((nq - 1) / kWStages) & 1u))
+            ok = false;
         if (!ok) atomicExch(&g_wide_error, 1);
     }
     const bool bad = bar_any(0, kRows, !ok);
