@@ -33,7 +33,8 @@ constexpr int kTile = kThreads * kItems;   // 4096 elements per block
 constexpr int kWarps = kThreads / 32;
 
 // ----------------------------------------------------------------------------
-// Exclusive scan of u32 (3 kernels).  `In` yields element i.
+// Exclusive scan of u32 (2 kernels: per-block sums, then each block adds the
+// sums of the blocks before it to its own exclusive prefix).  `In` yields element i.
 
 struct DirectIn {
     const uint32_t* p;
@@ -88,49 +89,32 @@ __global__ void __launch_bounds__(kThreads) scan_reduce_kernel(In in, int n, uin
     }
 }
 
-// Single block: exclusive scan of nb values in place (each thread a contiguous
-// segment of ceil(nb / 1024)), total -> *total.
-__global__ void __launch_bounds__(1024) scan_partials_kernel(uint32_t* partials, int nb, uint32_t* total)
-{
-    __shared__ uint32_t ws[32];
-    const int per = (nb + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(nb, lo + per);
-    uint32_t s = 0;
-#pragma unroll 8
-    for (int i = lo; i < hi; ++i) s += partials[i];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        uint32_t t = ws[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        ws[lane] = t;
-    }
-    __syncthreads();
-    uint32_t run = (w > 0 ? ws[w - 1] : 0u) + x - s;
-    for (int i = lo; i < hi; ++i) {
-        const uint32_t v = partials[i];
-        partials[i] = run;
-        run += v;
-    }
-    if (threadIdx.x == 1023) *total = ws[31];
-}
-
-// out[i] = partials[block] + exclusive prefix of in within the block.  out may alias in.
+// out[i] = (sum of the partials of the blocks before this one) + exclusive
+// prefix of in within the block; the last block also writes the total.  out
+// may alias in.
 template <class In>
-__global__ void __launch_bounds__(kThreads) scan_apply_kernel(In in, int n, uint32_t* out, const uint32_t* partials)
+__global__ void __launch_bounds__(kThreads) scan_apply_kernel(In in, int n, uint32_t* out, const uint32_t* partials,
+                                                             uint32_t* total)
 {
     __shared__ uint32_t sm[kTile + kTile / 32];
     __shared__ uint32_t ws[kWarps];
+    __shared__ uint32_t s_off;
     const int base = blockIdx.x * kTile;
+    {
+        uint32_t p = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kThreads) p += partials[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = p;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < kWarps; ++w) t += ws[w];
+            s_off = t;
+            if (blockIdx.x == gridDim.x - 1) *total = t + partials[blockIdx.x];
+        }
+        __syncthreads();
+    }
     for (int k = 0; k < kItems; ++k) {
         const int j = k * kThreads + threadIdx.x;
         const int i = base + j;
@@ -145,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) scan_apply_kernel(In in, int n, uint
         v[k] = sm[j + (j >> 5)];
         s += v[k];
     }
-    uint32_t run = block_exclusive_scan(s, ws, nullptr) + partials[blockIdx.x];
+    uint32_t run = block_exclusive_scan(s, ws, nullptr) + s_off;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int j = threadIdx.x * kItems + k;
@@ -170,9 +154,7 @@ le_status exclusive_scan(In in, int n, uint32_t* out, uint32_t* partials, uint32
     }
     scan_reduce_kernel<In><<<nb, kThreads, 0, s>>>(in, n, partials);
     LE_LAUNCHED();
-    scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nb, total);
-    LE_LAUNCHED();
-    scan_apply_kernel<In><<<nb, kThreads, 0, s>>>(in, n, out, partials);
+    scan_apply_kernel<In><<<nb, kThreads, 0, s>>>(in, n, out, partials, total);
     LE_LAUNCHED();
     return LE_OK;
 }
