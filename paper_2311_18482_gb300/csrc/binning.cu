@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
     const int row = rb + rloc;
     const bool row_ok = row < TY;
     const int C = super_base + blockIdx.y;
-    const int tx = 32 * seg + lane, slo = 32 * seg, shi = min(TX, 32 * seg + 32);
+    const int tx = 32 * seg + lane;
     const bool mine = row_ok && tx < TX && (!tile_act || tile_act[row * TX + tx]);
     const size_t tb = (size_t)(row * TX + tx) * nchunks;
     uint32_t ctr = mine ? base[tb + (size_t)C * cstride] : 0u;
