@@ -491,9 +491,17 @@ __global__ void __launch_bounds__(PlaceShape<NS>::kThreads) place_kernel(
     int n, const uint64_t* __restrict__ dsorted, const ushort4* __restrict__ drect, const float4* __restrict__ dell,
     const float* __restrict__ depth, int TX, int TY, int super_chunk, int cstride, int nchunks,
     const uint32_t* __restrict__ base, uint32_t* __restrict__ ids, uint64_t* __restrict__ keys,
-    const uint8_t* __restrict__ tile_act, const uint8_t* __restrict__ rows_act, int super_base)
+    const uint8_t* __restrict__ tile_act, const uint8_t* __restrict__ rows_act, int super_base,
+    uint8_t* __restrict__ zero_a, int zero_na, uint8_t* __restrict__ zero_r, int zero_nr)
 {
     using S = PlaceShape<NS>;
+    // block (0, 0) clears the flags the phase's render will set (16-byte aligned arrays)
+    if (zero_a && blockIdx.x == 0 && blockIdx.y == 0) {
+        for (int i = threadIdx.x; i < (zero_na + 15) / 16; i += blockDim.x)
+            reinterpret_cast<uint4*>(zero_a)[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = threadIdx.x; i < (zero_nr + 15) / 16; i += blockDim.x)
+            reinterpret_cast<uint4*>(zero_r)[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (rows_act && !rows_act[blockIdx.x]) return;
     __shared__ uint32_t sg[S::kBatch], sj[S::kBatch];
     __shared__ ushort4 sr[S::kBatch];
@@ -754,9 +762,13 @@ le_status bin_prepare(const le_camera* cam, int32_t n, const float* depth, const
         set_error("%d x %d screen tiles exceed the supported %d tiles / 256 columns", TX, TY, kMaxTiles);
         return LE_ERR_UNSUPPORTED;
     }
-    LE_CUDA(cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)ntiles, s));
+    // the ranges are zero unless ranges_kernel writes them all (K > 0)
+    const size_t range_bytes = sizeof(uint32_t) * 2 * (size_t)ntiles;
     *k_out = 0;
-    if (n == 0) return LE_OK;
+    if (n == 0) {
+        LE_CUDA(cudaMemsetAsync(tile_ranges, 0, range_bytes, s));
+        return LE_OK;
+    }
 
     // 1-2: sort the Gaussians by depth (stable: equal depths keep index order; culled last)
     LE_CUDA(cudaMemsetAsync(w.sort_state, 0, 4 * sort_state_words(n), s));
@@ -783,10 +795,14 @@ le_status bin_prepare(const le_camera* cam, int32_t n, const float* depth, const
     LE_CUDA(cudaStreamSynchronize(s));
     *k_out = K32;
     if ((int64_t)K32 > k_cap) {
+        LE_CUDA(cudaMemsetAsync(tile_ranges, 0, range_bytes, s));
         set_error("instance count K = %u exceeds k_cap = %lld", K32, (long long)k_cap);
         return LE_ERR_CAPACITY;
     }
-    if (K32 == 0) return LE_OK;
+    if (K32 == 0) {
+        LE_CUDA(cudaMemsetAsync(tile_ranges, 0, range_bytes, s));
+        return LE_OK;
+    }
     ranges_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(ntiles, w.nchunks, w.base, tile_ranges);
     LE_LAUNCHED();
     return LE_OK;
@@ -815,7 +831,8 @@ PlaceGrid place_grid(const le_camera* cam, const SortWs& w, bool lazy)
 // Step 5 for super-chunks [s0, s1): place the copies of the active tiles.
 le_status place(const le_camera* cam, int32_t n, const float* depth, const SortWs& w, const uint64_t* cur,
                 const PlaceGrid& g, int s0, int s1, const uint8_t* tile_act, const uint8_t* rows_act,
-                uint32_t* sorted_ids, uint64_t* sorted_keys, cudaStream_t s)
+                uint32_t* sorted_ids, uint64_t* sorted_keys, cudaStream_t s, uint8_t* zero_a = nullptr,
+                int zero_na = 0, uint8_t* zero_r = nullptr, int zero_nr = 0)
 {
     if (s1 <= s0) return LE_OK;
     const dim3 grid(g.ngroups, s1 - s0);
@@ -823,7 +840,8 @@ le_status place(const le_camera* cam, int32_t n, const float* depth, const SortW
 #define LE_PLACE(NS)                                                                                         \
     place_kernel<NS><<<grid, PlaceShape<NS>::kThreads, 0, s>>>(n, cur, w.drect, w.dell, depth, TX, TY,          \
                                                               w.chunk * g.cs, g.cs, w.nchunks, w.base,         \
-                                                              sorted_ids, sorted_keys, tile_act, rows_act, s0)
+                                                              sorted_ids, sorted_keys, tile_act, rows_act, s0, zero_a, zero_na,   \
+                                                              zero_r, zero_nr)
     switch (g.nk) {
         case 1: LE_PLACE(1); break;
         case 2: LE_PLACE(2); break;
@@ -911,10 +929,11 @@ extern "C" le_status le_bin_render_fwd(const le_camera* cam, int32_t n, const fl
         const uint8_t* r = phase == 0 ? nullptr : rows[phase & 1];
         uint8_t* na = act[(phase + 1) & 1];
         uint8_t* nr = rows[(phase + 1) & 1];
-        LE_CUDA(cudaMemsetAsync(na, 0, ntiles, s));
-        LE_CUDA(cudaMemsetAsync(nr, 0, ngroups, s));
         const int s0 = lo / g.cs, s1 = (hi + g.cs - 1) / g.cs;
-        if ((st = place(cam, n, depth, w, cur, g, s0, s1, a, r, sorted_ids, nullptr, s)) != LE_OK) return st;
+        // the placement also clears na and nr, which this phase's render sets
+        if ((st = place(cam, n, depth, w, cur, g, s0, s1, a, r, sorted_ids, nullptr, s, na, ntiles, nr, ngroups)) !=
+            LE_OK)
+            return st;
         if ((st = render_fwd_phase(cam, splat, sorted_ids, w.base, w.nchunks, lo, hi, a, na, nr, out_rgb, out_feat,
                                    out_unc, T_final, n_contrib, s)) != LE_OK)
             return st;

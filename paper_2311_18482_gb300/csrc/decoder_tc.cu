@@ -1342,6 +1342,18 @@ __global__ void selftest_wait_kernel()
     if (threadIdx.x == 0 && !mbar_wait(&bar, 0u)) atomicExch(&g_tc_error, 1);
 }
 
+// Up to seven FP32 arrays set to zero in one launch (block i clears array i).
+struct ZeroList {
+    float* p[7];
+    int n[7];
+};
+__global__ void __launch_bounds__(256) zero_list_kernel(ZeroList z)
+{
+    float* p = z.p[blockIdx.x];
+    const int n = z.n[blockIdx.x];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0.f;
+}
+
 // SM count of the calling thread's current device, read on every launch (a
 // cheap attribute query), so a process driving parts of different sizes gets
 // each one's own persistent grid.
@@ -1396,13 +1408,11 @@ le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_
     if (target) {
         a.loss = loss; a.d_feat = d_feat; a.d_unc = d_unc;
         a.dW1 = dg->W1; a.db1 = dg->b1; a.dW2 = dg->W2; a.db2 = dg->b2; a.dW3 = dg->W3; a.db3 = dg->b3;
-        LE_CUDA(cudaMemsetAsync(loss, 0, 2 * sizeof(float), s));
-        LE_CUDA(cudaMemsetAsync(dg->W1, 0, sizeof(float) * kH1 * kD, s));
-        LE_CUDA(cudaMemsetAsync(dg->b1, 0, sizeof(float) * kH1, s));
-        LE_CUDA(cudaMemsetAsync(dg->W2, 0, sizeof(float) * kH2 * kH1, s));
-        LE_CUDA(cudaMemsetAsync(dg->b2, 0, sizeof(float) * kH2, s));
-        LE_CUDA(cudaMemsetAsync(dg->W3, 0, sizeof(float) * a.ncb * kH2, s));
-        LE_CUDA(cudaMemsetAsync(dg->b3, 0, sizeof(float) * a.ncb, s));
+        // the loss and the weight gradients the kernel adds into, zeroed by one launch
+        const ZeroList zl{{loss, dg->W1, dg->b1, dg->W2, dg->b2, dg->W3, dg->b3},
+                          {2, kH1 * kD, kH1, kH2 * kH1, kH2, a.ncb * kH2, a.ncb}};
+        zero_list_kernel<<<7, 256, 0, s>>>(zl);
+        LE_LAUNCHED();
         const size_t smem = train_smem(a.ncb);
         le_status st = set_smem(dec_train_kernel, smem);
         if (st != LE_OK) return st;
