@@ -296,6 +296,20 @@ le_status le_project_bwd_adam(const le_camera* cam, const le_gaussians* g, const
                               const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
                               const le_adam_config* adam, void* stream);
 
+/* le_project_bwd_adam_extra -- le_project_bwd_adam that, in the same launch,
+ * also applies the same Adam step (Sec. 4; same step, lr, betas and eps; no
+ * clamp) to one more flat FP32 range: extra_param (in/out), extra_grad (in),
+ * extra_m, extra_v (in/out), n_extra elements each, every pointer 16-byte
+ * aligned -- e.g. the decoder parameters whose gradients le_decode wrote.  Per
+ * element the same operations as le_adam, so the range ends bit for bit as
+ * le_adam would leave it.  n_extra = 0: exactly le_project_bwd_adam.  g->n = 0
+ * with n_extra > 0 updates the range only.  Errors: LE_ERR_INVALID_ARG (as
+ * le_project_bwd_adam; n_extra < 0; a null or unaligned extra pointer). */
+le_status le_project_bwd_adam_extra(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                    const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
+                                    const le_adam_config* adam, float* extra_param, const float* extra_grad,
+                                    float* extra_m, float* extra_v, int64_t n_extra, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Semantic decoder D_MLP (Eq. 8, eq:lem_dec; supp. Tab. dmlp): per-pixel MLP
  * d_in(=8) -> h1 -> h2 -> n_cb, ReLU, ReLU, linear.  FP32 device weights

@@ -100,6 +100,9 @@ _SIG = {
                        C.POINTER(LeGaussianGrads), _P],
     "le_project_bwd_adam": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P,
                             C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads), C.POINTER(LeAdamConfig), _P],
+    "le_project_bwd_adam_extra": [C.POINTER(LeCamera), C.POINTER(LeGaussians), C.POINTER(LeProjected), _P,
+                                  C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads), C.POINTER(LeAdamConfig),
+                                  _P, _P, _P, _P, C.c_int64, _P],
     "le_decode_workspace": [C.c_int32, C.c_int32, C.POINTER(LeDecoder), C.POINTER(C.c_size_t)],
     "le_decode": [C.c_int32, C.c_int32, _P, _P, C.POINTER(LeDecoder), _P, C.c_float, C.c_float, _P, _P, _P,
                   C.POINTER(LeDecoderGrads), _P, _P, _P, _P, C.c_size_t, _P],
@@ -456,6 +459,19 @@ def le_project_bwd_adam(cam, g: Gaussians, proj: Projected, grad2d, m: Gaussians
     cfg = LeAdamConfig(int(step), lr, beta1, beta2, eps)
     _check(load().le_project_bwd_adam(C.byref(cs), C.byref(gs), C.byref(ps), _ptr(grad2d), C.byref(ms),
                                       C.byref(vs), C.byref(cfg), _stream()))
+
+
+def le_project_bwd_adam_extra(cam, g: Gaussians, proj: Projected, grad2d, m: Gaussians, v: Gaussians, step: int,
+                              extra_param, extra_grad, extra_m, extra_v, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """le_project_bwd_adam plus the same Adam step on one more flat FP32 range (extra_*, equal sizes)."""
+    n = extra_param.numel()
+    assert extra_grad.numel() == n and extra_m.numel() == n and extra_v.numel() == n
+    cs, gs, ps = camera_struct(cam), g.struct(), proj.struct()
+    ms, vs = grads_struct(m), grads_struct(v)
+    cfg = LeAdamConfig(int(step), lr, beta1, beta2, eps)
+    _check(load().le_project_bwd_adam_extra(C.byref(cs), C.byref(gs), C.byref(ps), _ptr(grad2d), C.byref(ms),
+                                            C.byref(vs), C.byref(cfg), _ptr(extra_param), _ptr(extra_grad),
+                                            _ptr(extra_m), _ptr(extra_v), C.c_int64(n), _stream()))
 
 
 def decoder_struct(W1, b1, W2, b2, W3, b3) -> LeDecoder:

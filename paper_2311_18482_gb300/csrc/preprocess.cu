@@ -394,6 +394,7 @@ __device__ __forceinline__ void warp_apply(const Sink& sk, int f, size_t base, i
 }
 
 struct GradSink {
+    static constexpr bool kExtra = false;
     float* d[7];
     __device__ __forceinline__ bool aligned(int f, size_t base) const
     {
@@ -412,8 +413,29 @@ struct GradSink {
 };
 
 struct AdamSink {
+    static constexpr bool kExtra = true;
     float *p[7], *m[7], *v[7];
     AdamParams h;
+    // one more flat range updated by the same step (no clamp), by the blocks
+    // past the Gaussians' (gblocks): xp, xg, xm, xv of xn elements, 16-byte aligned
+    float *xp = nullptr, *xm = nullptr, *xv = nullptr;
+    const float* xg = nullptr;
+    int64_t xn = 0;
+    int gblocks = 0;
+    // extra block b of nb: quads b * 128 + t, strided by nb * 128, then the xn % 4 tail
+    __device__ __forceinline__ void extra(int b, int nb) const
+    {
+        const int64_t n4 = xn / 4, t = (int64_t)b * blockDim.x + threadIdx.x, stride = (int64_t)nb * blockDim.x;
+        for (int64_t q = t; q < n4; q += stride) {
+            float4 pp = reinterpret_cast<float4*>(xp)[q], mm = reinterpret_cast<float4*>(xm)[q];
+            float4 vv = reinterpret_cast<float4*>(xv)[q];
+            adam_step4(pp, reinterpret_cast<const float4*>(xg)[q], mm, vv, h, -INFINITY, INFINITY);
+            reinterpret_cast<float4*>(xp)[q] = pp;
+            reinterpret_cast<float4*>(xm)[q] = mm;
+            reinterpret_cast<float4*>(xv)[q] = vv;
+        }
+        for (int64_t i = 4 * n4 + t; i < xn; i += stride) xp[i] = adam_step(xp[i], xg[i], xm[i], xv[i], h, -INFINITY, INFINITY);
+    }
     __device__ __forceinline__ bool aligned(int f, size_t base) const
     {
         return ((reinterpret_cast<uintptr_t>(p[f] + base) | reinterpret_cast<uintptr_t>(m[f] + base) |
@@ -622,6 +644,12 @@ __global__ void __launch_bounds__(128, 8) preprocess_bwd_kernel(
     __shared__ GradStage<NC> stage[4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     GradStage<NC>& S = stage[w];
+    if constexpr (Sink::kExtra) {
+        if ((int)blockIdx.x >= sk.gblocks) {
+            sk.extra((int)blockIdx.x - sk.gblocks, (int)gridDim.x - sk.gblocks);
+            return;
+        }
+    }
     const int gw = blockIdx.x * 128 + 32 * w;
     if (gw >= n) return;
     const int i = gw + lane;
@@ -700,7 +728,14 @@ static le_status launch_preprocess_backward(const le_camera* cam, const le_gauss
                                             const float* grad2d, const Sink& sk, cudaStream_t s)
 {
     const CamParams cp = cam_params(cam);
-    const int threads = 128, blocks = (g->n + threads - 1) / threads;
+    const int threads = 128, gblocks = (g->n + threads - 1) / threads;
+    // the blocks of the sink's extra range (none for GradSink)
+    int xblocks = 0;
+    if constexpr (Sink::kExtra) {
+        const int64_t q = (sk.xn + 3) / 4;
+        xblocks = sk.xn > 0 ? (int)((q + threads - 1) / threads < 64 ? (q + threads - 1) / threads : 64) : 0;
+    }
+    const int blocks = gblocks + xblocks;
 #define LE_PREB(DEG)                                                                                               \
     preprocess_bwd_kernel<DEG, Sink><<<blocks, threads, 0, s>>>(g->n, g->means, g->log_scales, g->quats,           \
                                                                 g->opacity_raw, g->sh, cp, pr->tiles_touched,      \
@@ -726,9 +761,16 @@ le_status preprocess_backward(const le_camera* cam, const le_gaussians* g, const
 
 le_status preprocess_backward_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
                                    const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
-                                   const AdamParams& h, cudaStream_t s)
+                                   const AdamParams& h, cudaStream_t s, float* xp, const float* xg, float* xm,
+                                   float* xv, int64_t xn)
 {
     AdamSink sk;
+    sk.xp = xp;
+    sk.xg = xg;
+    sk.xm = xm;
+    sk.xv = xv;
+    sk.xn = xn;
+    sk.gblocks = (g->n + 127) / 128;
     float* const p[7] = {const_cast<float*>(g->means), const_cast<float*>(g->log_scales), const_cast<float*>(g->quats),
                          const_cast<float*>(g->opacity_raw), const_cast<float*>(g->sh), const_cast<float*>(g->feat),
                          const_cast<float*>(g->unc)};

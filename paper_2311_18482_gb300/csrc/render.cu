@@ -25,7 +25,9 @@ le_status preprocess_backward(const le_camera* cam, const le_gaussians* g, const
                               const float* grad2d, const le_gaussian_grads* out, cudaStream_t s);
 le_status preprocess_backward_adam(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
                                    const float* grad2d, const le_gaussian_grads* m, const le_gaussian_grads* v,
-                                   const AdamParams& h, cudaStream_t s);
+                                   const AdamParams& h, cudaStream_t s, float* xp = nullptr,
+                                   const float* xg = nullptr, float* xm = nullptr, float* xv = nullptr,
+                                   int64_t xn = 0);
 le_status check_gaussians(const le_gaussians* g);
 
 namespace {
@@ -630,4 +632,32 @@ extern "C" le_status le_project_bwd_adam(const le_camera* cam, const le_gaussian
     return preprocess_backward_adam(cam, g, pr, grad2d, m, v,
                                     adam_params(adam->step, adam->lr, adam->beta1, adam->beta2, adam->eps),
                                     as_stream(stream));
+}
+
+extern "C" le_status le_project_bwd_adam_extra(const le_camera* cam, const le_gaussians* g, const le_projected* pr,
+                                               const float* grad2d, const le_gaussian_grads* m,
+                                               const le_gaussian_grads* v, const le_adam_config* adam,
+                                               float* extra_param, const float* extra_grad, float* extra_m,
+                                               float* extra_v, int64_t n_extra, void* stream)
+{
+    LE_TRACE("le_project_bwd_adam_extra");
+    le_status st = check_camera(cam);
+    if (st != LE_OK) return st;
+    if ((st = check_gaussians(g)) != LE_OK) return st;
+    LE_CHECK_ARG(pr != nullptr, "null projected struct");
+    LE_CHECK_ARG(adam != nullptr && adam->step >= 1, "adam config is null or step < 1");
+    LE_CHECK_ARG(n_extra >= 0, "n_extra < 0");
+    LE_CHECK_ARG(n_extra == 0 || (extra_param && extra_grad && extra_m && extra_v && aligned16(extra_param) &&
+                                  aligned16(extra_grad) && aligned16(extra_m) && aligned16(extra_v)),
+                 "the extra range's four arrays must be non-null and 16-byte aligned");
+    if (g->n == 0 && n_extra == 0) return LE_OK;
+    if (g->n > 0) {
+        LE_CHECK_ARG(pr->tiles_touched && pr->clamp_mask, "bad projected pointers");
+        LE_CHECK_ARG(grad2d && aligned16(grad2d), "grad2d must be non-null and 16-byte aligned");
+        if ((st = check_field_set(m, "first-moment")) != LE_OK) return st;
+        if ((st = check_field_set(v, "second-moment")) != LE_OK) return st;
+    }
+    return preprocess_backward_adam(cam, g, pr, grad2d, m, v,
+                                    adam_params(adam->step, adam->lr, adam->beta1, adam->beta2, adam->eps),
+                                    as_stream(stream), extra_param, extra_grad, extra_m, extra_v, n_extra);
 }

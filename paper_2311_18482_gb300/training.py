@@ -147,10 +147,12 @@ class TrainState:
             B.le_render_bwd_screen(cam, self.g, self.proj, ids, ranges, self.img, self.d_rgb, self.d_feat,
                                    self.d_unc, grad2d=self.grad2d)
             self._mark("render_bwd")
-            B.le_project_bwd_adam(cam, self.g, self.proj, self.grad2d, self.gm, self.gvv, self.step_count, lr=self.lr)
+            # the decoder parameters' Adam step rides in the same launch (their gradients are complete:
+            # le_decode wrote them before the render backward)
+            B.le_project_bwd_adam_extra(cam, self.g, self.proj, self.grad2d, self.gm, self.gvv, self.step_count,
+                                        self.params[d0:u0], self.grads[d0:u0], self.m[d0:u0], self.v[d0:u0],
+                                        lr=self.lr)
             self._mark("project_bwd_adam")
-            B.le_adam(self.params[d0:u0], self.grads[d0:u0], self.m[d0:u0], self.v[d0:u0], self.step_count,
-                      lr=self.lr)
         else:
             cs, gs, ps = B.camera_struct(cam), self.g.struct(), self.proj.struct()
             import ctypes as C

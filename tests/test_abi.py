@@ -57,6 +57,18 @@ def test_invalid_arguments_rejected_on_host(lib):
     # fused backward + Adam: null camera / config rejected before any GPU work
     assert lib.le_render_bwd_adam(None, None, None, None, None, None, None, None, None, None, None, None, None,
                                   None, None) == b.LE_ERR_INVALID_ARG
+    # the projection Adam with an extra range: negative size, unaligned extra pointer
+    cam.width, cam.height = 16, 16
+    g.n, g.sh_degree = 0, 0
+    cfg = b.LeAdamConfig(1, 1e-3, 0.9, 0.999, 1e-8)
+    f = lib.le_project_bwd_adam_extra
+    args = (C.byref(cam), C.byref(g), C.byref(p), None, None, None, C.byref(cfg))
+    assert f(*args, C.c_void_p(16), C.c_void_p(16), C.c_void_p(32), C.c_void_p(48), C.c_int64(-1),
+             None) == b.LE_ERR_INVALID_ARG
+    assert f(*args, C.c_void_p(18), C.c_void_p(16), C.c_void_p(32), C.c_void_p(48), C.c_int64(8),
+             None) == b.LE_ERR_INVALID_ARG
+    assert b"aligned" in lib.le_last_error()
+    assert f(*args, None, None, None, None, C.c_int64(0), None) == b.LE_OK      # nothing to do
     # misaligned Adam buffers
     assert lib.le_adam(C.c_int64(8), C.c_void_p(3), C.c_void_p(16), C.c_void_p(32), C.c_void_p(48), 1,
                        C.c_float(1e-3), C.c_float(0.9), C.c_float(0.999), C.c_float(1e-8), C.c_float(0),

@@ -129,6 +129,22 @@ def test_backward_halves_match_single_calls(leg, n):
             assert float((a - b).abs().max()) <= 1e-5 * max(float(b.abs().max()), 1e-6), k
     assert float(ga.unc.min()) >= 0.0 and float(ga.unc.max()) <= 1.0
     assert not torch.equal(ga.means, g.means)
+    # the same projection Adam with one more flat range in the launch (25,001 elements: quads and a tail):
+    # the Gaussians as without it, the range bit for bit as le_adam leaves it
+    n_x = 25001
+    px, gx = t(rng.standard_normal(n_x)), t(rng.standard_normal(n_x) * 1e-2)
+    mx, vx = t(rng.standard_normal(n_x) * 1e-3), t(rng.uniform(0, 1e-5, n_x))
+    gc = B.Gaussians(*(getattr(g, k).clone() for k in _F), g.sh_degree)
+    mc = B.Gaussians(*(m0[k].clone() for k in _F), g.sh_degree)
+    vc = B.Gaussians(*(v0[k].clone() for k in _F), g.sh_degree)
+    pxa, mxa, vxa = px.clone(), mx.clone(), vx.clone()
+    B.le_project_bwd_adam_extra(cam, gc, proj, g2a, mc, vc, 3, pxa, gx, mxa, vxa)
+    B.le_adam(px, gx, mx, vx, 3)
+    torch.cuda.synchronize()
+    for k in _F:
+        for x, y in ((ga, gc), (ma, mc), (va, vc)):
+            assert torch.equal(getattr(x, k), getattr(y, k)), k
+    assert torch.equal(pxa, px) and torch.equal(mxa, mx) and torch.equal(vxa, vx)
 
 
 def test_training_step_ragged_view(leg):
