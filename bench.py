@@ -120,7 +120,7 @@ def measured_peaks():
 STAGE_CALLS = {"preprocess": "le_preprocess (preprocess_kernel)",
                "bin_render": "le_bin_render_fwd (depth radix sort, chunk counts, scan, lazily placed copies "
                              "and compositing)",
-               "decoder": "le_rgb_l1 + le_decode fused (l1_kernel, dec_train_kernel)",
+               "decoder": "le_decode_l1 fused (dec_train_kernel with the RGB L1 term in the same pass)",
                "render_bwd": "le_render_bwd_screen (render_bwd_kernel)",
                "project_bwd_adam": "le_project_bwd_adam (preprocess_bwd_kernel with the Gaussians' Adam step "
                                    "fused in)",

@@ -352,6 +352,21 @@ le_status le_decode(int32_t mode, int32_t P, const float* feat, const float* unc
                     float* d_unc, const le_decoder_grads* dgrads, int32_t* argmax, float* prob, float* logits,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* le_decode_l1 -- a le_decode training call that also computes the RGB L1 term
+ * of Sec. 4 (le_rgb_l1) over the same P pixels: img, img_target [3,P] (the
+ * rendered colour and its target), loss_l1 [1] = mean |img - img_target| over
+ * the 3P values (overwritten), d_img [3,P] = sign(img - img_target) / (3P).
+ * The other arguments and outputs are le_decode's (training only; target
+ * non-null, P > 0).  With LE_DECODE_FUSED_BF16 at 8-64-128-N the tensor-core
+ * training kernel computes the L1 term in the same pass (no separate launch);
+ * otherwise it is le_rgb_l1 followed by le_decode.  d_img equals le_rgb_l1's
+ * bit for bit; loss_l1 matches it up to the order of its FP32 sums.
+ * Errors: those of le_decode and le_rgb_l1; a null L1 pointer. */
+le_status le_decode_l1(int32_t mode, int32_t P, const float* feat, const float* unc, const le_decoder* dec,
+                       const int32_t* target, float lambda_ce, float lambda_u, float* loss, float* d_feat,
+                       float* d_unc, const le_decoder_grads* dgrads, const float* img, const float* img_target,
+                       float* loss_l1, float* d_img, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------------------
  * le_query -- relevancy of the language feature map F = M_infer S against
  * text prompts (supp. Sec. "Inference"; relevancy "in accordance with LERF",

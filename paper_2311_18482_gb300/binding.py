@@ -104,6 +104,8 @@ _SIG = {
                                   C.POINTER(LeGaussianGrads), C.POINTER(LeGaussianGrads), C.POINTER(LeAdamConfig),
                                   _P, _P, _P, _P, C.c_int64, _P],
     "le_decode_workspace": [C.c_int32, C.c_int32, C.POINTER(LeDecoder), C.POINTER(C.c_size_t)],
+    "le_decode_l1": [C.c_int32, C.c_int32, _P, _P, C.POINTER(LeDecoder), _P, C.c_float, C.c_float, _P, _P, _P,
+                     C.POINTER(LeDecoderGrads), _P, _P, _P, _P, _P, C.c_size_t, _P],
     "le_decode": [C.c_int32, C.c_int32, _P, _P, C.POINTER(LeDecoder), _P, C.c_float, C.c_float, _P, _P, _P,
                   C.POINTER(LeDecoderGrads), _P, _P, _P, _P, C.c_size_t, _P],
     "le_query_workspace": [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
@@ -500,6 +502,15 @@ def le_decode_raw(mode, P, feat, unc, dec: LeDecoder, target, lambda_ce, lambda_
                             _ptr(loss), _ptr(d_feat), _ptr(d_unc), C.byref(dgrads) if dgrads is not None else None,
                             _ptr(argmax), _ptr(prob), _ptr(logits), _ptr(workspace),
                             0 if workspace is None else workspace.numel(), _stream()))
+
+
+def le_decode_l1_raw(mode, P, feat, unc, dec: LeDecoder, target, lambda_ce, lambda_u, loss, d_feat, d_unc,
+                     dgrads: LeDecoderGrads, img, img_target, loss_l1, d_img, workspace):
+    """A training call of le_decode plus the RGB L1 term of the same pixels (preallocated tensors)."""
+    _check(load().le_decode_l1(mode, P, _ptr(feat), _ptr(unc), C.byref(dec), _ptr(target), lambda_ce, lambda_u,
+                               _ptr(loss), _ptr(d_feat), _ptr(d_unc), C.byref(dgrads), _ptr(img), _ptr(img_target),
+                               _ptr(loss_l1), _ptr(d_img), _ptr(workspace),
+                               0 if workspace is None else workspace.numel(), _stream()))
 
 
 def le_decode(mode: int, feat, dec_t, unc=None, target=None, lambda_ce=1.0, lambda_u=1.0, want_prob=False,

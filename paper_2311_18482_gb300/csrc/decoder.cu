@@ -12,7 +12,8 @@ namespace leg {
 le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_decoder* dec, const int32_t* target,
                        float lambda_ce, float lambda_u, float* loss, float* d_feat, float* d_unc,
                        const le_decoder_grads* dg, int32_t* argmax, float* prob, void* ws, size_t ws_bytes,
-                       cudaStream_t s);
+                       cudaStream_t s, const float* img = nullptr, const float* img_t = nullptr,
+                       float* loss_l1 = nullptr, float* d_img = nullptr);
 size_t decode_fused_workspace(int32_t P, const le_decoder* dec);
 le_status check_fused_decoder(const le_decoder* dec, bool train);
 bool wide_decoder(const le_decoder* d);
@@ -282,4 +283,30 @@ extern "C" le_status le_decode(int32_t mode, int32_t P, const float* feat, const
     LE_CHECK_ARG((reinterpret_cast<uintptr_t>(workspace) & 255u) == 0, "workspace must be 256-byte aligned");
     return decode_unfused(P, feat, unc, dec, target, lambda_ce, lambda_u, loss, d_feat, d_unc, dgrads, argmax, prob,
                           logits, workspace, s);
+}
+
+extern "C" le_status le_decode_l1(int32_t mode, int32_t P, const float* feat, const float* unc,
+                                  const le_decoder* dec, const int32_t* target, float lambda_ce, float lambda_u,
+                                  float* loss, float* d_feat, float* d_unc, const le_decoder_grads* dgrads,
+                                  const float* img, const float* img_target, float* loss_l1, float* d_img,
+                                  void* workspace, size_t workspace_bytes, void* stream)
+{
+    LE_TRACE("le_decode_l1");
+    le_status st = check_decoder(dec);
+    if (st != LE_OK) return st;
+    LE_CHECK_ARG(P > 0, "P must be positive");
+    LE_CHECK_ARG(target != nullptr, "le_decode_l1 is a training call: target is null");
+    LE_CHECK_ARG(img && img_target && loss_l1 && d_img, "null L1 pointer");
+    // the 8-64-128 tensor-core training kernel computes the L1 term in the same pass
+    if (mode == LE_DECODE_FUSED_BF16 && !wide_decoder(dec) && check_fused_decoder(dec, true) == LE_OK) {
+        LE_CHECK_ARG(feat && unc && loss && d_feat && d_unc && dgrads, "training needs unc, loss, d_feat, d_unc, dgrads");
+        LE_CHECK_ARG(dgrads->W1 && dgrads->b1 && dgrads->W2 && dgrads->b2 && dgrads->W3 && dgrads->b3,
+                     "null decoder gradient pointer");
+        LE_CHECK_ARG(workspace_bytes >= decode_fused_workspace(P, dec), "workspace too small");
+        return decode_fused(P, feat, unc, dec, target, lambda_ce, lambda_u, loss, d_feat, d_unc, dgrads, nullptr,
+                            nullptr, workspace, workspace_bytes, as_stream(stream), img, img_target, loss_l1, d_img);
+    }
+    if ((st = le_rgb_l1(3 * (int64_t)P, img, img_target, loss_l1, d_img, stream)) != LE_OK) return st;
+    return le_decode(mode, P, feat, unc, dec, target, lambda_ce, lambda_u, loss, d_feat, d_unc, dgrads, nullptr,
+                     nullptr, nullptr, workspace, workspace_bytes, stream);
 }

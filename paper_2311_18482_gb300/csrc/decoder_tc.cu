@@ -64,6 +64,11 @@ struct DecArgs {
     // feature-map export
     int dd;                         // feature dims d (multiple of 64)
     __nv_bfloat16* fmap;            // [P, dd] out
+    // training with the RGB L1 term of the same pixels (nullable img): img, img_t [3, P],
+    // d_img [3, P] = sign(img - img_t) inv_l1, *loss_l1 += sum |img - img_t| inv_l1
+    const float *img, *img_t;
+    float *d_img, *loss_l1;
+    float inv_l1;
 };
 
 // Per-warpgroup state of the shared MLP front end.  With nhalf = 2 or 4,
@@ -568,7 +573,7 @@ __device__ __forceinline__ void add_bias16(float* v, const float* b, int c)
 }
 
 __device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bias, EpiCtx& e, int ntiles,
-                                               float& acc_ce, float& acc_u)
+                                               float& acc_ce, float& acc_u, float& acc_l1)
 {
     constexpr float kL2E = 1.4426950408889634f;
     const int row = e.row, h = e.h;
@@ -578,15 +583,23 @@ __device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bi
     const int c0 = min(nu, h * per) * 16, c1 = min(nu, (h + 1) * per) * 16;   // this half's logit columns
     float v[16];
     // this row's inputs of the slot's next tile, loaded one tile ahead so that
-    // their latency is not on the path from one tile's first MMA to the next
+    // their latency is not on the path from one tile's first MMA to the next:
+    // half 0 the feature, half 1 (with the L1 term) the image and its target
     float pf[8], pu = 0.f;
     int pt = -1;
     auto fetch = [&](int tile_n) {
         const int pxn = tile_n * 128 + row;
         const bool vn = tile_n < ntiles && pxn < a.P;
-        if (h == 0)
+        if (h == 0) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) pf[c] = vn ? a.feat[(size_t)c * a.P + pxn] : 0.f;
+        } else if (a.img) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                pf[c] = vn ? a.img[(size_t)c * a.P + pxn] : 0.f;
+                pf[3 + c] = vn ? a.img_t[(size_t)c * a.P + pxn] : 0.f;
+            }
+        }
         pu = vn ? a.unc[pxn] : 0.f;
         pt = vn ? a.target[pxn] : -1;
     };
@@ -607,6 +620,15 @@ __device__ __forceinline__ bool train_epilogue(const DecArgs& a, const float* bi
 #pragma unroll
             for (int c = 0; c < 8; ++c) v[c] = c == 0 ? 1.f : 0.f;
             sts_bf16x8(X1 + sbuf_off(row, 8, 16), v);
+            if (a.img && valid) {
+                // the RGB L1 term of this pixel (the same operations as le_rgb_l1)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float r = pf[c] - pf[3 + c];
+                    acc_l1 += fabsf(r);
+                    a.d_img[(size_t)c * a.P + px] = r > 0.f ? a.inv_l1 : (r < 0.f ? -a.inv_l1 : 0.f);
+                }
+            }
         }
         const float u = pu;
         const int t = pt;
@@ -779,7 +801,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) dec_train_kernel(DecArgs a)
     const uint32_t tb = *reinterpret_cast<volatile uint32_t*>(slot_addr);
     const int ntiles = (a.P + 127) / 128;
     bool ok = true;
-    float acc_ce = 0.f, acc_u = 0.f;
+    float acc_ce = 0.f, acc_u = 0.f, acc_l1 = 0.f;
     if (warp == 16) {
         if (lane == 0) {
             ok = train_mma_loop(a.ncb, f, smem_u32(E.p), slots_a, ready, done, tb, ntiles);
@@ -800,7 +822,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) dec_train_kernel(DecArgs a)
         e.lanef = (uint32_t)(32 * (warp & 3)) << 16;
         e.ph = 0;
         e.bar_id = 1 + e.s;
-        ok = train_epilogue(a, f.b1s, e, ntiles, acc_ce, acc_u);
+        ok = train_epilogue(a, f.b1s, e, ntiles, acc_ce, acc_u, acc_l1);
     }
     fence_before();
     const bool bad = __syncthreads_or(!ok);
@@ -841,11 +863,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1) dec_train_kernel(DecArgs a)
         for (int o = 16; o > 0; o >>= 1) {
             acc_ce += __shfl_xor_sync(0xffffffffu, acc_ce, o);
             acc_u += __shfl_xor_sync(0xffffffffu, acc_u, o);
+            acc_l1 += __shfl_xor_sync(0xffffffffu, acc_l1, o);
         }
         if (lane == 0 && ((warp >> 2) & 1) == 0) {
             atomicAdd(a.loss, acc_ce * a.invP);
             atomicAdd(a.loss + 1, acc_u * a.invP);
         }
+        if (lane == 0 && ((warp >> 2) & 1) == 1 && a.loss_l1) atomicAdd(a.loss_l1, acc_l1 * a.inv_l1);
     }
     fence_before();
     __syncthreads();
@@ -1342,10 +1366,10 @@ __global__ void selftest_wait_kernel()
     if (threadIdx.x == 0 && !mbar_wait(&bar, 0u)) atomicExch(&g_tc_error, 1);
 }
 
-// Up to seven FP32 arrays set to zero in one launch (block i clears array i).
+// Up to eight FP32 arrays set to zero in one launch (block i clears array i).
 struct ZeroList {
-    float* p[7];
-    int n[7];
+    float* p[8];
+    int n[8];
 };
 __global__ void __launch_bounds__(256) zero_list_kernel(ZeroList z)
 {
@@ -1390,9 +1414,15 @@ size_t decode_fused_workspace(int32_t, const le_decoder*) { return 0; }
 
 le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_decoder* d, const int32_t* target,
                        float lambda_ce, float lambda_u, float* loss, float* d_feat, float* d_unc,
-                       const le_decoder_grads* dg, int32_t* argmax, float* prob, void*, size_t, cudaStream_t s)
+                       const le_decoder_grads* dg, int32_t* argmax, float* prob, void*, size_t, cudaStream_t s,
+                       const float* img, const float* img_t, float* loss_l1, float* d_img)
 {
     DecArgs a{};
+    a.img = img;
+    a.img_t = img_t;
+    a.loss_l1 = loss_l1;
+    a.d_img = d_img;
+    a.inv_l1 = 1.0f / (float)(3 * (int64_t)P);
     a.P = P;
     a.ncb = d->n_cb;
     a.feat = feat;
@@ -1409,9 +1439,9 @@ le_status decode_fused(int32_t P, const float* feat, const float* unc, const le_
         a.loss = loss; a.d_feat = d_feat; a.d_unc = d_unc;
         a.dW1 = dg->W1; a.db1 = dg->b1; a.dW2 = dg->W2; a.db2 = dg->b2; a.dW3 = dg->W3; a.db3 = dg->b3;
         // the loss and the weight gradients the kernel adds into, zeroed by one launch
-        const ZeroList zl{{loss, dg->W1, dg->b1, dg->W2, dg->b2, dg->W3, dg->b3},
-                          {2, kH1 * kD, kH1, kH2 * kH1, kH2, a.ncb * kH2, a.ncb}};
-        zero_list_kernel<<<7, 256, 0, s>>>(zl);
+        const ZeroList zl{{loss, dg->W1, dg->b1, dg->W2, dg->b2, dg->W3, dg->b3, loss_l1},
+                          {2, kH1 * kD, kH1, kH2 * kH1, kH2, a.ncb * kH2, a.ncb, 1}};
+        zero_list_kernel<<<img ? 8 : 7, 256, 0, s>>>(zl);
         LE_LAUNCHED();
         const size_t smem = train_smem(a.ncb);
         le_status st = set_smem(dec_train_kernel, smem);

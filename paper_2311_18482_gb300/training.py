@@ -2,8 +2,9 @@
 driven entirely through the C ABI with preallocated device buffers:
 
   le_preprocess -> le_bin_render_fwd (binning + compositing, lazily placed)
-  -> le_rgb_l1 (RGB loss, Sec. 4; or le_rgb_loss with D-SSIM)
-  -> le_decode (D_MLP + uncertainty-weighted CE + L_u, Eqs. 8-12, training mode)
+  -> le_decode_l1 (D_MLP + uncertainty-weighted CE + L_u, Eqs. 8-12, training
+     mode, with the RGB L1 term of Sec. 4 in the same pass; or le_rgb_loss with
+     D-SSIM and le_decode)
   -> le_render_bwd_screen (screen-space gradients) -> le_project_bwd_adam
      (all Gaussian parameter gradients, each applied by Adam where it is
      computed; u clamped to [0,1], Sec. 3.4.2)
@@ -134,10 +135,13 @@ class TrainState:
             B.le_rgb_loss(self.img.rgb, rgb_target, self.lambda_ssim, loss=self.rgb_terms, grad=self.d_rgb,
                           workspace=self.rgb_ws)
             self.loss[0:1].copy_(self.rgb_terms[0:1])
+            B.le_decode_raw(self.mode, self.P, self.img.feat, self.img.unc, self.dec, idx_target, 1.0, 1.0,
+                            self.loss[1:3], self.d_feat, self.d_unc, self.dgrad, None, None, None, self.dec_ws)
         else:
-            B.le_rgb_l1(self.img.rgb, rgb_target, self.loss[0:1], self.d_rgb)
-        B.le_decode_raw(self.mode, self.P, self.img.feat, self.img.unc, self.dec, idx_target, 1.0, 1.0,
-                        self.loss[1:3], self.d_feat, self.d_unc, self.dgrad, None, None, None, self.dec_ws)
+            # the L1 term rides in the decoder's training pass (one launch fewer with the fused decoder)
+            B.le_decode_l1_raw(self.mode, self.P, self.img.feat, self.img.unc, self.dec, idx_target, 1.0, 1.0,
+                               self.loss[1:3], self.d_feat, self.d_unc, self.dgrad, self.img.rgb, rgb_target,
+                               self.loss[0:1], self.d_rgb, self.dec_ws)
         self._mark("decoder")
         self.step_count += 1
         u0, d0 = self.layout.unc_offset, self.dec_lo

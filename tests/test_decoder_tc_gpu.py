@@ -232,3 +232,52 @@ def test_trained_decoder_argmax_and_gain(leg, orc):
     print(f"trained decoder: fused/FP64 argmax agreement {agree:.5f}; accuracy trained {acc:.3f} vs untrained {acc0:.3f}")
     assert agree >= 0.999
     assert acc >= acc0 + 0.3
+
+
+@pytest.mark.parametrize("mode_name,P,widths", [("fused", 50001, (64, 128)), ("fused", 129, (64, 128)),
+                                                ("unfused", 3001, (64, 128)), ("fused", 3001, (128, 256))])
+def test_decode_l1_matches_separate_calls(leg, mode_name, P, widths):
+    """le_decode_l1 (the RGB L1 term in the decoder's training pass; at 8-64-128 inside the tensor-core
+    kernel, otherwise le_rgb_l1 + le_decode) against le_rgb_l1 followed by le_decode on the same
+    inputs: d_img bit for bit, d_feat and d_unc bit for bit (the same kernel per pixel), the losses
+    and weight gradients up to the order of their FP32 atomic sums.  The L1 loss is a sum of at most
+    2 x 152 x 8 nonnegative partials in either form: two orders of m such terms differ by at most
+    2 (m - 1) u of the sum (u = 2^-24)."""
+    import paper_2311_18482_gb300 as L
+    B = L.binding
+    mode = L.FUSED_BF16 if mode_name == "fused" else L.UNFUSED_FP32
+    ncb = 128
+    dec = synth.decoder_init(31, ncb, h1=widths[0], h2=widths[1])
+    feat, unc, tgt = _inputs(P, ncb, 32)
+    rng = np.random.default_rng(33)
+    img, img_t = _t(rng.uniform(0, 1, (3, P))), _t(rng.uniform(0, 1, (3, P)))
+    dec_t = _dec_t(dec)
+    ds = B.decoder_struct(*dec_t)
+    nb = B.le_decode_workspace(mode | B.DECODE_TRAIN, P, ds)
+    outs = []
+    for fused_l1 in (True, False):
+        o = dict(loss=torch.zeros(2, device="cuda"), d_feat=torch.empty(8, P, device="cuda"),
+                 d_unc=torch.empty(P, device="cuda"), dW=[torch.empty_like(x) for x in dec_t],
+                 l1=torch.full((1,), 7.0, device="cuda"), d_img=torch.full((3, P), 7.0, device="cuda"),
+                 ws=torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda"))
+        dg = B.decoder_grads_struct(o["dW"])
+        if fused_l1:
+            B.le_decode_l1_raw(mode, P, _t(feat), _t(unc), ds, _t(tgt, np.int32), 1.0, 1.0, o["loss"], o["d_feat"],
+                               o["d_unc"], dg, img, img_t, o["l1"], o["d_img"], o["ws"])
+        else:
+            B.le_rgb_l1(img, img_t, o["l1"], o["d_img"])
+            B.le_decode_raw(mode, P, _t(feat), _t(unc), ds, _t(tgt, np.int32), 1.0, 1.0, o["loss"], o["d_feat"],
+                            o["d_unc"], dg, None, None, None, o["ws"])
+        outs.append(o)
+    torch.cuda.synchronize()
+    L.le_device_status()
+    a, b = outs
+    assert torch.equal(a["d_img"], b["d_img"])
+    assert torch.equal(a["d_feat"], b["d_feat"]) and torch.equal(a["d_unc"], b["d_unc"])
+    m = 2 * 152 * 8
+    l1 = float(b["l1"][0])
+    assert abs(float(a["l1"][0]) - l1) <= 2 * (m - 1) * 2.0 ** -24 * l1
+    assert abs(l1 - float(np.abs(to_np(img).astype(np.float64) - to_np(img_t)).mean())) <= 1e-5 * l1
+    assert rel_err(to_np(a["loss"]), to_np(b["loss"])) <= 1e-5
+    for ga, gb in zip(a["dW"], b["dW"]):
+        assert rel_err(to_np(ga), to_np(gb)) <= 1e-5
